@@ -1,0 +1,194 @@
+"""Python binding of the plain FP64 CPU oracle (``glisse_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+benchmark's CPU-baseline / reference leg may import this module.  The product
+path (the CUDA library and its binding) never imports, links or calls it.
+
+``build()`` compiles the C file with gcc (no FMA contraction, no fast-math,
+OpenMP over particles) into ``oracle/_build/liboracle.so``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "glisse_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ALIVE, ESCAPE, KEPLER, NONFINITE = 0, -1, -2, -3
+
+
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC"]
+
+
+def compile_source(src: str, out: str) -> str:
+    """Compile an oracle source file into a shared object (used by build() and the mutant tests)."""
+    tmp = out + f".{os.getpid()}.tmp"
+    subprocess.run(["gcc", *CFLAGS, "-o", tmp, src, "-lm"], check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle if the shared object is missing or older than the source."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        compile_source(_SRC, _OUT)
+    return _OUT
+
+
+SOURCE = _SRC
+
+
+_override = []
+
+
+class using:
+    """Context manager: route this module's calls to another build of the oracle
+    (tests use it to check that the pins catch planted mistakes)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        _override.append(_bind(C.CDLL(self.path)))
+        return self
+
+    def __exit__(self, *exc):
+        _override.pop()
+        return False
+
+
+def lib():
+    global _lib
+    if _override:
+        return _override[-1]
+    with _lock:
+        if _lib is None:
+            _lib = _bind(C.CDLL(build()))
+    return _lib
+
+
+def _bind(L):
+    """Declare the C signatures on a loaded oracle library."""
+    dp = C.POINTER(C.c_double)
+    i64p = C.POINTER(C.c_int64)
+    i32p = C.POINTER(C.c_int32)
+    L.orc_G.restype = C.c_double
+    L.orc_kepler_drift.argtypes = [C.c_double, C.c_double, dp]
+    L.orc_kepler_drift.restype = C.c_int
+    L.orc_last_iters.restype = C.c_int
+    L.orc_planet_wh.argtypes = [C.c_double, C.c_int, dp, C.c_double, C.c_int64, dp, dp]
+    L.orc_planet_wh.restype = C.c_int
+    L.orc_rcrit.argtypes = [C.c_double, C.c_int, dp, C.c_int, C.c_double, dp]
+    L.orc_rcrit.restype = C.c_int
+    L.orc_particles.argtypes = [C.c_double, C.c_int, dp, dp, C.c_int64, C.c_double, dp, C.c_double, dp,
+                                C.c_int64, i64p, i32p, dp, dp, C.c_int64, C.c_int, C.c_int]
+    L.orc_particles.restype = C.c_int
+    L.orc_max_threads.restype = C.c_int
+    return L
+
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+
+def grav():
+    return lib().orc_G()
+
+
+def kepler_drift(mu: float, state, dt: float):
+    """Drift one heliocentric state [6] by dt about mu. Returns (new_state, status, newton_iters)."""
+    st = _f64(state, (6,)).copy()
+    rc = lib().orc_kepler_drift(float(mu), float(dt), _dp(st))
+    return st, rc, lib().orc_last_iters()
+
+
+def planet_wh(star_mass: float, planets, dt: float, n_steps: int, want_log: bool = True, want_energy: bool = False):
+    """Advance the planets n_steps.  Returns (planets_out [np][7], log [n+1][np][3] or None, energy or None)."""
+    pl = _f64(planets).copy()
+    np_ = pl.shape[0]
+    log = np.empty((n_steps + 1, np_, 3)) if want_log else None
+    en = np.empty(n_steps + 1) if want_energy else None
+    rc = lib().orc_planet_wh(float(star_mass), np_, _dp(pl), float(dt), int(n_steps),
+                             _dp(log) if log is not None else None, _dp(en) if en is not None else None)
+    if rc != 0:
+        raise RuntimeError(f"orc_planet_wh failed: {rc}")
+    return pl, log, en
+
+
+def rcrit(star_mass: float, planets, mode: int = 0, value: float = 1.0):
+    pl = _f64(planets)
+    out = np.empty(pl.shape[0])
+    rc = lib().orc_rcrit(float(star_mass), pl.shape[0], _dp(pl), int(mode), float(value), _dp(out))
+    if rc != 0:
+        raise ValueError("unbound planet")
+    return out
+
+
+class ParticleRun:
+    """State of an oracle particle integration that can be advanced in pieces."""
+
+    def __init__(self, star_mass, planet_masses, state, rcrit_, r_max):
+        self.m0 = float(star_mass)
+        self.pm = _f64(planet_masses).copy()
+        self.state = _f64(state).reshape(-1, 6).copy()
+        n = self.state.shape[0]
+        self.removal_step = np.full(n, -1, dtype=np.int64)
+        self.reason = np.zeros(n, dtype=np.int32)
+        self.margin = np.full(n, np.inf)
+        self.closest = np.full(n, np.inf)
+        self.rcrit = _f64(rcrit_).copy()
+        self.r_max = float(r_max)
+        self.step = 0
+        self.tested_first = False
+
+    def advance(self, log, dt: float, nthreads: int = 0):
+        """Advance by len(log)-1 steps using planet positions log[0..n] (log[0] at the current step)."""
+        log = _f64(log)
+        n = log.shape[0] - 1
+        npl = self.pm.shape[0]
+        rc = lib().orc_particles(self.m0, npl, _dp(self.pm), _dp(log), int(n), float(dt), _dp(self.rcrit),
+                                 self.r_max, _dp(self.state), self.state.shape[0],
+                                 self.removal_step.ctypes.data_as(C.POINTER(C.c_int64)),
+                                 self.reason.ctypes.data_as(C.POINTER(C.c_int32)), _dp(self.margin),
+                                 _dp(self.closest), int(self.step), 0 if self.tested_first else 1, int(nthreads))
+        if rc != 0:
+            raise RuntimeError(f"orc_particles failed: {rc}")
+        self.tested_first = True
+        self.step += n
+        return self
+
+
+def run(star_mass, planets, particles, dt, n_steps, k_hill=1.0, r_max=1000.0, enc_mode=0, nthreads=0):
+    """Whole-run convenience: planets and particles from a heliocentric start.
+
+    Returns a dict with the final particle state [n][6], removal_step, reason, margin, closest,
+    the planet log [n+1][np][3] and the final planets [np][7]."""
+    pl0 = _f64(planets)
+    rc_ = rcrit(star_mass, pl0, enc_mode, k_hill)
+    pl1, log, _ = planet_wh(star_mass, pl0, dt, n_steps)
+    pr = ParticleRun(star_mass, pl0[:, 0], particles, rc_, r_max)
+    pr.advance(log, dt, nthreads)
+    return {"state": pr.state, "removal_step": pr.removal_step, "reason": pr.reason, "margin": pr.margin,
+            "closest": pr.closest, "log": log, "planets": pl1, "rcrit": rc_}
+
+
+def max_threads() -> int:
+    return lib().orc_max_threads()

@@ -1,0 +1,74 @@
+"""Planted mistakes in the oracle must be caught by its pins (no GPU).
+
+Each case copies ``oracle/glisse_oracle.c``, plants one plausible mistake (a
+dropped term, a wrong sign, a wrong index, a transposed operand, an
+off-by-one), builds it, and runs a pin from test_oracle_pins.py against it:
+the pin has to fail.  This is the evidence that the pins constrain every
+part of the oracle, not only the parts that happen to be exercised.
+"""
+import os
+
+import pytest
+
+import oracle
+import test_oracle_pins as P
+
+MUTANTS = [
+    # (id, original text, planted text, pin to run)
+    ("drop_indirect_h0", "a[d] = h0[d] + dir[d];", "a[d] = dir[d];", "brute"),
+    ("planet_kick_suffix_sign", "+ S[d] / P->eta[k + 1];", "- S[d] / P->eta[k + 1];", "brute"),
+    ("jacobi_eta_index", "dst[i][d] = src[i][d] - msum[d] / P->eta[i];",
+     "dst[i][d] = src[i][d] - msum[d] / P->eta[i + 1];", "brute"),
+    ("planet_mu_jacobi", "double mu = ORC_G * P->m0 * P->eta[i + 1] / P->eta[i];", "double mu = ORC_G * P->m0;",
+     "brute"),
+    ("particle_kick_transposed", "dir[1] -= Gm[j] * dy / d3;", "dir[1] -= Gm[j] * dz / d3;", "brute"),
+    ("closing_kick_old_planets", "particle_accel(np, Gm, P1, st, a);", "particle_accel(np, Gm, P0, st, a);",
+     "brute"),
+    ("drift_dE_g_sign", "double g = (dM - (x - s)) / n;", "double g = (dM - (x + s)) / n;", "two_body"),
+    ("drift_dE_fdot", "double fd = -n * a * a * s / (r * r0);", "double fd = -n * a * s / (r * r0);", "two_body"),
+    ("drift_univ_g", "double g = dt - mu * G3;", "double g = dt - mu * G2;", "two_body_hyp"),
+    ("stumpff_series_sign", "term *= -z /", "term *= z /", "two_body_hyp"),
+    ("tie_break_highest", "if (d2 < rc2[j] && hit == 0) hit = j + 1;", "if (d2 < rc2[j]) hit = j + 1;", "tie"),
+    ("removal_step_off_by_one", "if (h) { rstep = step0 + k + 1; rsn = h; break; }",
+     "if (h) { rstep = step0 + k; rsn = h; break; }", "escape"),
+    ("hill_radius_cube", "rcrit[i] = value * (1.0 / inva) * cbrt(p[0] / (3.0 * m0));",
+     "rcrit[i] = value * (1.0 / inva) * cbrt(p[0] / m0);", "hill"),
+]
+
+
+def _run_pin(name):
+    if name == "brute":
+        P.test_brute_force_second_order(oracle)
+    elif name == "two_body":
+        for el in P.ELEMENTS[:4]:
+            P.test_two_body_single_drift(oracle, el, 0.5)
+    elif name == "two_body_hyp":
+        for el in P.ELEMENTS[4:]:
+            P.test_two_body_single_drift(oracle, el, 0.5)
+            P.test_two_body_single_drift(oracle, el, 300.0)
+    elif name == "tie":
+        P.test_tie_breaks(oracle)
+    elif name == "escape":
+        P.test_escape_step_matches_analytic_crossing(oracle)
+    elif name == "hill":
+        P.test_hill_radius_definition(oracle)
+    else:
+        raise KeyError(name)
+
+
+@pytest.mark.parametrize("mid,orig,planted,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pin_catches_planted_mistake(tmp_path, mid, orig, planted, pin):
+    src = open(oracle.SOURCE).read()
+    assert src.count(orig) == 1, f"mutation anchor for {mid} not unique"
+    mutated = tmp_path / f"orc_{mid}.c"
+    mutated.write_text(src.replace(orig, planted))
+    so = oracle.compile_source(str(mutated), str(tmp_path / f"orc_{mid}.so"))
+    with oracle.using(so):
+        with pytest.raises((AssertionError, RuntimeError, ValueError)):
+            _run_pin(pin)
+
+
+def test_unmutated_oracle_passes_the_same_pins():
+    for pin in ["two_body", "two_body_hyp", "tie", "escape", "hill"]:
+        _run_pin(pin)
+    assert os.path.exists(oracle.build())
