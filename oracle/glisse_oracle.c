@@ -138,12 +138,15 @@ static int drift_dE(double mu, double dt, double* st, double r0, double u, doubl
         if (F < 0.0) { if (x > lo) lo = x; }
         else { if (x < hi) hi = x; }
         double dx = -F / Fp;
+        /* a Newton step below the tolerance is the converged answer (checked before
+         * the safeguard: x + dx may round onto a bracket end) */
+        if (fabs(dx) <= 1e-15) { x += dx; conv = 1; break; }
         double xn = x + dx;
         /* safeguard: bisect when Newton leaves the bracket or does not halve the last step */
         if (!(xn > lo && xn < hi) || fabs(dx) > 0.5 * fabs(dxold)) { xn = 0.5 * (lo + hi); dx = xn - x; }
         dxold = dx;
         x = xn;
-        if (fabs(dx) <= 1e-15 || hi - lo <= 1e-15) { conv = 1; break; }
+        if (hi - lo <= 1e-15) { conv = 1; break; }
     }
     g_last_iters = it + 1;
     if (!conv) return ORC_EKEPLER;
@@ -206,12 +209,15 @@ static int drift_univ(double mu, double dt, double* st, double r0, double u, dou
         if (F < 0.0) { if (s > lo) lo = s; }
         else { if (s < hi) hi = s; }
         double ds = -F / Fp;
+        /* a Newton step below the tolerance is the converged answer (checked before
+         * the safeguard: s + ds may round onto a bracket end) */
+        if (fabs(ds) <= 1e-15 * fabs(s)) { s += ds; conv = 1; break; }
         double sn = s + ds;
         /* safeguard: bisect when Newton leaves the bracket or does not halve the last step */
         if (!(sn > lo && sn < hi) || fabs(ds) > 0.5 * fabs(dsold)) { sn = 0.5 * (lo + hi); ds = sn - s; }
         dsold = ds;
         s = sn;
-        if (fabs(ds) <= 1e-15 * fabs(s) || hi - lo <= 1e-15 * fabs(s)) { conv = 1; break; }
+        if (hi - lo <= 1e-15 * fabs(s)) { conv = 1; break; }
     }
     g_last_iters = it + 1;
     if (!conv) return ORC_EKEPLER;
@@ -451,9 +457,10 @@ int orc_rcrit(double m0, int np, const double* pl, int mode, double value, doubl
 /* A particle whose test fires keeps the state of step 3 (after the drift,   */
 /* before the closing kick), removal_step = k+1 (global index), reason =     */
 /* planet index 1..np (lowest index wins), or -1 for escape (encounter wins  */
-/* over escape).  A failed Kepler solve keeps the state at t_k before the    */
-/* opening kick, reason -2; a non-finite drift result keeps the same state,  */
-/* reason -3.  The test at t_0 itself is made when test_first != 0.          */
+/* over escape).  A failed Kepler solve keeps the state it had just before  */
+/* the drift (after the opening kick), reason -2; a non-finite drift result  */
+/* keeps the same state, reason -3 (reading: the paper only says such        */
+/* particles are deactivated).  The test at t_0 is made when test_first.     */
 /* margin[p] records min over all tests of |metric - 1| (metric = d^2 / R^2  */
 /* or r^2 / rmax^2); closest[p] records min over tests of d_j^2 / R_j^2.     */
 /* ------------------------------------------------------------------------ */
@@ -548,9 +555,9 @@ int orc_particles(double m0, int np, const double* pmass, const double* log_pos,
             const double* P1 = P0 + stride;
             double a[3];
             double saved[6];
-            memcpy(saved, st, sizeof st);
             particle_accel(np, Gm, P0, st, a);
             for (int d = 0; d < 3; ++d) st[3 + d] += 0.5 * dt * a[d];
+            memcpy(saved, st, sizeof st);
             int rc = orc_kepler_drift(mu, dt, st);
             int bad = 0;
             for (int d = 0; d < 6; ++d) if (!isfinite(st[d])) bad = 1;

@@ -31,6 +31,7 @@ MUTANTS = [
     ("tie_break_highest", "if (d2 < rc2[j] && hit == 0) hit = j + 1;", "if (d2 < rc2[j]) hit = j + 1;", "tie"),
     ("removal_step_off_by_one", "if (h) { rstep = step0 + k + 1; rsn = h; break; }",
      "if (h) { rstep = step0 + k; rsn = h; break; }", "escape"),
+    ("newton_converged_step_rejected", "if (fabs(dx) <= 1e-15) { x += dx; conv = 1; break; }", "", "energy"),
     ("hill_radius_cube", "rcrit[i] = value * (1.0 / inva) * cbrt(p[0] / (3.0 * m0));",
      "rcrit[i] = value * (1.0 / inva) * cbrt(p[0] / m0);", "hill"),
 ]
@@ -52,6 +53,8 @@ def _run_pin(name):
         P.test_escape_step_matches_analytic_crossing(oracle)
     elif name == "hill":
         P.test_hill_radius_definition(oracle)
+    elif name == "energy":
+        P.test_two_body_no_secular_energy_drift(oracle, P.JUPITER_LIKE)
     else:
         raise KeyError(name)
 
@@ -69,6 +72,6 @@ def test_pin_catches_planted_mistake(tmp_path, mid, orig, planted, pin):
 
 
 def test_unmutated_oracle_passes_the_same_pins():
-    for pin in ["two_body", "two_body_hyp", "tie", "escape", "hill"]:
+    for pin in ["two_body", "two_body_hyp", "tie", "escape", "hill", "energy"]:
         _run_pin(pin)
     assert os.path.exists(oracle.build())
