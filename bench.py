@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Benchmark of the GLISSE test-particle map on GB300 (one JSON line on stdout).
+
+Metric: FP64 particle-steps/s (and the fraction of the measured FP64 peak).
+Workload (default): 131072 test particles between Uranus-like and Neptune-like
+orbits under a 4-planet system (a in U[20, 29] AU, e in U[0, 0.1], Rayleigh
+inclinations sigma = 2 deg, dt = 0.5 yr), chunk 1024 steps, live-particle
+compaction after every chunk; seeded synthetic data (glisse_inputs).
+
+One benchmark step = one pass of the whole path over one chunk: the planet
+ephemeris for the next chunk (side stream), the particle map over 1024 steps,
+and compaction.  W untimed steps, then K steps each bracketed by CUDA events on
+the library's stream, with an L2 flush (256 MiB write) between steps outside
+the events; barrier + synchronize around the timed region; max over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload longrun|belt|tiny]
+  python bench.py --impl reference ...   # the plain FP64 CPU oracle on host cores
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64 particle-steps/s at 1 GB300 (4 planets, 1e5-1e6 particles); % FP64 peak"
+UNIT = "particle-steps/s"
+
+# FP64 work of one interior particle-step in the kernel's formulation (static count of
+# the source; ncu's executed DADD:DMUL:DFMA mix matches it): the fast Kepler drift with
+# the degree-3 Stumpff tier (4 DADD, 15 DMUL, 39 DFMA), the h0 term (3 DFMA), and per
+# planet 3 DADD + 4 DMUL + 8 DFMA (separation, |d|^2, k |d|^-3, velocity update).
+def fp64_instr_per_step(np_: int) -> int:
+    return 58 + 3 + 15 * np_
+
+
+def flop_per_step(np_: int) -> int:
+    # DFMA counts 2 FLOP, DADD / DMUL 1
+    return (4 + 15 + 2 * 39) + 2 * 3 + np_ * (3 + 4 + 2 * 8)
+
+
+# GB300 FP64 pipe: 2 DFMA per clock per SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
+# peak_sustained = 2 inst/cycle/SM), 152 SMs.
+DFMA_PER_CLK_PER_SM = 2
+
+
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "particle_chunk_kernel_longrun.txt")
+KERNEL_SOURCES = ["particles.cu", "kepler.cuh", "device_math.cuh", "glisse_internal.h"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2011_03484_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic():
+    """DRAM bytes per particle-kernel launch from the committed ncu summary, if it was
+    taken on the current kernel source (its hash line must match), else None."""
+    try:
+        vals = {}
+        for line in open(PROFILE_TRAFFIC):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_hash") != kernel_hash():
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        try:
+            sm = [float(r[1]) for r in rows]
+            smax = max(float(r[2]) for r in rows)
+        except ValueError:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_desc(w, n):
+    return (f"{w.name}: {n} test particles, 4 planets (a 5.2-30.1 AU), a in U[{w.a_range[0]:g},{w.a_range[1]:g}] AU, "
+            f"e in U[{w.e_range[0]:g},{w.e_range[1]:g}], sigma_i {w.sigma_i_deg:g} deg, dt {w.dt:g} yr, "
+            f"chunk {w.chunk}, compaction every chunk")
+
+
+def cpu_oracle_rate(w, planets, particles, steps_per_chunk, chunks, threads=0, warmup=0):
+    """Oracle particle-steps/s on host cores over `chunks` timed chunks of a particle
+    sample, after `warmup` untimed chunks of the same run."""
+    import oracle
+
+    oracle.build()
+    rc = oracle.rcrit(w.star_mass, planets, 0, w.k_hill)
+    run = oracle.ParticleRun(w.star_mass, planets[:, 0], particles, rc, w.r_max)
+    pl = planets.copy()
+    done, busy = 0, 0.0
+    for c in range(warmup + chunks):
+        pl2, log, _ = oracle.planet_wh(w.star_mass, pl, w.dt, steps_per_chunk)
+        alive0 = int((run.removal_step < 0).sum())
+        t0 = time.perf_counter()
+        run.advance(log, w.dt, threads)
+        el = time.perf_counter() - t0
+        pl = pl2
+        alive1 = int((run.removal_step < 0).sum())
+        if c >= warmup:
+            busy += el
+            # removed particles counted with half a chunk (their steps stop mid-chunk)
+            done += alive1 * steps_per_chunk + (alive0 - alive1) * steps_per_chunk // 2
+    cores = threads if threads > 0 else oracle.max_threads()
+    return done / busy, cores, busy
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import glisse_inputs as gi
+
+    w = gi.WORKLOADS[args.workload]
+    full = gi.make(args.workload)
+    ids = gi.subset_ids(args.workload, args.ref_particles)
+    sample = full["particles"][ids]
+    rate_t, cores, busy_t = cpu_oracle_rate(w, full["planets"], sample, w.chunk, args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate_t, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * busy_t / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(w, w.n), "sample_particles": len(ids), "steps_per_bench_step": w.chunk},
+        "cpu_baseline": {"value": rate_t, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{len(ids)} random ids of the {w.n}-particle workload, {w.chunk} steps per bench step"},
+        "e2e": {"value": rate_t, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="longrun", choices=["longrun", "belt", "tiny"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-particles", type=int, default=8192)
+    ap.add_argument("--cpu-particles", type=int, default=16384)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+
+    import glisse_inputs as gi
+    import paper_2011_03484_gb300 as G
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    G._build.build()
+    G.load()
+
+    w = gi.WORKLOADS[args.workload]
+    full = gi.make(args.workload)
+    if world > 1:
+        # weak scaling: every rank integrates its own seeded replica of the workload
+        rng = np.random.Generator(np.random.PCG64(w.seed + 1000 * rank))
+        planets = full["planets"]
+        particles = gi.particle_belt(rng, w.n, w.a_range, w.e_range, w.sigma_i_deg, w.star_mass)
+    else:
+        planets, particles = full["planets"], full["particles"]
+    n = particles.shape[0]
+    np_ = planets.shape[0]
+
+    stream = torch.cuda.current_stream(dev)
+    o = G.glisse_opts_default()
+    o.chunk_steps = w.chunk
+    o.resync_chunks = w.resync
+    o.enc_value = w.k_hill
+    o.r_max = w.r_max
+    o.timing = 1
+    o.cuda_stream = stream.cuda_stream
+    h = G.glisse_create(w.star_mass, planets, particles, w.dt, o)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def flush_l2():
+        flush.zero_()
+
+    for _ in range(args.warmup):
+        G.glisse_advance(h, w.chunk)
+    torch.cuda.synchronize(dev)
+    G.glisse_timings(h, reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    live_before = G.glisse_status(h)[0]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(dev.index or 0) as clocks:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush_l2()
+            starts[k].record(stream)
+            G.glisse_advance(h, w.chunk)
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall0
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    tm = G.glisse_timings(h)
+    live_after = G.glisse_status(h)[0]
+    G.glisse_destroy(h)
+    psteps = tm["particle_steps"]
+    if dist:
+        t = torch.tensor([total_ms, float(psteps)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_ms_all, psteps_all = float(tmax[0]), float(t[1])
+    else:
+        total_ms_all, psteps_all = total_ms, float(psteps)
+    value = psteps_all / (total_ms_all * 1e-3)
+
+    # roofline of the particle kernel: algorithmic FP64 work / its own device time, against
+    # the FP64 pipe peak from the unit counts (152 SMs x 2 DFMA/clk) at the clock sampled
+    # during the timed region (max clock if no sample)
+    csum = clocks.summary()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = csum["sm_mhz"] if csum else 2070.0
+    dfma_peak = n_sm * DFMA_PER_CLK_PER_SM * mhz * 1e6
+    probe_rate, probe_mhz = G.glisse_fp64_peak(20000)
+    kernel_ms = tm["particle_ms"] / max(tm["particle_launches"], 1)
+    steps_per_launch = psteps / max(tm["particle_launches"], 1)
+    achieved = flop_per_step(np_) * steps_per_launch / (kernel_ms * 1e-3)
+    peak = 2.0 * dfma_peak
+    pipe = fp64_instr_per_step(np_) * steps_per_launch / (kernel_ms * 1e-3) / dfma_peak
+    traffic = profile_traffic()
+
+    # end to end through the C ABI with host buffers: create (H2D) + one chunk + read (D2H)
+    e2e = None
+    if args.e2e_steps > 0:
+        times, done = [], 0
+        for k in range(args.e2e_steps + 1):
+            t0 = time.perf_counter()
+            sim = G.Simulation(w.star_mass, planets, particles, w.dt, chunk_steps=w.chunk, enc_value=w.k_hill,
+                               r_max=w.r_max, timing=1)
+            sim.advance(w.chunk)
+            out = sim.read()
+            st = sim.timings()["particle_steps"]
+            sim.close()
+            dt_ = time.perf_counter() - t0
+            if k > 0:
+                times.append(dt_)
+                done += st
+        e2e = {"value": done / sum(times), "unit": UNIT,
+               "h2d_bytes_per_step": int(particles.nbytes + planets.nbytes),
+               "d2h_bytes_per_step": int(out["state"].nbytes + out["removal_step"].nbytes +
+                                         out["removal_reason"].nbytes)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ids = gi.subset_ids(args.workload, args.cpu_particles)
+        rate, cores, busy = cpu_oracle_rate(w, planets, particles[ids], w.chunk, 2)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{len(ids)} random ids of the workload, 2 chunks of {w.chunk} steps "
+                         f"({busy:.1f} s wall on {cores} threads)"}
+
+    launches = tm["particle_launches"] + tm["ephemeris_launches"] + 3 * tm["compact_launches"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(w, n), "particles_per_gpu": n, "planets": np_,
+                   "steps_per_bench_step": w.chunk, "live_at_start": live_before, "live_at_end": live_after,
+                   "fraction_alive_at_end": live_after / n, "l2": "flushed (256 MiB write) between timed steps",
+                   "parallelism": f"replicas x{world} (independent particle sets, no collective)",
+                   "wall_s": t_wall},
+        "roofline": {"bound": "alu", "achieved": achieved * 1e-9, "peak": peak * 1e-9, "unit": "GFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "particle_chunk_kernel<4>",
+                     "kernel_ms_avg": kernel_ms, "flop_per_particle_step": flop_per_step(np_),
+                     "fp64_instr_per_particle_step": fp64_instr_per_step(np_), "fp64_pipe_frac": pipe,
+                     "peak_source": f"unit counts: {n_sm} SMs x {DFMA_PER_CLK_PER_SM} DFMA/clk x 2 FLOP x "
+                                    f"{mhz:.0f} MHz (SM clock sampled during the timed region)",
+                     "probe_dfma_per_s": probe_rate,
+                     "probe_frac_of_peak": probe_rate / dfma_peak},
+        "stage_ms_per_step": {"particle": tm["particle_ms"] / args.steps, "ephemeris": tm["ephemeris_ms"] / args.steps,
+                              "compaction": tm["compact_ms"] / args.steps},
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "gpu_launches": int(launches),
+        "clocks": csum,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * glisse.h -- C ABI of the GB300 (sm_103a) implementation of the GLISSE
+ * test-particle map (Zhang & Gladman, "GLISSE: A GPU-optimized planetary
+ * system integrator", arXiv 2011.03484).
+ *
+ * The library advances N massless test particles through the mixed-variable
+ * symplectic (Wisdom-Holman) map of section 2.2 under a central star and
+ * N_p <= GLISSE_MAX_PLANETS planets, removing particles on close encounter
+ * or escape.  All arithmetic is IEEE binary64 on the GPU.  Units are AU, yr
+ * and M_sun with G = 4 pi^2.
+ *
+ * Conventions
+ *   - Every function returns GLISSE_OK (0) or a negative GLISSE_E_* code;
+ *     glisse_strerror() names it.  After a GLISSE_E_CUDA error the context
+ *     should be destroyed.
+ *   - Host buffers are owned by the caller; the library copies them during
+ *     the call and keeps no pointer to them.  Device buffers passed to the
+ *     *_device functions are owned by the caller and must stay valid until
+ *     the call returns (the calls synchronise their stream before returning).
+ *   - A context belongs to the CUDA device that was current at
+ *     glisse_create() and to the stream given in its options (or a stream
+ *     the library creates).  Contexts are not thread-safe; distinct contexts
+ *     may be used from distinct threads.
+ *   - Particle ids are input indices 0..n-1; outputs are indexed by id.
+ */
+#ifndef GLISSE_H
+#define GLISSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GLISSE_MAX_PLANETS 8
+
+/* status codes */
+#define GLISSE_OK 0
+#define GLISSE_E_INVAL -1   /* bad argument (NULL, size, order, non-finite, unbound planet) */
+#define GLISSE_E_NOMEM -2   /* device or host allocation failed */
+#define GLISSE_E_CUDA -3    /* a CUDA call failed (no device, launch error, ...) */
+#define GLISSE_E_KEPLER -4  /* a planet's Kepler solve did not converge */
+#define GLISSE_E_TIMEOUT -5 /* a bounded device-side wait gave up */
+#define GLISSE_E_STATE -6   /* call not valid in the context's current state */
+
+/* removal reasons reported by glisse_read() */
+#define GLISSE_ALIVE 0
+/* 1..N_p: close encounter with planet j (1-based, in input order) */
+#define GLISSE_REMOVED_ESCAPE -1
+#define GLISSE_REMOVED_KEPLER -2
+#define GLISSE_REMOVED_NONFINITE -3
+
+/* Kepler solver modes */
+#define GLISSE_KEPLER_CONVERGE 0    /* iterate to convergence (default) */
+#define GLISSE_KEPLER_PAPER_FIXED 1 /* fixed iteration count, deactivate if not converged (section 2.2) */
+
+/* encounter criterion (section 2.2, close-encounter paragraph) */
+#define GLISSE_ENC_HILL 0  /* R_crit,j = enc_value * a_j (m_j / 3 m0)^(1/3) */
+#define GLISSE_ENC_FIXED 1 /* R_crit,j = enc_value (AU) for every planet */
+
+typedef struct glisse_ctx glisse_ctx; /* opaque; owned by the library */
+
+typedef struct {
+    int32_t chunk_steps;   /* planet chunk length C (section 2.2 "planetary chunk"), default 1024 */
+    int32_t resync_chunks; /* compact live particles every R chunks (section 2.2 "resync interval"), default 1 */
+    int32_t kepler_mode;   /* GLISSE_KEPLER_*, default CONVERGE */
+    int32_t kepler_iters;  /* iterations for PAPER_FIXED, default 5 (section 2.2) */
+    int32_t enc_mode;      /* GLISSE_ENC_*, default HILL */
+    int32_t timing;        /* non-zero: time every launch with CUDA events (see glisse_timings) */
+    double enc_value;      /* Hill multiple k (default 1.0) or fixed distance in AU */
+    double r_max;          /* escape radius in AU, default 1000; <= 0 disables the escape test */
+    void* cuda_stream;     /* cudaStream_t to run on; NULL = the library creates one */
+} glisse_opts;
+
+/* Fill *opts with the defaults listed above. */
+void glisse_opts_default(glisse_opts* opts);
+
+/*
+ * Create a context and copy the initial conditions to the device.
+ *   star_mass  : m0 in M_sun (> 0)
+ *   planets    : host [n_planets][7] = m, x, y, z, vx, vy, vz (heliocentric),
+ *                ordered by increasing initial osculating semi-major axis
+ *                (Jacobi indexing, section 2.2); 0 <= n_planets <= GLISSE_MAX_PLANETS
+ *   particles  : host [n_particles][6] = x, y, z, vx, vy, vz (heliocentric); may be
+ *                NULL when n_particles == 0
+ *   dt         : step in yr (non-zero, finite; negative integrates backwards)
+ *   opts       : NULL for defaults
+ * The removal test at t_0 (section 2.2: particles already inside R_crit or
+ * beyond r_max) is applied by the first glisse_advance() call.
+ * Errors: INVAL (sizes, ordering, non-finite planets, unbound planet), NOMEM, CUDA.
+ */
+int glisse_create(glisse_ctx** out, double star_mass, const double* planets, int32_t n_planets,
+                  const double* particles, int64_t n_particles, double dt, const glisse_opts* opts);
+
+/*
+ * Advance every live particle by n_steps steps of kick(dt/2) - Kepler drift(dt) -
+ * kick(dt/2) (section 2.2), integrating the planets on the GPU one chunk ahead.
+ * Returns after the work has finished on the context's stream.
+ * Errors: INVAL (n_steps < 0), STATE (external ephemeris too short), KEPLER, CUDA.
+ */
+int glisse_advance(glisse_ctx* ctx, int64_t n_steps);
+
+/*
+ * Copy results to host buffers indexed by particle id (any pointer may be NULL):
+ *   state        : [n][6] x, y, z, vx, vy, vz.  Live particles: synchronised state at
+ *                  the current time.  Removed particles: the state at removal
+ *                  (after the drift, before the closing half kick).
+ *   alive        : [n] 1 = live, 0 = removed
+ *   removal_step : [n] step index of removal, -1 while live
+ *   removal_reason: [n] GLISSE_ALIVE, planet 1..N_p, or GLISSE_REMOVED_*
+ */
+int glisse_read(glisse_ctx* ctx, double* state, uint8_t* alive, int64_t* removal_step, int32_t* removal_reason);
+
+/* Number of live particles, current step index and time (t = step * dt); pointers may be NULL. */
+int glisse_status(glisse_ctx* ctx, int64_t* n_live, int64_t* step, double* t);
+
+/*
+ * Planets at the particles' current time: host [n_planets][7] m, x, y, z, vx, vy, vz
+ * (heliocentric).  *t receives the time (may be NULL).
+ * Errors: STATE while an external ephemeris (below) is installed.
+ */
+int glisse_read_planets(glisse_ctx* ctx, double* planets, double* t);
+
+/*
+ * Test hook (section 2.2 notes any source of planet positions will do, e.g.
+ * interpolation from a history file): install planet positions for the next
+ * n_steps steps instead of the built-in integrator.
+ *   log : host [n_steps+1][n_planets][3] heliocentric positions at t_k .. t_{k+n}
+ *         where t_k is the current time.
+ * The common term h0 = -sum_j G m_j r_j / |r_j|^3 is computed from these positions.
+ * After these steps are consumed, glisse_advance() returns STATE until another
+ * log is installed; the built-in planets are no longer valid for this context.
+ */
+int glisse_set_ephemeris(glisse_ctx* ctx, const double* log, int64_t n_steps);
+
+/* Device time spent per stage since glisse_create (or the last reset), collected
+ * when opts.timing != 0 from CUDA events recorded on the stream each kernel runs
+ * on.  particle_steps is the exact number of steps the live particles advanced
+ * (a removed particle counts the steps up to its removal). */
+typedef struct {
+    double particle_ms;        /* particle-map kernel */
+    int64_t particle_launches;
+    int64_t particle_steps;
+    double ephemeris_ms;       /* planet kernel (side stream, overlaps the particles) */
+    int64_t ephemeris_launches;
+    double compact_ms;         /* stable partition (three kernels) */
+    int64_t compact_launches;
+} glisse_timing;
+
+/* Copy the counters to *out (may be NULL) and zero them when reset != 0.
+ * Errors: STATE when the context was created without opts.timing. */
+int glisse_timings(glisse_ctx* ctx, glisse_timing* out, int32_t reset);
+
+/* Release all device and host resources of the context (NULL is ignored). */
+void glisse_destroy(glisse_ctx* ctx);
+
+/* Static string naming a status code. */
+const char* glisse_strerror(int code);
+
+/*
+ * Device-level stable partition of live particles (section 2.2: "a stable
+ * partition algorithm" moves deactivated particles to the end so live ones
+ * keep their relative order).  All pointers are device pointers:
+ *   alive   : [n] uint8, non-zero = keep
+ *   src     : [6][ld] doubles (x, y, z, vx, vy, vz planes, leading dimension ld >= n)
+ *   src_id  : [n] int32
+ *   dst     : [6][ld] doubles, dst_id: [n] int32 (must not overlap src)
+ *   n_out   : [1] int64 (device) receives the number of kept entries
+ * Kept entries appear in dst in their original relative order.  Scratch memory
+ * is allocated and freed by the call.  Runs on `stream` (cudaStream_t, NULL =
+ * legacy default stream) and synchronises it before returning.
+ * Errors: INVAL, NOMEM, CUDA.
+ */
+int glisse_partition_device(int64_t n, int64_t ld, const uint8_t* alive, const double* src, const int32_t* src_id,
+                            double* dst, int32_t* dst_id, int64_t* n_out, void* stream);
+
+/*
+ * FP64 throughput probe: runs independent chains of fused multiply-adds on
+ * every SM for about `iterations` x 8 operations per thread and reports the
+ * achieved rate (FMA instructions per second per GPU) in *dfma_per_s and the
+ * mean SM clock in MHz seen by the kernel in *sm_mhz (either may be NULL).
+ * Used to state the FP64 roofline the particle kernel is measured against.
+ */
+int glisse_fp64_peak(int32_t iterations, double* dfma_per_s, double* sm_mhz);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLISSE_H */

@@ -1,0 +1,259 @@
+"""GB300-native GLISSE test-particle map: Python binding of libglisse.so.
+
+Thin ctypes layer over the C ABI in ``include/glisse.h``: the functions keep
+the C names and only marshal arguments (numpy arrays for host buffers, torch
+tensors or raw integers for device pointers).  Every step of the map runs in
+the library's CUDA kernels; there is no CPU fallback.  If the library has not
+been built (``paper_2011_03484_gb300._build.build()``) or no CUDA device is
+usable, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+GLISSE_OK = 0
+GLISSE_E_INVAL = -1
+GLISSE_E_NOMEM = -2
+GLISSE_E_CUDA = -3
+GLISSE_E_KEPLER = -4
+GLISSE_E_TIMEOUT = -5
+GLISSE_E_STATE = -6
+GLISSE_MAX_PLANETS = 8
+GLISSE_ALIVE = 0
+GLISSE_REMOVED_ESCAPE = -1
+GLISSE_REMOVED_KEPLER = -2
+GLISSE_REMOVED_NONFINITE = -3
+GLISSE_KEPLER_CONVERGE = 0
+GLISSE_KEPLER_PAPER_FIXED = 1
+GLISSE_ENC_HILL = 0
+GLISSE_ENC_FIXED = 1
+
+# every symbol the header declares (checked by the tests against the built library)
+EXPORTED = (
+    "glisse_opts_default", "glisse_create", "glisse_advance", "glisse_read", "glisse_status",
+    "glisse_read_planets", "glisse_set_ephemeris", "glisse_destroy", "glisse_strerror",
+    "glisse_partition_device", "glisse_fp64_peak", "glisse_timings",
+)
+
+
+class glisse_timing(C.Structure):
+    _fields_ = [
+        ("particle_ms", C.c_double),
+        ("particle_launches", C.c_int64),
+        ("particle_steps", C.c_int64),
+        ("ephemeris_ms", C.c_double),
+        ("ephemeris_launches", C.c_int64),
+        ("compact_ms", C.c_double),
+        ("compact_launches", C.c_int64),
+    ]
+
+
+class glisse_opts(C.Structure):
+    _fields_ = [
+        ("chunk_steps", C.c_int32),
+        ("resync_chunks", C.c_int32),
+        ("kepler_mode", C.c_int32),
+        ("kepler_iters", C.c_int32),
+        ("enc_mode", C.c_int32),
+        ("timing", C.c_int32),
+        ("enc_value", C.c_double),
+        ("r_max", C.c_double),
+        ("cuda_stream", C.c_void_p),
+    ]
+
+
+class GlisseError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libglisse.so (optionally building it first).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(
+            "libglisse.so is not built; run paper_2011_03484_gb300._build.build() (needs nvcc for sm_103a)")
+    L = C.CDLL(_build.LIB)
+    dp, i64p, i32p, u8p, vp = (C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_uint8), C.c_void_p)
+    L.glisse_opts_default.argtypes = [C.POINTER(glisse_opts)]
+    L.glisse_opts_default.restype = None
+    L.glisse_create.argtypes = [C.POINTER(vp), C.c_double, dp, C.c_int32, dp, C.c_int64, C.c_double,
+                                C.POINTER(glisse_opts)]
+    L.glisse_create.restype = C.c_int
+    L.glisse_advance.argtypes = [vp, C.c_int64]
+    L.glisse_advance.restype = C.c_int
+    L.glisse_read.argtypes = [vp, dp, u8p, i64p, i32p]
+    L.glisse_read.restype = C.c_int
+    L.glisse_status.argtypes = [vp, i64p, i64p, dp]
+    L.glisse_status.restype = C.c_int
+    L.glisse_read_planets.argtypes = [vp, dp, dp]
+    L.glisse_read_planets.restype = C.c_int
+    L.glisse_set_ephemeris.argtypes = [vp, dp, C.c_int64]
+    L.glisse_set_ephemeris.restype = C.c_int
+    L.glisse_destroy.argtypes = [vp]
+    L.glisse_destroy.restype = None
+    L.glisse_strerror.argtypes = [C.c_int]
+    L.glisse_strerror.restype = C.c_char_p
+    L.glisse_partition_device.argtypes = [C.c_int64, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
+    L.glisse_partition_device.restype = C.c_int
+    L.glisse_fp64_peak.argtypes = [C.c_int32, dp, dp]
+    L.glisse_fp64_peak.restype = C.c_int
+    L.glisse_timings.argtypes = [vp, C.POINTER(glisse_timing), C.c_int32]
+    L.glisse_timings.restype = C.c_int
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _check(rc, what):
+    if rc != GLISSE_OK:
+        raise GlisseError(rc, what)
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().glisse_strerror(int(code)).decode()
+    except RuntimeError:
+        return f"status {code}"
+
+
+def glisse_opts_default() -> glisse_opts:
+    o = glisse_opts()
+    load().glisse_opts_default(C.byref(o))
+    return o
+
+
+def glisse_create(star_mass, planets, particles, dt, opts: glisse_opts | None = None):
+    """Create a context from host arrays planets [np][7] and particles [n][6]; returns a handle."""
+    L = load()
+    pl = np.ascontiguousarray(planets, dtype=np.float64).reshape(-1, 7)
+    pa = np.ascontiguousarray(particles, dtype=np.float64).reshape(-1, 6)
+    h = C.c_void_p()
+    rc = L.glisse_create(C.byref(h), float(star_mass), _dp(pl) if pl.size else None, pl.shape[0],
+                         _dp(pa) if pa.size else None, pa.shape[0], float(dt),
+                         C.byref(opts) if opts is not None else None)
+    _check(rc, "glisse_create")
+    return h
+
+
+def glisse_advance(h, n_steps: int):
+    _check(load().glisse_advance(h, int(n_steps)), "glisse_advance")
+
+
+def glisse_read(h, n: int):
+    """Returns dict(state [n][6], alive [n] bool, removal_step [n], removal_reason [n])."""
+    st = np.empty((n, 6))
+    alive = np.empty(n, dtype=np.uint8)
+    steps = np.empty(n, dtype=np.int64)
+    rsn = np.empty(n, dtype=np.int32)
+    rc = load().glisse_read(h, _dp(st), alive.ctypes.data_as(C.POINTER(C.c_uint8)),
+                            steps.ctypes.data_as(C.POINTER(C.c_int64)), rsn.ctypes.data_as(C.POINTER(C.c_int32)))
+    _check(rc, "glisse_read")
+    return {"state": st, "alive": alive.astype(bool), "removal_step": steps, "removal_reason": rsn}
+
+
+def glisse_status(h):
+    nl, st, t = C.c_int64(), C.c_int64(), C.c_double()
+    _check(load().glisse_status(h, C.byref(nl), C.byref(st), C.byref(t)), "glisse_status")
+    return nl.value, st.value, t.value
+
+
+def glisse_read_planets(h, n_planets: int):
+    out = np.empty((n_planets, 7))
+    t = C.c_double()
+    _check(load().glisse_read_planets(h, _dp(out), C.byref(t)), "glisse_read_planets")
+    return out, t.value
+
+
+def glisse_set_ephemeris(h, log):
+    lg = np.ascontiguousarray(log, dtype=np.float64)
+    n = lg.shape[0] - 1
+    _check(load().glisse_set_ephemeris(h, _dp(lg) if lg.size else None, n), "glisse_set_ephemeris")
+
+
+def glisse_destroy(h):
+    if h:
+        load().glisse_destroy(h)
+
+
+def glisse_partition_device(n, ld, alive_ptr, src_ptr, src_id_ptr, dst_ptr, dst_id_ptr, n_out_ptr, stream=0):
+    """Device-level stable partition; all pointers are device addresses (ints)."""
+    rc = load().glisse_partition_device(int(n), int(ld), alive_ptr, src_ptr, src_id_ptr, dst_ptr, dst_id_ptr,
+                                        n_out_ptr, stream)
+    _check(rc, "glisse_partition_device")
+
+
+def glisse_timings(h, reset: bool = False) -> dict:
+    t = glisse_timing()
+    _check(load().glisse_timings(h, C.byref(t), 1 if reset else 0), "glisse_timings")
+    return {name: getattr(t, name) for name, _ in glisse_timing._fields_}
+
+
+def glisse_fp64_peak(iterations: int = 20000):
+    """(DFMA instructions per second, SM MHz) measured on the current device."""
+    r, mhz = C.c_double(), C.c_double()
+    _check(load().glisse_fp64_peak(int(iterations), C.byref(r), C.byref(mhz)), "glisse_fp64_peak")
+    return r.value, mhz.value
+
+
+class Simulation:
+    """Convenience owner of a context (same calls, Python lifetime)."""
+
+    def __init__(self, star_mass, planets, particles, dt, **opt):
+        o = glisse_opts_default()
+        for k, v in opt.items():
+            setattr(o, k, v)
+        self.n = int(np.asarray(particles).reshape(-1, 6).shape[0])
+        self.n_planets = int(np.asarray(planets).reshape(-1, 7).shape[0])
+        self.h = glisse_create(star_mass, planets, particles, dt, o)
+
+    def advance(self, n_steps):
+        glisse_advance(self.h, n_steps)
+        return self
+
+    def read(self):
+        return glisse_read(self.h, self.n)
+
+    def status(self):
+        return glisse_status(self.h)
+
+    def planets(self):
+        return glisse_read_planets(self.h, self.n_planets)
+
+    def set_ephemeris(self, log):
+        glisse_set_ephemeris(self.h, log)
+
+    def timings(self, reset=False):
+        return glisse_timings(self.h, reset)
+
+    def close(self):
+        if self.h:
+            glisse_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,314 @@
+// ephemeris.cu -- the planets: set-up and the chunked Wisdom-Holman map (section 2.2).
+//
+// The paper integrates the planets with the standard mixed-variable
+// symplectic (Wisdom-Holman) map in Jacobi coordinates, a "planetary chunk"
+// of steps ahead of the particles, and ships the heliocentric positions plus
+// the common indirect term h0 = -sum_j G m_j r_j / |r_j|^3 for every step.
+// Here that runs on the GPU in one warp (lane i = planet i) on a side stream,
+// one chunk ahead of the particle kernel.
+//
+// Jacobi coordinates (commented equations after Eq. 2 of the paper), planets
+// i = 1..N_p (lane i-1), star 0:
+//   eta_i = m0 + m_1 + ... + m_i
+//   r'_i = r_i - sum_{k<i} m_k r_k / eta_{i-1}        (helio -> Jacobi)
+//   r_i  = r'_i + sum_{k<i} (m_k / eta_k) r'_k         (Jacobi -> helio)
+// Kepler part of H: sum_i p'_i^2 / 2m'_i - G m0 m_i / |r'_i| with
+//   m'_i = m_i eta_{i-1} / eta_i, i.e. a Kepler drift with mu_i = G m0 eta_i / eta_{i-1}.
+// Interaction part: H_int = sum_i G m0 m_i (1/|r'_i| - 1/|r_i|) - sum_{i<j} G m_i m_j / |r_i - r_j|.
+// Its kick, by the chain rule through r(r'):
+//   dv'_k/dt = -(eta_k / eta_{k-1}) [ -G m0 r'_k / |r'_k|^3 + ghat_k + S_k / eta_k ]
+//   ghat_i = G m0 r_i / |r_i|^3 + sum_{j != i} G m_j (r_i - r_j) / |r_i - r_j|^3
+//   S_k = sum_{i > k} m_i ghat_i
+#include "glisse_internal.h"
+#include "kepler.cuh"
+
+namespace glisse {
+
+// Scans over the first n lanes (n <= 32, warp-uniform).  Lanes >= n must hold 0.
+// exclusive prefix: sum over lanes k < lane
+__device__ __forceinline__ double warp_excl_prefix(double v, int lane, int n) {
+    double incl = v;
+    for (int o = 1; o < n; o <<= 1) {
+        const double t = __shfl_up_sync(kFullMask, incl, o);
+        if (lane >= o) incl += t;
+    }
+    return incl - v;
+}
+
+// exclusive suffix: sum over lanes k > lane (k < n)
+__device__ __forceinline__ double warp_excl_suffix(double v, int lane, int n) {
+    double incl = v;
+    for (int o = 1; o < n; o <<= 1) {
+        const double t = __shfl_down_sync(kFullMask, incl, o);
+        if (lane + o < n) incl += t;
+    }
+    return incl - v;
+}
+
+// total over lanes < n, valid in lane 0
+__device__ __forceinline__ double warp_total0(double v, int lane, int n) {
+    return warp_excl_suffix(v, lane, n) + v;
+}
+
+// ---------------------------------------------------------------------------
+// Set-up: constants, Jacobi state, encounter radii.  One warp.
+//   planets : [np][7] heliocentric m, x, y, z, vx, vy, vz (device copy)
+//   jac     : out [2][np][3]: Jacobi positions then Jacobi velocities
+//   status  : out 0, or GLISSE_E_INVAL (unbound planet, or not ordered by a)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) eph_setup_kernel(const double* __restrict__ planets, int np, double m0, double G,
+                                                         int enc_mode, double enc_value, PlanetConsts* pc,
+                                                         double* jac, int* status) {
+    const int lane = threadIdx.x;
+    const bool on = lane < np;
+    const double m = on ? planets[7 * lane] : 0.0;
+    double r[3], v[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        r[d] = on ? planets[7 * lane + 1 + d] : 0.0;
+        v[d] = on ? planets[7 * lane + 4 + d] : 0.0;
+    }
+    // eta_i for this lane's planet (inclusive) and eta_{i-1}
+    const double eta_prev = m0 + warp_excl_prefix(m, lane, 32);
+    const double eta_i = eta_prev + m;
+    double q[3], w[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double mr = warp_excl_prefix(m * r[d], lane, 32);
+        const double mv = warp_excl_prefix(m * v[d], lane, 32);
+        q[d] = r[d] - mr / eta_prev;
+        w[d] = v[d] - mv / eta_prev;
+    }
+    // initial osculating heliocentric semi-major axis with mu = G (m0 + m_j)
+    const double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const double inva = 2.0 / rn - v2 / (G * (m0 + m));
+    const bool bound = inva > 0.0;
+    const double a = 1.0 / inva;
+    const double rcrit = (enc_mode == GLISSE_ENC_FIXED) ? enc_value : enc_value * a * cbrt(m / (3.0 * m0));
+    // ordering by increasing a
+    const double a_prev = __shfl_up_sync(kFullMask, a, 1);
+    const bool order_ok = (lane == 0) || !(a <= a_prev);
+    const unsigned bad = __ballot_sync(kFullMask, on && (!bound || !order_ok || !isfinite(rcrit)));
+    if (on) {
+        pc->m[lane] = m;
+        pc->eta[lane + 1] = eta_i;
+        pc->mu_jac[lane] = G * m0 * eta_i / eta_prev;
+        pc->gm[lane] = G * m;
+        pc->rcrit[lane] = rcrit;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            jac[3 * lane + d] = q[d];
+            jac[3 * np + 3 * lane + d] = w[d];
+        }
+    }
+    if (lane == 0) {
+        pc->np = np;
+        pc->m0 = m0;
+        pc->G = G;
+        pc->mu0 = G * m0;
+        pc->eta[0] = m0;
+        *status = bad ? GLISSE_E_INVAL : 0;
+    }
+}
+
+// Heliocentric positions and velocities of all lanes from Jacobi ones.
+__device__ __forceinline__ void jac_to_helio(const double q[3], double m_over_eta, int lane, int np, double r[3]) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) r[d] = q[d] + warp_excl_prefix(m_over_eta * q[d], lane, np);
+}
+
+// Jacobi acceleration of every lane's planet, and h0, at heliocentric positions r.
+// inv_eta = 1 / eta_i and ratio = eta_i / eta_{i-1} of this lane's planet.
+__device__ __forceinline__ void planet_accel(const PlanetConsts& pc, bool on, int lane, double inv_eta, double ratio,
+                                             const double q[3], const double r[3], double acc[3], double h0[3]) {
+    const int np = pc.np;
+    const double m = on ? pc.m[lane] : 0.0;
+    const double gm = on ? pc.gm[lane] : 0.0;
+    const double mu0 = pc.mu0;
+    // star term of ghat and this planet's share of h0
+    const double r2 = on ? fma(r[0], r[0], fma(r[1], r[1], r[2] * r[2])) : 1.0;
+    const double ir3 = k_rcube(r2, 1.0);
+    const double sun = mu0 * ir3, own = gm * ir3;
+    double gh[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        gh[d] = sun * r[d];
+        h0[d] = -warp_total0(own * r[d], lane, np);
+    }
+    // planet-planet terms
+    for (int j = 0; j < np; ++j) {
+        const double rjx = __shfl_sync(kFullMask, r[0], j);
+        const double rjy = __shfl_sync(kFullMask, r[1], j);
+        const double rjz = __shfl_sync(kFullMask, r[2], j);
+        const double gmj = pc.gm[j];
+        const double dx = r[0] - rjx, dy = r[1] - rjy, dz = r[2] - rjz;
+        const double d2 = (j == lane || !on) ? 1.0 : fma(dx, dx, fma(dy, dy, dz * dz));
+        const double s = (j == lane || !on) ? 0.0 : k_rcube(d2, gmj);
+        gh[0] = fma(s, dx, gh[0]);
+        gh[1] = fma(s, dy, gh[1]);
+        gh[2] = fma(s, dz, gh[2]);
+    }
+    // S_k = sum_{i>k} m_i ghat_i ; gradient ; Jacobi acceleration
+    const double q2 = on ? fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2])) : 1.0;
+    const double iq3 = k_rcube(q2, mu0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double S = warp_excl_suffix(on ? m * gh[d] : 0.0, lane, np);
+        const double grad = fma(S, inv_eta, fma(-iq3, q[d], gh[d]));
+        acc[d] = on ? -ratio * grad : 0.0;
+    }
+}
+
+// Write log step k (positions + h0) and the synchronised heliocentric states.
+__device__ __forceinline__ void emit_step(int k, int np, int S, int lane, bool on, double m_over_eta, const double r[3],
+                                          const double w[3], const double h0[3], double* __restrict__ log,
+                                          double* __restrict__ hist) {
+    double vh[3];
+    jac_to_helio(w, m_over_eta, lane, np, vh);
+    double* L = log + (size_t)k * S;
+    double* H = hist + (size_t)k * 6 * np;
+    if (on) {
+        L[kRec * lane + 0] = r[0];
+        L[kRec * lane + 1] = r[1];
+        L[kRec * lane + 2] = r[2];
+        L[kRec * lane + 3] = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            H[6 * lane + d] = r[d];
+            H[6 * lane + 3 + d] = vh[d];
+        }
+    }
+    if (lane == 0) {
+        L[kRec * np + 0] = h0[0];
+        L[kRec * np + 1] = h0[1];
+        L[kRec * np + 2] = h0[2];
+        L[kRec * np + 3] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Advance the planets nsteps steps from the Jacobi state `jac` (in place).
+// Writes log steps 0..nsteps (positions + h0, broadcast layout) and the
+// synchronised heliocentric states hist[0..nsteps][np][6].
+// status: set to GLISSE_E_KEPLER if a planet's drift fails.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) eph_chunk_kernel(const PlanetConsts* __restrict__ pcp, double* jac, double dt,
+                                                         int nsteps, double* __restrict__ log,
+                                                         double* __restrict__ hist, int* status) {
+    const PlanetConsts& pc = *pcp;
+    const int np = pc.np;
+    const int lane = threadIdx.x;
+    const bool on = lane < np;
+    const int S = log_stride(np);
+    double q[3], w[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        q[d] = on ? jac[3 * lane + d] : 1.0 + lane;
+        w[d] = on ? jac[3 * np + 3 * lane + d] : 0.0;
+    }
+    if (!on) {
+        q[1] = 0.0;
+        q[2] = 0.0;
+    }
+    const double m_over_eta = on ? pc.m[lane] / pc.eta[lane + 1] : 0.0;
+    const double inv_eta = on ? 1.0 / pc.eta[lane + 1] : 1.0;
+    const double ratio = on ? pc.eta[lane + 1] / pc.eta[lane] : 1.0;
+    const double mu = on ? pc.mu_jac[lane] : pc.mu0;
+    const float muf = d2f_bits(mu), dtf = d2f_bits(dt);
+    const double hdt = 0.5 * dt;
+    double r[3], acc[3], h0[3];
+
+
+    jac_to_helio(q, m_over_eta, lane, np, r);
+    planet_accel(pc, on, lane, inv_eta, ratio, q, r, acc, h0);
+    emit_step(0, np, S, lane, on, m_over_eta, r, w, h0, log, hist);
+    bool failed = false;
+    for (int k = 0; k < nsteps; ++k) {
+        // opening half kick
+#pragma unroll
+        for (int d = 0; d < 3; ++d) w[d] = fma(hdt, acc[d], w[d]);
+        // Kepler drift of each Jacobi body
+        double qr, qrinv;
+        radius_of(q[0], q[1], q[2], qr, qrinv);
+        const bool done = drift_fast(mu, muf, dt, dtf, on, qr, qrinv, q[0], q[1], q[2], w[0], w[1], w[2]);
+        if (on && !done) {
+            if (!drift_general(mu, dt, q[0], q[1], q[2], w[0], w[1], w[2])) failed = true;
+        }
+        jac_to_helio(q, m_over_eta, lane, np, r);
+        planet_accel(pc, on, lane, inv_eta, ratio, q, r, acc, h0);
+        // closing half kick: synchronised state at t_{k+1}
+#pragma unroll
+        for (int d = 0; d < 3; ++d) w[d] = fma(hdt, acc[d], w[d]);
+        emit_step(k + 1, np, S, lane, on, m_over_eta, r, w, h0, log, hist);
+    }
+    if (on) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            jac[3 * lane + d] = q[d];
+            jac[3 * np + 3 * lane + d] = w[d];
+        }
+    }
+    if (__any_sync(kFullMask, failed) && lane == 0) *status = GLISSE_E_KEPLER;
+}
+
+// ---------------------------------------------------------------------------
+// External positions -> log layout with h0.  One thread per step.
+//   pos : [n+1][np][3] heliocentric positions
+// ---------------------------------------------------------------------------
+__global__ void eph_external_kernel(const PlanetConsts* __restrict__ pcp, const double* __restrict__ pos, int64_t n1,
+                                    double* __restrict__ log) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n1) return;
+    const int np = pcp->np;
+    const int S = log_stride(np);
+    double hx = 0.0, hy = 0.0, hz = 0.0;
+    for (int j = 0; j < np; ++j) {
+        const double x = pos[(k * np + j) * 3 + 0], y = pos[(k * np + j) * 3 + 1], z = pos[(k * np + j) * 3 + 2];
+        const double r2 = fma(x, x, fma(y, y, z * z));
+        const double s = k_rcube(r2, pcp->gm[j]);
+        hx = fma(-s, x, hx);
+        hy = fma(-s, y, hy);
+        hz = fma(-s, z, hz);
+        log[k * S + kRec * j + 0] = x;
+        log[k * S + kRec * j + 1] = y;
+        log[k * S + kRec * j + 2] = z;
+        log[k * S + kRec * j + 3] = 0.0;
+    }
+    log[k * S + kRec * np + 0] = hx;
+    log[k * S + kRec * np + 1] = hy;
+    log[k * S + kRec * np + 2] = hz;
+    log[k * S + kRec * np + 3] = 0.0;
+}
+
+// host launchers ----------------------------------------------------------------
+cudaError_t launch_eph_setup(const double* planets, int np, double m0, double G, int enc_mode, double enc_value,
+                             PlanetConsts* pc, double* jac, int* status, cudaStream_t s) {
+    eph_setup_kernel<<<1, 32, 0, s>>>(planets, np, m0, G, enc_mode, enc_value, pc, jac, status);
+    return cudaGetLastError();
+}
+
+// The ephemeris is one serial warp.  Sharing an SM partition with particle
+// warps would slow it by the number of warps it shares the FP64 pipe with, so
+// its block asks for the largest dynamic shared-memory allocation a block may
+// have: no other block fits on that SM while it runs (the memory is unused).
+cudaError_t launch_eph_chunk(const PlanetConsts* pc, double* jac, double dt, int nsteps, double* log, double* hist,
+                             int* status, cudaStream_t s) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(eph_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return e;
+    eph_chunk_kernel<<<1, 32, (size_t)optin, s>>>(pc, jac, dt, nsteps, log, hist, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eph_external(const PlanetConsts* pc, const double* pos, int64_t n1, double* log, cudaStream_t s) {
+    const int bs = 128;
+    const int64_t grid = (n1 + bs - 1) / bs;
+    eph_external_kernel<<<(unsigned)grid, bs, 0, s>>>(pc, pos, n1, log);
+    return cudaGetLastError();
+}
+
+}  // namespace glisse

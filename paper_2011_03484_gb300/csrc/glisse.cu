@@ -1,0 +1,591 @@
+// glisse.cu -- host runtime behind the C ABI of include/glisse.h.
+//
+// Layout in device memory (one context):
+//   particles   two sets of [6][cap] double planes (x, y, z, vx, vy, vz) plus
+//               [cap] int32 ids; the live particles occupy slots 0..n_live-1 of
+//               the current set, in id order (stable compaction keeps it)
+//   alive       [cap] uint8 written by the particle kernel, reset after compaction
+//   per-id out  [N][6] state, [N] removal step, [N] reason
+//   planets     constants, Jacobi state [2][N_p][3]
+//   planet log  a ring of 3 chunk buffers, each [(C+1)][4 (N_p+1)] doubles of
+//               positions + h0, and [(C+1)][N_p][6] synchronised heliocentric
+//               states (for glisse_read_planets)
+//
+// Scheduling: chunk j of the planet log covers steps [jC, (j+1)C] of the
+// run.  The ephemeris kernel for chunk j+1 runs on a high-priority side stream
+// while the particle kernel works through chunk j on the main stream (the
+// paper's "planet chunk computed one ahead", section 2.2); events order the
+// ring-buffer reuse.  After each segment (a particle launch over at most one
+// chunk) live particles are compacted every resync_chunks segments.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "glisse_internal.h"
+
+namespace glisse {
+cudaError_t launch_eph_setup(const double*, int, double, double, int, double, PlanetConsts*, double*, int*,
+                             cudaStream_t);
+cudaError_t launch_eph_chunk(const PlanetConsts*, double*, double, int, double*, double*, int*, cudaStream_t);
+cudaError_t launch_eph_external(const PlanetConsts*, const double*, int64_t, double*, cudaStream_t);
+cudaError_t launch_particle_chunk(int, const ChunkArgs&, const ParticleConsts&, cudaStream_t);
+cudaError_t launch_compact(int64_t, const uint8_t*, const double*, const int32_t*, int64_t, double*, int32_t*,
+                           int64_t, int64_t*, int64_t*, cudaStream_t);
+int64_t compact_scratch_entries(int64_t);
+cudaError_t launch_export_live(int64_t, const double*, int64_t, const int32_t*, double*, cudaStream_t);
+cudaError_t launch_import(int64_t, const double*, double*, int64_t, int32_t*, cudaStream_t);
+}  // namespace glisse
+
+using namespace glisse;
+
+namespace {
+constexpr int kRing = 3;
+constexpr double kG = 4.0 * 3.14159265358979323846 * 3.14159265358979323846;
+}  // namespace
+
+struct glisse_ctx {
+    int device = 0;
+    cudaStream_t s = nullptr, se = nullptr;
+    bool own_s = false;
+    glisse_opts o{};
+    int np = 0;
+    double m0 = 0, dt = 0;
+    int C = 1024;
+    int64_t n_total = 0, cap = 0, n_live = 0, step = 0;
+    bool tested_first = false;
+    PlanetConsts hpc{};
+    ParticleConsts ppc{};
+    PlanetConsts* d_pc = nullptr;
+    double* d_jac = nullptr;
+    int* d_status = nullptr;
+    int* h_status = nullptr;
+    double* d_log[kRing] = {};
+    double* d_hist[kRing] = {};
+    int64_t chunk_of[kRing] = {-1, -1, -1};
+    cudaEvent_t ev_eph[kRing] = {};
+    cudaEvent_t ev_use[kRing] = {};
+    bool used[kRing] = {};
+    int64_t next_chunk = 0;
+    double* d_st[2] = {};
+    int32_t* d_id[2] = {};
+    int cur = 0;
+    uint8_t* d_alive = nullptr;
+    double* d_out_state = nullptr;
+    int64_t* d_out_step = nullptr;
+    int32_t* d_out_reason = nullptr;
+    int64_t* d_counts = nullptr;
+    int64_t* d_nlive = nullptr;
+    int64_t* h_nlive = nullptr;
+    unsigned long long* d_steps = nullptr;   // exact particle-step counter (timing mode)
+    unsigned long long* h_steps = nullptr;
+    int since_compact = 0;
+    bool external = false, planets_valid = true;
+    double* d_ext_log = nullptr;
+    int64_t ext_n = 0, ext_off = 0;
+    // optional per-launch timing
+    bool timing = false;
+    cudaEvent_t tp0 = nullptr, tp1 = nullptr, tc0 = nullptr, tc1 = nullptr;
+    cudaEvent_t te0[kRing] = {}, te1[kRing] = {};
+    bool eph_pending[kRing] = {};
+    glisse_timing acc{};
+};
+
+#define GL_CUDA(x)                               \
+    do {                                         \
+        cudaError_t e_ = (x);                    \
+        if (e_ != cudaSuccess) {                 \
+            (void)cudaGetLastError();            \
+            return GLISSE_E_CUDA;                \
+        }                                        \
+    } while (0)
+
+static int alloc_dev(void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        return GLISSE_E_NOMEM;
+    }
+    return e == cudaSuccess ? GLISSE_OK : GLISSE_E_CUDA;
+}
+
+#define GL_ALLOC(ptr, bytes)                                      \
+    do {                                                          \
+        int r_ = alloc_dev(reinterpret_cast<void**>(&(ptr)), (bytes)); \
+        if (r_ != GLISSE_OK) return r_;                           \
+    } while (0)
+
+extern "C" void glisse_opts_default(glisse_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->chunk_steps = 1024;
+    o->resync_chunks = 1;
+    o->kepler_mode = GLISSE_KEPLER_CONVERGE;
+    o->kepler_iters = 5;
+    o->enc_mode = GLISSE_ENC_HILL;
+    o->timing = 0;
+    o->enc_value = 1.0;
+    o->r_max = 1000.0;
+    o->cuda_stream = nullptr;
+}
+
+extern "C" const char* glisse_strerror(int code) {
+    switch (code) {
+        case GLISSE_OK: return "ok";
+        case GLISSE_E_INVAL: return "invalid argument";
+        case GLISSE_E_NOMEM: return "out of memory";
+        case GLISSE_E_CUDA: return "CUDA error";
+        case GLISSE_E_KEPLER: return "Kepler solve did not converge";
+        case GLISSE_E_TIMEOUT: return "device wait timed out";
+        case GLISSE_E_STATE: return "invalid in the current state";
+        default: return "unknown status";
+    }
+}
+
+static void ctx_free(glisse_ctx* c) {
+    if (!c) return;
+    if (c->s) cudaStreamSynchronize(c->s);
+    if (c->se) cudaStreamSynchronize(c->se);
+    for (int r = 0; r < kRing; ++r) {
+        cudaFree(c->d_log[r]);
+        cudaFree(c->d_hist[r]);
+        if (c->ev_eph[r]) cudaEventDestroy(c->ev_eph[r]);
+        if (c->ev_use[r]) cudaEventDestroy(c->ev_use[r]);
+        if (c->te0[r]) cudaEventDestroy(c->te0[r]);
+        if (c->te1[r]) cudaEventDestroy(c->te1[r]);
+    }
+    for (cudaEvent_t e : {c->tp0, c->tp1, c->tc0, c->tc1})
+        if (e) cudaEventDestroy(e);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(c->d_st[b]);
+        cudaFree(c->d_id[b]);
+    }
+    cudaFree(c->d_pc);
+    cudaFree(c->d_jac);
+    cudaFree(c->d_status);
+    cudaFree(c->d_alive);
+    cudaFree(c->d_out_state);
+    cudaFree(c->d_out_step);
+    cudaFree(c->d_out_reason);
+    cudaFree(c->d_counts);
+    cudaFree(c->d_nlive);
+    cudaFree(c->d_ext_log);
+    cudaFree(c->d_steps);
+    if (c->h_steps) cudaFreeHost(c->h_steps);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->h_nlive) cudaFreeHost(c->h_nlive);
+    if (c->se) cudaStreamDestroy(c->se);
+    if (c->own_s && c->s) cudaStreamDestroy(c->s);
+    delete c;
+}
+
+extern "C" void glisse_destroy(glisse_ctx* c) {
+    if (!c) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    ctx_free(c);
+    cudaSetDevice(prev);
+}
+
+// Enqueue the ephemeris for chunk j (and every earlier chunk not yet enqueued).
+static int ensure_chunk(glisse_ctx* c, int64_t j) {
+    while (c->next_chunk <= j) {
+        const int slot = (int)(c->next_chunk % kRing);
+        if (c->used[slot]) GL_CUDA(cudaStreamWaitEvent(c->se, c->ev_use[slot], 0));
+        if (c->timing) GL_CUDA(cudaEventRecord(c->te0[slot], c->se));
+        GL_CUDA(launch_eph_chunk(c->d_pc, c->d_jac, c->dt, c->C, c->d_log[slot], c->d_hist[slot], c->d_status, c->se));
+        if (c->timing) {
+            GL_CUDA(cudaEventRecord(c->te1[slot], c->se));
+            c->eph_pending[slot] = true;
+        }
+        GL_CUDA(cudaEventRecord(c->ev_eph[slot], c->se));
+        c->chunk_of[slot] = c->next_chunk;
+        c->used[slot] = false;
+        ++c->next_chunk;
+    }
+    return GLISSE_OK;
+}
+
+static int check_status(glisse_ctx* c) {
+    GL_CUDA(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    GL_CUDA(cudaStreamSynchronize(c->s));
+    return *c->h_status;
+}
+
+static int setup(glisse_ctx* c, const double* planets, const double* particles) {
+    const int np = c->np;
+    GL_CUDA(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
+    c->own_s = true;
+    if (c->o.cuda_stream) {
+        cudaStreamDestroy(c->s);
+        c->s = static_cast<cudaStream_t>(c->o.cuda_stream);
+        c->own_s = false;
+    }
+    int lo = 0, hi = 0;
+    GL_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    GL_CUDA(cudaStreamCreateWithPriority(&c->se, cudaStreamNonBlocking, hi));
+    for (int r = 0; r < kRing; ++r) {
+        GL_CUDA(cudaEventCreateWithFlags(&c->ev_eph[r], cudaEventDisableTiming));
+        GL_CUDA(cudaEventCreateWithFlags(&c->ev_use[r], cudaEventDisableTiming));
+    }
+    if (c->timing) {
+        for (int r = 0; r < kRing; ++r) {
+            GL_CUDA(cudaEventCreate(&c->te0[r]));
+            GL_CUDA(cudaEventCreate(&c->te1[r]));
+        }
+        GL_CUDA(cudaEventCreate(&c->tp0));
+        GL_CUDA(cudaEventCreate(&c->tp1));
+        GL_CUDA(cudaEventCreate(&c->tc0));
+        GL_CUDA(cudaEventCreate(&c->tc1));
+        GL_ALLOC(c->d_steps, sizeof(unsigned long long));
+        GL_CUDA(cudaMemset(c->d_steps, 0, sizeof(unsigned long long)));
+        GL_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&c->h_steps), sizeof(unsigned long long),
+                              cudaHostAllocDefault));
+    }
+    GL_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&c->h_status), sizeof(int), cudaHostAllocDefault));
+    GL_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&c->h_nlive), sizeof(int64_t), cudaHostAllocDefault));
+    const int S = log_stride(np);
+    GL_ALLOC(c->d_pc, sizeof(PlanetConsts));
+    GL_ALLOC(c->d_jac, sizeof(double) * 6 * std::max(np, 1));
+    GL_ALLOC(c->d_status, sizeof(int));
+    for (int r = 0; r < kRing; ++r) {
+        GL_ALLOC(c->d_log[r], sizeof(double) * (size_t)(c->C + 1) * S);
+        GL_ALLOC(c->d_hist[r], sizeof(double) * (size_t)(c->C + 1) * 6 * std::max(np, 1));
+    }
+    const int64_t cap = std::max<int64_t>(c->n_total, 1);
+    c->cap = cap;
+    for (int b = 0; b < 2; ++b) {
+        GL_ALLOC(c->d_st[b], sizeof(double) * 6 * (size_t)cap);
+        GL_ALLOC(c->d_id[b], sizeof(int32_t) * (size_t)cap);
+    }
+    GL_ALLOC(c->d_alive, (size_t)cap);
+    GL_ALLOC(c->d_out_state, sizeof(double) * 6 * (size_t)cap);
+    GL_ALLOC(c->d_out_step, sizeof(int64_t) * (size_t)cap);
+    GL_ALLOC(c->d_out_reason, sizeof(int32_t) * (size_t)cap);
+    GL_ALLOC(c->d_counts, sizeof(int64_t) * (size_t)compact_scratch_entries(cap));
+    GL_ALLOC(c->d_nlive, sizeof(int64_t));
+
+    // planets -> device, set-up kernel (Jacobi state, constants, encounter radii)
+    double* d_in = nullptr;
+    GL_ALLOC(d_in, sizeof(double) * 7 * std::max(np, 1));
+    cudaError_t e = cudaSuccess;
+    if (np > 0) e = cudaMemcpyAsync(d_in, planets, sizeof(double) * 7 * np, cudaMemcpyHostToDevice, c->s);
+    if (e == cudaSuccess)
+        e = launch_eph_setup(d_in, np, c->m0, kG, c->o.enc_mode, c->o.enc_value, c->d_pc, c->d_jac, c->d_status,
+                             c->s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&c->hpc, c->d_pc, sizeof(PlanetConsts), cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    cudaFree(d_in);
+    if (e != cudaSuccess) return GLISSE_E_CUDA;
+    if (*c->h_status != 0) return *c->h_status;
+
+    // particle constants (kernel parameters)
+    ParticleConsts& p = c->ppc;
+    std::memset(&p, 0, sizeof(p));
+    p.mu = c->hpc.mu0;
+    p.dt = c->dt;
+    p.half_dt = 0.5 * c->dt;
+    for (int j = 0; j < np; ++j) {
+        p.tgm_full[j] = c->dt * c->hpc.gm[j];
+        p.tgm_half[j] = 0.5 * c->dt * c->hpc.gm[j];
+        p.rc2[j] = c->hpc.rcrit[j] * c->hpc.rcrit[j];
+    }
+    p.rmax2 = c->o.r_max > 0.0 ? c->o.r_max * c->o.r_max : 0.0;
+    p.rmax = c->o.r_max > 0.0 ? c->o.r_max : 0.0;
+
+    // particles -> device SoA, ids, flags
+    if (c->n_total > 0) {
+        double* d_aos = nullptr;
+        GL_ALLOC(d_aos, sizeof(double) * 6 * (size_t)c->n_total);
+        e = cudaMemcpyAsync(d_aos, particles, sizeof(double) * 6 * (size_t)c->n_total, cudaMemcpyHostToDevice, c->s);
+        if (e == cudaSuccess) e = launch_import(c->n_total, d_aos, c->d_st[0], cap, c->d_id[0], c->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+        cudaFree(d_aos);
+        if (e != cudaSuccess) return GLISSE_E_CUDA;
+    }
+    GL_CUDA(cudaMemsetAsync(c->d_alive, 1, (size_t)cap, c->s));
+    GL_CUDA(cudaMemsetAsync(c->d_out_state, 0, sizeof(double) * 6 * (size_t)cap, c->s));
+    GL_CUDA(cudaMemsetAsync(c->d_out_step, 0xFF, sizeof(int64_t) * (size_t)cap, c->s));  // -1
+    GL_CUDA(cudaMemsetAsync(c->d_out_reason, 0, sizeof(int32_t) * (size_t)cap, c->s));
+    c->n_live = c->n_total;
+    // the first two planet chunks
+    GL_CUDA(cudaEventRecord(c->ev_use[0], c->s));  // order the side stream after the set-up
+    GL_CUDA(cudaStreamWaitEvent(c->se, c->ev_use[0], 0));
+    int rc = ensure_chunk(c, 1);
+    if (rc) return rc;
+    GL_CUDA(cudaStreamSynchronize(c->s));
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_create(glisse_ctx** out, double star_mass, const double* planets, int32_t n_planets,
+                             const double* particles, int64_t n_particles, double dt, const glisse_opts* opts) {
+    if (!out) return GLISSE_E_INVAL;
+    *out = nullptr;
+    glisse_opts o;
+    glisse_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(star_mass > 0.0) || !std::isfinite(star_mass)) return GLISSE_E_INVAL;
+    if (n_planets < 0 || n_planets > GLISSE_MAX_PLANETS) return GLISSE_E_INVAL;
+    if (n_planets > 0 && !planets) return GLISSE_E_INVAL;
+    if (n_particles < 0 || n_particles > INT32_MAX) return GLISSE_E_INVAL;
+    if (n_particles > 0 && !particles) return GLISSE_E_INVAL;
+    if (!(dt != 0.0) || !std::isfinite(dt)) return GLISSE_E_INVAL;
+    if (o.chunk_steps < 1 || o.chunk_steps > (1 << 20) || o.resync_chunks < 1) return GLISSE_E_INVAL;
+    if (o.kepler_mode != GLISSE_KEPLER_CONVERGE) return GLISSE_E_INVAL;
+    if (o.enc_mode != GLISSE_ENC_HILL && o.enc_mode != GLISSE_ENC_FIXED) return GLISSE_E_INVAL;
+    if (!(o.enc_value >= 0.0) || !std::isfinite(o.enc_value) || !std::isfinite(o.r_max)) return GLISSE_E_INVAL;
+    for (int64_t k = 0; k < 7 * (int64_t)n_planets; ++k)
+        if (!std::isfinite(planets[k])) return GLISSE_E_INVAL;
+    for (int j = 0; j < n_planets; ++j)
+        if (!(planets[7 * j] >= 0.0)) return GLISSE_E_INVAL;
+    glisse_ctx* c = new (std::nothrow) glisse_ctx();
+    if (!c) return GLISSE_E_NOMEM;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete c;
+        return GLISSE_E_CUDA;
+    }
+    c->o = o;
+    c->np = n_planets;
+    c->m0 = star_mass;
+    c->dt = dt;
+    c->C = o.chunk_steps;
+    c->n_total = n_particles;
+    c->timing = o.timing != 0;
+    int rc = setup(c, planets, particles);
+    if (rc != GLISSE_OK) {
+        ctx_free(c);
+        return rc;
+    }
+    *out = c;
+    return GLISSE_OK;
+}
+
+static int compact(glisse_ctx* c) {
+    const int nxt = c->cur ^ 1;
+    if (c->timing) GL_CUDA(cudaEventRecord(c->tc0, c->s));
+    GL_CUDA(launch_compact(c->n_live, c->d_alive, c->d_st[c->cur], c->d_id[c->cur], c->cap, c->d_st[nxt],
+                           c->d_id[nxt], c->cap, c->d_counts, c->d_nlive, c->s));
+    if (c->timing) GL_CUDA(cudaEventRecord(c->tc1, c->s));
+    GL_CUDA(cudaMemcpyAsync(c->h_nlive, c->d_nlive, sizeof(int64_t), cudaMemcpyDeviceToHost, c->s));
+    GL_CUDA(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    GL_CUDA(cudaStreamSynchronize(c->s));
+    if (c->timing) {
+        float ms = 0.f;
+        GL_CUDA(cudaEventElapsedTime(&ms, c->tc0, c->tc1));
+        c->acc.compact_ms += ms;
+        ++c->acc.compact_launches;
+    }
+    c->n_live = *c->h_nlive;
+    c->cur = nxt;
+    if (c->n_live > 0) GL_CUDA(cudaMemsetAsync(c->d_alive, 1, (size_t)c->n_live, c->s));
+    c->since_compact = 0;
+    return *c->h_status;
+}
+
+extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
+    if (!c || n_steps < 0) return GLISSE_E_INVAL;
+    if (n_steps == 0) return GLISSE_OK;
+    if (c->external && n_steps > c->ext_n - c->ext_off) return GLISSE_E_STATE;
+    if (!c->external && !c->planets_valid) return GLISSE_E_STATE;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != c->device) GL_CUDA(cudaSetDevice(c->device));
+    const int S = log_stride(c->np);
+    int64_t remaining = n_steps;
+    int rc = GLISSE_OK;
+    while (remaining > 0 && rc == GLISSE_OK) {
+        const double* log = nullptr;
+        int64_t m = 0;
+        int slot = -1;
+        if (c->external) {
+            m = std::min<int64_t>(remaining, c->C);
+            log = c->d_ext_log + (size_t)c->ext_off * S;
+        } else {
+            const int64_t j = c->step / c->C;
+            const int64_t off = c->step - j * c->C;
+            if ((rc = ensure_chunk(c, j + 1)) != GLISSE_OK) break;
+            slot = (int)(j % kRing);
+            if (c->chunk_of[slot] != j) {
+                rc = GLISSE_E_STATE;
+                break;
+            }
+            GL_CUDA(cudaStreamWaitEvent(c->s, c->ev_eph[slot], 0));
+            m = std::min<int64_t>(remaining, c->C - off);
+            log = c->d_log[slot] + (size_t)off * S;
+        }
+        if (c->n_live > 0) {
+            ChunkArgs a;
+            a.pc = nullptr;
+            a.log = log;
+            a.n = c->n_live;
+            a.ld = c->cap;
+            a.st = c->d_st[c->cur];
+            a.id = c->d_id[c->cur];
+            a.alive = c->d_alive;
+            a.step0 = c->step;
+            a.nsteps = (int32_t)m;
+            a.test_first = c->tested_first ? 0 : 1;
+            a.out_state = c->d_out_state;
+            a.out_step = c->d_out_step;
+            a.out_reason = c->d_out_reason;
+            a.steps_done = c->d_steps;
+            if (c->timing) GL_CUDA(cudaEventRecord(c->tp0, c->s));
+            GL_CUDA(launch_particle_chunk(c->np, a, c->ppc, c->s));
+            if (c->timing) {
+                GL_CUDA(cudaEventRecord(c->tp1, c->s));
+                GL_CUDA(cudaEventSynchronize(c->tp1));
+                float ms = 0.f;
+                GL_CUDA(cudaEventElapsedTime(&ms, c->tp0, c->tp1));
+                c->acc.particle_ms += ms;
+                ++c->acc.particle_launches;
+                GL_CUDA(cudaMemcpy(c->h_steps, c->d_steps, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+                c->acc.particle_steps = (int64_t)*c->h_steps;
+            }
+        }
+        if (c->timing && slot >= 0 && c->eph_pending[slot]) {
+            // the main stream has waited for this chunk's ephemeris: its events are complete
+            GL_CUDA(cudaEventSynchronize(c->te1[slot]));
+            float ms = 0.f;
+            GL_CUDA(cudaEventElapsedTime(&ms, c->te0[slot], c->te1[slot]));
+            c->acc.ephemeris_ms += ms;
+            ++c->acc.ephemeris_launches;
+            c->eph_pending[slot] = false;
+        }
+        c->tested_first = true;
+        if (slot >= 0) {
+            GL_CUDA(cudaEventRecord(c->ev_use[slot], c->s));
+            c->used[slot] = true;
+        }
+        c->step += m;
+        remaining -= m;
+        if (c->external) c->ext_off += m;
+        ++c->since_compact;
+        if (c->since_compact >= c->o.resync_chunks || remaining == 0) rc = compact(c);
+    }
+    if (rc == GLISSE_OK) rc = check_status(c);
+    if (prev != c->device) cudaSetDevice(prev);
+    return rc;
+}
+
+extern "C" int glisse_read(glisse_ctx* c, double* state, uint8_t* alive, int64_t* removal_step,
+                           int32_t* removal_reason) {
+    if (!c) return GLISSE_E_INVAL;
+    const int64_t n = c->n_total;
+    if (n == 0) return GLISSE_OK;
+    GL_CUDA(launch_export_live(c->n_live, c->d_st[c->cur], c->cap, c->d_id[c->cur], c->d_out_state, c->s));
+    if (state) GL_CUDA(cudaMemcpyAsync(state, c->d_out_state, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, c->s));
+    int64_t* steps = removal_step;
+    int64_t* tmp = nullptr;
+    if (!steps && alive) {
+        tmp = new (std::nothrow) int64_t[n];
+        if (!tmp) return GLISSE_E_NOMEM;
+        steps = tmp;
+    }
+    cudaError_t e = cudaSuccess;
+    if (steps) e = cudaMemcpyAsync(steps, c->d_out_step, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess && removal_reason)
+        e = cudaMemcpyAsync(removal_reason, c->d_out_reason, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    if (e == cudaSuccess && alive)
+        for (int64_t i = 0; i < n; ++i) alive[i] = steps[i] < 0 ? 1 : 0;
+    delete[] tmp;
+    return e == cudaSuccess ? GLISSE_OK : GLISSE_E_CUDA;
+}
+
+extern "C" int glisse_status(glisse_ctx* c, int64_t* n_live, int64_t* step, double* t) {
+    if (!c) return GLISSE_E_INVAL;
+    if (n_live) *n_live = c->n_live;
+    if (step) *step = c->step;
+    if (t) *t = (double)c->step * c->dt;
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_read_planets(glisse_ctx* c, double* planets, double* t) {
+    if (!c) return GLISSE_E_INVAL;
+    if (c->external || !c->planets_valid) return GLISSE_E_STATE;
+    if (t) *t = (double)c->step * c->dt;
+    if (c->np == 0) return GLISSE_OK;
+    if (!planets) return GLISSE_E_INVAL;
+    const int64_t j = c->step / c->C;
+    const int64_t off = c->step - j * c->C;
+    int rc = ensure_chunk(c, j);
+    if (rc) return rc;
+    const int slot = (int)(j % kRing);
+    if (c->chunk_of[slot] != j) return GLISSE_E_STATE;
+    GL_CUDA(cudaStreamSynchronize(c->se));
+    double buf[6 * GLISSE_MAX_PLANETS];
+    GL_CUDA(cudaMemcpy(buf, c->d_hist[slot] + (size_t)off * 6 * c->np, sizeof(double) * 6 * c->np,
+                       cudaMemcpyDeviceToHost));
+    for (int p = 0; p < c->np; ++p) {
+        planets[7 * p] = c->hpc.m[p];
+        for (int d = 0; d < 6; ++d) planets[7 * p + 1 + d] = buf[6 * p + d];
+    }
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_set_ephemeris(glisse_ctx* c, const double* log, int64_t n_steps) {
+    if (!c || n_steps < 1 || (!log && c->np > 0)) return GLISSE_E_INVAL;
+    const int S = log_stride(c->np);
+    GL_CUDA(cudaStreamSynchronize(c->s));
+    GL_CUDA(cudaStreamSynchronize(c->se));
+    cudaFree(c->d_ext_log);
+    c->d_ext_log = nullptr;
+    GL_ALLOC(c->d_ext_log, sizeof(double) * (size_t)(n_steps + 1) * S);
+    if (c->np > 0) {
+        double* d_pos = nullptr;
+        GL_ALLOC(d_pos, sizeof(double) * (size_t)(n_steps + 1) * 3 * c->np);
+        cudaError_t e = cudaMemcpyAsync(d_pos, log, sizeof(double) * (size_t)(n_steps + 1) * 3 * c->np,
+                                        cudaMemcpyHostToDevice, c->s);
+        if (e == cudaSuccess) e = launch_eph_external(c->d_pc, d_pos, n_steps + 1, c->d_ext_log, c->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+        cudaFree(d_pos);
+        if (e != cudaSuccess) return GLISSE_E_CUDA;
+    } else {
+        GL_CUDA(cudaMemsetAsync(c->d_ext_log, 0, sizeof(double) * (size_t)(n_steps + 1) * S, c->s));
+        GL_CUDA(cudaStreamSynchronize(c->s));
+    }
+    c->external = true;
+    c->planets_valid = false;
+    c->ext_n = n_steps;
+    c->ext_off = 0;
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_partition_device(int64_t n, int64_t ld, const uint8_t* alive, const double* src,
+                                       const int32_t* src_id, double* dst, int32_t* dst_id, int64_t* n_out,
+                                       void* stream) {
+    if (n < 0 || ld < n || !n_out) return GLISSE_E_INVAL;
+    if (n > 0 && (!alive || !src || !src_id || !dst || !dst_id)) return GLISSE_E_INVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t* counts = nullptr;
+    int rc = alloc_dev(reinterpret_cast<void**>(&counts), sizeof(int64_t) * (size_t)compact_scratch_entries(n));
+    if (rc) return rc;
+    cudaError_t e = launch_compact(n, alive, src, src_id, ld, dst, dst_id, ld, counts, n_out, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(counts);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GLISSE_E_CUDA;
+    }
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_timings(glisse_ctx* c, glisse_timing* out, int32_t reset) {
+    if (!c) return GLISSE_E_INVAL;
+    if (!c->timing) return GLISSE_E_STATE;
+    if (out) *out = c->acc;
+    if (reset) {
+        std::memset(&c->acc, 0, sizeof(c->acc));
+        GL_CUDA(cudaMemsetAsync(c->d_steps, 0, sizeof(unsigned long long), c->s));
+        GL_CUDA(cudaStreamSynchronize(c->s));
+    }
+    return GLISSE_OK;
+}

@@ -1,0 +1,62 @@
+// glisse_internal.h -- types shared by the CUDA translation units of the library.
+#pragma once
+#include <cstdint>
+
+#include "../../include/glisse.h"
+
+namespace glisse {
+
+constexpr int kMaxPlanets = GLISSE_MAX_PLANETS;
+
+// One record per body per step in the planet log: heliocentric x, y, z and a pad.
+// A log step holds N_p planet records followed by the record of the common
+// term h0 = -sum_j G m_j r_j / |r_j|^3 (section 2.2).  32-byte records let a
+// warp fetch a whole record with two 16-byte broadcast loads.
+constexpr int kRec = 4;
+__host__ __device__ constexpr int log_stride(int np) { return kRec * (np + 1); }
+
+// Planet system constants (written once by the set-up kernel, read by all kernels).
+struct PlanetConsts {
+    int np;
+    double m0;
+    double G;
+    double mu0;                      // G m0: the particles' Kepler parameter
+    double m[kMaxPlanets];
+    double eta[kMaxPlanets + 1];     // eta[0] = m0, eta[i] = m0 + m_1 + ... + m_i
+    double mu_jac[kMaxPlanets];      // G m0 eta_i / eta_{i-1}: Jacobi Kepler parameter of planet i
+    double gm[kMaxPlanets];          // G m_j
+    double rcrit[kMaxPlanets];       // encounter radius of planet j (0 disables)
+};
+
+// Particle-kernel constants derived from the planet constants and dt.
+struct ParticleConsts {
+    double mu;                        // G m0
+    double dt;
+    double half_dt;
+    double tgm_full[kMaxPlanets];     // dt G m_j
+    double tgm_half[kMaxPlanets];     // dt/2 G m_j
+    double rc2[kMaxPlanets];          // R_crit,j^2 (0: no test)
+    double rmax2;                     // r_max^2 (0: no test)
+    double rmax;                      // r_max (0: no test)
+};
+
+// Arguments of one particle-chunk launch.
+struct ChunkArgs {
+    const ParticleConsts* pc;
+    const double* log;    // log of this segment: step 0 = the particles' current time
+    int64_t n;            // live slots
+    int64_t ld;           // leading dimension of the state planes
+    double* st;           // [6][ld] x, y, z, vx, vy, vz planes
+    const int32_t* id;    // [n]
+    uint8_t* alive;       // [n] out: 1 = still live after the segment
+    int64_t step0;        // global index of the segment's first step
+    int32_t nsteps;       // steps in the segment (>= 1)
+    int32_t test_first;   // apply the removal test at the segment's step 0 first
+    // per-id outputs for particles removed during the segment
+    double* out_state;    // [N][6]
+    int64_t* out_step;    // [N]
+    int32_t* out_reason;  // [N]
+    unsigned long long* steps_done;  // optional: += steps advanced by live particles
+};
+
+}  // namespace glisse

@@ -1,0 +1,281 @@
+// kepler.cuh -- Kepler drift of one body for time dt about a central mass (FP64).
+//
+// Section 2.2 of the paper advances each particle along its two-body orbit
+// by solving Kepler's equation for the change of mean anomaly.  Here the
+// drift is written in universal variables (Stumpff / Danby G-functions),
+// which covers bound, parabolic and hyperbolic orbits with one formula:
+//
+//   G_k(s) = s^k c_k(beta s^2),  beta = 2 mu / r0 - v0^2,  c_k(z) = sum_n (-z)^n / (2n+k)!
+//   time equation  T(s) = r0 G1 + u G2 + mu G3 = dt,   u = r0 . v0
+//   T'(s) = r(s) = r0 G0 + u G1 + mu G2,   T''(s) = u G0 + (mu - beta r0) G1
+//   f - 1 = -mu G2 / r0,  g = dt - mu G3,  fdot = -mu G1 / (r r0),  gdot - 1 = -mu G2 / r
+//
+// drift_fast is the hot path.  It solves T(s) = dt in FP32 first (the FP32
+// pipe is nearly free next to the FP64 pipe), takes one FP64 Halley step from
+// that start (cubic convergence: a 1e-7 start lands below 1e-20), evaluates
+// c2, c3 with a polynomial whose degree the warp picks from its largest |z|,
+// and moves the G-functions to the corrected s with their addition formulas
+// instead of re-evaluating them.  Lanes outside its domain report false and
+// the caller runs drift_general for them only (the rest of the warp idles).
+#pragma once
+#include "device_math.cuh"
+
+namespace glisse {
+
+constexpr unsigned kFullMask = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------------------
+// Stumpff c2, c3 as truncated Taylor polynomials in z (Horner form).
+// Coefficients 1/(2n+2)! and 1/(2n+3)! with alternating signs.
+// ---------------------------------------------------------------------------
+template <int DEG>
+__device__ __forceinline__ void c23_poly(double z, double& c2, double& c3) {
+    constexpr double a[8] = {1.0 / 2.0, -1.0 / 24.0, 1.0 / 720.0, -1.0 / 40320.0, 1.0 / 3628800.0,
+                             -1.0 / 479001600.0, 1.0 / 87178291200.0, -1.0 / 20922789888000.0};
+    constexpr double b[8] = {1.0 / 6.0, -1.0 / 120.0, 1.0 / 5040.0, -1.0 / 362880.0, 1.0 / 39916800.0,
+                             -1.0 / 6227020800.0, 1.0 / 1307674368000.0, -1.0 / 355687428096000.0};
+    double p = a[DEG], q = b[DEG];
+#pragma unroll
+    for (int n = DEG - 1; n >= 0; --n) {
+        p = fma(p, z, a[n]);
+        q = fma(q, z, b[n]);
+    }
+    c2 = p;
+    c3 = q;
+}
+
+// c0..c3 for any z: quarter z until |z| <= 0.1, series there, then the
+// duplication formulas c0(4z) = 2 c0^2 - 1, c1(4z) = c0 c1, c2(4z) = c1^2 / 2,
+// c3(4z) = (c3 + c1 c2) / 4.
+__device__ inline void stumpff_any(double z, double& c0, double& c1, double& c2, double& c3) {
+    int k = 0;
+    while (fabs(z) > 0.1 && k < 80) {
+        z *= 0.25;
+        ++k;
+    }
+    c23_poly<7>(z, c2, c3);
+    c0 = fma(-z, c2, 1.0);
+    c1 = fma(-z, c3, 1.0);
+    for (; k > 0; --k) {
+        const double n3 = 0.25 * fma(c1, c2, c3);
+        const double n2 = 0.5 * c1 * c1;
+        const double n1 = c0 * c1;
+        const double n0 = fma(2.0 * c0, c0, -1.0);
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// General solver: any orbit, any dt.  Bound orbits first drop whole periods.
+// Newton iteration on T(s) - dt with a bisection safeguard (bisect whenever
+// Newton would leave the bracket or fails to halve the previous step).
+// Returns false if it does not converge within the iteration budget.
+// ---------------------------------------------------------------------------
+__device__ inline bool drift_general(double mu, double dt, double& x, double& y, double& z, double& vx, double& vy,
+                                     double& vz) {
+    const double r0 = sqrt(x * x + y * y + z * z);
+    const double v2 = vx * vx + vy * vy + vz * vz;
+    const double u = x * vx + y * vy + z * vz;
+    if (!(r0 > 0.0) || !isfinite(r0) || !isfinite(v2)) return false;
+    const double beta = 2.0 * mu / r0 - v2;
+    double tau = dt;
+    if (beta > 0.0) {
+        const double n = beta * sqrt(beta) / mu;  // mean motion sqrt(mu alpha^3), alpha = beta / mu
+        const double period = 6.283185307179586476925286766559 / n;
+        tau = dt - period * rint(dt / period);
+    }
+    if (tau == 0.0) return true;
+    const double sgn = tau > 0.0 ? 1.0 : -1.0;
+    double c0, c1, c2, c3;
+    // bracket: T(0) = 0 and T increases with s
+    double lo = 0.0, hi = tau / r0;
+    int grow = 0;
+    for (;;) {
+        stumpff_any(beta * hi * hi, c0, c1, c2, c3);
+        const double T = r0 * hi * c1 + u * hi * hi * c2 + mu * hi * hi * hi * c3;
+        if ((T - tau) * sgn >= 0.0) break;
+        lo = hi;
+        hi *= 2.0;
+        if (++grow > 200) return false;
+    }
+    if (sgn < 0.0) {
+        const double t = lo;
+        lo = hi;
+        hi = t;
+    }
+    double s = tau / r0;
+    if (!(s > lo && s < hi)) s = 0.5 * (lo + hi);
+    double dsold = hi - lo;
+    bool conv = false;
+    for (int it = 0; it < 300; ++it) {
+        stumpff_any(beta * s * s, c0, c1, c2, c3);
+        const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
+        const double F = r0 * G1 + u * G2 + mu * G3 - tau;
+        const double Fp = r0 * c0 + u * G1 + mu * G2;
+        if (F < 0.0) {
+            if (s > lo) lo = s;
+        } else {
+            if (s < hi) hi = s;
+        }
+        double ds = -F / Fp;
+        // a step below the tolerance is converged; test it before the safeguard,
+        // since s + ds can round onto a bracket end and look like an escape
+        if (fabs(ds) <= 1e-15 * fabs(s)) {
+            s += ds;
+            conv = true;
+            break;
+        }
+        double sn = s + ds;
+        if (!(sn > lo && sn < hi) || fabs(ds) > 0.5 * fabs(dsold)) {
+            sn = 0.5 * (lo + hi);
+            ds = sn - s;
+        }
+        dsold = ds;
+        s = sn;
+        if ((hi - lo) <= 1e-15 * fabs(s)) {
+            conv = true;
+            break;
+        }
+    }
+    if (!conv) return false;
+    stumpff_any(beta * s * s, c0, c1, c2, c3);
+    const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
+    const double r = r0 * c0 + u * G1 + mu * G2;
+    const double fm1 = -mu * G2 / r0;
+    const double g = tau - mu * G3;
+    const double fd = -mu * G1 / (r * r0);
+    const double gdm1 = -mu * G2 / r;
+    const double x0 = x, y0 = y, z0 = z;
+    x = fma(fm1, x0, fma(g, vx, x0));
+    y = fma(fm1, y0, fma(g, vy, y0));
+    z = fma(fm1, z0, fma(g, vz, z0));
+    vx = fma(fd, x0, fma(gdm1, vx, vx));
+    vy = fma(fd, y0, fma(gdm1, vy, vy));
+    vz = fma(fd, z0, fma(gdm1, vz, vz));
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Fast path.  Must be called by all 32 lanes of a warp together.
+//   part       : this lane's result is wanted (inactive lanes still execute)
+//   r0, rinv0  : |r| and 1/|r| of the current position; on success they are
+//                replaced by the values at the drifted position (r(s) is known
+//                from the solve, so the next step needs no square root)
+// On success (return true) the state is advanced; on false nothing changes.
+// ---------------------------------------------------------------------------
+// polynomial tiers: largest |z| in the warp picks the degree of c2, c3
+constexpr float kZ3 = 0.001953125f;  // 2^-9: degree 3 reaches 2^-56
+constexpr float kZ5 = 0.03125f;      // 2^-5: degree 5
+constexpr float kZ7 = 0.1f;          // degree 7 (fast-path limit)
+
+template <int DEG>
+__device__ __forceinline__ void fast_tail(double mu, double dt, double beta, double& r0, double& rinv0, double u,
+                                          double s0, float uf, float muf, float bf, float r0f, double& x, double& y,
+                                          double& z, double& vx, double& vy, double& vz, bool& ok) {
+    const double s2 = s0 * s0;
+    const double zz = beta * s2;
+    double c2, c3;
+    c23_poly<DEG>(zz, c2, c3);
+    const double G2 = s2 * c2;
+    const double G3 = (s2 * s0) * c3;
+    const double G1 = fma(-beta, G3, s0);
+    const double G0 = fma(-beta, G2, 1.0);
+    const double F = fma(r0, G1, fma(u, G2, fma(mu, G3, -dt)));
+    const double r = fma(r0, G0, fma(u, G1, mu * G2));
+    const double rinv = rcp_40(r);
+    const double dN = -F * rinv;
+    // Halley: dH = dN / (1 + dN T''/(2 T')) ~ dN (1 - k); k ~ 1e-8 needs only FP32
+    const float G0f = d2f_bits(G0), G1f = d2f_bits(G1);
+    const float Fpp = fmaf(uf, G0f, (muf - bf * r0f) * G1f);
+    const float dNf = d2f_bits(dN);
+    const float kf = 0.5f * dNf * Fpp * d2f_bits(rinv);
+    const double dH = fma(dN, -f2d_bits(kf), dN);
+    const double s1 = s0 + dH;
+    // G2(s+d) = G2 + d (G1 + d/2 G0),  G3(s+d) = G3 + d (G2 + d/2 G1)  (third order ~ d^3: negligible)
+    const float hf = 0.5f * d2f_bits(dH);
+    const double t2 = G1 + f2d_bits(hf * G0f);
+    const double t3 = G2 + f2d_bits(hf * G1f);
+    const double G2n = fma(dH, t2, G2);
+    const double G3n = fma(dH, t3, G3);
+    const double G1n = fma(-beta, G3n, s1);
+    // r(s+d) = r + T'' d + O(d^2): the correction is ~1e-9 r, so FP32 carries it
+    const double r1 = r + f2d_bits(Fpp * d2f_bits(dH));
+    const double rinv1 = rcp_refine(r1, rinv);
+    // domain checks (integer tests): r > 0 and the correction small against s
+    const bool good = (__double2hiint(r) > 0) && (exp_bits(dH) + 14 <= exp_bits(s0) || dH == 0.0);
+    ok = ok && good;
+    const double mur0 = mu * rinv0;
+    const double fm1 = -mur0 * G2n;
+    const double g = fma(-mu, G3n, dt);
+    const double fd = -(mur0 * rinv1) * G1n;
+    const double gdm1 = -(mu * rinv1) * G2n;
+    if (ok) {
+        const double x0 = x, y0 = y, z0 = z;
+        x = fma(fm1, x0, fma(g, vx, x0));
+        y = fma(fm1, y0, fma(g, vy, y0));
+        z = fma(fm1, z0, fma(g, vz, z0));
+        vx = fma(fd, x0, fma(gdm1, vx, vx));
+        vy = fma(fd, y0, fma(gdm1, vy, vy));
+        vz = fma(fd, z0, fma(gdm1, vz, vz));
+        r0 = r1;
+        rinv0 = rinv1;
+    }
+}
+
+// Returns true when the lane's drift was done here; false when the caller must
+// use drift_general (or when part == false).
+__device__ __forceinline__ bool drift_fast(double mu, float muf, double dt, float dtf, bool part, double& r0,
+                                           double& rinv0, double& x, double& y, double& z, double& vx, double& vy,
+                                           double& vz) {
+    const double u = fma(x, vx, fma(y, vy, z * vz));
+    const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
+    const double beta = fma(2.0 * mu, rinv0, -v2);
+
+    // ---- FP32 solve of T(s) = dt ------------------------------------------------
+    const float r0f = d2f_bits(r0), uf = d2f_bits(u), bf = d2f_bits(beta);
+    // domain: r0 and |v|^2 well inside the float range (integer exponent tests)
+    const int er = exp_bits(r0), ev = exp_bits(v2);
+    bool ok = part && er > 1023 - 60 && er < 1023 + 60 && ev < 1023 + 120 && ev > 1023 - 200;
+    float s = __fdividef(dtf, r0f);
+    float zf = 0.f, dsf = 0.f;
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+        zf = bf * s * s;
+        const float c2 = fmaf(zf, fmaf(zf, fmaf(zf, -1.0f / 40320.0f, 1.0f / 720.0f), -1.0f / 24.0f), 0.5f);
+        const float c3 = fmaf(zf, fmaf(zf, fmaf(zf, -1.0f / 362880.0f, 1.0f / 5040.0f), -1.0f / 120.0f), 1.0f / 6.0f);
+        const float s2f = s * s;
+        const float G1 = s * fmaf(-zf, c3, 1.0f);
+        const float G2 = s2f * c2;
+        const float G3 = s2f * s * c3;
+        const float F = fmaf(r0f, G1, fmaf(uf, G2, fmaf(muf, G3, -dtf)));
+        const float Fp = fmaf(r0f, fmaf(-zf, c2, 1.0f), fmaf(uf, G1, muf * G2));
+        dsf = -__fdividef(F, Fp);
+        s += dsf;
+    }
+    zf = bf * s * s;
+    ok = ok && (fabsf(zf) <= kZ7) && (fabsf(dsf) <= 1e-5f * fabsf(s) + 1e-30f) && isfinite(s);
+    // ---- warp-uniform polynomial degree ------------------------------------------
+    const unsigned zb = ok ? __float_as_uint(fabsf(zf)) : 0u;
+    const unsigned zmax = __reduce_max_sync(kFullMask, zb);
+    const double s0 = f2d_bits(s);
+    if (zmax <= __float_as_uint(kZ3)) {
+        fast_tail<3>(mu, dt, beta, r0, rinv0, u, s0, uf, muf, bf, r0f, x, y, z, vx, vy, vz, ok);
+    } else if (zmax <= __float_as_uint(kZ5)) {
+        fast_tail<5>(mu, dt, beta, r0, rinv0, u, s0, uf, muf, bf, r0f, x, y, z, vx, vy, vz, ok);
+    } else {
+        fast_tail<7>(mu, dt, beta, r0, rinv0, u, s0, uf, muf, bf, r0f, x, y, z, vx, vy, vz, ok);
+    }
+    return ok;
+}
+
+// |r| and 1/|r| of a position (used where no previous drift provides them).
+__device__ __forceinline__ void radius_of(double x, double y, double z, double& r, double& rinv) {
+    const double r2 = fma(x, x, fma(y, y, z * z));
+    rinv = rsqrt_full(r2);
+    r = r2 * rinv;
+}
+
+}  // namespace glisse

@@ -1,0 +1,108 @@
+"""The C-ABI library builds, loads and exports every declared entry point (no GPU needed).
+
+Only calls that do not reach the GPU are made here: option defaults, status
+strings and argument validation, which happens before any CUDA call.
+"""
+import ctypes as C
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "glisse.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(glisse_\w+)\s*\(", hdr)))
+
+
+@pytest.fixture(scope="module")
+def G():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    import paper_2011_03484_gb300 as G
+
+    G._build.build()
+    return G
+
+
+def test_library_exports_every_declared_symbol(G):
+    L = C.CDLL(G.library_path())
+    names = _declared()
+    assert names, "no declarations found"
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert sorted(G.EXPORTED) == names
+
+
+def test_opts_defaults(G):
+    o = G.glisse_opts_default()
+    assert o.chunk_steps == 1024 and o.resync_chunks == 1
+    assert o.kepler_mode == G.GLISSE_KEPLER_CONVERGE and o.kepler_iters == 5
+    assert o.enc_mode == G.GLISSE_ENC_HILL and o.enc_value == 1.0 and o.r_max == 1000.0
+
+
+def test_strerror_names_every_code(G):
+    for code in range(0, -7, -1):
+        s = G.strerror(code)
+        assert s and "unknown" not in s
+    assert "unknown" in G.strerror(-99)
+
+
+def test_argument_errors_before_any_cuda_call(G):
+    import glisse_inputs as gi
+
+    w = gi.make("tiny", n=4)
+    bad = [
+        dict(star_mass=0.0),
+        dict(star_mass=float("nan")),
+        dict(dt=0.0),
+        dict(dt=float("inf")),
+        dict(planets=np.zeros((9, 7))),  # more than GLISSE_MAX_PLANETS
+        dict(planets=np.vstack([w["planets"][:1] * [[-1, 1, 1, 1, 1, 1, 1]]])),  # negative mass
+        dict(planets=np.where(np.arange(7) == 2, np.nan, w["planets"])),
+    ]
+    for kw in bad:
+        args = dict(star_mass=1.0, planets=w["planets"], particles=w["particles"], dt=0.5)
+        args.update(kw)
+        with pytest.raises(G.GlisseError) as ei:
+            G.glisse_create(**args)
+        assert ei.value.code == G.GLISSE_E_INVAL, kw
+    o = G.glisse_opts_default()
+    o.chunk_steps = 0
+    with pytest.raises(G.GlisseError) as ei:
+        G.glisse_create(1.0, w["planets"], w["particles"], 0.5, o)
+    assert ei.value.code == G.GLISSE_E_INVAL
+    L = G.load()
+    assert L.glisse_advance(None, 1) == G.GLISSE_E_INVAL
+    assert L.glisse_read(None, None, None, None, None) == G.GLISSE_E_INVAL
+    assert L.glisse_partition_device(-1, 0, None, None, None, None, None, None, None) == G.GLISSE_E_INVAL
+    assert L.glisse_fp64_peak(0, None, None) == G.GLISSE_E_INVAL
+    L.glisse_destroy(None)
+
+
+def test_no_cpu_fallback_without_a_device(G):
+    """On a machine without a usable GPU a valid create fails with GLISSE_E_CUDA instead of computing."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import glisse_inputs as gi
+
+    w = gi.make("tiny", n=4)
+    with pytest.raises(G.GlisseError) as ei:
+        G.glisse_create(1.0, w["planets"], w["particles"], 0.5)
+    assert ei.value.code == G.GLISSE_E_CUDA
+
+
+def test_package_does_not_reference_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2011_03484_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in text.lower(), f

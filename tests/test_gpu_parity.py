@@ -1,0 +1,332 @@
+"""CUDA path vs oracle, through the C ABI, on seeded synthetic inputs (GPU).
+
+Sizes run from the tiny 1024-particle workload (whole-set comparison over
+10^4 steps) to the 131072- and 1048576-particle workloads in the launch
+configuration the benchmark times (chunk 1024, compaction every chunk),
+compared on random id subsets the oracle integrates one by one.  Edge cases:
+empty and ragged particle counts, no planets, one planet, orbits that leave
+the fast Kepler path, removal at t_0, escape, external ephemeris, chunk and
+segment boundaries.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import glisse_inputs as gi
+import parity
+from parity import assert_parity, compare
+
+pytestmark = pytest.mark.gpu
+
+G_ = 4.0 * math.pi * math.pi
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2011_03484_gb300 as G
+
+    G._build.build()
+    G.load()
+    return G
+
+
+def run_gpu(G, w, n_steps, splits=None, **opt):
+    sim = G.Simulation(w["star_mass"], w["planets"], w["particles"], w["dt"], **opt)
+    for m in (splits or [n_steps]):
+        sim.advance(m)
+    out = sim.read()
+    pl, t = sim.planets() if sim.n_planets else (None, None)
+    nl, step, _ = sim.status()
+    sim.close()
+    out["planets"] = pl
+    out["n_live"] = nl
+    out["step"] = step
+    return out
+
+
+def run_orc(orc, w, n_steps, ids=None, **kw):
+    pa = w["particles"] if ids is None else w["particles"][ids]
+    return orc.run(w["star_mass"], w["planets"], pa, w["dt"], n_steps, **kw)
+
+
+def run_orc_sens(orc, w, n_steps, ids=None, **kw):
+    """Oracle run plus its sensitivity to one-ulp input changes (see parity.py)."""
+    pa = w["particles"] if ids is None else w["particles"][ids]
+    base = orc.run(w["star_mass"], w["planets"], pa, w["dt"], n_steps, **kw)
+    runs = [orc.run(w["star_mass"], w["planets"], p, w["dt"], n_steps, **kw) for p in parity.perturbed_inputs(pa)]
+    sens, unstable = parity.sensitivity(base, runs)
+    return base, sens, unstable
+
+
+# ---------------------------------------------------------------------------
+# planets
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n_steps", [0, 1, 7, 1024, 1025, 10_000])
+def test_planet_ephemeris_parity(G, orc, n_steps):
+    """GPU Wisdom-Holman planets equal the oracle's within both sides' FP64 phase noise."""
+    w = gi.make("tiny", n=8)
+    g = run_gpu(G, w, n_steps)
+    pl, _, _ = orc.planet_wh(w["star_mass"], w["planets"], w["dt"], n_steps, want_log=False)
+    e = parity.rel_err(g["planets"][:, 1:], pl[:, 1:]).max()
+    dM = 2 * math.pi * w["dt"] / 5.2**1.5
+    tol = max(2 * 10 * 2.0**-53 * dM * max(n_steps, 1) ** 1.5, 1e-14)
+    assert e < tol, (e, tol)
+    np.testing.assert_array_equal(g["planets"][:, 0], w["planets"][:, 0])
+
+
+def test_planet_log_chunking_is_exact(G):
+    """The planet sequence does not depend on the chunk length (bitwise)."""
+    w = gi.make("tiny", n=4)
+    outs = [run_gpu(G, w, 777, chunk_steps=c)["planets"] for c in (1, 64, 1024)]
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
+
+
+# ---------------------------------------------------------------------------
+# the tiny workload, whole set, 10^4 steps
+# ---------------------------------------------------------------------------
+def test_tiny_workload_parity(G, orc):
+    w = gi.make("tiny")
+    n = 10_000
+    g = run_gpu(G, w, n)
+    o, sens, unstable = run_orc_sens(orc, w, n)
+    rep = compare(g, o, n, sens, unstable)
+    print(rep)
+    assert_parity(rep)
+    assert rep["removed"] > 0  # the workload exercises removal
+    assert rep["regular"] > 0.2 * rep["n"]
+    # without the sensitivity reruns: never within 5 R_crit -> 1e-10
+    rep5 = compare(g, o, n)
+    assert rep5["regular_over_tol"] == 0, rep5
+
+
+@pytest.mark.parametrize("n_steps", [1, 2, 100, 1500])
+def test_tiny_workload_short_runs(G, orc, n_steps):
+    w = gi.make("tiny", n=257)
+    rep = compare(run_gpu(G, w, n_steps), run_orc(orc, w, n_steps), n_steps)
+    assert_parity(rep)
+
+
+# ---------------------------------------------------------------------------
+# sizes and edge cases
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 127, 129, 1025, 2049])
+def test_ragged_particle_counts(G, orc, n):
+    w = gi.make("tiny", n=n) if n <= 1024 else gi.make("longrun", n=n)
+    rep = compare(run_gpu(G, w, 300), run_orc(orc, w, 300), 300)
+    assert_parity(rep)
+    assert rep["n"] == n
+
+
+def test_zero_particles(G):
+    w = gi.make("tiny", n=0)
+    g = run_gpu(G, w, 50)
+    assert g["state"].shape == (0, 6)
+    assert g["n_live"] == 0 and g["step"] == 50
+
+
+@pytest.mark.parametrize("np_", [0, 1, 2])
+def test_fewer_planets(G, orc, np_):
+    w = gi.make("tiny", n=300)
+    w = dict(w, planets=w["planets"][:np_])
+    o, sens, unstable = run_orc_sens(orc, w, 2000)
+    rep = compare(run_gpu(G, w, 2000), o, 2000, sens, unstable)
+    assert_parity(rep)
+
+
+def _orbit_states(mu, specs):
+    out = []
+    for a, e, inc, node, peri, M in specs:
+        out.append(gi.elements_to_cartesian(mu, a, e, inc, node, peri, M))
+    return np.array(out)
+
+
+def test_kepler_drift_all_orbit_types(G, orc):
+    """No planets: the GPU drift (fast path and general path) equals the pinned oracle drift."""
+    mu = G_
+    rng = np.random.default_rng(3)
+    k = 400
+    a = np.concatenate([rng.uniform(20, 60, k // 2), rng.uniform(0.3, 5.0, k // 4), rng.uniform(5, 20, k // 4)])
+    e = np.concatenate([rng.uniform(0, 0.4, k // 2), rng.uniform(0, 0.95, k // 2)])
+    ang = rng.uniform(0, 2 * np.pi, (4, k))
+    st = gi.elements_to_cartesian(mu, a, e, ang[0] * 0.2, ang[1], ang[2], ang[3])
+    # hyperbolic and near-parabolic states: speed above escape
+    hyp = st[:40].copy()
+    r = np.linalg.norm(hyp[:, :3], axis=1)
+    vesc = np.sqrt(2 * mu / r)
+    f = np.linspace(1.0001, 2.0, 40)
+    hyp[:, 3:] *= (f * vesc / np.linalg.norm(hyp[:, 3:], axis=1))[:, None]
+    st = np.vstack([st, hyp])
+    w = {"star_mass": 1.0, "planets": np.zeros((0, 7)), "particles": st, "dt": 0.5}
+    for n in (1, 200):
+        g = run_gpu(G, w, n, r_max=0.0)
+        o, sens, unstable = run_orc_sens(orc, w, n, r_max=0.0)
+        assert g["alive"].all() and (o["removal_step"] < 0).all()
+        err = parity.rel_err(g["state"], o["state"])
+        # orbits that cover many radians per step are ill-conditioned in any FP64
+        # implementation: compare with the oracle's own one-ulp sensitivity
+        bound = np.maximum(1e-13 * n**1.5, parity.SENS_FACTOR * sens)
+        bad = err > bound
+        assert not bad.any(), (n, err[bad][:5], bound[bad][:5], np.where(bad)[0][:5])
+
+
+def test_removal_at_t0_and_escape(G, orc):
+    w = gi.make("tiny", n=64)
+    pl = w["planets"]
+    rc = orc.rcrit(1.0, pl)
+    pa = w["particles"].copy()
+    pa[0, :3] = pl[1, 1:4] + [0.5 * rc[1], 0, 0]
+    pa[0, 3:] = pl[1, 4:7]
+    pa[1, :3] = [1200.0, 0.0, 0.0]  # beyond r_max at t_0
+    pa[2] = [300.0, 0.0, 0.0, 0.0, 2.0, 0.0]  # unbound, crosses r_max later
+    w = dict(w, particles=pa)
+    g = run_gpu(G, w, 3000)
+    o = run_orc(orc, w, 3000)
+    assert g["removal_step"][0] == 0 and g["removal_reason"][0] == 2
+    assert g["removal_step"][1] == 0 and g["removal_reason"][1] == -1
+    assert g["removal_reason"][2] == -1 and g["removal_step"][2] > 0
+    np.testing.assert_array_equal(g["state"][:2], pa[:2])
+    assert_parity(compare(g, o, 3000))
+
+
+def test_fixed_distance_criterion(G, orc):
+    w = gi.make("tiny", n=512)
+    g = run_gpu(G, w, 3000, enc_mode=G.GLISSE_ENC_FIXED, enc_value=1.5)
+    o = run_orc(orc, w, 3000, enc_mode=1, k_hill=1.5)
+    rep = compare(g, o, 3000)
+    assert_parity(rep)
+    assert rep["removed"] > 0
+
+
+# ---------------------------------------------------------------------------
+# segment / chunk / compaction boundaries
+# ---------------------------------------------------------------------------
+def test_split_invariance(G):
+    """advance(a) + advance(b) equals advance(a + b): removal steps exactly; live states to
+    the parity tolerance (a split replaces one merged kick by two half kicks, a
+    rounding-level change that the later steps carry like any other)."""
+    w = gi.make("tiny", n=1024)
+    n = 2500
+    ref = run_gpu(G, w, n)
+    for splits, opt in [([1000, 1500], {}), ([1, 1, 2498], {}), ([700, 700, 1100], {"chunk_steps": 300}),
+                        ([n], {"chunk_steps": 128, "resync_chunks": 3})]:
+        g = run_gpu(G, w, n, splits=splits, **opt)
+        np.testing.assert_array_equal(g["removal_step"], ref["removal_step"])
+        np.testing.assert_array_equal(g["removal_reason"], ref["removal_reason"])
+        alive = g["alive"]
+        e = parity.rel_err(g["state"][alive], ref["state"][alive])
+        assert np.median(e) < 1e-12, (splits, opt, np.median(e))
+        assert e.max() < 1e3 * parity.state_tol(n), (splits, opt, e.max())
+
+
+# ---------------------------------------------------------------------------
+# external ephemeris (circular restricted three-body problem)
+# ---------------------------------------------------------------------------
+def test_external_ephemeris_cr3bp(G, orc):
+    import pins
+
+    m1, a1, dt, n = 1e-3, 5.2, 0.5, 10_000
+    t = np.arange(n + 1) * dt
+    r1, v1 = pins.circular_planet(1.0, m1, a1, t)
+    k = 64
+    rng = np.random.default_rng(9)
+    st0 = gi.elements_to_cartesian(G_, rng.uniform(7.5, 10, k), rng.uniform(0, 0.03, k), np.zeros(k),
+                                   np.zeros(k), rng.uniform(0, 6, k), rng.uniform(0, 6, k))
+    planet0 = np.concatenate([[m1], r1[0], v1[0]])[None, :]
+    sim = G.Simulation(1.0, planet0, st0, dt, r_max=0.0, enc_value=0.0)
+    sim.set_ephemeris(r1[:, None, :])
+    sim.advance(n)
+    g = sim.read()
+    with pytest.raises(G.GlisseError) as ei:
+        sim.advance(1)
+    assert ei.value.code == G.GLISSE_E_STATE
+    with pytest.raises(G.GlisseError):
+        sim.planets()
+    sim.close()
+    def orc_run(p):
+        run = orc.ParticleRun(1.0, np.array([m1]), p, np.zeros(1), 0.0)
+        run.advance(r1[:, None, :], dt)
+        return {"state": run.state, "removal_step": run.removal_step}
+
+    base = orc_run(st0)
+    sens, _ = parity.sensitivity(base, [orc_run(p) for p in parity.perturbed_inputs(st0)])
+    e = parity.rel_err(g["state"], base["state"])
+    bound = np.maximum(parity.state_tol(n), parity.SENS_FACTOR * sens)
+    assert (e <= bound).all(), (e.max(), np.where(e > bound)[0])
+    cj0 = pins.jacobi_constant(1.0, m1, a1, 0.0, r1[0], v1[0], st0)
+    cj1 = pins.jacobi_constant(1.0, m1, a1, t[-1], r1[-1], v1[-1], g["state"])
+    assert np.abs((cj1 - cj0) / cj0).max() < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads in the benchmark's launch configuration, sampled
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,n_steps,k", [("longrun", 10_000, 2048), ("belt", 4096, 1024)])
+def test_full_size_sampled_parity(G, orc, name, n_steps, k):
+    w = gi.make(name)
+    g = run_gpu(G, w, n_steps)  # chunk 1024, compaction every chunk (defaults)
+    ids = gi.subset_ids(name, k)
+    o, sens, unstable = run_orc_sens(orc, w, n_steps, ids=ids)
+    sub = {key: g[key][ids] for key in ("state", "alive", "removal_step", "removal_reason")}
+    rep = compare(sub, o, n_steps, sens, unstable)
+    print(name, rep)
+    assert_parity(rep)
+    # every particle the GPU reports is consistent: removed ones have a reason and a step
+    assert np.all((g["removal_step"] >= 0) == ~g["alive"])
+    assert np.all((g["removal_reason"] != 0) == ~g["alive"])
+    assert g["n_live"] == int(g["alive"].sum())
+
+
+# ---------------------------------------------------------------------------
+# device-level partition, peak probe, error paths
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [0, 1, 2047, 2048, 2049, 100_000])
+def test_partition_device_stable(G, n):
+    import torch
+
+    gen = torch.Generator().manual_seed(n)
+    ld = n + 5
+    src = torch.randn(6, ld, dtype=torch.float64, generator=gen)
+    ids = torch.randperm(max(n, 1), generator=gen)[:n].to(torch.int32)
+    alive = (torch.rand(max(n, 1), generator=gen) < 0.7).to(torch.uint8)[:n]
+    d_src, d_ids, d_alive = src.cuda(), ids.cuda(), alive.cuda()
+    d_dst = torch.full((6, ld), float("nan"), dtype=torch.float64, device="cuda")
+    d_did = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
+    d_n = torch.zeros(1, dtype=torch.int64, device="cuda")
+    G.glisse_partition_device(n, ld, d_alive.data_ptr() if n else None, d_src.data_ptr(),
+                              d_ids.data_ptr() if n else None, d_dst.data_ptr(), d_did.data_ptr(), d_n.data_ptr())
+    keep = alive.bool().numpy()
+    m = int(keep.sum())
+    assert int(d_n.item()) == m
+    np.testing.assert_array_equal(d_dst.cpu().numpy()[:, :m], src.numpy()[:, :n][:, keep])
+    np.testing.assert_array_equal(d_did.cpu().numpy()[:m], ids.numpy()[keep])
+
+
+def test_fp64_peak_probe(G):
+    rate, mhz = G.glisse_fp64_peak(4000)
+    assert 1e11 < rate < 4e12
+    assert 500 < mhz < 3000
+
+
+def test_device_side_argument_errors(G):
+    w = gi.make("tiny", n=4)
+    swapped = w["planets"][[1, 0, 2, 3]]
+    with pytest.raises(G.GlisseError) as ei:
+        G.glisse_create(1.0, swapped, w["particles"], 0.5)
+    assert ei.value.code == G.GLISSE_E_INVAL
+    unbound = w["planets"].copy()
+    unbound[0, 4:7] *= 3.0
+    with pytest.raises(G.GlisseError) as ei:
+        G.glisse_create(1.0, unbound, w["particles"], 0.5)
+    assert ei.value.code == G.GLISSE_E_INVAL
+    sim = G.Simulation(1.0, w["planets"], w["particles"], 0.5)
+    with pytest.raises(G.GlisseError) as ei:
+        sim.advance(-1)
+    assert ei.value.code == G.GLISSE_E_INVAL
+    sim.advance(0)
+    assert sim.status()[1] == 0
+    sim.close()
