@@ -62,8 +62,8 @@ extern "C" {
 typedef struct glisse_ctx glisse_ctx; /* opaque; owned by the library */
 
 typedef struct {
-    int32_t chunk_steps;   /* planet chunk length C (section 2.2 "planetary chunk"), default 1024 */
-    int32_t resync_chunks; /* compact live particles every R chunks (section 2.2 "resync interval"), default 1 */
+    int32_t chunk_steps;   /* steps per planet chunk C (section 2.2), default 1024 */
+    int32_t resync_chunks; /* compact live particles every R chunks (section 2.2), default 1 */
     int32_t kepler_mode;   /* GLISSE_KEPLER_*, default CONVERGE */
     int32_t kepler_iters;  /* iterations for PAPER_FIXED, default 5 (section 2.2) */
     int32_t enc_mode;      /* GLISSE_ENC_*, default HILL */
@@ -159,9 +159,9 @@ void glisse_destroy(glisse_ctx* ctx);
 const char* glisse_strerror(int code);
 
 /*
- * Device-level stable partition of live particles (section 2.2: "a stable
- * partition algorithm" moves deactivated particles to the end so live ones
- * keep their relative order).  All pointers are device pointers:
+ * Device-level stable partition of live particles (section 2.2 moves
+ * deactivated particles to the end of the arrays with an order-preserving
+ * partition, so live ones keep their relative order).  All pointers are device pointers:
  *   alive   : [n] uint8, non-zero = keep
  *   src     : [6][ld] doubles (x, y, z, vx, vy, vz planes, leading dimension ld >= n)
  *   src_id  : [n] int32

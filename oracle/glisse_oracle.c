@@ -452,7 +452,7 @@ int orc_rcrit(double m0, int np, const double* pl, int mode, double value, doubl
 /*   1. kick(dt/2) with the acceleration at t_k                              */
 /*   2. Kepler drift of dt about mu = G m0                                   */
 /*   3. removal tests at t_{k+1} on the drifted position (reading: the paper */
-/*      tests "while computing the acceleration", i.e. at each kick time)    */
+/*      makes the test as part of the acceleration, i.e. at each kick time)  */
 /*   4. kick(dt/2) with the acceleration at t_{k+1}                          */
 /* A particle whose test fires keeps the state of step 3 (after the drift,   */
 /* before the closing kick), removal_step = k+1 (global index), reason =     */

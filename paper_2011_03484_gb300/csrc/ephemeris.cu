@@ -1,9 +1,9 @@
 // ephemeris.cu -- the planets: set-up and the chunked Wisdom-Holman map (section 2.2).
 //
 // The paper integrates the planets with the standard mixed-variable
-// symplectic (Wisdom-Holman) map in Jacobi coordinates, a "planetary chunk"
-// of steps ahead of the particles, and ships the heliocentric positions plus
-// the common indirect term h0 = -sum_j G m_j r_j / |r_j|^3 for every step.
+// symplectic (Wisdom-Holman) map in Jacobi coordinates, a chunk of steps
+// ahead of the particles, and ships the heliocentric positions plus the
+// common indirect term h0 = -sum_j G m_j r_j / |r_j|^3 for every step.
 // Here that runs on the GPU in one warp (lane i = planet i) on a side stream,
 // one chunk ahead of the particle kernel.
 //

@@ -13,8 +13,8 @@
 //
 // Scheduling: chunk j of the planet log covers steps [jC, (j+1)C] of the
 // run.  The ephemeris kernel for chunk j+1 runs on a high-priority side stream
-// while the particle kernel works through chunk j on the main stream (the
-// paper's "planet chunk computed one ahead", section 2.2); events order the
+// while the particle kernel works through chunk j on the main stream (section
+// 2.2 computes the planets one chunk ahead in the same way); events order the
 // ring-buffer reuse.  After each segment (a particle launch over at most one
 // chunk) live particles are compacted every resync_chunks segments.
 #include <cuda_runtime.h>
