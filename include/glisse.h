@@ -176,6 +176,32 @@ int glisse_partition_device(int64_t n, int64_t ld, const uint8_t* alive, const d
                             double* dst, int32_t* dst_id, int64_t* n_out, void* stream);
 
 /*
+ * Same stable partition as glisse_partition_device, for callers that must not
+ * allocate device memory (for example while a CUDA graph is being captured,
+ * under a framework or pool allocator that owns all device memory, or in a
+ * loop that cannot afford an allocation's synchronisation or its failure).
+ * The paper has no counterpart; this is a property of this library only.
+ *   - Allocates nothing: no cudaMalloc / cudaFree or allocating library call.
+ *     Its scratch is a fixed array of GLISSE_PARTITION_NOALLOC_MAX / 2048
+ *     int64 (256 KiB) inside the library's device image, present on every GPU
+ *     that loads the library until the process exits.
+ *   - n above GLISSE_PARTITION_NOALLOC_MAX returns GLISSE_E_INVAL.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     outside any stream capture.
+ *   - All calls on a device share the one array (its contents are left over
+ *     from the previous call and are never assumed to be zero).  Calls whose
+ *     GPU work overlaps -- e.g. from two host threads on two streams -- race on
+ *     it and give wrong results; serialise them.  Each call synchronises its
+ *     stream before returning.
+ * Arguments, results and errors are those of glisse_partition_device.
+ */
+#define GLISSE_PARTITION_NOALLOC_MAX 67108864
+int glisse_partition_device_noalloc(int64_t n, int64_t ld, const uint8_t* alive, const double* src,
+                                    const int32_t* src_id, double* dst, int32_t* dst_id, int64_t* n_out,
+                                    void* stream);
+
+/*
  * FP64 throughput probe: runs independent chains of fused multiply-adds on
  * every SM for about `iterations` x 8 operations per thread and reports the
  * achieved rate (FMA instructions per second per GPU) in *dfma_per_s and the

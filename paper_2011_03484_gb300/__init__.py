@@ -37,8 +37,10 @@ GLISSE_ENC_FIXED = 1
 EXPORTED = (
     "glisse_opts_default", "glisse_create", "glisse_advance", "glisse_read", "glisse_status",
     "glisse_read_planets", "glisse_set_ephemeris", "glisse_destroy", "glisse_strerror",
-    "glisse_partition_device", "glisse_fp64_peak", "glisse_timings",
+    "glisse_partition_device", "glisse_fp64_peak", "glisse_timings", "glisse_partition_device_noalloc",
 )
+
+GLISSE_PARTITION_NOALLOC_MAX = 67108864
 
 
 class glisse_timing(C.Structure):
@@ -114,6 +116,8 @@ def load(build_if_missing: bool = False):
     L.glisse_strerror.restype = C.c_char_p
     L.glisse_partition_device.argtypes = [C.c_int64, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
     L.glisse_partition_device.restype = C.c_int
+    L.glisse_partition_device_noalloc.argtypes = [C.c_int64, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
+    L.glisse_partition_device_noalloc.restype = C.c_int
     L.glisse_fp64_peak.argtypes = [C.c_int32, dp, dp]
     L.glisse_fp64_peak.restype = C.c_int
     L.glisse_timings.argtypes = [vp, C.POINTER(glisse_timing), C.c_int32]
@@ -202,6 +206,16 @@ def glisse_partition_device(n, ld, alive_ptr, src_ptr, src_id_ptr, dst_ptr, dst_
     rc = load().glisse_partition_device(int(n), int(ld), alive_ptr, src_ptr, src_id_ptr, dst_ptr, dst_id_ptr,
                                         n_out_ptr, stream)
     _check(rc, "glisse_partition_device")
+
+
+def glisse_partition_device_noalloc(n, ld, alive_ptr, src_ptr, src_id_ptr, dst_ptr, dst_id_ptr, n_out_ptr,
+                                    stream=0):
+    """Stable partition without allocating: the scratch is a fixed array in the library's
+    device image (limit GLISSE_PARTITION_NOALLOC_MAX slots).  For callers that must not
+    allocate device memory.  Calls that overlap on the GPU share that array and race."""
+    rc = load().glisse_partition_device_noalloc(int(n), int(ld), alive_ptr, src_ptr, src_id_ptr, dst_ptr,
+                                                dst_id_ptr, n_out_ptr, stream)
+    _check(rc, "glisse_partition_device_noalloc")
 
 
 def glisse_timings(h, reset: bool = False) -> dict:
