@@ -140,6 +140,34 @@ def dist_env():
     return rank, world, local
 
 
+def replica_particles(w, rank: int):
+    """Particles of rank `rank` under weak scaling: rank 0 uses the workload itself, every
+    other rank an independent seeded replica of the same shape (no data is exchanged)."""
+    import numpy as np
+
+    import glisse_inputs as gi
+
+    if rank == 0:
+        return gi.make(w.name)["particles"]
+    rng = np.random.Generator(np.random.PCG64(w.seed + 1000 * rank))
+    return gi.particle_belt(rng, w.n, w.a_range, w.e_range, w.sigma_i_deg, w.star_mass)
+
+
+def reduce_over_ranks(total_ms: float, particle_steps: float, device=None):
+    """(max over ranks of the timed milliseconds, sum over ranks of particle-steps).
+    The only cross-rank traffic of the benchmark; with one process it is the identity."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return total_ms, particle_steps
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    n = torch.tensor([particle_steps], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 def workload_desc(w, n):
     return (f"{w.name}: {n} test particles, 4 planets (a 5.2-30.1 AU), a in U[{w.a_range[0]:g},{w.a_range[1]:g}] AU, "
             f"e in U[{w.e_range[0]:g},{w.e_range[1]:g}], sigma_i {w.sigma_i_deg:g} deg, dt {w.dt:g} yr, "
@@ -198,13 +226,101 @@ def reference_arm(args):
     return 0
 
 
+def batched_arm(args):
+    """256 independent systems (N_p 2..8, ~3.4e6 particles, dt = P_inner / 20) in one
+    context: planet chunks of all systems, the persistent particle kernel, compaction
+    and task rebuild replayed as a captured CUDA graph per chunk."""
+    import numpy as np
+    import torch
+
+    import glisse_inputs as gi
+    import paper_2011_03484_gb300 as G
+
+    rank, world, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    G._build.build()
+    G.load()
+    b = gi.make_batched(seed=4 + 1000 * rank)
+    C = 1024
+    stream = torch.cuda.current_stream(dev)
+    args_b = (b["star_mass"], b["n_planets"], b["planets"], b["n_particles"], b["particles"], b["dt"])
+    sim = G.BatchSimulation(*args_b, chunk_steps=C, cuda_stream=stream.cuda_stream)
+    tuned = sim.tune(256) if args.tune else None
+    C_run = tuned[0] if tuned else C
+    for _ in range(args.warmup):
+        sim.advance(C_run)
+    torch.cuda.synchronize(dev)
+    live0 = sim.status()[0]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(dev.index or 0) as clocks:
+        done = 0
+        for k in range(args.steps):
+            flush.zero_()
+            n_before = sim.status()[0]
+            starts[k].record(stream)
+            sim.advance(C_run)
+            ends[k].record(stream)
+            n_after = sim.status()[0]
+            done += (n_before + n_after) // 2 * C_run
+        torch.cuda.synchronize(dev)
+    total_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+    live1 = sim.status()[0]
+    sim.close()
+    value = done / (total_ms * 1e-3)
+    # per-stage device times from a timing-mode copy (direct launches with events)
+    simt = G.BatchSimulation(*args_b, chunk_steps=C_run, timing=1, cuda_stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        simt.advance(C_run)
+    simt.timings(reset=True)
+    for _ in range(min(args.steps, 3)):
+        simt.advance(C_run)
+    tm = simt.timings()
+    simt.close()
+    csum = clocks.summary()
+    mhz = csum["sm_mhz"] if csum else 2070.0
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    dfma_peak = n_sm * DFMA_PER_CLK_PER_SM * mhz * 1e6
+    w_np = float(np.sum(b["n_planets"] * b["n_particles"]) / np.sum(b["n_particles"]))
+    kernel_ms = tm["particle_ms"] / max(tm["particle_launches"], 1)
+    spl = tm["particle_steps"] / max(tm["particle_launches"], 1)
+    flop = flop_per_step(0) + (flop_per_step(1) - flop_per_step(0)) * w_np
+    instr = fp64_instr_per_step(0) + (fp64_instr_per_step(1) - fp64_instr_per_step(0)) * w_np
+    achieved = flop * spl / (kernel_ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batched: {len(b['star_mass'])} systems, N_p 2..8, {int(b['n_particles'].sum())} "
+                               f"particles, dt = P_inner/20, chunk {C_run}, one graph per chunk",
+                   "live_at_start": live0, "live_at_end": live1, "tuned": tuned,
+                   "particle_weighted_planets": w_np},
+        "roofline": {"bound": "alu", "achieved": achieved * 1e-9, "peak": 2 * dfma_peak * 1e-9, "unit": "GFLOP/s",
+                     "frac": achieved / (2 * dfma_peak), "traffic": None, "kernel": "batch_particle_kernel",
+                     "kernel_ms_avg": kernel_ms,
+                     "fp64_pipe_frac": instr * spl / (kernel_ms * 1e-3) / dfma_peak,
+                     "flop_per_particle_step": flop},
+        "stage_ms_per_step": {"particle": tm["particle_ms"] / max(tm["particle_launches"], 1),
+                              "ephemeris": tm["ephemeris_ms"] / max(tm["ephemeris_launches"], 1),
+                              "compaction": tm["compact_ms"] / max(tm["compact_launches"], 1)},
+        "gpu_launches": 7 * args.steps,
+        "clocks": csum,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="longrun", choices=["longrun", "belt", "tiny"])
+    ap.add_argument("--workload", default="longrun", choices=["longrun", "belt", "tiny", "batched"])
+    ap.add_argument("--tune", action="store_true", help="batched: run the autotuner before timing")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-particles", type=int, default=8192)
     ap.add_argument("--cpu-particles", type=int, default=16384)
@@ -214,6 +330,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "batched":
+        return batched_arm(args)
 
     import numpy as np
     import torch
@@ -236,13 +354,8 @@ def main():
 
     w = gi.WORKLOADS[args.workload]
     full = gi.make(args.workload)
-    if world > 1:
-        # weak scaling: every rank integrates its own seeded replica of the workload
-        rng = np.random.Generator(np.random.PCG64(w.seed + 1000 * rank))
-        planets = full["planets"]
-        particles = gi.particle_belt(rng, w.n, w.a_range, w.e_range, w.sigma_i_deg, w.star_mass)
-    else:
-        planets, particles = full["planets"], full["particles"]
+    # weak scaling: every rank integrates its own seeded replica of the workload
+    planets, particles = full["planets"], replica_particles(w, rank)
     n = particles.shape[0]
     np_ = planets.shape[0]
 
@@ -287,14 +400,7 @@ def main():
     live_after = G.glisse_status(h)[0]
     G.glisse_destroy(h)
     psteps = tm["particle_steps"]
-    if dist:
-        t = torch.tensor([total_ms, float(psteps)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms_all, psteps_all = float(tmax[0]), float(t[1])
-    else:
-        total_ms_all, psteps_all = total_ms, float(psteps)
+    total_ms_all, psteps_all = reduce_over_ranks(total_ms, float(psteps), dev)
     value = psteps_all / (total_ms_all * 1e-3)
 
     # roofline of the particle kernel: algorithmic FP64 work / its own device time, against

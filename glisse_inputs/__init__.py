@@ -155,6 +155,63 @@ def make(name: str, n: int | None = None):
     }
 
 
+def make_batched(seed: int = 4, n_systems: int = 256, n_min: int = 512, n_max: int = 65536, star_mass: float = 1.0):
+    """Many independent systems (the batched workload).
+
+    Per system, drawn in this order from PCG64(seed): the planet count N_p
+    uniform in {2..8}; planet masses log-uniform in [1e-5, 1e-3] M_sun; the
+    innermost semi-major axis uniform in [1, 5] AU, each next one at least 10
+    mutual Hill radii further out (a_{i+1} = a_i (1 + 5k)/(1 - 5k) (1 + U[0, 0.3]),
+    k = ((m_i + m_{i+1}) / 3 m0)^(1/3)); e in U[0, 0.05], i in U[0, 2] deg and
+    uniform angles for each planet; then the particle count log-uniform in
+    [n_min, n_max]; particles half between the two outermost planets (10% of
+    the gap kept clear at each end) and half beyond the outermost one
+    (a in U[1.2, 1.6] a_out), e in U[0, 0.05], Rayleigh sigma_i = 1 deg.
+    dt is 1/20 of the innermost planet's period.  With the defaults about 4e6
+    particles in all.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = {"star_mass": [], "n_planets": [], "planets": [], "n_particles": [], "particles": [], "dt": []}
+    for _ in range(n_systems):
+        npl = int(rng.integers(2, 9))
+        m = np.exp(rng.uniform(np.log(1e-5), np.log(1e-3), npl))
+        a = np.empty(npl)
+        a[0] = rng.uniform(1.0, 5.0)
+        for i in range(npl - 1):
+            k = ((m[i] + m[i + 1]) / (3.0 * star_mass)) ** (1.0 / 3.0)
+            a[i + 1] = a[i] * (1 + 5 * k) / (1 - 5 * k) * (1.0 + rng.uniform(0.0, 0.3))
+        e = rng.uniform(0.0, 0.05, npl)
+        inc = np.radians(rng.uniform(0.0, 2.0, npl))
+        ang = rng.uniform(0.0, 2 * np.pi, (3, npl))
+        st = elements_to_cartesian(G * (star_mass + m), a, e, inc, ang[0], ang[1], ang[2])
+        planets = np.concatenate([m[:, None], st], axis=1)
+        n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        between = rng.uniform(0.0, 1.0, n) < 0.5
+        gap = a[-1] - a[-2]
+        pa = np.where(between, rng.uniform(a[-2] + 0.1 * gap, a[-1] - 0.1 * gap, n),
+                      a[-1] * rng.uniform(1.2, 1.6, n))
+        pe = rng.uniform(0.0, 0.05, n)
+        u = rng.uniform(0.0, 1.0, n)
+        pinc = np.radians(1.0) * np.sqrt(-2.0 * np.log1p(-u))
+        pang = rng.uniform(0.0, 2 * np.pi, (3, n))
+        parts = elements_to_cartesian(G * star_mass, pa, pe, pinc, pang[0], pang[1], pang[2])
+        period = 2 * np.pi * np.sqrt(a[0] ** 3 / (G * (star_mass + m[0])))
+        out["star_mass"].append(star_mass)
+        out["n_planets"].append(npl)
+        out["planets"].append(planets)
+        out["n_particles"].append(n)
+        out["particles"].append(parts)
+        out["dt"].append(period / 20.0)
+    return {
+        "star_mass": np.array(out["star_mass"]),
+        "n_planets": np.array(out["n_planets"], dtype=np.int32),
+        "planets": np.ascontiguousarray(np.concatenate(out["planets"], axis=0)),
+        "n_particles": np.array(out["n_particles"], dtype=np.int64),
+        "particles": np.ascontiguousarray(np.concatenate(out["particles"], axis=0)),
+        "dt": np.array(out["dt"]),
+    }
+
+
 def subset_ids(name: str, k: int):
     """Sorted random subset of k particle ids of a workload (seeded by the workload)."""
     w = WORKLOADS[name]

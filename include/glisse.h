@@ -210,6 +210,60 @@ int glisse_partition_device_noalloc(int64_t n, int64_t ld, const uint8_t* alive,
  */
 int glisse_fp64_peak(int32_t iterations, double* dfma_per_s, double* sm_mhz);
 
+/* ------------------------------------------------------------------------ */
+/* Many independent systems in one context (a batch).                        */
+/* Each system has its own star, 0..GLISSE_MAX_PLANETS planets, particles    */
+/* and step dt; all advance the same number of steps (each of its own dt).   */
+/* The per-chunk work -- planet chunks of every system (one warp each), one  */
+/* persistent particle launch that takes 32-particle tasks from a device    */
+/* work counter, compaction and the task-table rebuild -- keeps every size   */
+/* on the device and is replayed as a captured CUDA graph.                   */
+/* ------------------------------------------------------------------------ */
+typedef struct glisse_batch glisse_batch; /* opaque; owned by the library */
+
+/*
+ * Create a batch.  Host arrays, systems concatenated in order:
+ *   star_mass  : [n_systems]
+ *   n_planets  : [n_systems]  (0..GLISSE_MAX_PLANETS; each system's planets
+ *                ordered by increasing initial semi-major axis)
+ *   planets    : [sum n_planets][7] m, x, y, z, vx, vy, vz (heliocentric)
+ *   n_particles: [n_systems]  (>= 0)
+ *   particles  : [sum n_particles][6] heliocentric (particle id = row index)
+ *   dt         : [n_systems] non-zero
+ *   opts       : NULL for defaults; chunk_steps, enc_mode, enc_value, r_max,
+ *                timing and cuda_stream apply to every system.
+ * Errors: INVAL, NOMEM, CUDA.
+ */
+int glisse_batch_create(glisse_batch** out, int32_t n_systems, const double* star_mass, const int32_t* n_planets,
+                        const double* planets, const int64_t* n_particles, const double* particles, const double* dt,
+                        const glisse_opts* opts);
+
+/* Advance every system by n_steps steps (section 2.2 map per system).  Errors: INVAL, KEPLER, CUDA. */
+int glisse_batch_advance(glisse_batch* b, int64_t n_steps);
+
+/* Results by particle id (rows of the create call's particle array); pointers may be NULL.
+ * Same meaning as glisse_read. */
+int glisse_batch_read(glisse_batch* b, double* state, uint8_t* alive, int64_t* removal_step,
+                      int32_t* removal_reason);
+
+/* Live particles over all systems and the step index (pointers may be NULL). */
+int glisse_batch_status(glisse_batch* b, int64_t* n_live, int64_t* step);
+
+/* Stage timings of the batch (opts.timing != 0), as glisse_timings. */
+int glisse_batch_timings(glisse_batch* b, glisse_timing* out, int32_t reset);
+
+/*
+ * Autotuner: tries chunk lengths {256, 512, 1024, 2048} and particle-kernel
+ * block sizes {64, 128, 256} on a scratch copy of the batch (trial_steps steps
+ * each, <= 0 for 256) and keeps the fastest in live particle-steps per second.
+ * The batch itself does not move.  *chunk_steps and *block_threads (may be
+ * NULL) receive the choice.  Errors: INVAL, NOMEM, CUDA.
+ */
+int glisse_batch_tune(glisse_batch* b, int32_t trial_steps, int32_t* chunk_steps, int32_t* block_threads);
+
+/* Release the batch (NULL is ignored). */
+void glisse_batch_destroy(glisse_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,6 +38,8 @@ EXPORTED = (
     "glisse_opts_default", "glisse_create", "glisse_advance", "glisse_read", "glisse_status",
     "glisse_read_planets", "glisse_set_ephemeris", "glisse_destroy", "glisse_strerror",
     "glisse_partition_device", "glisse_fp64_peak", "glisse_timings", "glisse_partition_device_noalloc",
+    "glisse_batch_create", "glisse_batch_advance", "glisse_batch_read", "glisse_batch_status",
+    "glisse_batch_timings", "glisse_batch_tune", "glisse_batch_destroy",
 )
 
 GLISSE_PARTITION_NOALLOC_MAX = 67108864
@@ -122,6 +124,20 @@ def load(build_if_missing: bool = False):
     L.glisse_fp64_peak.restype = C.c_int
     L.glisse_timings.argtypes = [vp, C.POINTER(glisse_timing), C.c_int32]
     L.glisse_timings.restype = C.c_int
+    L.glisse_batch_create.argtypes = [C.POINTER(vp), C.c_int32, dp, i32p, dp, i64p, dp, dp, C.POINTER(glisse_opts)]
+    L.glisse_batch_create.restype = C.c_int
+    L.glisse_batch_advance.argtypes = [vp, C.c_int64]
+    L.glisse_batch_advance.restype = C.c_int
+    L.glisse_batch_read.argtypes = [vp, dp, u8p, i64p, i32p]
+    L.glisse_batch_read.restype = C.c_int
+    L.glisse_batch_status.argtypes = [vp, i64p, i64p]
+    L.glisse_batch_status.restype = C.c_int
+    L.glisse_batch_timings.argtypes = [vp, C.POINTER(glisse_timing), C.c_int32]
+    L.glisse_batch_timings.restype = C.c_int
+    L.glisse_batch_tune.argtypes = [vp, C.c_int32, i32p, i32p]
+    L.glisse_batch_tune.restype = C.c_int
+    L.glisse_batch_destroy.argtypes = [vp]
+    L.glisse_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -229,6 +245,100 @@ def glisse_fp64_peak(iterations: int = 20000):
     r, mhz = C.c_double(), C.c_double()
     _check(load().glisse_fp64_peak(int(iterations), C.byref(r), C.byref(mhz)), "glisse_fp64_peak")
     return r.value, mhz.value
+
+
+def glisse_batch_create(star_mass, n_planets, planets, n_particles, particles, dt, opts: glisse_opts | None = None):
+    """Batch of independent systems from concatenated host arrays; returns a handle."""
+    L = load()
+    m0 = np.ascontiguousarray(star_mass, dtype=np.float64)
+    npl = np.ascontiguousarray(n_planets, dtype=np.int32)
+    npa = np.ascontiguousarray(n_particles, dtype=np.int64)
+    pl = np.ascontiguousarray(planets, dtype=np.float64).reshape(-1, 7)
+    pa = np.ascontiguousarray(particles, dtype=np.float64).reshape(-1, 6)
+    d = np.ascontiguousarray(dt, dtype=np.float64)
+    h = C.c_void_p()
+    rc = L.glisse_batch_create(C.byref(h), len(m0), _dp(m0), npl.ctypes.data_as(C.POINTER(C.c_int32)),
+                               _dp(pl) if pl.size else None, npa.ctypes.data_as(C.POINTER(C.c_int64)),
+                               _dp(pa) if pa.size else None, _dp(d), C.byref(opts) if opts is not None else None)
+    _check(rc, "glisse_batch_create")
+    return h
+
+
+def glisse_batch_advance(h, n_steps: int):
+    _check(load().glisse_batch_advance(h, int(n_steps)), "glisse_batch_advance")
+
+
+def glisse_batch_read(h, n: int):
+    st = np.empty((n, 6))
+    alive = np.empty(n, dtype=np.uint8)
+    steps = np.empty(n, dtype=np.int64)
+    rsn = np.empty(n, dtype=np.int32)
+    rc = load().glisse_batch_read(h, _dp(st), alive.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                  steps.ctypes.data_as(C.POINTER(C.c_int64)),
+                                  rsn.ctypes.data_as(C.POINTER(C.c_int32)))
+    _check(rc, "glisse_batch_read")
+    return {"state": st, "alive": alive.astype(bool), "removal_step": steps, "removal_reason": rsn}
+
+
+def glisse_batch_status(h):
+    nl, st = C.c_int64(), C.c_int64()
+    _check(load().glisse_batch_status(h, C.byref(nl), C.byref(st)), "glisse_batch_status")
+    return nl.value, st.value
+
+
+def glisse_batch_timings(h, reset: bool = False) -> dict:
+    t = glisse_timing()
+    _check(load().glisse_batch_timings(h, C.byref(t), 1 if reset else 0), "glisse_batch_timings")
+    return {name: getattr(t, name) for name, _ in glisse_timing._fields_}
+
+
+def glisse_batch_tune(h, trial_steps: int = 256):
+    c, t = C.c_int32(), C.c_int32()
+    _check(load().glisse_batch_tune(h, int(trial_steps), C.byref(c), C.byref(t)), "glisse_batch_tune")
+    return c.value, t.value
+
+
+def glisse_batch_destroy(h):
+    if h:
+        load().glisse_batch_destroy(h)
+
+
+class BatchSimulation:
+    """Owner of a batch of independent systems (same calls, Python lifetime)."""
+
+    def __init__(self, star_mass, n_planets, planets, n_particles, particles, dt, **opt):
+        o = glisse_opts_default()
+        for k, v in opt.items():
+            setattr(o, k, v)
+        self.n = int(np.sum(n_particles))
+        self.h = glisse_batch_create(star_mass, n_planets, planets, n_particles, particles, dt, o)
+
+    def advance(self, n_steps):
+        glisse_batch_advance(self.h, n_steps)
+        return self
+
+    def read(self):
+        return glisse_batch_read(self.h, self.n)
+
+    def status(self):
+        return glisse_batch_status(self.h)
+
+    def timings(self, reset=False):
+        return glisse_batch_timings(self.h, reset)
+
+    def tune(self, trial_steps=256):
+        return glisse_batch_tune(self.h, trial_steps)
+
+    def close(self):
+        if self.h:
+            glisse_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Simulation:

@@ -167,16 +167,18 @@ __device__ __forceinline__ void emit_step(int k, int np, int S, int lane, bool o
     double vh[3];
     jac_to_helio(w, m_over_eta, lane, np, vh);
     double* L = log + (size_t)k * S;
-    double* H = hist + (size_t)k * 6 * np;
     if (on) {
         L[kRec * lane + 0] = r[0];
         L[kRec * lane + 1] = r[1];
         L[kRec * lane + 2] = r[2];
         L[kRec * lane + 3] = 0.0;
+        if (hist) {
+            double* H = hist + (size_t)k * 6 * np;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            H[6 * lane + d] = r[d];
-            H[6 * lane + 3 + d] = vh[d];
+            for (int d = 0; d < 3; ++d) {
+                H[6 * lane + d] = r[d];
+                H[6 * lane + 3 + d] = vh[d];
+            }
         }
     }
     if (lane == 0) {
@@ -193,10 +195,8 @@ __device__ __forceinline__ void emit_step(int k, int np, int S, int lane, bool o
 // synchronised heliocentric states hist[0..nsteps][np][6].
 // status: set to GLISSE_E_KEPLER if a planet's drift fails.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) eph_chunk_kernel(const PlanetConsts* __restrict__ pcp, double* jac, double dt,
-                                                         int nsteps, double* __restrict__ log,
-                                                         double* __restrict__ hist, int* status) {
-    const PlanetConsts& pc = *pcp;
+__device__ __forceinline__ void eph_advance(const PlanetConsts& pc, double* jac, double dt, int nsteps,
+                                            double* __restrict__ log, double* __restrict__ hist, int* status) {
     const int np = pc.np;
     const int lane = threadIdx.x;
     const bool on = lane < np;
@@ -252,6 +252,24 @@ __global__ void __launch_bounds__(32) eph_chunk_kernel(const PlanetConsts* __res
     if (__any_sync(kFullMask, failed) && lane == 0) *status = GLISSE_E_KEPLER;
 }
 
+__global__ void __launch_bounds__(32) eph_chunk_kernel(const PlanetConsts* __restrict__ pcp, double* jac, double dt,
+                                                         int nsteps, double* __restrict__ log,
+                                                         double* __restrict__ hist, int* status) {
+    eph_advance(*pcp, jac, dt, nsteps, log, hist, status);
+}
+
+// Many independent systems: block b advances system b (one warp each).
+//   jac  : [n_sys][2][kMaxPlanets][3] Jacobi states (per-system stride 6 kMaxPlanets)
+//   log  : system b's log at log + log_off[b] (stride 4 (np_b + 1) doubles per step)
+//   dt   : [n_sys] steps
+__global__ void __launch_bounds__(32) eph_batch_kernel(const PlanetConsts* __restrict__ pcs, double* jac,
+                                                         const double* __restrict__ dt, int nsteps,
+                                                         double* __restrict__ log, const int64_t* __restrict__ log_off,
+                                                         int* status) {
+    const int b = blockIdx.x;
+    eph_advance(pcs[b], jac + (size_t)b * 6 * kMaxPlanets, dt[b], nsteps, log + log_off[b], nullptr, status);
+}
+
 // ---------------------------------------------------------------------------
 // External positions -> log layout with h0.  One thread per step.
 //   pos : [n+1][np][3] heliocentric positions
@@ -301,6 +319,13 @@ cudaError_t launch_eph_chunk(const PlanetConsts* pc, double* jac, double dt, int
         e = cudaFuncSetAttribute(eph_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
     eph_chunk_kernel<<<1, 32, (size_t)optin, s>>>(pc, jac, dt, nsteps, log, hist, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eph_batch(const PlanetConsts* pcs, int n_sys, double* jac, const double* dt, int nsteps,
+                             double* log, const int64_t* log_off, int* status, cudaStream_t s) {
+    if (n_sys <= 0) return cudaSuccess;
+    eph_batch_kernel<<<n_sys, 32, 0, s>>>(pcs, jac, dt, nsteps, log, log_off, status);
     return cudaGetLastError();
 }
 

@@ -59,4 +59,37 @@ struct ChunkArgs {
     unsigned long long* steps_done;  // optional: += steps advanced by live particles
 };
 
+// Device-resident clock of a batch (so a captured chunk graph can be replayed).
+struct BatchClock {
+    int64_t step;        // global index of the next chunk's first step
+    int32_t test_first;  // 1 until the first chunk has run
+    int32_t pad;
+};
+
+// Arguments of the persistent batched particle kernel.  Task t covers
+// particles [task_start[t], task_start[t] + task_count[t]) of system task_sys[t]
+// (task_count <= 32: one warp).
+struct BatchArgs {
+    const ParticleConsts* pcs;  // [n_sys]
+    const int32_t* np_of;       // [n_sys]
+    const double* log;          // all systems' planet logs
+    const int64_t* log_off;     // [n_sys] offset of each system's log (doubles)
+    const int32_t* task_sys;
+    const int64_t* task_start;
+    const int32_t* task_count;
+    const int64_t* n_tasks;     // device scalar
+    int* counter;               // work counter, zero before the launch
+    const BatchClock* clock;
+    int64_t ld;
+    double* st;                 // [6][ld]
+    const int32_t* id;
+    uint8_t* alive;
+    int64_t* cnt_new;           // [n_sys] += particles still live after the chunk
+    int32_t nsteps;
+    double* out_state;
+    int64_t* out_step;
+    int32_t* out_reason;
+    unsigned long long* steps_done;
+};
+
 }  // namespace glisse

@@ -76,6 +76,94 @@ __device__ __forceinline__ int test_only(double x, double y, double z, const dou
     return hit;
 }
 
+// The map for one lane over nsteps steps of the log L (L step 0 = the lane's
+// current time).  State in registers; act / reason / rstep record removal.
+// pc may live in the constant bank (kernel parameter) or in shared memory.
+template <int NP>
+__device__ __forceinline__ void advance_lane(const ParticleConsts& pc, const double* __restrict__ L, int64_t step0,
+                                             int nsteps, bool test_first, double& x, double& y, double& z, double& vx,
+                                             double& vy, double& vz, bool& act, int& reason, int64_t& rstep) {
+    const float muf = d2f_bits(pc.mu), dtf = d2f_bits(pc.dt);
+    const bool has_rmax = __double_as_longlong(pc.rmax) != 0;
+    const int S = log_stride(NP);
+
+    if (test_first) {
+        const int h = test_only<NP>(x, y, z, L, pc.rc2, pc.rmax2);
+        if (act && h != 0) {
+            act = false;
+            reason = h;
+            rstep = step0;
+        }
+    }
+    if (act) kick_test<NP>(x, y, z, vx, vy, vz, L, pc.half_dt, pc.tgm_half, pc.rc2);
+    double r0, rinv0;
+    radius_of(x, y, z, r0, rinv0);
+
+    for (int k = 0; k < nsteps; ++k) {
+        if (!__any_sync(kFullMask, act)) break;
+        const double* __restrict__ Ln = L + (size_t)(k + 1) * S;
+        const double sx = x, sy = y, sz = z, svx = vx, svy = vy, svz = vz;
+        const double sr0 = r0, srinv0 = rinv0;
+        const bool done = drift_fast(pc.mu, muf, pc.dt, dtf, act, r0, rinv0, x, y, z, vx, vy, vz);
+        bool failed = false;
+        if (act && !done) {
+            failed = !drift_general(pc.mu, pc.dt, x, y, z, vx, vy, vz);
+            radius_of(x, y, z, r0, rinv0);
+        }
+        const bool bad = nonfinite_bits(x) || nonfinite_bits(y) || nonfinite_bits(z) || nonfinite_bits(vx) ||
+                         nonfinite_bits(vy) || nonfinite_bits(vz);
+        if (act && (failed || bad)) {
+            x = sx;
+            y = sy;
+            z = sz;
+            vx = svx;
+            vy = svy;
+            vz = svz;
+            r0 = sr0;
+            rinv0 = srinv0;
+            act = false;
+            reason = failed ? GLISSE_REMOVED_KEPLER : GLISSE_REMOVED_NONFINITE;
+            rstep = step0 + k + 1;
+        }
+        // escape: |r| > r_max, with |r| from the drift (integer compare of positive doubles)
+        int hit = (has_rmax && lt_nonneg(pc.rmax, r0)) ? GLISSE_REMOVED_ESCAPE : 0;
+        const bool last = (k + 1 == nsteps);
+        double nvx = vx, nvy = vy, nvz = vz;
+        int enc;
+        if (last)
+            enc = kick_test<NP>(x, y, z, nvx, nvy, nvz, Ln, pc.half_dt, pc.tgm_half, pc.rc2);
+        else
+            enc = kick_test<NP>(x, y, z, nvx, nvy, nvz, Ln, pc.dt, pc.tgm_full, pc.rc2);
+        hit = enc ? enc : hit;
+        if (act) {
+            if (hit != 0) {
+                act = false;
+                reason = hit;
+                rstep = step0 + k + 1;
+            } else {
+                vx = nvx;
+                vy = nvy;
+                vz = nvz;
+            }
+        }
+    }
+}
+
+// Write a removed particle's result under its id.
+__device__ __forceinline__ void store_removed(int64_t pid, double x, double y, double z, double vx, double vy,
+                                              double vz, int64_t rstep, int reason, double* out_state,
+                                              int64_t* out_step, int32_t* out_reason) {
+    double* o = out_state + 6 * pid;
+    o[0] = x;
+    o[1] = y;
+    o[2] = z;
+    o[3] = vx;
+    o[4] = vy;
+    o[5] = vz;
+    out_step[pid] = rstep;
+    out_reason[pid] = reason;
+}
+
 template <int NP>
 __global__ void __launch_bounds__(kParticleBlock) particle_chunk_kernel(const ChunkArgs a, const ParticleConsts pc) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -102,71 +190,7 @@ __global__ void __launch_bounds__(kParticleBlock) particle_chunk_kernel(const Ch
     const bool started = act;
     int reason = 0;
     int64_t rstep = -1;
-    const float muf = d2f_bits(pc.mu), dtf = d2f_bits(pc.dt);
-    const bool has_rmax = __double_as_longlong(pc.rmax) != 0;
-    const int S = log_stride(NP);
-    const double* __restrict__ L = a.log;
-
-    if (a.test_first) {
-        const int h = test_only<NP>(x, y, z, L, pc.rc2, pc.rmax2);
-        if (act && h != 0) {
-            act = false;
-            reason = h;
-            rstep = a.step0;
-        }
-    }
-    if (act) kick_test<NP>(x, y, z, vx, vy, vz, L, pc.half_dt, pc.tgm_half, pc.rc2);
-    double r0, rinv0;
-    radius_of(x, y, z, r0, rinv0);
-
-    for (int k = 0; k < a.nsteps; ++k) {
-        if (!__any_sync(kFullMask, act)) break;
-        const double* __restrict__ Ln = L + (size_t)(k + 1) * S;
-        const double sx = x, sy = y, sz = z, svx = vx, svy = vy, svz = vz;
-        const double sr0 = r0, srinv0 = rinv0;
-        const bool done = drift_fast(pc.mu, muf, pc.dt, dtf, act, r0, rinv0, x, y, z, vx, vy, vz);
-        bool failed = false;
-        if (act && !done) {
-            failed = !drift_general(pc.mu, pc.dt, x, y, z, vx, vy, vz);
-            radius_of(x, y, z, r0, rinv0);
-        }
-        const bool bad = nonfinite_bits(x) || nonfinite_bits(y) || nonfinite_bits(z) || nonfinite_bits(vx) ||
-                         nonfinite_bits(vy) || nonfinite_bits(vz);
-        if (act && (failed || bad)) {
-            x = sx;
-            y = sy;
-            z = sz;
-            vx = svx;
-            vy = svy;
-            vz = svz;
-            r0 = sr0;
-            rinv0 = srinv0;
-            act = false;
-            reason = failed ? GLISSE_REMOVED_KEPLER : GLISSE_REMOVED_NONFINITE;
-            rstep = a.step0 + k + 1;
-        }
-        // escape: |r| > r_max, with |r| from the drift (integer compare of positive doubles)
-        int hit = (has_rmax && lt_nonneg(pc.rmax, r0)) ? GLISSE_REMOVED_ESCAPE : 0;
-        const bool last = (k + 1 == a.nsteps);
-        double nvx = vx, nvy = vy, nvz = vz;
-        int enc;
-        if (last)
-            enc = kick_test<NP>(x, y, z, nvx, nvy, nvz, Ln, pc.half_dt, pc.tgm_half, pc.rc2);
-        else
-            enc = kick_test<NP>(x, y, z, nvx, nvy, nvz, Ln, pc.dt, pc.tgm_full, pc.rc2);
-        hit = enc ? enc : hit;
-        if (act) {
-            if (hit != 0) {
-                act = false;
-                reason = hit;
-                rstep = a.step0 + k + 1;
-            } else {
-                vx = nvx;
-                vy = nvy;
-                vz = nvz;
-            }
-        }
-    }
+    advance_lane<NP>(pc, a.log, a.step0, a.nsteps, a.test_first != 0, x, y, z, vx, vy, vz, act, reason, rstep);
     if (a.steps_done) {
         // steps this particle actually advanced in the segment (exact work count)
         const unsigned adv = !started ? 0u : (rstep >= 0 ? (unsigned)(rstep - a.step0) : (unsigned)a.nsteps);
@@ -181,19 +205,107 @@ __global__ void __launch_bounds__(kParticleBlock) particle_chunk_kernel(const Ch
         a.st[4 * ld + i] = vy;
         a.st[5 * ld + i] = vz;
         a.alive[i] = act ? 1 : 0;
-        if (rstep >= 0) {
-            const int64_t pid = a.id[i];
-            double* o = a.out_state + 6 * pid;
-            o[0] = x;
-            o[1] = y;
-            o[2] = z;
-            o[3] = vx;
-            o[4] = vy;
-            o[5] = vz;
-            a.out_step[pid] = rstep;
-            a.out_reason[pid] = reason;
-        }
+        if (rstep >= 0) store_removed(a.id[i], x, y, z, vx, vy, vz, rstep, reason, a.out_state, a.out_step,
+                                      a.out_reason);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Batched systems: a persistent kernel.  Each warp takes the next task from
+// the work counter, stages its system's constants in a warp-private slot of
+// shared memory and runs advance_lane with that system's planet count.
+// ---------------------------------------------------------------------------
+template <int NP>
+__device__ __forceinline__ void batch_task(const BatchArgs& a, const ParticleConsts& pc, int s, int64_t start,
+                                           int cnt, int lane, int64_t step0, bool test_first) {
+    const int64_t i = start + lane;
+    const bool in = lane < cnt;
+    const int64_t ld = a.ld;
+    double x = 1.0, y = 0.0, z = 0.0, vx = 0.0, vy = 6.283185307179586, vz = 0.0;
+    if (in) {
+        x = a.st[i];
+        y = a.st[ld + i];
+        z = a.st[2 * ld + i];
+        vx = a.st[3 * ld + i];
+        vy = a.st[4 * ld + i];
+        vz = a.st[5 * ld + i];
+    }
+    bool act = in && a.alive[i] != 0;
+    const bool started = act;
+    int reason = 0;
+    int64_t rstep = -1;
+    advance_lane<NP>(pc, a.log + a.log_off[s], step0, a.nsteps, test_first, x, y, z, vx, vy, vz, act, reason, rstep);
+    const unsigned live = __reduce_add_sync(kFullMask, act ? 1u : 0u);
+    if (lane == 0 && live) atomicAdd(reinterpret_cast<unsigned long long*>(a.cnt_new + s), (unsigned long long)live);
+    if (a.steps_done) {
+        const unsigned adv = !started ? 0u : (rstep >= 0 ? (unsigned)(rstep - step0) : (unsigned)a.nsteps);
+        const unsigned wsum = __reduce_add_sync(kFullMask, adv);
+        if (lane == 0 && wsum) atomicAdd(a.steps_done, (unsigned long long)wsum);
+    }
+    if (in) {
+        a.st[i] = x;
+        a.st[ld + i] = y;
+        a.st[2 * ld + i] = z;
+        a.st[3 * ld + i] = vx;
+        a.st[4 * ld + i] = vy;
+        a.st[5 * ld + i] = vz;
+        a.alive[i] = act ? 1 : 0;
+        if (rstep >= 0) store_removed(a.id[i], x, y, z, vx, vy, vz, rstep, reason, a.out_state, a.out_step,
+                                      a.out_reason);
+    }
+}
+
+constexpr int kBatchMaxWarps = 8;  // largest block of the batched kernel: 256 threads
+
+__global__ void __launch_bounds__(32 * kBatchMaxWarps) batch_particle_kernel(const BatchArgs a) {
+    __shared__ ParticleConsts s_pc[kBatchMaxWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntask = *a.n_tasks;
+    const int64_t step0 = a.clock->step;
+    const bool test_first = a.clock->test_first != 0;
+    constexpr int kWords = (int)(sizeof(ParticleConsts) / sizeof(double));
+    static_assert(sizeof(ParticleConsts) % sizeof(double) == 0, "constants must be whole doubles");
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.counter, 1);
+        t = __shfl_sync(kFullMask, t, 0);
+        if (t >= ntask) break;
+        const int s = a.task_sys[t];
+        const int64_t start = a.task_start[t];
+        const int cnt = a.task_count[t];
+        const double* src = reinterpret_cast<const double*>(a.pcs + s);
+        double* dst = reinterpret_cast<double*>(&s_pc[warp]);
+        for (int w = lane; w < kWords; w += 32) dst[w] = src[w];
+        __syncwarp();
+        const ParticleConsts& pc = s_pc[warp];
+        switch (a.np_of[s]) {
+#define GLISSE_BCASE(N) \
+    case N: batch_task<N>(a, pc, s, start, cnt, lane, step0, test_first); break;
+            GLISSE_BCASE(0)
+            GLISSE_BCASE(1)
+            GLISSE_BCASE(2)
+            GLISSE_BCASE(3)
+            GLISSE_BCASE(4)
+            GLISSE_BCASE(5)
+            GLISSE_BCASE(6)
+            GLISSE_BCASE(7)
+            GLISSE_BCASE(8)
+#undef GLISSE_BCASE
+            default: break;
+        }
+        __syncwarp();
+    }
+}
+
+// Persistent launch: `blocks` blocks of `threads` threads (a multiple of 32, <= 256).
+cudaError_t launch_batch_particles(const BatchArgs& a, int blocks, int threads, cudaStream_t s) {
+    if (threads < 32 || threads > 32 * kBatchMaxWarps || threads % 32) return cudaErrorInvalidValue;
+    batch_particle_kernel<<<blocks, threads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_particles_occupancy(int threads, int* blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_particle_kernel, threads, 0);
 }
 
 cudaError_t launch_particle_chunk(int np, const ChunkArgs& a, const ParticleConsts& pc, cudaStream_t s) {
