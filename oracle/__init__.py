@@ -93,6 +93,9 @@ def _bind(L):
                                 C.c_int64, i64p, i32p, dp, dp, C.c_int64, C.c_int, C.c_int]
     L.orc_particles.restype = C.c_int
     L.orc_max_threads.restype = C.c_int
+    L.orc_particles_jvp.argtypes = [C.c_double, C.c_int, dp, dp, C.c_int64, C.c_double, dp, C.c_double, dp, dp,
+                                    C.c_int64, dp, dp, i64p, i32p, C.c_int, C.c_int]
+    L.orc_particles_jvp.restype = C.c_int
     return L
 
 
@@ -188,6 +191,40 @@ def run(star_mass, planets, particles, dt, n_steps, k_hill=1.0, r_max=1000.0, en
     pr.advance(log, dt, nthreads)
     return {"state": pr.state, "removal_step": pr.removal_step, "reason": pr.reason, "margin": pr.margin,
             "closest": pr.closest, "log": log, "planets": pl1, "rcrit": rc_}
+
+
+def particles_jvp(star_mass, planet_masses, log, dt, state0, direction, rcrit_, r_max, test_first=True,
+                  nthreads=0):
+    """Tangent map by complex step: (final state [n][6], J @ direction [n][6], removal_step, reason)."""
+    pm = _f64(planet_masses)
+    log = _f64(log)
+    s0 = _f64(state0).reshape(-1, 6)
+    dr = _f64(direction).reshape(-1, 6)
+    n = s0.shape[0]
+    s1 = np.empty_like(s0)
+    jv = np.empty_like(s0)
+    rs = np.empty(n, dtype=np.int64)
+    rn = np.empty(n, dtype=np.int32)
+    rc = lib().orc_particles_jvp(float(star_mass), pm.shape[0], _dp(pm), _dp(log), log.shape[0] - 1, float(dt),
+                                 _dp(_f64(rcrit_)), float(r_max), _dp(s0), _dp(dr), n, _dp(s1), _dp(jv),
+                                 rs.ctypes.data_as(C.POINTER(C.c_int64)), rn.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 1 if test_first else 0, int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"orc_particles_jvp failed: {rc}")
+    return s1, jv, rs, rn
+
+
+def particles_jacobian(star_mass, planet_masses, log, dt, state0, rcrit_, r_max, nthreads=0):
+    """Full 6x6 Jacobian per particle [n][6][6] (column c = derivative along input coordinate c)."""
+    s0 = _f64(state0).reshape(-1, 6)
+    n = s0.shape[0]
+    J = np.empty((n, 6, 6))
+    for c in range(6):
+        e = np.zeros_like(s0)
+        e[:, c] = 1.0
+        _, jv, _, _ = particles_jvp(star_mass, planet_masses, log, dt, s0, e, rcrit_, r_max, nthreads=nthreads)
+        J[:, :, c] = jv
+    return J
 
 
 def max_threads() -> int:

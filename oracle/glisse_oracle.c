@@ -35,6 +35,7 @@
  *
  * Readings of points the paper leaves open are listed at each function.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -606,4 +607,258 @@ int orc_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tangent map by complex-step differentiation (reading for the derivative   */
+/* of the map; the paper has no tangent map).  The particle map above is     */
+/* repeated in complex arithmetic on state + i h dir, h = 1e-20: every step  */
+/* is an analytic function of the state, so Im(result) / h is the exact     */
+/* directional derivative J dir up to rounding (no difference quotient, no   */
+/* cancellation).  Control flow (branches, convergence, removal tests)       */
+/* follows the real parts.  Each Newton solve runs to convergence on the    */
+/* real part and then takes two plain complex Newton steps, which carry the  */
+/* imaginary part to the root of the perturbed equation.                    */
+/* ------------------------------------------------------------------------ */
+typedef double complex cplx;
+
+static void stumpff_c(cplx z, cplx c[4])
+{
+    if (cabs(z) < 1.0) {
+        for (int k = 0; k < 4; ++k) {
+            double fact = 1.0;
+            for (int i = 2; i <= k; ++i) fact *= (double)i;
+            cplx term = 1.0 / fact;
+            cplx sum = term;
+            for (int n = 1; n < 40; ++n) {
+                term *= -z / ((double)(2 * n + k - 1) * (double)(2 * n + k));
+                sum += term;
+                if (cabs(term) < 1e-20 * cabs(sum)) break;
+            }
+            c[k] = sum;
+        }
+    } else if (creal(z) > 0.0) {
+        cplx w = csqrt(z);
+        c[0] = ccos(w);
+        c[1] = csin(w) / w;
+        c[2] = (1.0 - ccos(w)) / z;
+        c[3] = (w - csin(w)) / (z * w);
+    } else {
+        cplx w = csqrt(-z);
+        c[0] = ccosh(w);
+        c[1] = csinh(w) / w;
+        c[2] = (ccosh(w) - 1.0) / (-z);
+        c[3] = (csinh(w) - w) / (-z * w);
+    }
+}
+
+static void apply_fg_c(cplx* st, cplx f, cplx g, cplx fd, cplx gd)
+{
+    cplx x0 = st[0], y0 = st[1], z0 = st[2], vx = st[3], vy = st[4], vz = st[5];
+    st[0] = f * x0 + g * vx;
+    st[1] = f * y0 + g * vy;
+    st[2] = f * z0 + g * vz;
+    st[3] = fd * x0 + gd * vx;
+    st[4] = fd * y0 + gd * vy;
+    st[5] = fd * z0 + gd * vz;
+}
+
+static int drift_dE_c(double mu, double dt, cplx* st, cplx r0, cplx u, cplx alpha)
+{
+    cplx a = 1.0 / alpha;
+    cplx n = csqrt(mu / (a * a * a));
+    cplx ec = 1.0 - r0 / a;
+    cplx es = u / (n * a * a);
+    double e = sqrt(creal(ec) * creal(ec) + creal(es) * creal(es));
+    cplx dM = n * dt;
+    double k = floor(creal(dM) / (2.0 * ORC_PI) + 0.5);
+    dM = dM - k * (2.0 * ORC_PI);
+    double lo = creal(dM) - 2.0 * e - 1e-14, hi = creal(dM) + 2.0 * e + 1e-14;
+    cplx x = dM / (1.0 - ec);
+    if (!(creal(x) > lo && creal(x) < hi)) x = 0.5 * (lo + hi);
+    double dxold = hi - lo;
+    int conv = 0;
+    for (int it = 0; it < 200 && !conv; ++it) {
+        cplx F = x - ec * csin(x) + es * (1.0 - ccos(x)) - dM;
+        cplx Fp = 1.0 - ec * ccos(x) + es * csin(x);
+        if (creal(F) < 0.0) { if (creal(x) > lo) lo = creal(x); }
+        else { if (creal(x) < hi) hi = creal(x); }
+        cplx dx = -F / Fp;
+        if (fabs(creal(dx)) <= 1e-15) { x += dx; conv = 1; break; }
+        double xn = creal(x) + creal(dx);
+        if (!(xn > lo && xn < hi) || fabs(creal(dx)) > 0.5 * fabs(dxold)) dx = 0.5 * (lo + hi) - creal(x);
+        dxold = creal(dx);
+        x += dx;
+        if (hi - lo <= 1e-15) conv = 1;
+    }
+    if (!conv) return ORC_EKEPLER;
+    for (int it = 0; it < 2; ++it) {
+        cplx F = x - ec * csin(x) + es * (1.0 - ccos(x)) - dM;
+        cplx Fp = 1.0 - ec * ccos(x) + es * csin(x);
+        x -= F / Fp;
+    }
+    cplx sx = csin(x), cx = ccos(x);
+    cplx omc = 1.0 - cx;
+    cplx f = 1.0 - (a / r0) * omc;
+    cplx g = (dM - (x - sx)) / n;
+    cplx r = a * (1.0 - ec * cx + es * sx);
+    cplx fd = -n * a * a * sx / (r * r0);
+    cplx gd = 1.0 - (a / r) * omc;
+    apply_fg_c(st, f, g, fd, gd);
+    return ORC_OK;
+}
+
+static int drift_univ_c(double mu, double dt0, cplx* st, cplx r0, cplx u, cplx alpha)
+{
+    cplx beta = mu * alpha;
+    cplx dt = dt0;
+    if (creal(alpha) > 0.0) {
+        cplx n = csqrt(mu * alpha * alpha * alpha);
+        cplx P = 2.0 * ORC_PI / n;
+        double k = floor(dt0 / creal(P) + 0.5);
+        dt = dt0 - k * P;
+    }
+    if (creal(dt) == 0.0) return ORC_OK;
+    double sgn = creal(dt) > 0.0 ? 1.0 : -1.0;
+    cplx c[4];
+    double lo = 0.0, hi = creal(dt / r0);
+    int grow = 0;
+    for (;;) {
+        stumpff_c(beta * hi * hi, c);
+        cplx T = r0 * hi * c[1] + u * hi * hi * c[2] + mu * hi * hi * hi * c[3];
+        if (creal(T - dt) * sgn >= 0.0) break;
+        lo = hi;
+        hi *= 2.0;
+        if (++grow > 200) return ORC_EKEPLER;
+    }
+    if (sgn < 0.0) { double t = lo; lo = hi; hi = t; }
+    cplx s = dt / r0;
+    if (!(creal(s) > lo && creal(s) < hi)) s = 0.5 * (lo + hi);
+    double dsold = hi - lo;
+    int conv = 0;
+    for (int it = 0; it < 300 && !conv; ++it) {
+        stumpff_c(beta * s * s, c);
+        cplx F = r0 * s * c[1] + u * s * s * c[2] + mu * s * s * s * c[3] - dt;
+        cplx Fp = r0 * c[0] + u * s * c[1] + mu * s * s * c[2];
+        if (creal(F) < 0.0) { if (creal(s) > lo) lo = creal(s); }
+        else { if (creal(s) < hi) hi = creal(s); }
+        cplx ds = -F / Fp;
+        if (fabs(creal(ds)) <= 1e-15 * fabs(creal(s))) { s += ds; conv = 1; break; }
+        double sn = creal(s) + creal(ds);
+        if (!(sn > lo && sn < hi) || fabs(creal(ds)) > 0.5 * fabs(dsold)) ds = 0.5 * (lo + hi) - creal(s);
+        dsold = creal(ds);
+        s += ds;
+        if (hi - lo <= 1e-15 * fabs(creal(s))) conv = 1;
+    }
+    if (!conv) return ORC_EKEPLER;
+    for (int it = 0; it < 2; ++it) {
+        stumpff_c(beta * s * s, c);
+        cplx F = r0 * s * c[1] + u * s * s * c[2] + mu * s * s * s * c[3] - dt;
+        cplx Fp = r0 * c[0] + u * s * c[1] + mu * s * s * c[2];
+        s -= F / Fp;
+    }
+    stumpff_c(beta * s * s, c);
+    cplx G1 = s * c[1], G2 = s * s * c[2], G3 = s * s * s * c[3];
+    cplx r = r0 * c[0] + u * G1 + mu * G2;
+    apply_fg_c(st, 1.0 - mu * G2 / r0, dt - mu * G3, -mu * G1 / (r * r0), 1.0 - mu * G2 / r);
+    return ORC_OK;
+}
+
+static int kepler_drift_c(double mu, double dt, cplx* st)
+{
+    cplx r0 = csqrt(st[0] * st[0] + st[1] * st[1] + st[2] * st[2]);
+    cplx v2 = st[3] * st[3] + st[4] * st[4] + st[5] * st[5];
+    cplx u = st[0] * st[3] + st[1] * st[4] + st[2] * st[5];
+    cplx alpha = 2.0 / r0 - v2 / mu;
+    if (dt == 0.0) return ORC_OK;
+    if (creal(alpha) > 0.0 && creal(r0 * alpha) >= 1e-3) return drift_dE_c(mu, dt, st, r0, u, alpha);
+    return drift_univ_c(mu, dt, st, r0, u, alpha);
+}
+
+static void particle_accel_c(int np, const double* Gm, const double* pos, const cplx* r, cplx* a)
+{
+    double h0[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < np; ++j) {
+        const double* rj = pos + 3 * j;
+        double rj2 = rj[0] * rj[0] + rj[1] * rj[1] + rj[2] * rj[2];
+        double rj3 = rj2 * sqrt(rj2);
+        for (int d = 0; d < 3; ++d) h0[d] -= Gm[j] * rj[d] / rj3;
+    }
+    cplx dir[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < np; ++j) {
+        const double* rj = pos + 3 * j;
+        cplx dx = r[0] - rj[0], dy = r[1] - rj[1], dz = r[2] - rj[2];
+        cplx d2 = dx * dx + dy * dy + dz * dz;
+        cplx d3 = d2 * csqrt(d2);
+        dir[0] -= Gm[j] * dx / d3;
+        dir[1] -= Gm[j] * dy / d3;
+        dir[2] -= Gm[j] * dz / d3;
+    }
+    for (int d = 0; d < 3; ++d) a[d] = h0[d] + dir[d];
+}
+
+/* Tangent map of orc_particles: for each particle, state0 + i h dir through
+ * nsteps steps (planet log as in orc_particles, removal tests on the real
+ * part).  Outputs the final state (real part), J dir (imaginary part / h),
+ * removal step and reason.  A removed particle's derivative is that of its
+ * frozen state. */
+int orc_particles_jvp(double m0, int np, const double* pmass, const double* log_pos, int64_t nsteps, double dt,
+                      const double* rcrit, double rmax, const double* state0, const double* dir, int64_t npart,
+                      double* state1, double* jvp, int64_t* removal_step, int32_t* reason, int test_first,
+                      int nthreads)
+{
+    if (np < 0 || np > ORC_MAXP || nsteps < 0 || npart < 0) return ORC_EINVAL;
+    const double h = 1e-20;
+    double Gm[ORC_MAXP], rc2[ORC_MAXP];
+    for (int j = 0; j < np; ++j) { Gm[j] = ORC_G * pmass[j]; rc2[j] = rcrit[j] * rcrit[j]; }
+    double rmax2 = rmax > 0.0 ? rmax * rmax : 0.0;
+    double mu = ORC_G * m0;
+    size_t stride = (size_t)3 * np;
+#ifdef _OPENMP
+    int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nt)
+#endif
+    for (int64_t p = 0; p < npart; ++p) {
+        cplx st[6];
+        for (int d = 0; d < 6; ++d) st[d] = state0[6 * p + d] + I * (h * dir[6 * p + d]);
+        double mg = INFINITY, cl = INFINITY;
+        int64_t rstep = -1;
+        int rsn = 0;
+        double re[6];
+        if (test_first) {
+            for (int d = 0; d < 6; ++d) re[d] = creal(st[d]);
+            int hh = particle_test(np, log_pos, rc2, rmax2, re, &mg, &cl);
+            if (hh) { rstep = 0; rsn = hh; }
+        }
+        for (int64_t k = 0; k < nsteps && rstep < 0; ++k) {
+            const double* P0 = log_pos + (size_t)k * stride;
+            const double* P1 = P0 + stride;
+            cplx a[3];
+            particle_accel_c(np, Gm, P0, st, a);
+            for (int d = 0; d < 3; ++d) st[3 + d] += 0.5 * dt * a[d];
+            cplx saved[6];
+            memcpy(saved, st, sizeof st);
+            int rc = kepler_drift_c(mu, dt, st);
+            int bad = 0;
+            for (int d = 0; d < 6; ++d) if (!isfinite(creal(st[d]))) bad = 1;
+            if (rc || bad) {
+                memcpy(st, saved, sizeof st);
+                rstep = k + 1;
+                rsn = rc == ORC_EKEPLER ? RSN_KEPLER : RSN_NONFINITE;
+                break;
+            }
+            for (int d = 0; d < 6; ++d) re[d] = creal(st[d]);
+            int hh = particle_test(np, P1, rc2, rmax2, re, &mg, &cl);
+            if (hh) { rstep = k + 1; rsn = hh; break; }
+            particle_accel_c(np, Gm, P1, st, a);
+            for (int d = 0; d < 3; ++d) st[3 + d] += 0.5 * dt * a[d];
+        }
+        for (int d = 0; d < 6; ++d) {
+            state1[6 * p + d] = creal(st[d]);
+            jvp[6 * p + d] = cimag(st[d]) / h;
+        }
+        removal_step[p] = rstep;
+        reason[p] = rsn;
+    }
+    return ORC_OK;
 }
