@@ -211,6 +211,45 @@ int glisse_partition_device_noalloc(int64_t n, int64_t ld, const uint8_t* alive,
 int glisse_fp64_peak(int32_t iterations, double* dfma_per_s, double* sm_mhz);
 
 /* ------------------------------------------------------------------------ */
+/* Derivatives of the map (tangent and adjoint).                              */
+/* The map of section 2.2 is differentiated with respect to the particles'   */
+/* initial states (planet positions are data).  A glisse_diff object holds   */
+/* the planet log of a fixed run of n_steps and the checkpoint storage; the */
+/* forward pass maps initial to final states and can carry tangent vectors   */
+/* (J t); the backward pass returns J^T g for a cotangent g of the final     */
+/* states, recomputing each checkpoint interval from its stored state.       */
+/* All state arrays are device pointers in [n][6] layout (x, y, z, vx, vy,   */
+/* vz per particle); tangents are [n_tangents][n][6].                        */
+/* ------------------------------------------------------------------------ */
+typedef struct glisse_diff glisse_diff; /* opaque; owned by the library */
+
+/* Planets as in glisse_create; n_particles states per forward call; the planet
+ * log of n_steps steps is computed on the device here.  checkpoint_every >= 1:
+ * the backward pass recomputes that many steps per segment (storage: 48 B per
+ * particle per checkpoint plus 72 B per particle per step of one segment).
+ * opts: enc_mode, enc_value and r_max apply.  Errors: INVAL, NOMEM, CUDA, KEPLER. */
+int glisse_diff_create(glisse_diff** out, double star_mass, const double* planets, int32_t n_planets,
+                       int64_t n_particles, double dt, int64_t n_steps, int32_t checkpoint_every,
+                       const glisse_opts* opts);
+
+/* state0 -> state1 over n_steps (explicit half kicks; removal as in glisse_advance, a
+ * removed particle's output being its frozen state).  n_tangents (0..6) tangent
+ * vectors tangent0 are carried to tangent1 = J tangent0.  log_growth[i] (may be
+ * NULL) receives log(|J t_0| / |t_0|) of tangent 0, a stability indicator.
+ * removal_step / removal_reason (device, may be NULL) as in glisse_read.
+ * Synchronises `stream` (cudaStream_t).  Errors: INVAL, CUDA. */
+int glisse_diff_forward(glisse_diff* d, const double* state0, double* state1, int32_t n_tangents,
+                        const double* tangent0, double* tangent1, double* log_growth, int64_t* removal_step,
+                        int32_t* removal_reason, void* stream);
+
+/* grad_state0 = J^T grad_state1 for the states of the last forward call (J of each
+ * particle's own map).  Errors: STATE before any forward call, INVAL, CUDA. */
+int glisse_diff_backward(glisse_diff* d, const double* grad_state1, double* grad_state0, void* stream);
+
+/* Release the object (NULL is ignored). */
+void glisse_diff_destroy(glisse_diff* d);
+
+/* ------------------------------------------------------------------------ */
 /* Many independent systems in one context (a batch).                        */
 /* Each system has its own star, 0..GLISSE_MAX_PLANETS planets, particles    */
 /* and step dt; all advance the same number of steps (each of its own dt).   */

@@ -40,6 +40,7 @@ EXPORTED = (
     "glisse_partition_device", "glisse_fp64_peak", "glisse_timings", "glisse_partition_device_noalloc",
     "glisse_batch_create", "glisse_batch_advance", "glisse_batch_read", "glisse_batch_status",
     "glisse_batch_timings", "glisse_batch_tune", "glisse_batch_destroy",
+    "glisse_diff_create", "glisse_diff_forward", "glisse_diff_backward", "glisse_diff_destroy",
 )
 
 GLISSE_PARTITION_NOALLOC_MAX = 67108864
@@ -138,6 +139,15 @@ def load(build_if_missing: bool = False):
     L.glisse_batch_tune.restype = C.c_int
     L.glisse_batch_destroy.argtypes = [vp]
     L.glisse_batch_destroy.restype = None
+    L.glisse_diff_create.argtypes = [C.POINTER(vp), C.c_double, dp, C.c_int32, C.c_int64, C.c_double, C.c_int64,
+                                     C.c_int32, C.POINTER(glisse_opts)]
+    L.glisse_diff_create.restype = C.c_int
+    L.glisse_diff_forward.argtypes = [vp, vp, vp, C.c_int32, vp, vp, vp, vp, vp, vp]
+    L.glisse_diff_forward.restype = C.c_int
+    L.glisse_diff_backward.argtypes = [vp, vp, vp, vp]
+    L.glisse_diff_backward.restype = C.c_int
+    L.glisse_diff_destroy.argtypes = [vp]
+    L.glisse_diff_destroy.restype = None
     _lib = L
     return L
 
@@ -381,3 +391,146 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Derivatives of the map (device arrays are torch CUDA float64 tensors)
+# ---------------------------------------------------------------------------
+def glisse_diff_create(star_mass, planets, n_particles, dt, n_steps, checkpoint_every=256, opts=None):
+    L = load()
+    pl = np.ascontiguousarray(planets, dtype=np.float64).reshape(-1, 7)
+    h = C.c_void_p()
+    rc = L.glisse_diff_create(C.byref(h), float(star_mass), _dp(pl) if pl.size else None, pl.shape[0],
+                              int(n_particles), float(dt), int(n_steps), int(checkpoint_every),
+                              C.byref(opts) if opts is not None else None)
+    _check(rc, "glisse_diff_create")
+    return h
+
+
+def glisse_diff_forward(h, state0, state1, tangent0=None, tangent1=None, log_growth=None, removal_step=None,
+                        removal_reason=None, stream=0):
+    """All arguments after h are device addresses (ints) or None; see include/glisse.h."""
+    T = 0 if tangent0 is None else tangent0[1]
+    rc = load().glisse_diff_forward(h, state0, state1, T, None if tangent0 is None else tangent0[0],
+                                    tangent1, log_growth, removal_step, removal_reason, stream)
+    _check(rc, "glisse_diff_forward")
+
+
+def glisse_diff_backward(h, grad_state1, grad_state0, stream=0):
+    _check(load().glisse_diff_backward(h, grad_state1, grad_state0, stream), "glisse_diff_backward")
+
+
+def glisse_diff_destroy(h):
+    if h:
+        load().glisse_diff_destroy(h)
+
+
+class DiffMap:
+    """Differentiable run of the map over a fixed number of steps for n particles.
+
+    forward(state0 [n, 6]) -> state1 [n, 6] (plus tangents J t and a growth
+    indicator); backward(g [n, 6]) -> J^T g for the last forward call.  Both run
+    in the library's kernels; tensors must be CUDA float64 and contiguous."""
+
+    def __init__(self, star_mass, planets, n_particles, dt, n_steps, checkpoint_every=256, **opt):
+        o = glisse_opts_default()
+        for k, v in opt.items():
+            setattr(o, k, v)
+        self.n = int(n_particles)
+        self.h = glisse_diff_create(star_mass, planets, n_particles, dt, n_steps, checkpoint_every, o)
+        self.forward_calls = 0
+
+    @staticmethod
+    def _ptr(t):
+        return None if t is None else t.data_ptr()
+
+    def forward(self, state0, tangents=None):
+        import torch
+
+        state0 = state0.contiguous()
+        assert state0.is_cuda and state0.dtype == torch.float64 and state0.shape == (self.n, 6)
+        state1 = torch.empty_like(state0)
+        growth = torch.empty(self.n, dtype=torch.float64, device=state0.device)
+        rstep = torch.empty(self.n, dtype=torch.int64, device=state0.device)
+        reason = torch.empty(self.n, dtype=torch.int32, device=state0.device)
+        tan1 = None
+        tan0 = None
+        if tangents is not None:
+            tangents = tangents.contiguous()
+            assert tangents.dim() == 3 and tangents.shape[1:] == (self.n, 6)
+            tan1 = torch.empty_like(tangents)
+            tan0 = (tangents.data_ptr(), tangents.shape[0])
+        stream = torch.cuda.current_stream(state0.device).cuda_stream
+        glisse_diff_forward(self.h, state0.data_ptr(), state1.data_ptr(), tan0, self._ptr(tan1),
+                            growth.data_ptr() if tangents is not None else None, rstep.data_ptr(),
+                            reason.data_ptr(), stream)
+        self.forward_calls += 1
+        return state1, tan1, (growth if tangents is not None else None), rstep, reason
+
+    def backward(self, grad_state1):
+        import torch
+
+        g = grad_state1.contiguous()
+        out = torch.empty_like(g)
+        stream = torch.cuda.current_stream(g.device).cuda_stream
+        glisse_diff_backward(self.h, g.data_ptr(), out.data_ptr(), stream)
+        return out
+
+    def close(self):
+        if self.h:
+            glisse_diff_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _growth_seed(state0):
+    """Default tangent for the growth indicator: unit vectors along r and along v."""
+    import torch
+
+    r = state0[:, :3] / state0[:, :3].norm(dim=1, keepdim=True)
+    v = state0[:, 3:] / state0[:, 3:].norm(dim=1, keepdim=True)
+    return (torch.cat([r, v], dim=1) / 2**0.5).unsqueeze(0)
+
+
+def _make_autograd():
+    import torch
+
+    class GlisseMap(torch.autograd.Function):
+        """state1, log_growth = GlisseMap.apply(state0, diff_map).
+
+        Differentiable with respect to state0 through the hand-written adjoint
+        kernel (glisse_diff_backward); log_growth (log |J t| / |t| for the
+        default tangent along r and v) is returned as a non-differentiable
+        stability indicator."""
+
+        @staticmethod
+        def forward(ctx, state0, dmap):
+            state1, _, growth, _, _ = dmap.forward(state0, _growth_seed(state0))
+            ctx.dmap = dmap
+            ctx.call = dmap.forward_calls
+            ctx.mark_non_differentiable(growth)
+            return state1, growth
+
+        @staticmethod
+        def backward(ctx, grad_state1, grad_growth):
+            if ctx.dmap.forward_calls != ctx.call:
+                raise RuntimeError("DiffMap was run forward again before this backward; use one DiffMap per use")
+            return ctx.dmap.backward(grad_state1), None
+
+    return GlisseMap
+
+
+_glisse_map_cls = None
+
+
+def glisse_map():
+    """The torch.autograd.Function of the differentiable map (created on first use)."""
+    global _glisse_map_cls
+    if _glisse_map_cls is None:
+        _glisse_map_cls = _make_autograd()
+    return _glisse_map_cls

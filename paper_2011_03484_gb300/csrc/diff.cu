@@ -1,0 +1,457 @@
+// diff.cu -- tangent (forward-mode) and adjoint (reverse-mode) maps of the
+// particle map, for gradients of final states with respect to initial states.
+//
+// The map of one step is K(t_{k+1}, dt/2) o D(dt) o K(t_k, dt/2) with
+//   kick  K(tau): v += tau a(r),  a(r) = h0 - sum_j G m_j d_j / |d_j|^3, d_j = r - r_j
+//   drift D(dt):  the two-body flow (kepler.cuh), derivatives in drift_tangent / drift_adjoint.
+// The kick's Jacobian is dv'/dr = tau A(r) with the symmetric tidal matrix
+//   tau A w = -sum_j s_j (w - 3 d_j (d_j . w) / |d_j|^2),  s_j = tau G m_j / |d_j|^3,
+// so the tangent adds tau A dr to dv and the adjoint adds tau A lv to lr.
+// Planet positions are data (no derivative with respect to the planets).
+//
+// Forward: one thread per particle carries the state and up to kMaxTangents
+// tangent vectors through n steps (explicit half kicks) and stores the
+// synchronised state every K steps.  Backward: for each K-step segment from
+// the last, the thread recomputes the segment from its checkpoint, keeping the
+// pre-drift state and the post-drift position of every step in a scratch
+// buffer, then runs the adjoint kicks and drifts backwards through it.
+// A removed particle's output is its frozen state; its derivatives are those
+// of that frozen state (the steps after removal contribute nothing).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "glisse_internal.h"
+#include "kepler.cuh"
+
+namespace glisse {
+cudaError_t launch_eph_setup(const double*, int, double, double, int, double, PlanetConsts*, double*, int*,
+                             cudaStream_t);
+cudaError_t launch_eph_chunk(const PlanetConsts*, double*, double, int, double*, double*, int*, cudaStream_t);
+
+constexpr int kMaxTangents = 6;
+constexpr int kDiffBlock = 128;
+
+struct DiffArgs {
+    const double* log;      // [nsteps + 1] planet log steps
+    int64_t n;              // particles
+    int64_t nsteps;
+    int32_t K;              // checkpoint interval
+    int32_t ntan;           // tangent vectors (0..kMaxTangents)
+    const double* state0;   // [n][6]
+    double* state1;         // [n][6]
+    const double* tan0;     // [ntan][n][6]
+    double* tan1;           // [ntan][n][6]
+    double* log_growth;     // [n] log(|J t0| / |t0|) of tangent 0, or null
+    int64_t* rstep;         // [n] removal step (-1 live)
+    int32_t* reason;        // [n]
+    double* ckpt;           // [ceil(nsteps / K)][6][n]
+    double* scratch;        // [K][9][n]
+    const double* grad1;    // [n][6]
+    double* grad0;          // [n][6]
+};
+
+// v += tau a(r) for the log step L; returns the lowest planet index whose encounter test fires.
+template <int NP>
+__device__ __forceinline__ int kick_state(double st[6], const double* __restrict__ L, double tau,
+                                          const double (&tgm)[kMaxPlanets], const double (&rc2)[kMaxPlanets]) {
+    const double h0x = L[kRec * NP], h0y = L[kRec * NP + 1], h0z = L[kRec * NP + 2];
+    st[3] = fma(tau, h0x, st[3]);
+    st[4] = fma(tau, h0y, st[4]);
+    st[5] = fma(tau, h0z, st[5]);
+    int hit = 0;
+#pragma unroll
+    for (int j = NP - 1; j >= 0; --j) {
+        const double dx = st[0] - L[kRec * j], dy = st[1] - L[kRec * j + 1], dz = st[2] - L[kRec * j + 2];
+        const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        hit = lt_nonneg(d2, rc2[j]) ? (j + 1) : hit;
+        const double s = k_rcube(d2, tgm[j]);
+        st[3] = fma(-s, dx, st[3]);
+        st[4] = fma(-s, dy, st[4]);
+        st[5] = fma(-s, dz, st[5]);
+    }
+    return hit;
+}
+
+// out += tau A(r) w  (tgm = tau G m_j)
+template <int NP>
+__device__ __forceinline__ void kick_jac(const double r[3], const double* __restrict__ L,
+                                         const double (&tgm)[kMaxPlanets], const double w[3], double out[3]) {
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const double dx = r[0] - L[kRec * j], dy = r[1] - L[kRec * j + 1], dz = r[2] - L[kRec * j + 2];
+        const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        const double s = k_rcube(d2, tgm[j]);
+        const double c = 3.0 * (dx * w[0] + dy * w[1] + dz * w[2]) / d2;
+        out[0] -= s * (w[0] - c * dx);
+        out[1] -= s * (w[1] - c * dy);
+        out[2] -= s * (w[2] - c * dz);
+    }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kDiffBlock) diff_forward_kernel(const DiffArgs a, const ParticleConsts pc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int S = log_stride(NP);
+    const int T = a.ntan;
+    double st[6], t[kMaxTangents][6];
+    for (int c = 0; c < 6; ++c) st[c] = a.state0[6 * i + c];
+    for (int k = 0; k < kMaxTangents; ++k)
+        for (int c = 0; c < 6; ++c) t[k][c] = (k < T) ? a.tan0[((int64_t)k * a.n + i) * 6 + c] : 0.0;
+    double n0 = 0.0;
+    for (int c = 0; c < 6; ++c) n0 += t[0][c] * t[0][c];
+    int64_t rstep = -1;
+    int reason = 0;
+    const bool has_rmax = __double_as_longlong(pc.rmax) != 0;
+    // removal test at t_0
+    {
+        double tmp[6];
+        for (int c = 0; c < 6; ++c) tmp[c] = st[c];
+        const int hit = kick_state<NP>(tmp, a.log, 0.0, pc.tgm_half, pc.rc2);
+        const double r2 = st[0] * st[0] + st[1] * st[1] + st[2] * st[2];
+        const int esc = (has_rmax && lt_nonneg(pc.rmax2, r2)) ? GLISSE_REMOVED_ESCAPE : 0;
+        if (hit || esc) {
+            rstep = 0;
+            reason = hit ? hit : esc;
+        }
+    }
+    for (int64_t k = 0; k < a.nsteps && rstep < 0; ++k) {
+        if (k % a.K == 0) {
+            double* cp = a.ckpt + (k / a.K) * 6 * a.n;
+            for (int c = 0; c < 6; ++c) cp[c * a.n + i] = st[c];
+        }
+        const double* L0 = a.log + k * S;
+        const double* L1 = L0 + S;
+        // opening half kick (tangents first: A is evaluated at r, which the kick leaves unchanged)
+        for (int q = 0; q < T; ++q) kick_jac<NP>(st, L0, pc.tgm_half, t[q], t[q] + 3);
+        kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);
+        double pre[6];
+        for (int c = 0; c < 6; ++c) pre[c] = st[c];
+        DriftScalars d;
+        if (!drift_scalars(pc.mu, pc.dt, pre, d)) {
+            rstep = k + 1;
+            reason = GLISSE_REMOVED_KEPLER;
+            break;
+        }
+        for (int c = 0; c < 3; ++c) {
+            st[c] = d.f * pre[c] + d.g * pre[3 + c];
+            st[3 + c] = d.fd * pre[c] + d.gd * pre[3 + c];
+        }
+        bool bad = false;
+        for (int c = 0; c < 6; ++c) bad |= nonfinite_bits(st[c]);
+        if (bad) {
+            for (int c = 0; c < 6; ++c) st[c] = pre[c];
+            rstep = k + 1;
+            reason = GLISSE_REMOVED_NONFINITE;
+            break;
+        }
+        for (int q = 0; q < T; ++q) drift_tangent(pc.mu, pre, d, t[q]);
+        // tests at t_{k+1}, then the closing half kick
+        const double r2 = st[0] * st[0] + st[1] * st[1] + st[2] * st[2];
+        int hit = (has_rmax && lt_nonneg(pc.rmax2, r2)) ? GLISSE_REMOVED_ESCAPE : 0;
+        double nst[6];
+        for (int c = 0; c < 6; ++c) nst[c] = st[c];
+        const int enc = kick_state<NP>(nst, L1, pc.half_dt, pc.tgm_half, pc.rc2);
+        hit = enc ? enc : hit;
+        if (hit) {
+            rstep = k + 1;
+            reason = hit;
+            break;
+        }
+        for (int q = 0; q < T; ++q) kick_jac<NP>(st, L1, pc.tgm_half, t[q], t[q] + 3);
+        for (int c = 0; c < 6; ++c) st[c] = nst[c];
+    }
+    for (int c = 0; c < 6; ++c) a.state1[6 * i + c] = st[c];
+    for (int q = 0; q < T; ++q)
+        for (int c = 0; c < 6; ++c) a.tan1[((int64_t)q * a.n + i) * 6 + c] = t[q][c];
+    if (a.log_growth) {
+        double n1 = 0.0;
+        for (int c = 0; c < 6; ++c) n1 += t[0][c] * t[0][c];
+        a.log_growth[i] = (T > 0 && n0 > 0.0) ? 0.5 * log(n1 / n0) : 0.0;
+    }
+    a.rstep[i] = rstep;
+    a.reason[i] = reason;
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kDiffBlock) diff_backward_kernel(const DiffArgs a, const ParticleConsts pc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int S = log_stride(NP);
+    double l[6];
+    for (int c = 0; c < 6; ++c) l[c] = a.grad1[6 * i + c];
+    const int64_t rstep = a.rstep[i];
+    const int reason = a.reason[i];
+    const int64_t kend = rstep >= 0 ? rstep : a.nsteps;  // steps the particle took (last one maybe partial)
+    // the last step of a removed particle stops after the drift (encounter / escape)
+    // or before it (Kepler failure / non-finite)
+    const bool cut_after_drift = rstep > 0 && reason != GLISSE_REMOVED_KEPLER && reason != GLISSE_REMOVED_NONFINITE;
+    const bool cut_before_drift = rstep > 0 && !cut_after_drift;
+    if (kend > 0) {
+        const int64_t nseg = (kend + a.K - 1) / a.K;
+        for (int64_t cseg = nseg - 1; cseg >= 0; --cseg) {
+            const int64_t k0 = cseg * a.K;
+            const int64_t k1 = min(k0 + (int64_t)a.K, kend);
+            double st[6];
+            const double* cp = a.ckpt + cseg * 6 * a.n;
+            for (int c = 0; c < 6; ++c) st[c] = cp[c * a.n + i];
+            // recompute the segment: pre-drift state (6) and post-drift position (3) per step
+            for (int64_t k = k0; k < k1; ++k) {
+                const double* L0 = a.log + k * S;
+                kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);
+                double* sc = a.scratch + (k - k0) * 9 * a.n + i;
+                for (int c = 0; c < 6; ++c) sc[c * a.n] = st[c];
+                if (k == kend - 1 && cut_before_drift) break;
+                DriftScalars d;
+                drift_scalars(pc.mu, pc.dt, st, d);
+                double pre[6];
+                for (int c = 0; c < 6; ++c) pre[c] = st[c];
+                for (int c = 0; c < 3; ++c) {
+                    st[c] = d.f * pre[c] + d.g * pre[3 + c];
+                    st[3 + c] = d.fd * pre[c] + d.gd * pre[3 + c];
+                }
+                for (int c = 0; c < 3; ++c) sc[(6 + c) * a.n] = st[c];
+                if (k + 1 < k1) kick_state<NP>(st, a.log + (k + 1) * S, pc.half_dt, pc.tgm_half, pc.rc2);
+            }
+            // adjoint sweep, last step first
+            for (int64_t k = k1 - 1; k >= k0; --k) {
+                const double* sc = a.scratch + (k - k0) * 9 * a.n + i;
+                double pre[6], post[3];
+                for (int c = 0; c < 6; ++c) pre[c] = sc[c * a.n];
+                for (int c = 0; c < 3; ++c) post[c] = sc[(6 + c) * a.n];
+                const bool last = (k == kend - 1);
+                if (!(last && (cut_after_drift || cut_before_drift))) {
+                    // closing half kick at t_{k+1}: lr += (dt/2) A(post) lv
+                    kick_jac<NP>(post, a.log + (k + 1) * S, pc.tgm_half, l + 3, l);
+                }
+                if (!(last && cut_before_drift)) {
+                    DriftScalars d;
+                    drift_scalars(pc.mu, pc.dt, pre, d);
+                    drift_adjoint(pc.mu, pre, d, l);
+                }
+                // opening half kick at t_k: lr += (dt/2) A(pre) lv
+                kick_jac<NP>(pre, a.log + k * S, pc.tgm_half, l + 3, l);
+            }
+        }
+    }
+    for (int c = 0; c < 6; ++c) a.grad0[6 * i + c] = l[c];
+}
+
+#define GLISSE_DIFF_SWITCH(KERNEL)                                         \
+    switch (np) {                                                          \
+        case 0: KERNEL<0><<<grid, kDiffBlock, 0, s>>>(a, pc); break;       \
+        case 1: KERNEL<1><<<grid, kDiffBlock, 0, s>>>(a, pc); break;       \
+        case 2: KERNEL<2><<<grid, kDiffBlock, 0, s>>>(a, pc); break;       \
+        case 3: KERNEL<3><<<grid, kDiffBlock, 0, s>>>(a, pc); break;       \
+        case 4: KERNEL<4><<<grid, kDiffBlock, 0, s>>>(a, pc); break;       \
+        case 5: KERNEL<5><<<grid, kDiffBlock, 0, s>>>(a, pc); break;       \
+        case 6: KERNEL<6><<<grid, kDiffBlock, 0, s>>>(a, pc); break;       \
+        case 7: KERNEL<7><<<grid, kDiffBlock, 0, s>>>(a, pc); break;       \
+        case 8: KERNEL<8><<<grid, kDiffBlock, 0, s>>>(a, pc); break;       \
+        default: return cudaErrorInvalidValue;                             \
+    }
+
+static cudaError_t launch_diff_forward(int np, const DiffArgs& a, const ParticleConsts& pc, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((a.n + kDiffBlock - 1) / kDiffBlock);
+    GLISSE_DIFF_SWITCH(diff_forward_kernel)
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_diff_backward(int np, const DiffArgs& a, const ParticleConsts& pc, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((a.n + kDiffBlock - 1) / kDiffBlock);
+    GLISSE_DIFF_SWITCH(diff_backward_kernel)
+    return cudaGetLastError();
+}
+
+}  // namespace glisse
+
+using namespace glisse;
+
+struct glisse_diff {
+    int device = 0;
+    int np = 0;
+    int64_t n = 0, nsteps = 0;
+    int K = 256;
+    ParticleConsts pc{};
+    double* d_log = nullptr;
+    double* d_ckpt = nullptr;
+    double* d_scratch = nullptr;
+    int64_t* d_rstep = nullptr;
+    int32_t* d_reason = nullptr;
+    bool have_forward = false;
+};
+
+static void diff_free(glisse_diff* d) {
+    if (!d) return;
+    void* ptrs[] = {d->d_log, d->d_ckpt, d->d_scratch, d->d_rstep, d->d_reason};
+    for (void* p : ptrs) cudaFree(p);
+    delete d;
+}
+
+extern "C" void glisse_diff_destroy(glisse_diff* d) { diff_free(d); }
+
+#define GD_CUDA(x)                    \
+    do {                              \
+        cudaError_t e_ = (x);         \
+        if (e_ != cudaSuccess) {      \
+            (void)cudaGetLastError(); \
+            rc = GLISSE_E_CUDA;       \
+            goto fail;                \
+        }                             \
+    } while (0)
+
+extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const double* planets, int32_t n_planets,
+                                  int64_t n_particles, double dt, int64_t n_steps, int32_t checkpoint_every,
+                                  const glisse_opts* opts) {
+    if (!out) return GLISSE_E_INVAL;
+    *out = nullptr;
+    glisse_opts o;
+    glisse_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(star_mass > 0.0) || n_planets < 0 || n_planets > GLISSE_MAX_PLANETS || (n_planets > 0 && !planets) ||
+        n_particles < 0 || n_steps < 0 || !(dt != 0.0) || !std::isfinite(dt) || checkpoint_every < 1)
+        return GLISSE_E_INVAL;
+    for (int64_t k = 0; k < 7 * (int64_t)n_planets; ++k)
+        if (!std::isfinite(planets[k])) return GLISSE_E_INVAL;
+    glisse_diff* d = new (std::nothrow) glisse_diff();
+    if (!d) return GLISSE_E_NOMEM;
+    int rc = GLISSE_OK;
+    const double G = 4.0 * 3.14159265358979323846 * 3.14159265358979323846;
+    const int S = log_stride(n_planets);
+    double* d_pl = nullptr;
+    double* d_jac = nullptr;
+    PlanetConsts* d_pc = nullptr;
+    int* d_status = nullptr;
+    PlanetConsts hpc;
+    int status = 0;
+    d->np = n_planets;
+    d->n = n_particles;
+    d->nsteps = n_steps;
+    d->K = checkpoint_every;
+    if (cudaGetDevice(&d->device) != cudaSuccess) {
+        rc = GLISSE_E_CUDA;
+        goto fail;
+    }
+    {
+        const int64_t nck = std::max<int64_t>((n_steps + d->K - 1) / d->K, 1);
+        const int64_t np1 = std::max<int64_t>(n_particles, 1);
+        if (cudaMalloc(&d->d_log, sizeof(double) * (size_t)(n_steps + 1) * S) != cudaSuccess ||
+            cudaMalloc(&d->d_ckpt, sizeof(double) * (size_t)nck * 6 * np1) != cudaSuccess ||
+            cudaMalloc(&d->d_scratch, sizeof(double) * (size_t)d->K * 9 * np1) != cudaSuccess ||
+            cudaMalloc(&d->d_rstep, sizeof(int64_t) * np1) != cudaSuccess ||
+            cudaMalloc(&d->d_reason, sizeof(int32_t) * np1) != cudaSuccess) {
+            (void)cudaGetLastError();
+            rc = GLISSE_E_NOMEM;
+            goto fail;
+        }
+    }
+    GD_CUDA(cudaMalloc(&d_pl, sizeof(double) * 7 * std::max(n_planets, 1)));
+    GD_CUDA(cudaMalloc(&d_jac, sizeof(double) * 6 * std::max(n_planets, 1)));
+    GD_CUDA(cudaMalloc(&d_pc, sizeof(PlanetConsts)));
+    GD_CUDA(cudaMalloc(&d_status, sizeof(int)));
+    if (n_planets > 0) GD_CUDA(cudaMemcpy(d_pl, planets, sizeof(double) * 7 * n_planets, cudaMemcpyHostToDevice));
+    GD_CUDA(launch_eph_setup(d_pl, n_planets, star_mass, G, o.enc_mode, o.enc_value, d_pc, d_jac, d_status, 0));
+    GD_CUDA(cudaMemcpy(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) {
+        rc = status;
+        goto fail;
+    }
+    // planet log for the whole run (the ephemeris is serial in time)
+    GD_CUDA(launch_eph_chunk(d_pc, d_jac, dt, (int)n_steps, d->d_log, nullptr, d_status, 0));
+    GD_CUDA(cudaMemcpy(&hpc, d_pc, sizeof(PlanetConsts), cudaMemcpyDeviceToHost));
+    GD_CUDA(cudaMemcpy(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) {
+        rc = status;
+        goto fail;
+    }
+    std::memset(&d->pc, 0, sizeof(d->pc));
+    d->pc.mu = hpc.mu0;
+    d->pc.dt = dt;
+    d->pc.half_dt = 0.5 * dt;
+    for (int j = 0; j < n_planets; ++j) {
+        d->pc.tgm_full[j] = dt * hpc.gm[j];
+        d->pc.tgm_half[j] = 0.5 * dt * hpc.gm[j];
+        d->pc.rc2[j] = hpc.rcrit[j] * hpc.rcrit[j];
+    }
+    d->pc.rmax2 = o.r_max > 0.0 ? o.r_max * o.r_max : 0.0;
+    d->pc.rmax = o.r_max > 0.0 ? o.r_max : 0.0;
+    cudaFree(d_pl);
+    cudaFree(d_jac);
+    cudaFree(d_pc);
+    cudaFree(d_status);
+    *out = d;
+    return GLISSE_OK;
+fail:
+    cudaFree(d_pl);
+    cudaFree(d_jac);
+    cudaFree(d_pc);
+    cudaFree(d_status);
+    diff_free(d);
+    return rc;
+}
+
+extern "C" int glisse_diff_forward(glisse_diff* d, const double* state0, double* state1, int32_t n_tangents,
+                                   const double* tangent0, double* tangent1, double* log_growth,
+                                   int64_t* removal_step, int32_t* removal_reason, void* stream) {
+    if (!d || n_tangents < 0 || n_tangents > kMaxTangents) return GLISSE_E_INVAL;
+    if (d->n > 0 && (!state0 || !state1)) return GLISSE_E_INVAL;
+    if (n_tangents > 0 && (!tangent0 || !tangent1)) return GLISSE_E_INVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DiffArgs a{};
+    a.log = d->d_log;
+    a.n = d->n;
+    a.nsteps = d->nsteps;
+    a.K = d->K;
+    a.ntan = n_tangents;
+    a.state0 = state0;
+    a.state1 = state1;
+    a.tan0 = tangent0;
+    a.tan1 = tangent1;
+    a.log_growth = log_growth;
+    a.rstep = d->d_rstep;
+    a.reason = d->d_reason;
+    a.ckpt = d->d_ckpt;
+    cudaError_t e = launch_diff_forward(d->np, a, d->pc, s);
+    if (e == cudaSuccess && removal_step && d->n > 0)
+        e = cudaMemcpyAsync(removal_step, d->d_rstep, sizeof(int64_t) * d->n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && removal_reason && d->n > 0)
+        e = cudaMemcpyAsync(removal_reason, d->d_reason, sizeof(int32_t) * d->n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GLISSE_E_CUDA;
+    }
+    d->have_forward = true;
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_diff_backward(glisse_diff* d, const double* grad_state1, double* grad_state0, void* stream) {
+    if (!d) return GLISSE_E_INVAL;
+    if (!d->have_forward) return GLISSE_E_STATE;
+    if (d->n > 0 && (!grad_state1 || !grad_state0)) return GLISSE_E_INVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DiffArgs a{};
+    a.log = d->d_log;
+    a.n = d->n;
+    a.nsteps = d->nsteps;
+    a.K = d->K;
+    a.rstep = d->d_rstep;
+    a.reason = d->d_reason;
+    a.ckpt = d->d_ckpt;
+    a.scratch = d->d_scratch;
+    a.grad1 = grad_state1;
+    a.grad0 = grad_state0;
+    cudaError_t e = launch_diff_backward(d->np, a, d->pc, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GLISSE_E_CUDA;
+    }
+    return GLISSE_OK;
+}

@@ -74,20 +74,24 @@ __device__ inline void stumpff_any(double z, double& c0, double& c1, double& c2,
 // Newton would leave the bracket or fails to halve the previous step).
 // Returns false if it does not converge within the iteration budget.
 // ---------------------------------------------------------------------------
-__device__ inline bool drift_general(double mu, double dt, double& x, double& y, double& z, double& vx, double& vy,
-                                     double& vz) {
-    const double r0 = sqrt(x * x + y * y + z * z);
-    const double v2 = vx * vx + vy * vy + vz * vz;
-    const double u = x * vx + y * vy + z * vz;
-    if (!(r0 > 0.0) || !isfinite(r0) || !isfinite(v2)) return false;
-    const double beta = 2.0 * mu / r0 - v2;
-    double tau = dt;
+// Solve T(s) = r0 G1 + u G2 + mu G3 = tau for s, where tau is dt minus whole
+// periods for bound orbits (k periods removed; tau = dt - k P).  Newton with a
+// bisection safeguard.  Returns false if it does not converge.
+__device__ inline bool universal_solve(double mu, double dt, double r0, double u, double beta, double& s_out,
+                                       double& tau_out, double& k_out) {
+    double tau = dt, kper = 0.0;
     if (beta > 0.0) {
         const double n = beta * sqrt(beta) / mu;  // mean motion sqrt(mu alpha^3), alpha = beta / mu
         const double period = 6.283185307179586476925286766559 / n;
-        tau = dt - period * rint(dt / period);
+        kper = rint(dt / period);
+        tau = dt - period * kper;
     }
-    if (tau == 0.0) return true;
+    tau_out = tau;
+    k_out = kper;
+    if (tau == 0.0) {
+        s_out = 0.0;
+        return true;
+    }
     const double sgn = tau > 0.0 ? 1.0 : -1.0;
     double c0, c1, c2, c3;
     // bracket: T(0) = 0 and T increases with s
@@ -109,7 +113,6 @@ __device__ inline bool drift_general(double mu, double dt, double& x, double& y,
     double s = tau / r0;
     if (!(s > lo && s < hi)) s = 0.5 * (lo + hi);
     double dsold = hi - lo;
-    bool conv = false;
     for (int it = 0; it < 300; ++it) {
         stumpff_any(beta * s * s, c0, c1, c2, c3);
         const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
@@ -124,9 +127,8 @@ __device__ inline bool drift_general(double mu, double dt, double& x, double& y,
         // a step below the tolerance is converged; test it before the safeguard,
         // since s + ds can round onto a bracket end and look like an escape
         if (fabs(ds) <= 1e-15 * fabs(s)) {
-            s += ds;
-            conv = true;
-            break;
+            s_out = s + ds;
+            return true;
         }
         double sn = s + ds;
         if (!(sn > lo && sn < hi) || fabs(ds) > 0.5 * fabs(dsold)) {
@@ -136,11 +138,28 @@ __device__ inline bool drift_general(double mu, double dt, double& x, double& y,
         dsold = ds;
         s = sn;
         if ((hi - lo) <= 1e-15 * fabs(s)) {
-            conv = true;
-            break;
+            s_out = s;
+            return true;
         }
     }
-    if (!conv) return false;
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// General solver: any orbit, any dt.  Bound orbits first drop whole periods.
+// Returns false if the solve does not converge within the iteration budget.
+// ---------------------------------------------------------------------------
+__device__ inline bool drift_general(double mu, double dt, double& x, double& y, double& z, double& vx, double& vy,
+                                     double& vz) {
+    const double r0 = sqrt(x * x + y * y + z * z);
+    const double v2 = vx * vx + vy * vy + vz * vz;
+    const double u = x * vx + y * vy + z * vz;
+    if (!(r0 > 0.0) || !isfinite(r0) || !isfinite(v2)) return false;
+    const double beta = 2.0 * mu / r0 - v2;
+    double s, tau, kper;
+    if (!universal_solve(mu, dt, r0, u, beta, s, tau, kper)) return false;
+    if (tau == 0.0) return true;
+    double c0, c1, c2, c3;
     stumpff_any(beta * s * s, c0, c1, c2, c3);
     const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
     const double r = r0 * c0 + u * G1 + mu * G2;
@@ -276,6 +295,154 @@ __device__ __forceinline__ void radius_of(double x, double y, double z, double& 
     const double r2 = fma(x, x, fma(y, y, z * z));
     rinv = rsqrt_full(r2);
     r = r2 * rinv;
+}
+
+// ---------------------------------------------------------------------------
+// Derivatives of the drift (tangent and adjoint maps).
+//
+// With G_n(s, beta) = s^n c_n(beta s^2):  dG_n/ds = G_{n-1} (dG_0/ds = -beta G_1)
+// and dG_n/dbeta = -(s G_{n+1} - n G_{n+2}) / 2 (from the series term by term).
+// s solves T(s) = r0 G1 + u G2 + mu G3 = tau with tau = dt - k P(beta),
+// P = 2 pi mu beta^(-3/2), so by implicit differentiation
+//   ds = (dtau - G1 dr0 - G2 du - T_beta dbeta) / R,   R = T'(s),
+//   T_beta = r0 G1_beta + u G2_beta + mu G3_beta,   dtau = 1.5 k P dbeta / beta,
+// and r0 = |r|, u = r . v, beta = 2 mu / r0 - v . v.
+// ---------------------------------------------------------------------------
+// c0..c5 for any z (c4, c5 by series below |z| = 0.1, else c_{n+2} = (1/n! - c_n) / z).
+__device__ inline void stumpff_all(double z, double c[6]) {
+    stumpff_any(z, c[0], c[1], c[2], c[3]);
+    if (fabs(z) <= 0.1) {
+        // c4 = sum (-z)^n / (2n+4)!, c5 = sum (-z)^n / (2n+5)!, n = 0..7
+        const double a4[8] = {1.0 / 24.0, -1.0 / 720.0, 1.0 / 40320.0, -1.0 / 3628800.0, 1.0 / 479001600.0,
+                              -1.0 / 87178291200.0, 1.0 / 20922789888000.0, -1.0 / 6402373705728000.0};
+        const double a5[8] = {1.0 / 120.0, -1.0 / 5040.0, 1.0 / 362880.0, -1.0 / 39916800.0, 1.0 / 6227020800.0,
+                              -1.0 / 1307674368000.0, 1.0 / 355687428096000.0, -1.0 / 121645100408832000.0};
+        double p = a4[7], q = a5[7];
+        for (int n = 6; n >= 0; --n) {
+            p = fma(p, z, a4[n]);
+            q = fma(q, z, a5[n]);
+        }
+        c[4] = p;
+        c[5] = q;
+    } else {
+        c[4] = (0.5 - c[2]) / z;
+        c[5] = (1.0 / 6.0 - c[3]) / z;
+    }
+}
+
+struct DriftScalars {
+    double r0, u, beta, tau, dtau_dbeta, s;
+    double G[6], Gb[4];  // G_0..G_5 and dG_n/dbeta, n = 0..3
+    double R, f, g, fd, gd;
+};
+
+// Drift scalars of one body at its current state (general solver; FP64 throughout).
+__device__ inline bool drift_scalars(double mu, double dt, const double st[6], DriftScalars& d) {
+    d.r0 = sqrt(st[0] * st[0] + st[1] * st[1] + st[2] * st[2]);
+    const double v2 = st[3] * st[3] + st[4] * st[4] + st[5] * st[5];
+    d.u = st[0] * st[3] + st[1] * st[4] + st[2] * st[5];
+    d.beta = 2.0 * mu / d.r0 - v2;
+    double kper;
+    if (!universal_solve(mu, dt, d.r0, d.u, d.beta, d.s, d.tau, kper)) return false;
+    d.dtau_dbeta = 0.0;
+    if (kper != 0.0) {
+        const double period = 6.283185307179586476925286766559 * mu / (d.beta * sqrt(d.beta));
+        d.dtau_dbeta = 1.5 * kper * period / d.beta;
+    }
+    double c[6];
+    stumpff_all(d.beta * d.s * d.s, c);
+    double sp = 1.0;
+    for (int n = 0; n < 6; ++n) {
+        d.G[n] = sp * c[n];
+        sp *= d.s;
+    }
+    for (int n = 0; n < 4; ++n) d.Gb[n] = -0.5 * (d.s * d.G[n + 1] - n * d.G[n + 2]);
+    d.R = d.r0 * d.G[0] + d.u * d.G[1] + mu * d.G[2];
+    d.f = 1.0 - mu * d.G[2] / d.r0;
+    d.g = d.tau - mu * d.G[3];
+    d.fd = -mu * d.G[1] / (d.R * d.r0);
+    d.gd = 1.0 - mu * d.G[2] / d.R;
+    return true;
+}
+
+// Tangent of the drift: (dr, dv) at the start -> (dr1, dv1) at the end (in place).
+__device__ inline void drift_tangent(double mu, const double st[6], const DriftScalars& d, double t[6]) {
+    const double *r = st, *v = st + 3;
+    const double dr0 = (r[0] * t[0] + r[1] * t[1] + r[2] * t[2]) / d.r0;
+    const double du = (t[0] * v[0] + t[1] * v[1] + t[2] * v[2]) + (r[0] * t[3] + r[1] * t[4] + r[2] * t[5]);
+    const double dbeta = -2.0 * mu * dr0 / (d.r0 * d.r0) - 2.0 * (v[0] * t[3] + v[1] * t[4] + v[2] * t[5]);
+    const double dtau = d.dtau_dbeta * dbeta;
+    const double Tb = d.r0 * d.Gb[1] + d.u * d.Gb[2] + mu * d.Gb[3];
+    const double ds = (dtau - d.G[1] * dr0 - d.G[2] * du - Tb * dbeta) / d.R;
+    const double dG0 = -d.beta * d.G[1] * ds + d.Gb[0] * dbeta;
+    const double dG1 = d.G[0] * ds + d.Gb[1] * dbeta;
+    const double dG2 = d.G[1] * ds + d.Gb[2] * dbeta;
+    const double dG3 = d.G[2] * ds + d.Gb[3] * dbeta;
+    const double df = -mu * (dG2 - d.G[2] * dr0 / d.r0) / d.r0;
+    const double dg = dtau - mu * dG3;
+    const double dR = dr0 * d.G[0] + d.r0 * dG0 + du * d.G[1] + d.u * dG1 + mu * dG2;
+    const double dfd = -mu * (dG1 - d.G[1] * (dR / d.R + dr0 / d.r0)) / (d.R * d.r0);
+    const double dgd = -mu * (dG2 - d.G[2] * dR / d.R) / d.R;
+    double o[6];
+    for (int i = 0; i < 3; ++i) {
+        o[i] = df * r[i] + d.f * t[i] + dg * v[i] + d.g * t[3 + i];
+        o[3 + i] = dfd * r[i] + d.fd * t[i] + dgd * v[i] + d.gd * t[3 + i];
+    }
+    for (int i = 0; i < 6; ++i) t[i] = o[i];
+}
+
+// Adjoint of the drift: cotangent (lr1, lv1) at the end -> (lr, lv) at the start (in place).
+__device__ inline void drift_adjoint(double mu, const double st[6], const DriftScalars& d, double l[6]) {
+    const double *r = st, *v = st + 3;
+    const double lf = l[0] * r[0] + l[1] * r[1] + l[2] * r[2];
+    const double lg = l[0] * v[0] + l[1] * v[1] + l[2] * v[2];
+    const double lfd = l[3] * r[0] + l[4] * r[1] + l[5] * r[2];
+    const double lgd = l[3] * v[0] + l[4] * v[1] + l[5] * v[2];
+    double lr[3], lv[3];
+    for (int i = 0; i < 3; ++i) {
+        lr[i] = d.f * l[i] + d.fd * l[3 + i];
+        lv[i] = d.g * l[i] + d.gd * l[3 + i];
+    }
+    // f = 1 - mu G2 / r0;  g = tau - mu G3;  fd = -mu G1 / (R r0);  gd = 1 - mu G2 / R
+    double lG0 = 0.0, lG1 = 0.0, lG2 = 0.0, lG3 = 0.0, lR = 0.0, lr0 = 0.0, lu = 0.0, lbeta = 0.0;
+    double ltau = lg;
+    lG2 += -mu * lf / d.r0;
+    lr0 += mu * d.G[2] * lf / (d.r0 * d.r0);
+    lG3 += -mu * lg;
+    lG1 += -mu * lfd / (d.R * d.r0);
+    lR += -d.fd * lfd / d.R;
+    lr0 += -d.fd * lfd / d.r0;
+    lG2 += -mu * lgd / d.R;
+    lR += mu * d.G[2] * lgd / (d.R * d.R);
+    // R = r0 G0 + u G1 + mu G2
+    lr0 += d.G[0] * lR;
+    lG0 += d.r0 * lR;
+    lu += d.G[1] * lR;
+    lG1 += d.u * lR;
+    lG2 += mu * lR;
+    // G_n(s, beta)
+    const double ls = -d.beta * d.G[1] * lG0 + d.G[0] * lG1 + d.G[1] * lG2 + d.G[2] * lG3;
+    lbeta += d.Gb[0] * lG0 + d.Gb[1] * lG1 + d.Gb[2] * lG2 + d.Gb[3] * lG3;
+    // s(tau, r0, u, beta)
+    const double Tb = d.r0 * d.Gb[1] + d.u * d.Gb[2] + mu * d.Gb[3];
+    ltau += ls / d.R;
+    lr0 += -d.G[1] * ls / d.R;
+    lu += -d.G[2] * ls / d.R;
+    lbeta += -Tb * ls / d.R;
+    // tau(beta)
+    lbeta += d.dtau_dbeta * ltau;
+    // beta(r0, v) = 2 mu / r0 - v.v
+    lr0 += -2.0 * mu * lbeta / (d.r0 * d.r0);
+    for (int i = 0; i < 3; ++i) lv[i] += -2.0 * lbeta * v[i];
+    // u = r . v ; r0 = |r|
+    for (int i = 0; i < 3; ++i) {
+        lr[i] += lu * v[i] + lr0 * r[i] / d.r0;
+        lv[i] += lu * r[i];
+    }
+    for (int i = 0; i < 3; ++i) {
+        l[i] = lr[i];
+        l[3 + i] = lv[i];
+    }
 }
 
 }  // namespace glisse

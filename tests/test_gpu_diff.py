@@ -1,0 +1,168 @@
+"""Tangent and adjoint maps on the GPU (glisse_diff_*), through the C ABI.
+
+Checked against the oracle's complex-step tangent map, central finite
+differences (h = 1e-7 AU), the symplectic structure of the Jacobian, the
+dot-product identity <g, J t> = <J^T g, t> between the two kernels, and the
+independence of the gradient from the checkpoint interval; the
+torch.autograd.Function is checked against the tangent kernel.
+"""
+import numpy as np
+import pytest
+
+import glisse_inputs as gi
+import parity
+
+pytestmark = pytest.mark.gpu
+
+OMEGA = np.block([[np.zeros((3, 3)), np.eye(3)], [-np.eye(3), np.zeros((3, 3))]])
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2011_03484_gb300 as G
+
+    G._build.build()
+    G.load()
+    return G
+
+
+def _workload(n):
+    w = gi.make("diff", n=n)
+    return w, w["planets"], w["particles"]
+
+
+def _cuda(a):
+    import torch
+
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def gpu_jacobian(G, pl, s0, dt, n_steps, K=256):
+    import torch
+
+    n = s0.shape[0]
+    dm = G.DiffMap(1.0, pl, n, dt, n_steps, K)
+    e = np.zeros((6, n, 6))
+    for c in range(6):
+        e[c, :, c] = 1.0
+    s1, t1, growth, rstep, reason = dm.forward(_cuda(s0), _cuda(e))
+    dm.close()
+    J = t1.cpu().numpy().transpose(1, 2, 0)  # [n][6 out][6 in]
+    return s1.cpu().numpy(), J, rstep.cpu().numpy(), reason.cpu().numpy()
+
+
+def test_tangent_matches_oracle_complex_step(G, orc):
+    """64 particles of the 65536-particle differentiation workload over 10^4 steps."""
+    w, pl, s0 = _workload(64)
+    n = 10_000
+    s1, J, rstep, reason = gpu_jacobian(G, pl, s0, w["dt"], n)
+    _, log, _ = orc.planet_wh(1.0, pl, w["dt"], n)
+    rc = orc.rcrit(1.0, pl)
+    Jo = orc.particles_jacobian(1.0, pl[:, 0], log, w["dt"], s0, rc, 1000.0)
+    o = orc.run(1.0, pl, s0, w["dt"], n)
+    np.testing.assert_array_equal(rstep, o["removal_step"])
+    # relative to each particle's Jacobian scale; chaotic particles amplify rounding in J as in the state
+    err = np.abs(J - Jo).max(axis=(1, 2)) / np.abs(Jo).max(axis=(1, 2))
+    regular = (o["closest"] >= 25.0) & (o["removal_step"] < 0)
+    print("tangent rel err: regular max", err[regular].max(), "all median", np.median(err))
+    assert regular.sum() > 10
+    assert err[regular].max() < 1e-8
+    assert np.median(err) < 1e-8
+
+
+def test_jacobian_is_symplectic(G):
+    w, pl, s0 = _workload(128)
+    _, J, rstep, _ = gpu_jacobian(G, pl, s0, w["dt"], 3000)
+    for p in np.where(rstep < 0)[0]:
+        M = J[p].T @ OMEGA @ J[p]
+        assert np.abs(M - OMEGA).max() < 1e-12 * max(1.0, np.abs(J[p]).max() ** 2), p
+
+
+def test_tangent_matches_central_differences(G):
+    import torch
+
+    w, pl, s0 = _workload(32)
+    n = 2000
+    _, J, rstep, _ = gpu_jacobian(G, pl, s0, w["dt"], n)
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n)
+    h = 1e-7  # AU
+    for c in range(3):
+        e = np.zeros_like(s0)
+        e[:, c] = h
+        sp = dm.forward(_cuda(s0 + e))[0].cpu().numpy()
+        sm = dm.forward(_cuda(s0 - e))[0].cpu().numpy()
+        fd = (sp - sm) / (2 * h)
+        err = np.abs(fd - J[:, :, c]).max(axis=1) / np.abs(J).max(axis=(1, 2))
+        assert err[rstep < 0].max() < 1e-5, (c, err.max())
+    dm.close()
+
+
+def test_adjoint_is_the_transpose_of_the_tangent(G):
+    """<g, J t> = <J^T g, t> per particle, with J t from the forward kernel and J^T g from the backward one."""
+    import torch
+
+    w, pl, s0 = _workload(2048)
+    n = 3000
+    rng = np.random.default_rng(5)
+    t = rng.normal(size=s0.shape)
+    g = rng.normal(size=s0.shape)
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n, 128)
+    s1, t1, _, rstep, _ = dm.forward(_cuda(s0), _cuda(t[None]))
+    gT = dm.backward(_cuda(g)).cpu().numpy()
+    dm.close()
+    Jt = t1[0].cpu().numpy()
+    lhs = (g * Jt).sum(axis=1)
+    rhs = (gT * t).sum(axis=1)
+    scale = np.abs(g).sum(axis=1) * np.abs(Jt).max(axis=1) + np.abs(gT).max(axis=1) * np.abs(t).sum(axis=1)
+    rel = np.abs(lhs - rhs) / scale
+    print("dot-product test: max", rel.max(), "removed", int((rstep.cpu().numpy() >= 0).sum()))
+    assert rel.max() < 1e-11
+
+
+def test_gradient_independent_of_checkpoint_interval(G):
+    w, pl, s0 = _workload(256)
+    n = 700
+    g = np.random.default_rng(6).normal(size=s0.shape)
+    outs = []
+    for K in (1, 7, 256, 1000):
+        dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n, K)
+        dm.forward(_cuda(s0))
+        outs.append(dm.backward(_cuda(g)).cpu().numpy())
+        dm.close()
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+
+
+def test_autograd_function(G):
+    import torch
+
+    w, pl, s0 = _workload(64)
+    n = 1000
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n)
+    x = _cuda(s0).requires_grad_(True)
+    s1, growth = G.glisse_map().apply(x, dm)
+    wgt = _cuda(np.random.default_rng(7).normal(size=s0.shape))
+    (s1 * wgt).sum().backward()
+    _, J, rstep, _ = gpu_jacobian(G, pl, s0, w["dt"], n)
+    ref = np.einsum("pij,pi->pj", J, wgt.cpu().numpy())
+    got = x.grad.cpu().numpy()
+    err = np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)
+    assert err.max() < 1e-10, err.max()
+    assert torch.isfinite(growth).all() and growth.requires_grad is False
+    dm.close()
+
+
+def test_removed_particles_have_frozen_state_derivatives(G, orc):
+    """Particles removed at t_0 map to themselves: identity Jacobian and gradient."""
+    w, pl, s0 = _workload(16)
+    rc = orc.rcrit(1.0, pl)
+    s0 = s0.copy()
+    s0[0, :3] = pl[2, 1:4] + [0.3 * rc[2], 0, 0]
+    s0[0, 3:] = pl[2, 4:7]
+    s1, J, rstep, reason = gpu_jacobian(G, pl, s0, w["dt"], 200)
+    assert rstep[0] == 0 and reason[0] == 3
+    np.testing.assert_array_equal(s1[0], s0[0])
+    np.testing.assert_array_equal(J[0], np.eye(6))
