@@ -24,6 +24,9 @@ _lib = None
 
 ALIVE, ESCAPE, KEPLER, NONFINITE = 0, -1, -2, -3
 
+# convergence required of the paper's fixed-iteration Kepler solve (section 2.2)
+PAPER_KEPLER_TOL = 1e-14
+
 
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC"]
 
@@ -92,6 +95,12 @@ def _bind(L):
     L.orc_particles.argtypes = [C.c_double, C.c_int, dp, dp, C.c_int64, C.c_double, dp, C.c_double, dp,
                                 C.c_int64, i64p, i32p, dp, dp, C.c_int64, C.c_int, C.c_int]
     L.orc_particles.restype = C.c_int
+    L.orc_kepler_drift_fixed.argtypes = [C.c_double, C.c_double, dp, C.c_int, C.c_double, dp]
+    L.orc_kepler_drift_fixed.restype = C.c_int
+    L.orc_particles_ex.argtypes = [C.c_double, C.c_int, dp, dp, C.c_int64, C.c_double, dp, C.c_double, dp,
+                                   C.c_int64, i64p, i32p, dp, dp, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_double,
+                                   dp]
+    L.orc_particles_ex.restype = C.c_int
     L.orc_max_threads.restype = C.c_int
     L.orc_particles_jvp.argtypes = [C.c_double, C.c_int, dp, dp, C.c_int64, C.c_double, dp, C.c_double, dp, dp,
                                     C.c_int64, dp, dp, i64p, i32p, C.c_int, C.c_int]
@@ -123,6 +132,14 @@ def kepler_drift(mu: float, state, dt: float):
     return st, rc, lib().orc_last_iters()
 
 
+def kepler_drift_fixed(mu: float, state, dt: float, iters: int = 5, tol: float = PAPER_KEPLER_TOL):
+    """The paper's fixed-iteration drift. Returns (new_state, status, |last Newton step|)."""
+    st = _f64(state, (6,)).copy()
+    ldx = C.c_double()
+    rc = lib().orc_kepler_drift_fixed(float(mu), float(dt), _dp(st), int(iters), float(tol), C.byref(ldx))
+    return st, rc, ldx.value
+
+
 def planet_wh(star_mass: float, planets, dt: float, n_steps: int, want_log: bool = True, want_energy: bool = False):
     """Advance the planets n_steps.  Returns (planets_out [np][7], log [n+1][np][3] or None, energy or None)."""
     pl = _f64(planets).copy()
@@ -148,7 +165,10 @@ def rcrit(star_mass: float, planets, mode: int = 0, value: float = 1.0):
 class ParticleRun:
     """State of an oracle particle integration that can be advanced in pieces."""
 
-    def __init__(self, star_mass, planet_masses, state, rcrit_, r_max):
+    def __init__(self, star_mass, planet_masses, state, rcrit_, r_max, kepler_iters=0,
+                 kepler_tol=PAPER_KEPLER_TOL):
+        """kepler_iters > 0 selects the paper's fixed-iteration Kepler solve with that many
+        Newton steps (kepler_dx then records the largest |last step| seen per particle)."""
         self.m0 = float(star_mass)
         self.pm = _f64(planet_masses).copy()
         self.state = _f64(state).reshape(-1, 6).copy()
@@ -161,36 +181,41 @@ class ParticleRun:
         self.r_max = float(r_max)
         self.step = 0
         self.tested_first = False
+        self.kepler_iters = int(kepler_iters)
+        self.kepler_tol = float(kepler_tol)
+        self.kepler_dx = np.zeros(n)
 
     def advance(self, log, dt: float, nthreads: int = 0):
         """Advance by len(log)-1 steps using planet positions log[0..n] (log[0] at the current step)."""
         log = _f64(log)
         n = log.shape[0] - 1
         npl = self.pm.shape[0]
-        rc = lib().orc_particles(self.m0, npl, _dp(self.pm), _dp(log), int(n), float(dt), _dp(self.rcrit),
-                                 self.r_max, _dp(self.state), self.state.shape[0],
-                                 self.removal_step.ctypes.data_as(C.POINTER(C.c_int64)),
-                                 self.reason.ctypes.data_as(C.POINTER(C.c_int32)), _dp(self.margin),
-                                 _dp(self.closest), int(self.step), 0 if self.tested_first else 1, int(nthreads))
+        rc = lib().orc_particles_ex(self.m0, npl, _dp(self.pm), _dp(log), int(n), float(dt), _dp(self.rcrit),
+                                    self.r_max, _dp(self.state), self.state.shape[0],
+                                    self.removal_step.ctypes.data_as(C.POINTER(C.c_int64)),
+                                    self.reason.ctypes.data_as(C.POINTER(C.c_int32)), _dp(self.margin),
+                                    _dp(self.closest), int(self.step), 0 if self.tested_first else 1, int(nthreads),
+                                    self.kepler_iters, self.kepler_tol, _dp(self.kepler_dx))
         if rc != 0:
-            raise RuntimeError(f"orc_particles failed: {rc}")
+            raise RuntimeError(f"orc_particles_ex failed: {rc}")
         self.tested_first = True
         self.step += n
         return self
 
 
-def run(star_mass, planets, particles, dt, n_steps, k_hill=1.0, r_max=1000.0, enc_mode=0, nthreads=0):
+def run(star_mass, planets, particles, dt, n_steps, k_hill=1.0, r_max=1000.0, enc_mode=0, nthreads=0,
+        kepler_iters=0):
     """Whole-run convenience: planets and particles from a heliocentric start.
 
     Returns a dict with the final particle state [n][6], removal_step, reason, margin, closest,
-    the planet log [n+1][np][3] and the final planets [np][7]."""
+    kepler_dx (fixed-iteration mode only), the planet log [n+1][np][3] and the final planets [np][7]."""
     pl0 = _f64(planets)
     rc_ = rcrit(star_mass, pl0, enc_mode, k_hill)
     pl1, log, _ = planet_wh(star_mass, pl0, dt, n_steps)
-    pr = ParticleRun(star_mass, pl0[:, 0], particles, rc_, r_max)
+    pr = ParticleRun(star_mass, pl0[:, 0], particles, rc_, r_max, kepler_iters=kepler_iters)
     pr.advance(log, dt, nthreads)
     return {"state": pr.state, "removal_step": pr.removal_step, "reason": pr.reason, "margin": pr.margin,
-            "closest": pr.closest, "log": log, "planets": pl1, "rcrit": rc_}
+            "closest": pr.closest, "kepler_dx": pr.kepler_dx, "log": log, "planets": pl1, "rcrit": rc_}
 
 
 def particles_jvp(star_mass, planet_masses, log, dt, state0, direction, rcrit_, r_max, test_first=True,

@@ -258,6 +258,78 @@ int orc_kepler_drift(double mu, double dt, double* st)
 int orc_last_iters(void) { return g_last_iters; }
 
 /* ------------------------------------------------------------------------ */
+/* The paper's own solver (section 2.2): Newton's method on Kepler's         */
+/* equation with a fixed, user-set number of iterations (five by default),   */
+/* started from a "judicious" guess; a particle whose solve has not reached  */
+/* the 1e-14 convergence the paper quotes is deactivated.                    */
+/* Readings: the equation is taken in the difference form of drift_dE,       */
+/*     F(x) = x - ec sin x + es (1 - cos x) - dM,                            */
+/* the guess is x0 = dM / (1 - ec) (dM reduced to [-pi, pi]), every         */
+/* iteration is a plain Newton step x <- x - F(x)/F'(x) with no safeguard,   */
+/* and "converged" means the last step satisfies |dx| <= tol (absolute, in   */
+/* radians).  Orbits outside the eccentric-anomaly branch (unbound or nearly */
+/* radial) are not covered by the paper and use the converged universal-     */
+/* variable drift.  *last_dx receives |dx| of the last step (0 when the      */
+/* universal branch ran).                                                    */
+/* ------------------------------------------------------------------------ */
+static int drift_dE_fixed(double mu, double dt, double* st, double r0, double u, double alpha, int iters,
+                          double tol, double* last_dx)
+{
+    double a = 1.0 / alpha;
+    double n = sqrt(mu / (a * a * a));
+    double ec = 1.0 - r0 / a;
+    double es = u / (n * a * a);
+    double dM = n * dt;
+    double k = floor(dM / (2.0 * ORC_PI) + 0.5);
+    dM = dM - k * (2.0 * ORC_PI);
+    double x = dM / (1.0 - ec);
+    double dx = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        double s = sin(x), c = cos(x);
+        double F = x - ec * s + es * (1.0 - c) - dM;
+        double Fp = 1.0 - ec * c + es * s;
+        dx = -F / Fp;
+        x = x + dx;
+    }
+    g_last_iters = iters;
+    *last_dx = fabs(dx);
+    if (!(fabs(dx) <= tol)) return ORC_EKEPLER;
+    double s = sin(x), c = cos(x);
+    double omc = 1.0 - c;
+    double f = 1.0 - (a / r0) * omc;
+    double g = (dM - (x - s)) / n;
+    double r = a * (1.0 - ec * c + es * s);
+    double fd = -n * a * a * s / (r * r0);
+    double gd = 1.0 - (a / r) * omc;
+    double x0 = st[0], y0 = st[1], z0 = st[2], vx = st[3], vy = st[4], vz = st[5];
+    st[0] = f * x0 + g * vx;
+    st[1] = f * y0 + g * vy;
+    st[2] = f * z0 + g * vz;
+    st[3] = fd * x0 + gd * vx;
+    st[4] = fd * y0 + gd * vy;
+    st[5] = fd * z0 + gd * vz;
+    return ORC_OK;
+}
+
+/* Public: drift with the paper's fixed-iteration solve (see above).  Returns
+ * 0, ORC_EKEPLER when the last Newton step exceeds tol (st unchanged), or
+ * ORC_ENONFINITE on bad input. */
+int orc_kepler_drift_fixed(double mu, double dt, double* st, int iters, double tol, double* last_dx)
+{
+    *last_dx = 0.0;
+    if (iters < 1) return ORC_EINVAL;
+    for (int i = 0; i < 6; ++i) if (!isfinite(st[i])) return ORC_ENONFINITE;
+    double r0 = sqrt(st[0] * st[0] + st[1] * st[1] + st[2] * st[2]);
+    if (!(r0 > 0.0)) return ORC_ENONFINITE;
+    double v2 = st[3] * st[3] + st[4] * st[4] + st[5] * st[5];
+    double u = st[0] * st[3] + st[1] * st[4] + st[2] * st[5];
+    double alpha = 2.0 / r0 - v2 / mu;
+    if (alpha > 0.0 && r0 * alpha >= 1e-3) return drift_dE_fixed(mu, dt, st, r0, u, alpha, iters, tol, last_dx);
+    if (dt == 0.0) return ORC_OK;
+    return drift_univ(mu, dt, st, r0, u, alpha);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Planets: Wisdom-Holman MVS in Jacobi coordinates (section 2.2).            */
 /* Index convention: planets 1..np (array index 0..np-1), star 0.            */
 /*   eta_i = m0 + sum_{j<=i} m_j                                             */
@@ -526,11 +598,12 @@ static int particle_test(int np, const double* pos, const double* rc2, double rm
  *   test_first: test at t_0 before the first step
  *   nthreads: OpenMP threads (<= 0: library default)
  */
-int orc_particles(double m0, int np, const double* pmass, const double* log_pos, int64_t nsteps, double dt,
-                  const double* rcrit, double rmax, double* state, int64_t npart, int64_t* removal_step,
-                  int32_t* reason, double* margin, double* closest, int64_t step0, int test_first, int nthreads)
+int orc_particles_ex(double m0, int np, const double* pmass, const double* log_pos, int64_t nsteps, double dt,
+                     const double* rcrit, double rmax, double* state, int64_t npart, int64_t* removal_step,
+                     int32_t* reason, double* margin, double* closest, int64_t step0, int test_first, int nthreads,
+                     int kepler_iters, double kepler_tol, double* kepler_dx)
 {
-    if (np < 0 || np > ORC_MAXP || nsteps < 0 || npart < 0) return ORC_EINVAL;
+    if (np < 0 || np > ORC_MAXP || nsteps < 0 || npart < 0 || kepler_iters < 0) return ORC_EINVAL;
     double Gm[ORC_MAXP], rc2[ORC_MAXP];
     for (int j = 0; j < np; ++j) { Gm[j] = ORC_G * pmass[j]; rc2[j] = rcrit[j] * rcrit[j]; }
     double rmax2 = rmax > 0.0 ? rmax * rmax : 0.0;
@@ -545,6 +618,7 @@ int orc_particles(double m0, int np, const double* pmass, const double* log_pos,
         double st[6];
         memcpy(st, state + 6 * p, sizeof st);
         double mg = margin[p], cl = closest[p];
+        double kdx = kepler_dx ? kepler_dx[p] : 0.0;
         int64_t rstep = -1;
         int rsn = 0;
         if (test_first) {
@@ -559,7 +633,14 @@ int orc_particles(double m0, int np, const double* pmass, const double* log_pos,
             particle_accel(np, Gm, P0, st, a);
             for (int d = 0; d < 3; ++d) st[3 + d] += 0.5 * dt * a[d];
             memcpy(saved, st, sizeof st);
-            int rc = orc_kepler_drift(mu, dt, st);
+            int rc;
+            if (kepler_iters > 0) {
+                double ldx;
+                rc = orc_kepler_drift_fixed(mu, dt, st, kepler_iters, kepler_tol, &ldx);
+                if (ldx > kdx) kdx = ldx;
+            } else {
+                rc = orc_kepler_drift(mu, dt, st);
+            }
             int bad = 0;
             for (int d = 0; d < 6; ++d) if (!isfinite(st[d])) bad = 1;
             if (rc == ORC_EKEPLER || rc == ORC_ENONFINITE || bad) {
@@ -578,15 +659,25 @@ int orc_particles(double m0, int np, const double* pmass, const double* log_pos,
         reason[p] = rsn;
         margin[p] = mg;
         closest[p] = cl;
+        if (kepler_dx) kepler_dx[p] = kdx;
     }
     return ORC_OK;
 }
 
+int orc_particles(double m0, int np, const double* pmass, const double* log_pos, int64_t nsteps, double dt,
+                  const double* rcrit, double rmax, double* state, int64_t npart, int64_t* removal_step,
+                  int32_t* reason, double* margin, double* closest, int64_t step0, int test_first, int nthreads)
+{
+    return orc_particles_ex(m0, np, pmass, log_pos, nsteps, dt, rcrit, rmax, state, npart, removal_step, reason,
+                            margin, closest, step0, test_first, nthreads, 0, 0.0, NULL);
+}
+
 /* Convenience: planets and particles together for nsteps from a heliocentric
  * start, exactly as a user of the library would run them. */
-int orc_run(double m0, int np, double* pl, double dt, int64_t nsteps, const double* rcrit, double rmax,
-            double* state, int64_t npart, int64_t* removal_step, int32_t* reason, double* margin, double* closest,
-            int test_first, int nthreads)
+int orc_run_ex(double m0, int np, double* pl, double dt, int64_t nsteps, const double* rcrit, double rmax,
+               double* state, int64_t npart, int64_t* removal_step, int32_t* reason, double* margin,
+               double* closest, int test_first, int nthreads, int kepler_iters, double kepler_tol,
+               double* kepler_dx)
 {
     double* log = (double*)malloc(sizeof(double) * (size_t)(nsteps + 1) * 3 * (np > 0 ? np : 1));
     if (!log) return ORC_EINVAL;
@@ -594,10 +685,18 @@ int orc_run(double m0, int np, double* pl, double dt, int64_t nsteps, const doub
     for (int j = 0; j < np; ++j) pm[j] = pl[7 * j];
     int rc = orc_planet_wh(m0, np, pl, dt, nsteps, log, NULL);
     if (rc == 0)
-        rc = orc_particles(m0, np, pm, log, nsteps, dt, rcrit, rmax, state, npart, removal_step, reason, margin,
-                           closest, 0, test_first, nthreads);
+        rc = orc_particles_ex(m0, np, pm, log, nsteps, dt, rcrit, rmax, state, npart, removal_step, reason,
+                              margin, closest, 0, test_first, nthreads, kepler_iters, kepler_tol, kepler_dx);
     free(log);
     return rc;
+}
+
+int orc_run(double m0, int np, double* pl, double dt, int64_t nsteps, const double* rcrit, double rmax,
+            double* state, int64_t npart, int64_t* removal_step, int32_t* reason, double* margin, double* closest,
+            int test_first, int nthreads)
+{
+    return orc_run_ex(m0, np, pl, dt, nsteps, rcrit, rmax, state, npart, removal_step, reason, margin, closest,
+                      test_first, nthreads, 0, 0.0, NULL);
 }
 
 int orc_max_threads(void)

@@ -11,6 +11,7 @@ import os
 import pytest
 
 import oracle
+import test_oracle_paper_mode as PM
 import test_oracle_pins as P
 import test_oracle_tangent as PT
 
@@ -39,6 +40,11 @@ MUTANTS = [
      "cplx dx = r[0] - rj[0], dy = r[1] - rj[1], dz = r[1] - rj[2];", "tangent_fd"),
     ("hill_radius_cube", "rcrit[i] = value * (1.0 / inva) * cbrt(p[0] / (3.0 * m0));",
      "rcrit[i] = value * (1.0 / inva) * cbrt(p[0] / m0);", "hill"),
+    ("paper_start_guess", "double x = dM / (1.0 - ec);\n    double dx = 0.0;", "double x = dM;\n    double dx = 0.0;",
+     "paper_newton"),
+    ("paper_iteration_count", "for (int it = 0; it < iters; ++it) {", "for (int it = 1; it < iters; ++it) {",
+     "paper_newton"),
+    ("paper_accepts_unconverged", "if (!(fabs(dx) <= tol)) return ORC_EKEPLER;", "", "paper_claim"),
 ]
 
 
@@ -64,6 +70,10 @@ def _run_pin(name):
         PT.test_tangent_matches_central_differences(oracle)
     elif name == "energy":
         P.test_two_body_no_secular_energy_drift(oracle, P.JUPITER_LIKE)
+    elif name == "paper_newton":
+        PM.test_last_step_matches_the_iteration_in_high_precision(oracle)
+    elif name == "paper_claim":
+        PM.test_five_iterations_reach_the_papers_convergence(oracle)
     else:
         raise KeyError(name)
 
@@ -83,6 +93,7 @@ def test_pin_catches_planted_mistake(tmp_path, mid, orig, planted, pin):
 
 
 def test_unmutated_oracle_passes_the_same_pins():
-    for pin in ["two_body", "two_body_hyp", "tie", "escape", "hill", "energy", "tangent_sym", "tangent_fd"]:
+    for pin in ["two_body", "two_body_hyp", "tie", "escape", "hill", "energy", "tangent_sym", "tangent_fd",
+                "paper_newton", "paper_claim"]:
         _run_pin(pin)
     assert os.path.exists(oracle.build())

@@ -1,0 +1,136 @@
+"""Pins of the oracle's fixed-iteration Kepler solve (the paper's own solver, section 2.2), no GPU.
+
+* the paper's statement: five iterations converge to 1e-14 for e < 0.8,
+  20 AU < a < 70 AU and steps up to 120 days;
+* with the solve converged, the drift is the exact two-body motion (mpmath);
+* the last Newton step the oracle reports equals the K-th step of the same
+  iteration carried out in 50-digit arithmetic from the stated start
+  x0 = dM / (1 - e cos E0), so a wrong start or iteration count fails;
+* a particle whose solve does not converge is removed (reason -2) with the
+  state it had before that drift, and the others match the converged solver.
+"""
+import numpy as np
+import pytest
+
+import glisse_inputs as gi
+import pins
+
+MU = gi.G
+
+
+def _random_states(n, a_range, e_range, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(*a_range, n)
+    e = rng.uniform(*e_range, n)
+    inc = np.radians(rng.uniform(0.0, 10.0, n))
+    return gi.elements_to_cartesian(MU, a, e, inc, *rng.uniform(0.0, 2 * np.pi, (3, n)))
+
+
+def test_five_iterations_reach_the_papers_convergence(orc):
+    """e < 0.8, 20 < a < 70 AU, dt = 120 days: five iterations converge within 1e-14."""
+    st = _random_states(3000, (20.0, 70.0), (0.0, 0.8), 1)
+    dt = 120.0 / 365.25
+    worst = 0.0
+    for p in range(len(st)):
+        s = st[p]
+        for _ in range(2):
+            s, rc, ldx = orc.kepler_drift_fixed(MU, s, dt, 5)
+            assert rc == 0, (p, ldx)
+            worst = max(worst, ldx)
+    assert worst <= orc.PAPER_KEPLER_TOL, worst
+    # fewer iterations do not: the criterion is live on this range
+    fails = sum(orc.kepler_drift_fixed(MU, st[p], dt, 2)[1] != 0 for p in range(len(st)))
+    assert fails > len(st) // 2
+
+
+def test_converged_fixed_drift_is_the_exact_two_body_motion(orc):
+    pytest.importorskip("mpmath")
+    for e in (0.0, 0.05, 0.4, 0.7):
+        for M0 in (0.3, 2.9):
+            s0 = pins.analytic_state(MU, 25.0, e, 0.3, 1.1, 2.2, M0)
+            dt = 0.5
+            s1, rc, ldx = orc.kepler_drift_fixed(MU, s0, dt, 5)
+            assert rc == 0 and ldx <= orc.PAPER_KEPLER_TOL
+            ref = pins.propagate_exact(MU, s0, dt, dps=40)
+            err = np.abs(s1 - ref).max() / np.abs(ref).max()
+            assert err < 1e-14 * max(1.0, 1.0 / (1.0 - e)), (e, M0, err)
+
+
+def _newton_last_step(state, dt, iters):
+    """K plain Newton steps on x - ec sin x + es (1 - cos x) = dM from x0 = dM / (1 - ec), in 50 digits."""
+    import mpmath as mp
+
+    mp.mp.dps = 50
+    x, y, z, vx, vy, vz = (mp.mpf(float(c)) for c in state)
+    mu = mp.mpf(MU)  # the double value of G m0 that the oracle uses
+    r0 = mp.sqrt(x * x + y * y + z * z)
+    u = x * vx + y * vy + z * vz
+    alpha = 2 / r0 - (vx * vx + vy * vy + vz * vz) / mu
+    a = 1 / alpha
+    n = mp.sqrt(mu / a**3)
+    ec = 1 - r0 / a
+    es = u / (n * a * a)
+    dM = n * dt
+    dM = dM - mp.floor(dM / (2 * mp.pi) + mp.mpf(0.5)) * 2 * mp.pi
+    xe = dM / (1 - ec)
+    dx = mp.mpf(0)
+    for _ in range(iters):
+        F = xe - ec * mp.sin(xe) + es * (1 - mp.cos(xe)) - dM
+        Fp = 1 - ec * mp.cos(xe) + es * mp.sin(xe)
+        dx = -F / Fp
+        xe += dx
+    return abs(float(dx))
+
+
+def test_last_step_matches_the_iteration_in_high_precision(orc):
+    pytest.importorskip("mpmath")
+    st = _random_states(40, (20.0, 40.0), (0.3, 0.9), 2)
+    checked = 0
+    for K in (1, 2, 3):
+        for p in range(len(st)):
+            _, rc, ldx = orc.kepler_drift_fixed(MU, st[p], 2.0, K)
+            ref = _newton_last_step(st[p], 2.0, K)
+            if ref < 1e-13:
+                continue  # near FP64 noise of convergence: the double iteration cannot follow it
+            # the double iteration evaluates F with absolute rounding ~1e-16 |x| (|x| <= pi here)
+            assert abs(ldx - ref) <= 1e-6 * ref + 1e-15, (K, p, ldx, ref)
+            if abs(ref - orc.PAPER_KEPLER_TOL) > 1e-15:
+                assert (rc != 0) == (ref > orc.PAPER_KEPLER_TOL)
+            checked += 1
+    assert checked > 40
+
+
+def test_unconverged_particles_are_removed_with_their_pre_drift_state(orc):
+    w = gi.make("tiny", n=8)
+    pl = w["planets"]
+    st = _random_states(300, (21.0, 28.0), (0.5, 0.95), 3)
+    n = 300
+    _, log, _ = orc.planet_wh(1.0, pl, 0.5, n)
+    rc_ = orc.rcrit(1.0, pl)
+    fixed = orc.ParticleRun(1.0, pl[:, 0], st, rc_, 1000.0, kepler_iters=3).advance(log, 0.5)
+    conv = orc.ParticleRun(1.0, pl[:, 0], st, rc_, 1000.0).advance(log, 0.5)
+    kep = fixed.reason == orc.KEPLER
+    assert kep.sum() > 10 and (conv.reason == orc.KEPLER).sum() == 0
+    assert np.all(fixed.kepler_dx[kep] > orc.PAPER_KEPLER_TOL)
+    assert np.all(fixed.kepler_dx[fixed.removal_step < 0] <= orc.PAPER_KEPLER_TOL)
+    # removed at step k: the state after the opening half kick of step k-1, i.e. what the converged
+    # run holds after k-1 steps plus that half kick (identical up to the rounding of converged solves)
+    checked = 0
+    for p in np.where(kep)[0][:20]:
+        k = int(fixed.removal_step[p])
+        before = orc.ParticleRun(1.0, pl[:, 0], st[p:p + 1], rc_, 1000.0).advance(log[:k], 0.5)
+        if before.removal_step[0] >= 0:
+            continue
+        s = before.state[0].copy()
+        d = s[:3] - log[k - 1]
+        acc = -np.sum(gi.G * pl[:, 0, None] * d / np.linalg.norm(d, axis=1)[:, None] ** 3, axis=0)
+        acc -= np.sum(gi.G * pl[:, 0, None] * log[k - 1] / np.linalg.norm(log[k - 1], axis=1)[:, None] ** 3, axis=0)
+        s[3:] += 0.25 * acc  # dt/2 = 0.25
+        err = np.abs(fixed.state[p] - s).max() / np.abs(s).max()
+        assert err < 1e-11 * k, (p, k, err)
+        checked += 1
+    assert checked > 5
+    # particles that never failed follow the converged solver
+    ok = fixed.removal_step < 0
+    e = np.abs(fixed.state[ok] - conv.state[ok]).max(axis=1) / np.abs(conv.state[ok]).max(axis=1)
+    assert np.median(e) < 1e-12
