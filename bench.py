@@ -37,15 +37,16 @@ UNIT = "particle-steps/s"
 
 # FP64 work of one interior particle-step in the kernel's formulation (static count of
 # the source; ncu's executed DADD:DMUL:DFMA mix matches it): the fast Kepler drift with
-# the degree-3 Stumpff tier (4 DADD, 15 DMUL, 39 DFMA), the h0 term (3 DFMA), and per
-# planet 3 DADD + 4 DMUL + 8 DFMA (separation, |d|^2, k |d|^-3, velocity update).
+# the degree-3 Stumpff tier (4 DADD, 11 DMUL, 39 DFMA), the h0 term (3 DFMA), and per
+# planet 3 DADD + 2 DMUL + 8 DFMA (separation, |d|^2, k |d|^-3 with the seed's square
+# and cube formed in integer arithmetic, velocity update).
 def fp64_instr_per_step(np_: int) -> int:
-    return 58 + 3 + 15 * np_
+    return 54 + 3 + 13 * np_
 
 
 def flop_per_step(np_: int) -> int:
     # DFMA counts 2 FLOP, DADD / DMUL 1
-    return (4 + 15 + 2 * 39) + 2 * 3 + np_ * (3 + 4 + 2 * 8)
+    return (4 + 11 + 2 * 39) + 2 * 3 + np_ * (3 + 2 + 2 * 8)
 
 
 # GB300 FP64 pipe: 2 DFMA per clock per SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
@@ -54,7 +55,7 @@ DFMA_PER_CLK_PER_SM = 2
 
 
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "particle_chunk_kernel_longrun.txt")
-KERNEL_SOURCES = ["particles.cu", "kepler.cuh", "device_math.cuh", "glisse_internal.h"]
+KERNEL_SOURCES = ["particle_map.cuh", "particles.cu", "kepler.cuh", "device_math.cuh", "glisse_internal.h"]
 
 
 def kernel_hash() -> str:
@@ -174,14 +175,15 @@ def workload_desc(w, n):
             f"chunk {w.chunk}, compaction every chunk")
 
 
-def cpu_oracle_rate(w, planets, particles, steps_per_chunk, chunks, threads=0, warmup=0):
+def cpu_oracle_rate(w, planets, particles, steps_per_chunk, chunks, threads=0, warmup=0, kepler_iters=0):
     """Oracle particle-steps/s on host cores over `chunks` timed chunks of a particle
-    sample, after `warmup` untimed chunks of the same run."""
+    sample, after `warmup` untimed chunks of the same run (kepler_iters > 0: the
+    paper's fixed-iteration Kepler solve)."""
     import oracle
 
     oracle.build()
     rc = oracle.rcrit(w.star_mass, planets, 0, w.k_hill)
-    run = oracle.ParticleRun(w.star_mass, planets[:, 0], particles, rc, w.r_max)
+    run = oracle.ParticleRun(w.star_mass, planets[:, 0], particles, rc, w.r_max, kepler_iters=kepler_iters)
     pl = planets.copy()
     done, busy = 0, 0.0
     for c in range(warmup + chunks):
@@ -313,18 +315,89 @@ def batched_arm(args):
     return 0
 
 
+def diff_arm(args):
+    """Differentiation workload: 65536 particles (a 22-28 AU, e < 0.05, sigma_i 1 deg),
+    10^4 steps, checkpoints every 256 steps.  Times the plain map, the differentiable
+    forward pass (without and with one tangent vector) and the adjoint pass, and
+    reports each as particle-steps/s and as a cost ratio to the plain map."""
+    import numpy as np
+    import torch
+
+    import glisse_inputs as gi
+    import paper_2011_03484_gb300 as G
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    G._build.build()
+    G.load()
+    w = gi.WORKLOADS["diff"]
+    full = gi.make("diff")
+    pl, s0 = full["planets"], full["particles"]
+    n, n_steps, K = s0.shape[0], w.n_steps, 256
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1), out
+
+    # plain map over the same steps (chunk 1024, compaction every chunk)
+    sim = G.Simulation(1.0, pl, s0, w.dt, cuda_stream=stream.cuda_stream, timing=1)
+    sim.advance(w.chunk)  # warm-up
+    sim.timings(reset=True)
+    ms_map, _ = timed(lambda: sim.advance(n_steps))
+    steps_map = sim.timings()["particle_steps"]
+    sim.close()
+    x0 = torch.as_tensor(s0, dtype=torch.float64, device=dev)
+    warm = G.DiffMap(1.0, pl, n, w.dt, 64, K)
+    warm.forward(x0)
+    warm.backward(torch.ones_like(x0))
+    warm.close()
+    dm = G.DiffMap(1.0, pl, n, w.dt, n_steps, K)
+    ms_fwd, out = timed(lambda: dm.forward(x0))
+    live = int((out[3] < 0).sum().item())
+    ms_bwd, _ = timed(lambda: dm.backward(torch.ones_like(x0)))
+    tan = G._growth_seed(x0)
+    ms_fwd_t, _ = timed(lambda: dm.forward(x0, tan))
+    dm.close()
+    ps = n * n_steps  # particle-steps of the differentiable run (removed particles stop early)
+    line = {
+        "metric": "FP64 particle-steps/s of the differentiable map (forward, adjoint) vs the plain map",
+        "value": ps / ((ms_fwd + ms_bwd) * 1e-3), "unit": "particle-steps/s (forward + adjoint)",
+        "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": ms_fwd + ms_bwd, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"diff: {n} particles, 4 planets, a 22-28 AU, e<0.05, {n_steps} steps, "
+                               f"checkpoints every {K} steps", "live_at_end": live},
+        "plain_map": {"ms": ms_map, "particle_steps_per_s": steps_map / (ms_map * 1e-3)},
+        "diff_forward": {"ms": ms_fwd, "particle_steps_per_s": ps / (ms_fwd * 1e-3)},
+        "diff_forward_with_tangent": {"ms": ms_fwd_t, "particle_steps_per_s": ps / (ms_fwd_t * 1e-3)},
+        "adjoint": {"ms": ms_bwd, "particle_steps_per_s": ps / (ms_bwd * 1e-3)},
+        "cost_ratio_to_plain_map": {"forward": ms_fwd / ms_map, "forward_with_tangent": ms_fwd_t / ms_map,
+                                    "forward_plus_adjoint": (ms_fwd + ms_bwd) / ms_map},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="longrun", choices=["longrun", "belt", "tiny", "batched"])
+    ap.add_argument("--workload", default="longrun", choices=["longrun", "belt", "tiny", "batched", "diff"])
     ap.add_argument("--tune", action="store_true", help="batched: run the autotuner before timing")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-particles", type=int, default=8192)
     ap.add_argument("--cpu-particles", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kepler", default="converge", choices=["converge", "paper"],
+                    help="paper: the paper's fixed-iteration Kepler solve (GLISSE_KEPLER_PAPER_FIXED)")
+    ap.add_argument("--kepler-iters", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -332,6 +405,8 @@ def main():
         return reference_arm(args)
     if args.workload == "batched":
         return batched_arm(args)
+    if args.workload == "diff":
+        return diff_arm(args)
 
     import numpy as np
     import torch
@@ -367,6 +442,10 @@ def main():
     o.r_max = w.r_max
     o.timing = 1
     o.cuda_stream = stream.cuda_stream
+    paper = args.kepler == "paper"
+    kmode = G.GLISSE_KEPLER_PAPER_FIXED if paper else G.GLISSE_KEPLER_CONVERGE
+    o.kepler_mode = kmode
+    o.kepler_iters = args.kepler_iters
     h = G.glisse_create(w.star_mass, planets, particles, w.dt, o)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -425,7 +504,7 @@ def main():
         for k in range(args.e2e_steps + 1):
             t0 = time.perf_counter()
             sim = G.Simulation(w.star_mass, planets, particles, w.dt, chunk_steps=w.chunk, enc_value=w.k_hill,
-                               r_max=w.r_max, timing=1)
+                               r_max=w.r_max, timing=1, kepler_mode=kmode, kepler_iters=args.kepler_iters)
             sim.advance(w.chunk)
             out = sim.read()
             st = sim.timings()["particle_steps"]
@@ -442,7 +521,8 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         ids = gi.subset_ids(args.workload, args.cpu_particles)
-        rate, cores, busy = cpu_oracle_rate(w, planets, particles[ids], w.chunk, 2)
+        rate, cores, busy = cpu_oracle_rate(w, planets, particles[ids], w.chunk, 2,
+                                            kepler_iters=args.kepler_iters if paper else 0)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{len(ids)} random ids of the workload, 2 chunks of {w.chunk} steps "
                          f"({busy:.1f} s wall on {cores} threads)"}
@@ -457,7 +537,9 @@ def main():
                    "fraction_alive_at_end": live_after / n, "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": f"replicas x{world} (independent particle sets, no collective)",
                    "wall_s": t_wall},
-        "roofline": {"bound": "alu", "achieved": achieved * 1e-9, "peak": peak * 1e-9, "unit": "GFLOP/s",
+        "kepler": (f"paper fixed-iteration solve, {args.kepler_iters} Newton iterations (library sin/cos)"
+                   if paper else "converged (FP32 pre-solve + FP64 Halley step)"),
+        "roofline": None if paper else {"bound": "alu", "achieved": achieved * 1e-9, "peak": peak * 1e-9, "unit": "GFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "particle_chunk_kernel<4>",
                      "kernel_ms_avg": kernel_ms, "flop_per_particle_step": flop_per_step(np_),
                      "fp64_instr_per_particle_step": fp64_instr_per_step(np_), "fp64_pipe_frac": pipe,

@@ -54,6 +54,16 @@ extern "C" {
 /* Kepler solver modes */
 #define GLISSE_KEPLER_CONVERGE 0    /* iterate to convergence (default) */
 #define GLISSE_KEPLER_PAPER_FIXED 1 /* fixed iteration count, deactivate if not converged (section 2.2) */
+/* PAPER_FIXED: kepler_iters Newton steps on Kepler's equation in the eccentric
+ * anomaly, started at x0 = dM / (1 - e cos E0); a particle whose last step
+ * exceeds GLISSE_PAPER_KEPLER_TOL (the 1e-14 convergence section 2.2 quotes)
+ * is removed with GLISSE_REMOVED_KEPLER, keeping its state from before the
+ * drift.  Unbound or nearly radial orbits (r alpha < 1e-3), which the paper
+ * does not treat, use the converged universal-variable solve.  Only
+ * glisse_create accepts it; the batched and differentiable entry points
+ * return GLISSE_E_INVAL. */
+#define GLISSE_PAPER_KEPLER_TOL 1e-14
+#define GLISSE_MAX_KEPLER_ITERS 64
 
 /* encounter criterion (section 2.2, close-encounter paragraph) */
 #define GLISSE_ENC_HILL 0  /* R_crit,j = enc_value * a_j (m_j / 3 m0)^(1/3) */
@@ -65,7 +75,7 @@ typedef struct {
     int32_t chunk_steps;   /* steps per planet chunk C (section 2.2), default 1024 */
     int32_t resync_chunks; /* compact live particles every R chunks (section 2.2), default 1 */
     int32_t kepler_mode;   /* GLISSE_KEPLER_*, default CONVERGE */
-    int32_t kepler_iters;  /* iterations for PAPER_FIXED, default 5 (section 2.2) */
+    int32_t kepler_iters;  /* iterations for PAPER_FIXED (1..GLISSE_MAX_KEPLER_ITERS), default 5 (section 2.2) */
     int32_t enc_mode;      /* GLISSE_ENC_*, default HILL */
     int32_t timing;        /* non-zero: time every launch with CUDA events (see glisse_timings) */
     double enc_value;      /* Hill multiple k (default 1.0) or fixed distance in AU */

@@ -30,6 +30,8 @@ GLISSE_REMOVED_KEPLER = -2
 GLISSE_REMOVED_NONFINITE = -3
 GLISSE_KEPLER_CONVERGE = 0
 GLISSE_KEPLER_PAPER_FIXED = 1
+GLISSE_PAPER_KEPLER_TOL = 1e-14
+GLISSE_MAX_KEPLER_ITERS = 64
 GLISSE_ENC_HILL = 0
 GLISSE_ENC_FIXED = 1
 

@@ -36,10 +36,43 @@ __device__ __forceinline__ double rcp_seed(double x) {
 __device__ __forceinline__ double rsqrt_full(double x);
 
 // k * x^(-3/2) for normal x > 0 (the inverse-cube distance factor of a kick).
-// y = seed (20 significant bits, so y*y is exact), e = 1 - x y^2:
+// y = seed, e = 1 - x y^2:
 //   x^(-3/2) = y^3 (1 - e)^(-3/2) = y^3 (1 + 3e/2 + 15e^2/8 + O(e^3)).
-// 6 FP64 instructions.
+// y^2 (exact) and y^3 (correctly rounded) come from integer arithmetic on the
+// seed's 21-bit significand (seed_powers), so 4 FP64 instructions remain.
 __device__ __forceinline__ double k_rcube(double x, double k);
+
+// |t|^2 exactly and t^3 correctly rounded (ties away from zero) for a double t
+// whose significand has at most 21 bits (the low 32 bits of its encoding are
+// zero), by integer multiplication of the significands: m^2 has 42 bits and
+// m^3 at most 63.  Returns false (results unspecified) when t is zero,
+// subnormal, non-finite or |t| is outside [2^-300, 2^300].
+__device__ __forceinline__ bool seed_powers(double t, double& t2, double& t3) {
+    const int hi = __double2hiint(t);
+    const int et = (hi >> 20) & 0x7FF;  // biased exponent: t = m 2^(et - 1043)
+    const unsigned m = ((unsigned)hi & 0xFFFFFu) | 0x100000u;
+    const unsigned long long m2 = (unsigned long long)m * m;  // [2^40, 2^42)
+    const unsigned long long m3 = m2 * m;                     // [2^60, 2^63)
+    // t^2 = m2 2^(2 et - 2086); with the leading bit of m2 at 40 + a the
+    // significand m2 << (12 - a) lies in [2^52, 2^53) and the biased exponent
+    // is 2 et - 1023 + a.  Adding the significand (implicit bit included) to
+    // (exponent - 1) << 52 assembles the encoding.
+    const int a = (int)(m2 >> 41);
+    const unsigned long long q2 = m2 << (12 - a);
+    const long long e2 = (long long)(2 * et - 1024 + a) << 52;
+    t2 = __longlong_as_double(e2 + (long long)q2);
+    // t^3 = m3 2^(3 et - 3129); leading bit at 60 + b (b = 0, 1, 2); keep the
+    // top 53 bits with rounding: shift right by 8 + b after adding half of
+    // the last kept unit.  A carry to 2^53 moves into the exponent field.
+    const unsigned h3 = (unsigned)(m3 >> 32);
+    const int b = min((int)(h3 >> 29), 2);
+    const int sh = 8 + b;
+    const unsigned long long q3 = (m3 + (1ull << (sh - 1))) >> sh;
+    const long long e3 = (long long)(3 * et - 2047 + b) << 52;
+    const long long sign = (long long)(hi & 0x80000000) << 32;
+    t3 = __longlong_as_double((e3 + (long long)q3) | sign);
+    return (unsigned)(et - 723) <= 600u;
+}
 
 // 1/x to about 2^-40 from the MUFU seed and one Newton step (2 FP64 instructions).
 __device__ __forceinline__ double rcp_40(double x) {
@@ -82,6 +115,35 @@ __device__ __forceinline__ double f2d_bits(float f) {
     return __hiloint2double((int)hi, (int)lo);
 }
 
+// |s|^2 exactly and s^3 correctly rounded (ties away from zero) for a float s,
+// as doubles, by integer multiplication of the 24-bit significand m: m^2 has
+// 48 bits, m^3 = 2^32 H + L is formed from two 32 x 32 products and rounded
+// to 53 bits.  Returns false (results unspecified) when s is zero,
+// subnormal or non-finite.
+__device__ __forceinline__ bool float_powers(float s, double& s2, double& s3) {
+    const unsigned bits = __float_as_uint(s);
+    const int ef = (int)((bits >> 23) & 0xFFu);  // s = m 2^(ef - 150)
+    const unsigned m = (bits & 0x7FFFFFu) | 0x800000u;
+    const unsigned long long m2 = (unsigned long long)m * m;  // [2^46, 2^48)
+    // s^2 = m2 2^(2 ef - 300): leading bit of m2 at 46 + a, significand
+    // m2 << (6 - a) in [2^52, 2^53), biased exponent 2 ef + 769 + a
+    const int a = (int)(m2 >> 47);
+    const long long e2 = (long long)(2 * ef + 768 + a) << 52;
+    s2 = __longlong_as_double(e2 + (long long)(m2 << (6 - a)));
+    // m^3 = m2 m = 2^32 H + L with H = m2_hi m + (m2_lo m >> 32) in [2^37, 2^40)
+    const unsigned long long p1 = (unsigned long long)(unsigned)m2 * m;
+    const unsigned long long H0 = (unsigned long long)(unsigned)(m2 >> 32) * m + (p1 >> 32);
+    const int b = min((int)(H0 >> 38), 2);  // leading bit of m^3 at 69 + b
+    const int sh = 17 + b;                  // keep 53 bits
+    const unsigned long long L = (p1 & 0xFFFFFFFFull) + (1ull << (sh - 1));
+    const unsigned long long H = H0 + (L >> 32);
+    const unsigned long long q3 = (H << (32 - sh)) | ((L & 0xFFFFFFFFull) >> sh);  // [2^52, 2^53]
+    const long long e3 = (long long)(3 * ef + 641 + b) << 52;
+    const long long sign = (long long)(bits & 0x80000000u) << 32;
+    s3 = __longlong_as_double((e3 + (long long)q3) | sign);
+    return (unsigned)(ef - 1) < 254u;
+}
+
 __device__ __forceinline__ double rsqrt_full(double x) {
     const double y = rsqrt_seed(x);
     const double y2 = y * y;
@@ -93,9 +155,10 @@ __device__ __forceinline__ double rsqrt_full(double x) {
 
 __device__ __forceinline__ double k_rcube(double x, double k) {
     const double y = rsqrt_seed(x);
-    const double y2 = y * y;
+    double y2, y3;
+    const bool ok = seed_powers(y, y2, y3);
     const double e = fma(-x, y2, 1.0);
-    const double w = (y2 * y) * k;
+    const double w = ok ? y3 * k : __longlong_as_double(0x7FF8000000000000ll);
     const float ef = d2f_bits(e);
     const double c = fma(1.5, e, f2d_bits(1.875f * ef * ef));
     return fma(w, c, w);

@@ -229,9 +229,10 @@ __device__ __forceinline__ void eph_advance(const PlanetConsts& pc, double* jac,
 #pragma unroll
         for (int d = 0; d < 3; ++d) w[d] = fma(hdt, acc[d], w[d]);
         // Kepler drift of each Jacobi body
-        double qr, qrinv;
-        radius_of(q[0], q[1], q[2], qr, qrinv);
-        const bool done = drift_fast(mu, muf, dt, dtf, on, qr, qrinv, q[0], q[1], q[2], w[0], w[1], w[2]);
+        double qr, qmur;
+        radius_of(q[0], q[1], q[2], qr, qmur);
+        qmur *= mu;
+        const bool done = drift_fast(mu, muf, dt, dtf, on, qr, qmur, q[0], q[1], q[2], w[0], w[1], w[2]);
         if (on && !done) {
             if (!drift_general(mu, dt, q[0], q[1], q[2], w[0], w[1], w[2])) failed = true;
         }

@@ -33,6 +33,7 @@ cudaError_t launch_eph_setup(const double*, int, double, double, int, double, Pl
 cudaError_t launch_eph_chunk(const PlanetConsts*, double*, double, int, double*, double*, int*, cudaStream_t);
 cudaError_t launch_eph_external(const PlanetConsts*, const double*, int64_t, double*, cudaStream_t);
 cudaError_t launch_particle_chunk(int, const ChunkArgs&, const ParticleConsts&, cudaStream_t);
+cudaError_t launch_particle_chunk_paper(int, const ChunkArgs&, const ParticleConsts&, cudaStream_t);
 cudaError_t launch_compact(int64_t, const uint8_t*, const double*, const int32_t*, int64_t, double*, int32_t*,
                            int64_t, int64_t*, int64_t*, cudaStream_t);
 int64_t compact_scratch_entries(int64_t);
@@ -298,6 +299,8 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles) 
         p.rc2[j] = c->hpc.rcrit[j] * c->hpc.rcrit[j];
     }
     p.rmax2 = c->o.r_max > 0.0 ? c->o.r_max * c->o.r_max : 0.0;
+    p.kepler_iters = c->o.kepler_mode == GLISSE_KEPLER_PAPER_FIXED ? c->o.kepler_iters : 0;
+    p.kepler_tol = GLISSE_PAPER_KEPLER_TOL;
     p.rmax = c->o.r_max > 0.0 ? c->o.r_max : 0.0;
 
     // particles -> device SoA, ids, flags
@@ -338,7 +341,9 @@ extern "C" int glisse_create(glisse_ctx** out, double star_mass, const double* p
     if (n_particles > 0 && !particles) return GLISSE_E_INVAL;
     if (!(dt != 0.0) || !std::isfinite(dt)) return GLISSE_E_INVAL;
     if (o.chunk_steps < 1 || o.chunk_steps > (1 << 20) || o.resync_chunks < 1) return GLISSE_E_INVAL;
-    if (o.kepler_mode != GLISSE_KEPLER_CONVERGE) return GLISSE_E_INVAL;
+    if (o.kepler_mode != GLISSE_KEPLER_CONVERGE && o.kepler_mode != GLISSE_KEPLER_PAPER_FIXED) return GLISSE_E_INVAL;
+    if (o.kepler_mode == GLISSE_KEPLER_PAPER_FIXED && (o.kepler_iters < 1 || o.kepler_iters > GLISSE_MAX_KEPLER_ITERS))
+        return GLISSE_E_INVAL;
     if (o.enc_mode != GLISSE_ENC_HILL && o.enc_mode != GLISSE_ENC_FIXED) return GLISSE_E_INVAL;
     if (!(o.enc_value >= 0.0) || !std::isfinite(o.enc_value) || !std::isfinite(o.r_max)) return GLISSE_E_INVAL;
     for (int64_t k = 0; k < 7 * (int64_t)n_planets; ++k)
@@ -438,7 +443,10 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
             a.out_reason = c->d_out_reason;
             a.steps_done = c->d_steps;
             if (c->timing) GL_CUDA(cudaEventRecord(c->tp0, c->s));
-            GL_CUDA(launch_particle_chunk(c->np, a, c->ppc, c->s));
+            if (c->o.kepler_mode == GLISSE_KEPLER_PAPER_FIXED)
+                GL_CUDA(launch_particle_chunk_paper(c->np, a, c->ppc, c->s));
+            else
+                GL_CUDA(launch_particle_chunk(c->np, a, c->ppc, c->s));
             if (c->timing) {
                 GL_CUDA(cudaEventRecord(c->tp1, c->s));
                 GL_CUDA(cudaEventSynchronize(c->tp1));

@@ -38,6 +38,9 @@ struct ParticleConsts {
     double rc2[kMaxPlanets];          // R_crit,j^2 (0: no test)
     double rmax2;                     // r_max^2 (0: no test)
     double rmax;                      // r_max (0: no test)
+    double kepler_tol;                // fixed-iteration mode: largest accepted last Newton step
+    int32_t kepler_iters;             // fixed-iteration mode: Newton iterations per drift
+    int32_t pad_;
 };
 
 // Arguments of one particle-chunk launch.

@@ -178,9 +178,71 @@ __device__ inline bool drift_general(double mu, double dt, double& x, double& y,
 }
 
 // ---------------------------------------------------------------------------
+// The paper's solver (section 2.2): Newton's method on Kepler's equation with
+// a fixed number of iterations from a starting guess, and deactivation of a
+// particle whose solve has not converged to the quoted 1e-14.  Bound orbits
+// with r0 alpha >= 1e-3 use the equation for x = E - E0 in difference form,
+//   F(x) = x - ec sin x + es (1 - cos x) - dM,
+//   ec = 1 - r0 alpha (= e cos E0),  es = u / (n a^2) (= e sin E0),  dM = n dt,
+// with dM reduced to [-pi, pi] by whole periods, the start x0 = dM / (1 - ec)
+// and plain Newton steps (no safeguard).  "Converged" means the last step has
+// |dx| <= tol.  Other orbits (unbound or nearly radial), which the paper does
+// not treat, use the converged universal-variable solver.  Library sin, cos,
+// sqrt and division: this mode reproduces the paper's algorithm, it is not
+// the tuned path.
+// Returns 0 (drifted), 1 (not converged: state unchanged) or 2 (the
+// universal-variable solver failed: state unchanged).
+// ---------------------------------------------------------------------------
+__device__ inline int drift_paper(double mu, double dt, int iters, double tol, double& x, double& y, double& z,
+                                  double& vx, double& vy, double& vz) {
+    const double r0 = sqrt(x * x + y * y + z * z);
+    const double v2 = vx * vx + vy * vy + vz * vz;
+    const double u = x * vx + y * vy + z * vz;
+    const double alpha = 2.0 / r0 - v2 / mu;
+    if (!(alpha > 0.0 && r0 * alpha >= 1e-3)) {
+        if (dt == 0.0) return 0;
+        return drift_general(mu, dt, x, y, z, vx, vy, vz) ? 0 : 2;
+    }
+    constexpr double kTwoPi = 6.283185307179586476925286766559;
+    const double a = 1.0 / alpha;
+    const double n = sqrt(mu / (a * a * a));
+    const double ec = 1.0 - r0 / a;
+    const double es = u / (n * a * a);
+    double dM = n * dt;
+    dM = dM - floor(dM / kTwoPi + 0.5) * kTwoPi;
+    double xe = dM / (1.0 - ec);
+    double dx = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        double sx, cx;
+        sincos(xe, &sx, &cx);
+        const double F = xe - ec * sx + es * (1.0 - cx) - dM;
+        const double Fp = 1.0 - ec * cx + es * sx;
+        dx = -F / Fp;
+        xe = xe + dx;
+    }
+    if (!(fabs(dx) <= tol)) return 1;
+    double sx, cx;
+    sincos(xe, &sx, &cx);
+    const double omc = 1.0 - cx;
+    const double f = 1.0 - (a / r0) * omc;
+    const double g = (dM - (xe - sx)) / n;
+    const double r = a * (1.0 - ec * cx + es * sx);
+    const double fd = -n * a * a * sx / (r * r0);
+    const double gd = 1.0 - (a / r) * omc;
+    const double x0 = x, y0 = y, z0 = z, vx0 = vx, vy0 = vy, vz0 = vz;
+    x = f * x0 + g * vx0;
+    y = f * y0 + g * vy0;
+    z = f * z0 + g * vz0;
+    vx = fd * x0 + gd * vx0;
+    vy = fd * y0 + gd * vy0;
+    vz = fd * z0 + gd * vz0;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
 // Fast path.  Must be called by all 32 lanes of a warp together.
 //   part       : this lane's result is wanted (inactive lanes still execute)
-//   r0, rinv0  : |r| and 1/|r| of the current position; on success they are
+//   r0, mur0   : |r| and mu/|r| of the current position; on success they are
 //                replaced by the values at the drifted position (r(s) is known
 //                from the solve, so the next step needs no square root)
 // On success (return true) the state is advanced; on false nothing changes.
@@ -190,25 +252,28 @@ constexpr float kZ3 = 0.001953125f;  // 2^-9: degree 3 reaches 2^-56
 constexpr float kZ5 = 0.03125f;      // 2^-5: degree 5
 constexpr float kZ7 = 0.1f;          // degree 7 (fast-path limit)
 
+// s0 is the FP32 root (24 significant bits), s2 = s0^2 exact and s3 = s0^3
+// rounded once (float_powers).  The Halley step removes the start error of
+// ~2^-24 |s|; its cubic convergence leaves far below 2^-60.
 template <int DEG>
-__device__ __forceinline__ void fast_tail(double mu, double dt, double beta, double& r0, double& rinv0, double u,
-                                          double s0, float uf, float muf, float bf, float r0f, double& x, double& y,
-                                          double& z, double& vx, double& vy, double& vz, bool& ok) {
-    const double s2 = s0 * s0;
+__device__ __forceinline__ void fast_tail(double mu, double dt, double beta, double& r0, double& mur0, double u,
+                                          double q, double s0, double s2, double s3, float uf, float bf, double& x,
+                                          double& y, double& z, double& vx, double& vy, double& vz, bool& ok) {
     const double zz = beta * s2;
     double c2, c3;
     c23_poly<DEG>(zz, c2, c3);
     const double G2 = s2 * c2;
-    const double G3 = (s2 * s0) * c3;
+    const double G3 = s3 * c3;
     const double G1 = fma(-beta, G3, s0);
-    const double G0 = fma(-beta, G2, 1.0);
+    // r = T'(s) = r0 G0 + u G1 + mu G2 = r0 + q G2 + u G1  (q = mu - beta r0, G0 = 1 - beta G2)
     const double F = fma(r0, G1, fma(u, G2, fma(mu, G3, -dt)));
-    const double r = fma(r0, G0, fma(u, G1, mu * G2));
+    const double r = fma(u, G1, fma(q, G2, r0));
     const double rinv = rcp_40(r);
     const double dN = -F * rinv;
     // Halley: dH = dN / (1 + dN T''/(2 T')) ~ dN (1 - k); k ~ 1e-8 needs only FP32
-    const float G0f = d2f_bits(G0), G1f = d2f_bits(G1);
-    const float Fpp = fmaf(uf, G0f, (muf - bf * r0f) * G1f);
+    const float G2f = d2f_bits(G2), G1f = d2f_bits(G1);
+    const float G0f = fmaf(-bf, G2f, 1.0f);
+    const float Fpp = fmaf(uf, G0f, d2f_bits(q) * G1f);  // T''(s) = u G0 + q G1
     const float dNf = d2f_bits(dN);
     const float kf = 0.5f * dNf * Fpp * d2f_bits(rinv);
     const double dH = fma(dN, -f2d_bits(kf), dN);
@@ -226,11 +291,11 @@ __device__ __forceinline__ void fast_tail(double mu, double dt, double beta, dou
     // domain checks (integer tests): r > 0 and the correction small against s
     const bool good = (__double2hiint(r) > 0) && (exp_bits(dH) + 14 <= exp_bits(s0) || dH == 0.0);
     ok = ok && good;
-    const double mur0 = mu * rinv0;
     const double fm1 = -mur0 * G2n;
     const double g = fma(-mu, G3n, dt);
     const double fd = -(mur0 * rinv1) * G1n;
-    const double gdm1 = -(mu * rinv1) * G2n;
+    const double mur1 = mu * rinv1;
+    const double gdm1 = -mur1 * G2n;
     if (ok) {
         const double x0 = x, y0 = y, z0 = z;
         x = fma(fm1, x0, fma(g, vx, x0));
@@ -240,18 +305,18 @@ __device__ __forceinline__ void fast_tail(double mu, double dt, double beta, dou
         vy = fma(fd, y0, fma(gdm1, vy, vy));
         vz = fma(fd, z0, fma(gdm1, vz, vz));
         r0 = r1;
-        rinv0 = rinv1;
+        mur0 = mur1;
     }
 }
 
 // Returns true when the lane's drift was done here; false when the caller must
 // use drift_general (or when part == false).
 __device__ __forceinline__ bool drift_fast(double mu, float muf, double dt, float dtf, bool part, double& r0,
-                                           double& rinv0, double& x, double& y, double& z, double& vx, double& vy,
+                                           double& mur0, double& x, double& y, double& z, double& vx, double& vy,
                                            double& vz) {
     const double u = fma(x, vx, fma(y, vy, z * vz));
     const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
-    const double beta = fma(2.0 * mu, rinv0, -v2);
+    const double beta = fma(2.0, mur0, -v2);
 
     // ---- FP32 solve of T(s) = dt ------------------------------------------------
     const float r0f = d2f_bits(r0), uf = d2f_bits(u), bf = d2f_bits(beta);
@@ -279,13 +344,17 @@ __device__ __forceinline__ bool drift_fast(double mu, float muf, double dt, floa
     // ---- warp-uniform polynomial degree ------------------------------------------
     const unsigned zb = ok ? __float_as_uint(fabsf(zf)) : 0u;
     const unsigned zmax = __reduce_max_sync(kFullMask, zb);
+    // s0 = the FP32 root; s0^2 exact and s0^3 rounded once, in integer arithmetic
     const double s0 = f2d_bits(s);
+    double s2, s3;
+    ok = float_powers(s, s2, s3) && ok;
+    const double q = fma(-beta, r0, mu);
     if (zmax <= __float_as_uint(kZ3)) {
-        fast_tail<3>(mu, dt, beta, r0, rinv0, u, s0, uf, muf, bf, r0f, x, y, z, vx, vy, vz, ok);
+        fast_tail<3>(mu, dt, beta, r0, mur0, u, q, s0, s2, s3, uf, bf, x, y, z, vx, vy, vz, ok);
     } else if (zmax <= __float_as_uint(kZ5)) {
-        fast_tail<5>(mu, dt, beta, r0, rinv0, u, s0, uf, muf, bf, r0f, x, y, z, vx, vy, vz, ok);
+        fast_tail<5>(mu, dt, beta, r0, mur0, u, q, s0, s2, s3, uf, bf, x, y, z, vx, vy, vz, ok);
     } else {
-        fast_tail<7>(mu, dt, beta, r0, rinv0, u, s0, uf, muf, bf, r0f, x, y, z, vx, vy, vz, ok);
+        fast_tail<7>(mu, dt, beta, r0, mur0, u, q, s0, s2, s3, uf, bf, x, y, z, vx, vy, vz, ok);
     }
     return ok;
 }

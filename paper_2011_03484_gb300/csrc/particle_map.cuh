@@ -1,0 +1,252 @@
+// particle_map.cuh -- the test-particle map over one segment of a planet chunk
+// (shared by the translation units that instantiate it for each drift mode).
+//
+// Section 2.2: one thread per particle; the particle is loaded once, carried
+// in registers through every step of the chunk, and stored once.  Each step
+// is kick(dt/2) - Kepler drift(dt) - kick(dt/2) with the kick
+//   dv/dt = h0 - sum_j G m_j (r - r_j) / |r - r_j|^3,  h0 = -sum_j G m_j r_j / |r_j|^3,
+// and the removal test (encounter |r - r_j| < R_crit,j, escape |r| > r_max)
+// made at every kick time on the drifted position.  Inside a segment the
+// closing half kick of step k and the opening half kick of step k+1 use the
+// same planet positions, so they are applied as one kick of dt; the segment's
+// first and last kicks are half kicks so that the stored state is the
+// synchronised one.
+//
+// A removed particle keeps the state it had after the drift and before the
+// closing kick, gets removal_step = k+1 and the reason (planet 1..N_p, lowest
+// index first; encounter before escape), and its lane idles until the warp
+// finishes or compaction drops it.  A failed Kepler solve or a non-finite
+// result keeps the state from before the drift (reasons -2 / -3).
+#pragma once
+#include "glisse_internal.h"
+#include "kepler.cuh"
+
+namespace glisse {
+
+constexpr int kParticleBlock = 128;
+
+// drift used by the particle map: the converged fast solver (default) or the
+// paper's fixed-iteration solve (GLISSE_KEPLER_PAPER_FIXED)
+constexpr int kDriftConverge = 0;
+constexpr int kDriftPaper = 1;
+
+// Read-only broadcast load of one 32-byte log record.
+__device__ __forceinline__ void load_rec(const double* __restrict__ p, double& x, double& y, double& z) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    x = a.x;
+    y = a.y;
+    z = __ldg(p + 2);
+}
+
+// Kick with the log step L by tau (tgm[j] = tau G m_j), and the encounter test.
+// Returns the lowest 1-based planet index whose test fires, or 0.
+template <int NP>
+__device__ __forceinline__ int kick_test(double x, double y, double z, double& vx, double& vy, double& vz,
+                                         const double* __restrict__ L, double tau, const double (&tgm)[kMaxPlanets],
+                                         const double (&rc2)[kMaxPlanets]) {
+    double hx, hy, hz;
+    load_rec(L + kRec * NP, hx, hy, hz);
+    vx = fma(tau, hx, vx);
+    vy = fma(tau, hy, vy);
+    vz = fma(tau, hz, vz);
+    int hit = 0;
+#pragma unroll
+    for (int j = NP - 1; j >= 0; --j) {
+        double px, py, pz;
+        load_rec(L + kRec * j, px, py, pz);
+        const double dx = x - px, dy = y - py, dz = z - pz;
+        const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        hit = lt_nonneg(d2, rc2[j]) ? (j + 1) : hit;
+        const double s = k_rcube(d2, tgm[j]);
+        vx = fma(-s, dx, vx);
+        vy = fma(-s, dy, vy);
+        vz = fma(-s, dz, vz);
+    }
+    return hit;
+}
+
+// Removal test without a kick (used at t_0).
+template <int NP>
+__device__ __forceinline__ int test_only(double x, double y, double z, const double* __restrict__ L,
+                                         const double (&rc2)[kMaxPlanets], double rmax2) {
+    int hit = 0;
+    const double r2 = fma(x, x, fma(y, y, z * z));
+    if (__double_as_longlong(rmax2) != 0 && lt_nonneg(rmax2, r2)) hit = GLISSE_REMOVED_ESCAPE;
+#pragma unroll
+    for (int j = NP - 1; j >= 0; --j) {
+        double px, py, pz;
+        load_rec(L + kRec * j, px, py, pz);
+        const double dx = x - px, dy = y - py, dz = z - pz;
+        const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        hit = lt_nonneg(d2, rc2[j]) ? (j + 1) : hit;
+    }
+    return hit;
+}
+
+// The map for one lane over nsteps steps of the log L (L step 0 = the lane's
+// current time).  State in registers; act / reason / rstep record removal.
+// pc may live in the constant bank (kernel parameter) or in shared memory.
+template <int NP, int MODE = kDriftConverge>
+__device__ __forceinline__ void advance_lane(const ParticleConsts& pc, const double* __restrict__ L, int64_t step0,
+                                             int nsteps, bool test_first, double& x, double& y, double& z, double& vx,
+                                             double& vy, double& vz, bool& act, int& reason, int64_t& rstep) {
+    const float muf = d2f_bits(pc.mu), dtf = d2f_bits(pc.dt);
+    const bool has_rmax = __double_as_longlong(pc.rmax) != 0;
+    const int S = log_stride(NP);
+
+    if (test_first) {
+        const int h = test_only<NP>(x, y, z, L, pc.rc2, pc.rmax2);
+        if (act && h != 0) {
+            act = false;
+            reason = h;
+            rstep = step0;
+        }
+    }
+    if (act) kick_test<NP>(x, y, z, vx, vy, vz, L, pc.half_dt, pc.tgm_half, pc.rc2);
+    double r0, mur0;
+    radius_of(x, y, z, r0, mur0);
+    mur0 *= pc.mu;
+
+    for (int k = 0; k < nsteps; ++k) {
+        if (!__any_sync(kFullMask, act)) break;
+        const double* __restrict__ Ln = L + (size_t)(k + 1) * S;
+        const double sx = x, sy = y, sz = z, svx = vx, svy = vy, svz = vz;
+        const double sr0 = r0, smur0 = mur0;
+        bool failed = false;
+        if constexpr (MODE == kDriftConverge) {
+            const bool done = drift_fast(pc.mu, muf, pc.dt, dtf, act, r0, mur0, x, y, z, vx, vy, vz);
+            if (act && !done) {
+                failed = !drift_general(pc.mu, pc.dt, x, y, z, vx, vy, vz);
+                radius_of(x, y, z, r0, mur0);
+                mur0 *= pc.mu;
+            }
+        } else {
+            if (act) {
+                failed = drift_paper(pc.mu, pc.dt, pc.kepler_iters, pc.kepler_tol, x, y, z, vx, vy, vz) != 0;
+                radius_of(x, y, z, r0, mur0);
+            }
+        }
+        const bool bad = nonfinite_bits(x) || nonfinite_bits(y) || nonfinite_bits(z) || nonfinite_bits(vx) ||
+                         nonfinite_bits(vy) || nonfinite_bits(vz);
+        if (act && (failed || bad)) {
+            x = sx;
+            y = sy;
+            z = sz;
+            vx = svx;
+            vy = svy;
+            vz = svz;
+            r0 = sr0;
+            mur0 = smur0;
+            act = false;
+            reason = failed ? GLISSE_REMOVED_KEPLER : GLISSE_REMOVED_NONFINITE;
+            rstep = step0 + k + 1;
+        }
+        // escape: |r| > r_max, with |r| from the drift (integer compare of positive doubles)
+        int hit = (has_rmax && lt_nonneg(pc.rmax, r0)) ? GLISSE_REMOVED_ESCAPE : 0;
+        const bool last = (k + 1 == nsteps);
+        double nvx = vx, nvy = vy, nvz = vz;
+        int enc;
+        if (last)
+            enc = kick_test<NP>(x, y, z, nvx, nvy, nvz, Ln, pc.half_dt, pc.tgm_half, pc.rc2);
+        else
+            enc = kick_test<NP>(x, y, z, nvx, nvy, nvz, Ln, pc.dt, pc.tgm_full, pc.rc2);
+        hit = enc ? enc : hit;
+        if (act) {
+            if (hit != 0) {
+                act = false;
+                reason = hit;
+                rstep = step0 + k + 1;
+            } else {
+                vx = nvx;
+                vy = nvy;
+                vz = nvz;
+            }
+        }
+    }
+}
+
+// Write a removed particle's result under its id.
+__device__ __forceinline__ void store_removed(int64_t pid, double x, double y, double z, double vx, double vy,
+                                              double vz, int64_t rstep, int reason, double* out_state,
+                                              int64_t* out_step, int32_t* out_reason) {
+    double* o = out_state + 6 * pid;
+    o[0] = x;
+    o[1] = y;
+    o[2] = z;
+    o[3] = vx;
+    o[4] = vy;
+    o[5] = vz;
+    out_step[pid] = rstep;
+    out_reason[pid] = reason;
+}
+
+template <int NP, int MODE>
+__global__ void __launch_bounds__(kParticleBlock) particle_chunk_kernel(const ChunkArgs a, const ParticleConsts pc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool in = i < a.n;
+    const int64_t ld = a.ld;
+    double x, y, z, vx, vy, vz;
+    if (in) {
+        x = a.st[i];
+        y = a.st[ld + i];
+        z = a.st[2 * ld + i];
+        vx = a.st[3 * ld + i];
+        vy = a.st[4 * ld + i];
+        vz = a.st[5 * ld + i];
+    } else {
+        // idle lanes carry a harmless circular orbit so the shared drift stays finite
+        x = 1.0;
+        y = 0.0;
+        z = 0.0;
+        vx = 0.0;
+        vy = 6.283185307179586;
+        vz = 0.0;
+    }
+    bool act = in && a.alive[i] != 0;
+    const bool started = act;
+    int reason = 0;
+    int64_t rstep = -1;
+    advance_lane<NP, MODE>(pc, a.log, a.step0, a.nsteps, a.test_first != 0, x, y, z, vx, vy, vz, act, reason,
+                           rstep);
+    if (a.steps_done) {
+        // steps this particle actually advanced in the segment (exact work count)
+        const unsigned adv = !started ? 0u : (rstep >= 0 ? (unsigned)(rstep - a.step0) : (unsigned)a.nsteps);
+        const unsigned wsum = __reduce_add_sync(kFullMask, adv);
+        if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(a.steps_done, (unsigned long long)wsum);
+    }
+    if (in) {
+        a.st[i] = x;
+        a.st[ld + i] = y;
+        a.st[2 * ld + i] = z;
+        a.st[3 * ld + i] = vx;
+        a.st[4 * ld + i] = vy;
+        a.st[5 * ld + i] = vz;
+        a.alive[i] = act ? 1 : 0;
+        if (rstep >= 0) store_removed(a.id[i], x, y, z, vx, vy, vz, rstep, reason, a.out_state, a.out_step,
+                                      a.out_reason);
+    }
+}
+
+template <int MODE>
+cudaError_t launch_particle_chunk_mode(int np, const ChunkArgs& a, const ParticleConsts& pc, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    const int64_t grid = (a.n + kParticleBlock - 1) / kParticleBlock;
+    switch (np) {
+#define GLISSE_CASE(N) \
+    case N: particle_chunk_kernel<N, MODE><<<(unsigned)grid, kParticleBlock, 0, s>>>(a, pc); break;
+        GLISSE_CASE(0)
+        GLISSE_CASE(1)
+        GLISSE_CASE(2)
+        GLISSE_CASE(3)
+        GLISSE_CASE(4)
+        GLISSE_CASE(5)
+        GLISSE_CASE(6)
+        GLISSE_CASE(7)
+        GLISSE_CASE(8)
+#undef GLISSE_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace glisse

@@ -77,6 +77,22 @@ def test_argument_errors_before_any_cuda_call(G):
     with pytest.raises(G.GlisseError) as ei:
         G.glisse_create(1.0, w["planets"], w["particles"], 0.5, o)
     assert ei.value.code == G.GLISSE_E_INVAL
+    # Kepler modes: unknown mode, iteration counts outside 1..GLISSE_MAX_KEPLER_ITERS
+    for mode, iters in ((7, 5), (G.GLISSE_KEPLER_PAPER_FIXED, 0), (G.GLISSE_KEPLER_PAPER_FIXED, 65)):
+        o = G.glisse_opts_default()
+        o.kepler_mode, o.kepler_iters = mode, iters
+        with pytest.raises(G.GlisseError) as ei:
+            G.glisse_create(1.0, w["planets"], w["particles"], 0.5, o)
+        assert ei.value.code == G.GLISSE_E_INVAL, (mode, iters)
+    # the fixed-iteration mode is for glisse_create only
+    o = G.glisse_opts_default()
+    o.kepler_mode = G.GLISSE_KEPLER_PAPER_FIXED
+    with pytest.raises(G.GlisseError) as ei:
+        G.glisse_diff_create(1.0, w["planets"], 4, 0.5, 10, 4, o)
+    assert ei.value.code == G.GLISSE_E_INVAL
+    with pytest.raises(G.GlisseError) as ei:
+        G.glisse_batch_create([1.0], [4], w["planets"], [4], w["particles"], [0.5], o)
+    assert ei.value.code == G.GLISSE_E_INVAL
     L = G.load()
     assert L.glisse_advance(None, 1) == G.GLISSE_E_INVAL
     assert L.glisse_read(None, None, None, None, None) == G.GLISSE_E_INVAL

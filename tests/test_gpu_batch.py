@@ -48,11 +48,12 @@ def offsets(b):
 
 
 def oracle_batch(orc, b, n_steps, ids_per_system=None):
-    """Oracle run system by system; returns concatenated results (+ sensitivity)."""
+    """Oracle run system by system; returns concatenated results, sensitivity, unstable mask,
+    particle ids and the mean anomaly each particle advances (for the phase-scaled bounds)."""
     po, ao = offsets(b)
     keys = ("state", "removal_step", "reason", "margin", "closest")
     outs = {k: [] for k in keys}
-    sens_all, unst_all, idx = [], [], []
+    sens_all, unst_all, idx, phase = [], [], [], []
     for s in range(len(b["star_mass"])):
         pl = b["planets"][po[s]:po[s + 1]]
         rows = np.arange(ao[s], ao[s + 1]) if ids_per_system is None else ids_per_system[s]
@@ -67,8 +68,10 @@ def oracle_batch(orc, b, n_steps, ids_per_system=None):
         sens_all.append(sens)
         unst_all.append(unst)
         idx.append(rows)
+        phase.append(parity.phase_advance(pa, gi.G * b["star_mass"][s], b["dt"][s], n_steps))
     o = {k: np.concatenate(v) for k, v in outs.items()}
-    return o, np.concatenate(sens_all), np.concatenate(unst_all), np.concatenate(idx)
+    return (o, np.concatenate(sens_all), np.concatenate(unst_all), np.concatenate(idx),
+            np.concatenate(phase))
 
 
 def run_batch(G, b, n_steps, splits=None, **opt):
@@ -90,8 +93,8 @@ def test_batch_matches_oracle_system_by_system(G, orc):
     b = small_batch()
     n = 1500
     g = run_batch(G, b, n, chunk_steps=256)
-    o, sens, unst, ids = oracle_batch(orc, b, n)
-    rep = parity.compare(sub(g, ids), o, n, sens, unst)
+    o, sens, unst, ids, ph = oracle_batch(orc, b, n)
+    rep = parity.compare(sub(g, ids), o, n, sens, unst, ph)
     print(rep)
     parity.assert_parity(rep)
     assert rep["removed"] > 0
@@ -154,8 +157,8 @@ def test_autotuner_keeps_the_state(G, orc):
     g = sim.read()
     g["n_live"], g["step"] = sim.status()
     sim.close()
-    o, sens, unst, ids = oracle_batch(orc, b, 1000)
-    parity.assert_parity(parity.compare(sub(g, ids), o, 1000, sens, unst))
+    o, sens, unst, ids, ph = oracle_batch(orc, b, 1000)
+    parity.assert_parity(parity.compare(sub(g, ids), o, 1000, sens, unst, ph))
 
 
 def test_full_batched_workload_sampled(G, orc):
@@ -170,8 +173,8 @@ def test_full_batched_workload_sampled(G, orc):
            for s in systems}
     bb = dict(b)
     ids_per_system = [per.get(s, np.zeros(0, dtype=np.int64)) for s in range(len(b["star_mass"]))]
-    o, sens, unst, ids = oracle_batch(orc, bb, n, ids_per_system)
-    rep = parity.compare(sub(g, ids), o, n, sens, unst)
+    o, sens, unst, ids, ph = oracle_batch(orc, bb, n, ids_per_system)
+    rep = parity.compare(sub(g, ids), o, n, sens, unst, ph)
     print(rep)
     parity.assert_parity(rep)
     assert g["n_live"] == int(g["alive"].sum())
