@@ -101,6 +101,14 @@ def _bind(L):
                                    C.c_int64, i64p, i32p, dp, dp, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_double,
                                    dp]
     L.orc_particles_ex.restype = C.c_int
+    u8p = C.POINTER(C.c_uint8)
+    L.orc_elements.argtypes = [C.c_double, dp, dp]
+    L.orc_elements.restype = C.c_int
+    L.orc_barycentre.argtypes = [C.c_double, C.c_int, dp, dp, dp]
+    L.orc_barycentre.restype = None
+    L.orc_sample.argtypes = [C.c_double, C.c_int, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, dp, u8p,
+                             C.c_int64, dp, dp, u8p, u8p, i32p]
+    L.orc_sample.restype = C.c_int
     L.orc_max_threads.restype = C.c_int
     L.orc_particles_jvp.argtypes = [C.c_double, C.c_int, dp, dp, C.c_int64, C.c_double, dp, C.c_double, dp, dp,
                                     C.c_int64, dp, dp, i64p, i32p, C.c_int, C.c_int]
@@ -250,6 +258,73 @@ def particles_jacobian(star_mass, planet_masses, log, dt, state0, rcrit_, r_max,
         _, jv, _, _ = particles_jvp(star_mass, planet_masses, log, dt, s0, e, rcrit_, r_max, nthreads=nthreads)
         J[:, :, c] = jv
     return J
+
+
+def elements(mu: float, states):
+    """Osculating elements [n][6] (a, e, i, Omega, omega, M) of states [n][6] about mu."""
+    st = _f64(states).reshape(-1, 6)
+    out = np.empty_like(st)
+    for p in range(st.shape[0]):
+        row = np.ascontiguousarray(st[p])
+        el = np.empty(6)
+        if lib().orc_elements(float(mu), _dp(row), _dp(el)) != 0:
+            el[:] = np.nan
+        out[p] = el
+    return out
+
+
+def barycentre(star_mass, planet_masses, planet_states):
+    """Heliocentric state [6] of the barycentre of the star and planets ([np][6] heliocentric states)."""
+    pm = _f64(planet_masses).reshape(-1)
+    pl = _f64(planet_states).reshape(-1, 6)
+    R = np.empty(6)
+    lib().orc_barycentre(float(star_mass), pm.shape[0], _dp(pm), _dp(pl), _dp(R))
+    return R
+
+
+def run_sampled(star_mass, planets, particles, dt, n_steps, every, frame=1, res_planet=-1, res_p=0, res_q=0,
+                avoid_deg=10.0, k_hill=1.0, r_max=1000.0, nthreads=0):
+    """run() with an element sample every `every` steps (at steps every, 2 every, ... <= n_steps).
+
+    Returns the run() dict plus elements [n_samples][n][6] (NaN rows for particles not live at the
+    sample), sample_steps, phi [n_samples][n] (NaN where not used), near0, near180, count."""
+    pl = _f64(planets).copy()
+    pa = _f64(particles).reshape(-1, 6)
+    n = pa.shape[0]
+    pm = np.ascontiguousarray(pl[:, 0])
+    rc_ = rcrit(star_mass, pl, 0, k_hill)
+    pr = ParticleRun(star_mass, pm, pa, rc_, r_max)
+    near0 = np.zeros(n, dtype=np.uint8)
+    near180 = np.zeros(n, dtype=np.uint8)
+    count = np.zeros(n, dtype=np.int32)
+    elems, phis, steps, logs = [], [], [], []
+    done = 0
+    while done < n_steps:
+        m = min(every - done % every, n_steps - done)
+        pl, log, _ = planet_wh(star_mass, pl, dt, m)
+        logs.append(log if not logs else log[1:])
+        pr.advance(log, dt, nthreads)
+        done += m
+        if done % every == 0:
+            live = (pr.removal_step < 0).astype(np.uint8)
+            el = np.empty((n, 6))
+            ph = np.empty(n)
+            hel = np.ascontiguousarray(pl[:, 1:])
+            rc = lib().orc_sample(float(star_mass), pl.shape[0], _dp(pm), _dp(hel), int(frame), int(res_planet),
+                                  int(res_p), int(res_q), float(np.radians(avoid_deg)), _dp(pr.state),
+                                  live.ctypes.data_as(C.POINTER(C.c_uint8)), n, _dp(el), _dp(ph),
+                                  near0.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                  near180.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                  count.ctypes.data_as(C.POINTER(C.c_int32)))
+            if rc != 0:
+                raise RuntimeError(f"orc_sample failed: {rc}")
+            elems.append(el)
+            phis.append(ph)
+            steps.append(done)
+    return {"state": pr.state, "removal_step": pr.removal_step, "reason": pr.reason, "margin": pr.margin,
+            "closest": pr.closest, "planets": pl, "log": np.concatenate(logs) if logs else None,
+            "elements": np.array(elems).reshape(-1, n, 6), "phi": np.array(phis).reshape(-1, n),
+            "sample_steps": np.array(steps, dtype=np.int64), "near0": near0, "near180": near180, "count": count}
 
 
 def max_threads() -> int:

@@ -699,6 +699,140 @@ int orc_run(double m0, int np, double* pl, double dt, int64_t nsteps, const doub
                       test_first, nthreads, 0, 0.0, NULL);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Orbital elements and the resonant argument (section 3: the runs log       */
+/* osculating elements at a fixed interval, and a particle is counted as     */
+/* librating in the p:q resonance with a planet when                         */
+/*     phi = p lambda - q lambda_N - (p - q) varpi                           */
+/* never comes within 10 degrees of 0, or never within 10 degrees of 180,    */
+/* over the logged samples; lambda = varpi + M is the mean longitude and     */
+/* varpi = Omega + omega the longitude of pericentre).                      */
+/* Readings: elements are those of the two-body orbit about mu in the frame  */
+/* asked for; the heliocentric frame uses mu = G m0 for particles and        */
+/* G (m0 + m_j) for planet j, the barycentric frame (the frame of the        */
+/* paper's 3:1 study) subtracts the barycentre of star and planets and uses  */
+/* mu = G (m0 + sum m_j) for every body.  Angles are in [0, 2 pi); for       */
+/* e = 0 the pericentre is put at the node, for i = 0 the node on the x      */
+/* axis.  Only bound samples (e < 1) of the particle and planet count.      */
+/* ------------------------------------------------------------------------ */
+static double wrap_2pi(double x)
+{
+    double y = fmod(x, 2.0 * ORC_PI);
+    return y < 0.0 ? y + 2.0 * ORC_PI : y;
+}
+
+/* el = a, e, i, Omega, omega, M (hyperbolic orbits: M = e sinh F - F, not wrapped) */
+int orc_elements(double mu, const double* st, double* el)
+{
+    double x = st[0], y = st[1], z = st[2], vx = st[3], vy = st[4], vz = st[5];
+    double r = sqrt(x * x + y * y + z * z);
+    if (!(r > 0.0) || !(mu > 0.0)) return ORC_EINVAL;
+    double v2 = vx * vx + vy * vy + vz * vz;
+    double rv = x * vx + y * vy + z * vz;
+    /* angular momentum h = r x v */
+    double hx = y * vz - z * vy, hy = z * vx - x * vz, hz = x * vy - y * vx;
+    double h = sqrt(hx * hx + hy * hy + hz * hz);
+    if (!(h > 0.0)) return ORC_EINVAL;
+    /* eccentricity vector ((v^2 - mu/r) r - (r.v) v) / mu */
+    double c = v2 - mu / r;
+    double ex = (c * x - rv * vx) / mu, ey = (c * y - rv * vy) / mu, ez = (c * z - rv * vz) / mu;
+    double e = sqrt(ex * ex + ey * ey + ez * ez);
+    double a = 1.0 / (2.0 / r - v2 / mu);
+    double hxy = sqrt(hx * hx + hy * hy);
+    double inc = atan2(hxy, hz);
+    /* ascending node along z x h = (-hy, hx, 0) */
+    double Om = hxy > 0.0 ? atan2(hx, -hy) : 0.0;
+    /* in-plane basis: P towards the node, Q = h_hat x P */
+    double Px = cos(Om), Py = sin(Om);
+    double Qx = -hz * Py / h, Qy = hz * Px / h, Qz = (hx * Py - hy * Px) / h;
+    double u = atan2(x * Qx + y * Qy + z * Qz, x * Px + y * Py); /* argument of latitude */
+    double om = e > 0.0 ? atan2(ex * Qx + ey * Qy + ez * Qz, ex * Px + ey * Py) : 0.0;
+    double f = u - om; /* true anomaly */
+    double M;
+    if (e < 1.0) {
+        double E = atan2(sqrt(1.0 - e * e) * sin(f), e + cos(f));
+        M = wrap_2pi(E - e * sin(E));
+    } else if (e > 1.0) {
+        double F = 2.0 * atanh(sqrt((e - 1.0) / (e + 1.0)) * tan(0.5 * f));
+        M = e * sinh(F) - F;
+    } else {
+        double D = tan(0.5 * f);
+        M = D + D * D * D / 3.0;
+    }
+    el[0] = a;
+    el[1] = e;
+    el[2] = inc;
+    el[3] = wrap_2pi(Om);
+    el[4] = wrap_2pi(om);
+    el[5] = M;
+    return ORC_OK;
+}
+
+/* Heliocentric state of the barycentre of star and planets: sum m_j s_j / (m0 + sum m_j). */
+void orc_barycentre(double m0, int np, const double* pm, const double* pl, double* R)
+{
+    double mt = m0;
+    for (int j = 0; j < np; ++j) mt += pm[j];
+    for (int d = 0; d < 6; ++d) {
+        double acc = 0.0;
+        for (int j = 0; j < np; ++j) acc += pm[j] * pl[6 * j + d];
+        R[d] = acc / mt;
+    }
+}
+
+/* One sample: elements of every particle with live[p] != 0 (NaN rows otherwise) in the
+ * given frame (0 heliocentric, 1 barycentric); with res_planet >= 0 also the resonant
+ * argument phi[p] (NaN when not used) and the running flags near0 / near180 / count.
+ *   pl: [np][6] heliocentric planet states at the sample time; pm: [np] masses. */
+int orc_sample(double m0, int np, const double* pm, const double* pl, int frame, int res_planet, int res_p,
+               int res_q, double avoid, const double* state, const uint8_t* live, int64_t npart, double* elem,
+               double* phi, uint8_t* near0, uint8_t* near180, int32_t* count)
+{
+    if (np < 0 || np > ORC_MAXP || res_planet >= np || (frame != 0 && frame != 1)) return ORC_EINVAL;
+    double R[6] = {0, 0, 0, 0, 0, 0};
+    double mt = m0;
+    for (int j = 0; j < np; ++j) mt += pm[j];
+    if (frame == 1) orc_barycentre(m0, np, pm, pl, R);
+    double mu_p = ORC_G * (frame == 1 ? mt : m0);
+    double lamN = 0.0;
+    int resok = 0;
+    if (res_planet >= 0) {
+        double sN[6], elN[6];
+        for (int d = 0; d < 6; ++d) sN[d] = pl[6 * res_planet + d] - R[d];
+        double muN = ORC_G * (frame == 1 ? mt : m0 + pm[res_planet]);
+        if (orc_elements(muN, sN, elN) == ORC_OK && elN[1] < 1.0) {
+            lamN = elN[3] + elN[4] + elN[5];
+            resok = 1;
+        }
+    }
+    for (int64_t p = 0; p < npart; ++p) {
+        double* o = elem + 6 * p;
+        if (phi) phi[p] = NAN;
+        if (!live[p]) {
+            for (int d = 0; d < 6; ++d) o[d] = NAN;
+            continue;
+        }
+        double s[6];
+        for (int d = 0; d < 6; ++d) s[d] = state[6 * p + d] - R[d];
+        if (orc_elements(mu_p, s, o) != ORC_OK) {
+            for (int d = 0; d < 6; ++d) o[d] = NAN;
+            continue;
+        }
+        if (res_planet >= 0 && resok && o[1] < 1.0) {
+            double varpi = o[3] + o[4];
+            double lam = varpi + o[5];
+            double ph = wrap_2pi(res_p * lam - res_q * lamN - (res_p - res_q) * varpi);
+            double d0 = ph < ORC_PI ? ph : 2.0 * ORC_PI - ph;
+            double d180 = fabs(ph - ORC_PI);
+            if (phi) phi[p] = ph;
+            if (d0 < avoid) near0[p] = 1;
+            if (d180 < avoid) near180[p] = 1;
+            count[p] += 1;
+        }
+    }
+    return ORC_OK;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

@@ -11,6 +11,7 @@ import os
 import pytest
 
 import oracle
+import test_oracle_elements as PE
 import test_oracle_paper_mode as PM
 import test_oracle_pins as P
 import test_oracle_tangent as PT
@@ -45,6 +46,13 @@ MUTANTS = [
     ("paper_iteration_count", "for (int it = 0; it < iters; ++it) {", "for (int it = 1; it < iters; ++it) {",
      "paper_newton"),
     ("paper_accepts_unconverged", "if (!(fabs(dx) <= tol)) return ORC_EKEPLER;", "", "paper_claim"),
+    ("elements_node_sign", "double Om = hxy > 0.0 ? atan2(hx, -hy) : 0.0;",
+     "double Om = hxy > 0.0 ? atan2(-hx, hy) : 0.0;", "elements"),
+    ("elements_anomaly_eccentric", "M = wrap_2pi(E - e * sin(E));", "M = wrap_2pi(E);", "elements"),
+    ("barycentre_total_mass", "R[d] = acc / mt;", "R[d] = acc / m0;", "barycentre"),
+    ("resonant_planet_multiplier", "res_p * lam - res_q * lamN - (res_p - res_q) * varpi",
+     "res_p * lam - res_p * lamN - (res_p - res_q) * varpi", "libration"),
+    ("libration_window_inverted", "if (d0 < avoid) near0[p] = 1;", "if (d0 > avoid) near0[p] = 1;", "libration"),
 ]
 
 
@@ -74,6 +82,12 @@ def _run_pin(name):
         PM.test_last_step_matches_the_iteration_in_high_precision(oracle)
     elif name == "paper_claim":
         PM.test_five_iterations_reach_the_papers_convergence(oracle)
+    elif name == "elements":
+        PE.test_elements_invert_the_generator(oracle)
+    elif name == "barycentre":
+        PE.test_barycentre_has_zero_momentum(oracle)
+    elif name == "libration":
+        PE.test_resonant_particles_librate_and_others_circulate(oracle)
     else:
         raise KeyError(name)
 
@@ -94,6 +108,6 @@ def test_pin_catches_planted_mistake(tmp_path, mid, orig, planted, pin):
 
 def test_unmutated_oracle_passes_the_same_pins():
     for pin in ["two_body", "two_body_hyp", "tie", "escape", "hill", "energy", "tangent_sym", "tangent_fd",
-                "paper_newton", "paper_claim"]:
+                "paper_newton", "paper_claim", "elements", "barycentre", "libration"]:
         _run_pin(pin)
     assert os.path.exists(oracle.build())
