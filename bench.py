@@ -398,6 +398,9 @@ def main():
     ap.add_argument("--kepler", default="converge", choices=["converge", "paper"],
                     help="paper: the paper's fixed-iteration Kepler solve (GLISSE_KEPLER_PAPER_FIXED)")
     ap.add_argument("--kepler-iters", type=int, default=5)
+    ap.add_argument("--sample-every", type=int, default=0,
+                    help="take barycentric element samples with a 3:2 libration test against the outermost "
+                         "planet every K steps (flags only, no element log)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -447,6 +450,9 @@ def main():
     o.kepler_mode = kmode
     o.kepler_iters = args.kepler_iters
     h = G.glisse_create(w.star_mass, planets, particles, w.dt, o)
+    if args.sample_every > 0:
+        G.glisse_set_sampling(h, args.sample_every, frame=G.GLISSE_FRAME_BARY, max_samples=0, res_planet=np_ - 1,
+                              res_p=3, res_q=2, avoid_deg=10.0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def flush_l2():
@@ -539,6 +545,8 @@ def main():
                    "wall_s": t_wall},
         "kepler": (f"paper fixed-iteration solve, {args.kepler_iters} Newton iterations (library sin/cos)"
                    if paper else "converged (FP32 pre-solve + FP64 Halley step)"),
+        "sampling": (f"barycentric elements + 3:2 libration test every {args.sample_every} steps"
+                     if args.sample_every > 0 else None),
         "roofline": None if paper else {"bound": "alu", "achieved": achieved * 1e-9, "peak": peak * 1e-9, "unit": "GFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "particle_chunk_kernel<4>",
                      "kernel_ms_avg": kernel_ms, "flop_per_particle_step": flop_per_step(np_),

@@ -69,6 +69,10 @@ extern "C" {
 #define GLISSE_ENC_HILL 0  /* R_crit,j = enc_value * a_j (m_j / 3 m0)^(1/3) */
 #define GLISSE_ENC_FIXED 1 /* R_crit,j = enc_value (AU) for every planet */
 
+/* element frames for glisse_set_sampling */
+#define GLISSE_FRAME_HELIO 0 /* heliocentric; mu = G m0 (particles), G (m0 + m_j) (planet j) */
+#define GLISSE_FRAME_BARY 1  /* barycentre of star and planets; mu = G (m0 + sum m_j) for every body */
+
 typedef struct glisse_ctx glisse_ctx; /* opaque; owned by the library */
 
 typedef struct {
@@ -141,6 +145,7 @@ int glisse_read_planets(glisse_ctx* ctx, double* planets, double* t);
  * The common term h0 = -sum_j G m_j r_j / |r_j|^3 is computed from these positions.
  * After these steps are consumed, glisse_advance() returns STATE until another
  * log is installed; the built-in planets are no longer valid for this context.
+ * Returns STATE while element sampling is set (glisse_set_sampling).
  */
 int glisse_set_ephemeris(glisse_ctx* ctx, const double* log, int64_t n_steps);
 
@@ -236,7 +241,7 @@ typedef struct glisse_diff glisse_diff; /* opaque; owned by the library */
 /* Planets as in glisse_create; n_particles states per forward call; the planet
  * log of n_steps steps is computed on the device here.  checkpoint_every >= 1:
  * the backward pass recomputes that many steps per segment (storage: 48 B per
- * particle per checkpoint plus 72 B per particle per step of one segment).
+ * particle per checkpoint plus 88 B per particle per step of one segment).
  * opts: enc_mode, enc_value and r_max apply.  Errors: INVAL, NOMEM, CUDA, KEPLER. */
 int glisse_diff_create(glisse_diff** out, double star_mass, const double* planets, int32_t n_planets,
                        int64_t n_particles, double dt, int64_t n_steps, int32_t checkpoint_every,
@@ -258,6 +263,51 @@ int glisse_diff_backward(glisse_diff* d, const double* grad_state1, double* grad
 
 /* Release the object (NULL is ignored). */
 void glisse_diff_destroy(glisse_diff* d);
+
+/* ------------------------------------------------------------------------ */
+/* Element sampling and resonance libration (section 3: osculating elements */
+/* are logged at a fixed interval, and a particle librates in the p:q       */
+/* resonance with a planet when                                             */
+/*     phi = p lambda - q lambda_planet - (p - q) varpi                     */
+/* never comes within avoid_deg of 0, or never within avoid_deg of 180     */
+/* degrees, over the samples; lambda = varpi + M, varpi = Omega + omega).   */
+/* A sample is taken at every global step that is a multiple of `every`,   */
+/* on the particles live at that step, by a kernel that runs between the   */
+/* particle segments (glisse_advance ends a segment at each sample step).  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t every;       /* steps between samples, >= 1 */
+    int32_t frame;       /* GLISSE_FRAME_HELIO or GLISSE_FRAME_BARY */
+    int64_t max_samples; /* samples of elements kept on the device (0: none, flags only);
+                            needs 48 B per particle per sample */
+    int32_t res_planet;  /* 0-based planet of the resonance (e.g. 3 for the 4th), -1: no libration test */
+    int32_t res_p;       /* p >= 1 of the p:q resonance (3 for 3:1, 5 for 5:2) */
+    int32_t res_q;       /* q >= 0 */
+    int32_t pad_;
+    double avoid_deg;    /* window half-width in degrees, 0 < avoid_deg < 90 (10 in section 3) */
+} glisse_sampling;
+
+/* Start sampling with *s (replacing earlier settings and discarding their
+ * samples and flags), or stop it with s == NULL.  Needs the internal planet
+ * integration (GLISSE_E_STATE after glisse_set_ephemeris: no planet
+ * velocities).  Errors: INVAL (bad field), STATE, NOMEM, CUDA. */
+int glisse_set_sampling(glisse_ctx* ctx, const glisse_sampling* s);
+
+/* Copy up to max_samples samples to host memory: elements [max_samples][n][6]
+ * (a, e, i, Omega, omega, M per particle id, angles in radians; NaN rows for
+ * particles not live at the sample) and sample_steps [max_samples] (global
+ * step of each sample; may be NULL).  *n_samples receives the number copied.
+ * Samples past the max_samples given to glisse_set_sampling are not kept.
+ * Errors: INVAL, STATE (sampling not set), CUDA. */
+int glisse_read_elements(glisse_ctx* ctx, double* elements, int64_t* sample_steps, int64_t max_samples,
+                         int64_t* n_samples);
+
+/* Copy the libration flags per particle id to host memory: near0[n] / near180[n]
+ * = 1 if phi came within the window of 0 / 180 degrees in some sample,
+ * count[n] = samples that entered the test (bound particle and planet).  A
+ * particle librates when count > 0 and (near0 == 0 or near180 == 0).  Any
+ * pointer may be NULL.  Errors: INVAL, STATE (no libration test set), CUDA. */
+int glisse_read_libration(glisse_ctx* ctx, uint8_t* near0, uint8_t* near180, int32_t* count);
 
 /* ------------------------------------------------------------------------ */
 /* Many independent systems in one context (a batch).                        */

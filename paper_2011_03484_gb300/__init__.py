@@ -34,6 +34,8 @@ GLISSE_PAPER_KEPLER_TOL = 1e-14
 GLISSE_MAX_KEPLER_ITERS = 64
 GLISSE_ENC_HILL = 0
 GLISSE_ENC_FIXED = 1
+GLISSE_FRAME_HELIO = 0
+GLISSE_FRAME_BARY = 1
 
 # every symbol the header declares (checked by the tests against the built library)
 EXPORTED = (
@@ -43,6 +45,7 @@ EXPORTED = (
     "glisse_batch_create", "glisse_batch_advance", "glisse_batch_read", "glisse_batch_status",
     "glisse_batch_timings", "glisse_batch_tune", "glisse_batch_destroy",
     "glisse_diff_create", "glisse_diff_forward", "glisse_diff_backward", "glisse_diff_destroy",
+    "glisse_set_sampling", "glisse_read_elements", "glisse_read_libration",
 )
 
 GLISSE_PARTITION_NOALLOC_MAX = 67108864
@@ -71,6 +74,19 @@ class glisse_opts(C.Structure):
         ("enc_value", C.c_double),
         ("r_max", C.c_double),
         ("cuda_stream", C.c_void_p),
+    ]
+
+
+class glisse_sampling(C.Structure):
+    _fields_ = [
+        ("every", C.c_int32),
+        ("frame", C.c_int32),
+        ("max_samples", C.c_int64),
+        ("res_planet", C.c_int32),
+        ("res_p", C.c_int32),
+        ("res_q", C.c_int32),
+        ("pad_", C.c_int32),
+        ("avoid_deg", C.c_double),
     ]
 
 
@@ -150,6 +166,12 @@ def load(build_if_missing: bool = False):
     L.glisse_diff_backward.restype = C.c_int
     L.glisse_diff_destroy.argtypes = [vp]
     L.glisse_diff_destroy.restype = None
+    L.glisse_set_sampling.argtypes = [vp, C.POINTER(glisse_sampling)]
+    L.glisse_set_sampling.restype = C.c_int
+    L.glisse_read_elements.argtypes = [vp, dp, i64p, C.c_int64, i64p]
+    L.glisse_read_elements.restype = C.c_int
+    L.glisse_read_libration.argtypes = [vp, u8p, u8p, i32p]
+    L.glisse_read_libration.restype = C.c_int
     _lib = L
     return L
 
@@ -203,6 +225,40 @@ def glisse_read(h, n: int):
                             steps.ctypes.data_as(C.POINTER(C.c_int64)), rsn.ctypes.data_as(C.POINTER(C.c_int32)))
     _check(rc, "glisse_read")
     return {"state": st, "alive": alive.astype(bool), "removal_step": steps, "removal_reason": rsn}
+
+
+def glisse_set_sampling(h, every=None, frame=GLISSE_FRAME_BARY, max_samples=0, res_planet=-1, res_p=0, res_q=0,
+                        avoid_deg=10.0):
+    """Start element sampling every `every` steps (None: stop sampling)."""
+    if every is None:
+        _check(load().glisse_set_sampling(h, None), "glisse_set_sampling")
+        return
+    sp = glisse_sampling(int(every), int(frame), int(max_samples), int(res_planet), int(res_p), int(res_q), 0,
+                         float(avoid_deg))
+    _check(load().glisse_set_sampling(h, C.byref(sp)), "glisse_set_sampling")
+
+
+def glisse_read_elements(h, n: int, max_samples: int):
+    """Returns (elements [k][n][6], sample_steps [k]) for the k <= max_samples kept samples."""
+    el = np.empty((max(max_samples, 0), n, 6))
+    steps = np.empty(max(max_samples, 0), dtype=np.int64)
+    k = C.c_int64()
+    _check(load().glisse_read_elements(h, _dp(el) if max_samples > 0 else None,
+                                       steps.ctypes.data_as(C.POINTER(C.c_int64)), int(max_samples),
+                                       C.byref(k)), "glisse_read_elements")
+    return el[:k.value], steps[:k.value]
+
+
+def glisse_read_libration(h, n: int):
+    """Returns dict(near0, near180 [n] bool, count [n], librating [n] bool)."""
+    n0 = np.zeros(n, dtype=np.uint8)
+    n1 = np.zeros(n, dtype=np.uint8)
+    cnt = np.zeros(n, dtype=np.int32)
+    _check(load().glisse_read_libration(h, n0.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                        n1.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                        cnt.ctypes.data_as(C.POINTER(C.c_int32))), "glisse_read_libration")
+    return {"near0": n0.astype(bool), "near180": n1.astype(bool), "count": cnt,
+            "librating": (cnt > 0) & ~(n0.astype(bool) & n1.astype(bool))}
 
 
 def glisse_status(h):
@@ -382,6 +438,16 @@ class Simulation:
 
     def timings(self, reset=False):
         return glisse_timings(self.h, reset)
+
+    def set_sampling(self, every=None, **kw):
+        self.max_samples = int(kw.get("max_samples", 0)) if every is not None else 0
+        glisse_set_sampling(self.h, every, **kw)
+
+    def elements(self):
+        return glisse_read_elements(self.h, self.n, getattr(self, "max_samples", 0))
+
+    def libration(self):
+        return glisse_read_libration(self.h, self.n)
 
     def close(self):
         if self.h:

@@ -41,6 +41,8 @@ cudaError_t launch_export_live(int64_t, const double*, int64_t, const int32_t*, 
 cudaError_t launch_import(int64_t, const double*, double*, int64_t, int32_t*, cudaStream_t);
 }  // namespace glisse
 
+#include <vector>
+
 using namespace glisse;
 
 namespace {
@@ -93,6 +95,15 @@ struct glisse_ctx {
     cudaEvent_t te0[kRing] = {}, te1[kRing] = {};
     bool eph_pending[kRing] = {};
     glisse_timing acc{};
+    // element sampling / libration test (glisse_set_sampling)
+    bool samp_on = false;
+    glisse_sampling samp{};
+    double* d_elem = nullptr;               // [max_samples][n_total][6] by id
+    std::vector<int64_t> samp_steps;        // global step of each kept sample
+    int64_t samp_seen = 0;                  // samples taken (kept or not)
+    uint8_t* d_near0 = nullptr;
+    uint8_t* d_near180 = nullptr;
+    int32_t* d_count = nullptr;
 };
 
 #define GL_CUDA(x)                               \
@@ -165,6 +176,10 @@ static void ctx_free(glisse_ctx* c) {
         cudaFree(c->d_st[b]);
         cudaFree(c->d_id[b]);
     }
+    cudaFree(c->d_elem);
+    cudaFree(c->d_near0);
+    cudaFree(c->d_near180);
+    cudaFree(c->d_count);
     cudaFree(c->d_pc);
     cudaFree(c->d_jac);
     cudaFree(c->d_status);
@@ -395,6 +410,102 @@ static int compact(glisse_ctx* c) {
     return *c->h_status;
 }
 
+// One element sample on the stream (after the particle segment, before compaction).
+static int take_sample(glisse_ctx* c, const double* planets_at_step, int64_t step) {
+    SampleArgs a;
+    a.n = c->n_live;
+    a.ld = c->cap;
+    a.st = c->d_st[c->cur];
+    a.id = c->d_id[c->cur];
+    a.alive = c->d_alive;
+    a.planets = planets_at_step;
+    a.pc = c->d_pc;
+    a.frame = c->samp.frame;
+    a.res_planet = c->samp.res_planet;
+    a.res_p = c->samp.res_p;
+    a.res_q = c->samp.res_q;
+    a.avoid = c->samp.avoid_deg * (3.14159265358979323846 / 180.0);
+    a.elem = nullptr;
+    if ((int64_t)c->samp_steps.size() < c->samp.max_samples) {
+        a.elem = c->d_elem + (size_t)c->samp_steps.size() * 6 * c->n_total;
+        // NaN rows (all-ones bit pattern) for ids not live at this sample
+        GL_CUDA(cudaMemsetAsync(a.elem, 0xFF, sizeof(double) * 6 * c->n_total, c->s));
+        c->samp_steps.push_back(step);
+    }
+    a.near0 = c->d_near0;
+    a.near180 = c->d_near180;
+    a.count = c->d_count;
+    GL_CUDA(launch_sample(a, c->s));
+    ++c->samp_seen;
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_set_sampling(glisse_ctx* c, const glisse_sampling* sp) {
+    if (!c) return GLISSE_E_INVAL;
+    if (sp) {
+        if (sp->every < 1 || (sp->frame != GLISSE_FRAME_HELIO && sp->frame != GLISSE_FRAME_BARY) ||
+            sp->max_samples < 0 || sp->res_planet < -1 || sp->res_planet >= c->np)
+            return GLISSE_E_INVAL;
+        if (sp->res_planet >= 0 && (sp->res_p < 1 || sp->res_q < 0 || !(sp->avoid_deg > 0.0) ||
+                                    !(sp->avoid_deg < 90.0)))
+            return GLISSE_E_INVAL;
+        if (c->external) return GLISSE_E_STATE;
+        if (sp->max_samples > 0 && (uint64_t)sp->max_samples > (uint64_t)1 << 40) return GLISSE_E_NOMEM;
+    }
+    GL_CUDA(cudaStreamSynchronize(c->s));
+    cudaFree(c->d_elem);
+    cudaFree(c->d_near0);
+    cudaFree(c->d_near180);
+    cudaFree(c->d_count);
+    c->d_elem = nullptr;
+    c->d_near0 = c->d_near180 = nullptr;
+    c->d_count = nullptr;
+    c->samp_steps.clear();
+    c->samp_seen = 0;
+    c->samp_on = false;
+    if (!sp) return GLISSE_OK;
+    c->samp = *sp;
+    const size_t n = (size_t)std::max<int64_t>(c->n_total, 1);
+    if (sp->max_samples > 0) GL_ALLOC(c->d_elem, sizeof(double) * 6 * n * (size_t)sp->max_samples);
+    GL_ALLOC(c->d_near0, n);
+    GL_ALLOC(c->d_near180, n);
+    GL_ALLOC(c->d_count, sizeof(int32_t) * n);
+    GL_CUDA(cudaMemsetAsync(c->d_near0, 0, n, c->s));
+    GL_CUDA(cudaMemsetAsync(c->d_near180, 0, n, c->s));
+    GL_CUDA(cudaMemsetAsync(c->d_count, 0, sizeof(int32_t) * n, c->s));
+    GL_CUDA(cudaStreamSynchronize(c->s));
+    c->samp_on = true;
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_read_elements(glisse_ctx* c, double* elements, int64_t* sample_steps, int64_t max_samples,
+                                    int64_t* n_samples) {
+    if (!c || max_samples < 0 || !n_samples) return GLISSE_E_INVAL;
+    if (!c->samp_on) return GLISSE_E_STATE;
+    const int64_t k = std::min<int64_t>(max_samples, (int64_t)c->samp_steps.size());
+    if (k > 0 && !elements) return GLISSE_E_INVAL;
+    GL_CUDA(cudaStreamSynchronize(c->s));
+    if (k > 0)
+        GL_CUDA(cudaMemcpy(elements, c->d_elem, sizeof(double) * 6 * (size_t)c->n_total * (size_t)k,
+                           cudaMemcpyDeviceToHost));
+    if (sample_steps)
+        for (int64_t i = 0; i < k; ++i) sample_steps[i] = c->samp_steps[(size_t)i];
+    *n_samples = k;
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_read_libration(glisse_ctx* c, uint8_t* near0, uint8_t* near180, int32_t* count) {
+    if (!c) return GLISSE_E_INVAL;
+    if (!c->samp_on || c->samp.res_planet < 0) return GLISSE_E_STATE;
+    GL_CUDA(cudaStreamSynchronize(c->s));
+    const size_t n = (size_t)c->n_total;
+    if (n == 0) return GLISSE_OK;
+    if (near0) GL_CUDA(cudaMemcpy(near0, c->d_near0, n, cudaMemcpyDeviceToHost));
+    if (near180) GL_CUDA(cudaMemcpy(near180, c->d_near180, n, cudaMemcpyDeviceToHost));
+    if (count) GL_CUDA(cudaMemcpy(count, c->d_count, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    return GLISSE_OK;
+}
+
 extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
     if (!c || n_steps < 0) return GLISSE_E_INVAL;
     if (n_steps == 0) return GLISSE_OK;
@@ -425,6 +536,11 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
             GL_CUDA(cudaStreamWaitEvent(c->s, c->ev_eph[slot], 0));
             m = std::min<int64_t>(remaining, c->C - off);
             log = c->d_log[slot] + (size_t)off * S;
+            if (c->samp_on) {
+                // end the segment at the next sample step
+                const int64_t next = (c->step / c->samp.every + 1) * c->samp.every;
+                m = std::min<int64_t>(m, next - c->step);
+            }
         }
         if (c->n_live > 0) {
             ChunkArgs a;
@@ -468,6 +584,12 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
             c->eph_pending[slot] = false;
         }
         c->tested_first = true;
+        if (c->samp_on && slot >= 0 && (c->step + m) % c->samp.every == 0) {
+            // sample the particles live at step + m, with the planets of that step
+            const int64_t off = c->step - (c->step / c->C) * c->C;
+            if ((rc = take_sample(c, c->d_hist[slot] + (size_t)(off + m) * 6 * c->np, c->step + m)) != GLISSE_OK)
+                break;
+        }
         if (slot >= 0) {
             GL_CUDA(cudaEventRecord(c->ev_use[slot], c->s));
             c->used[slot] = true;
@@ -541,6 +663,7 @@ extern "C" int glisse_read_planets(glisse_ctx* c, double* planets, double* t) {
 
 extern "C" int glisse_set_ephemeris(glisse_ctx* c, const double* log, int64_t n_steps) {
     if (!c || n_steps < 1 || (!log && c->np > 0)) return GLISSE_E_INVAL;
+    if (c->samp_on) return GLISSE_E_STATE;  // sampling needs the planets' velocities
     const int S = log_stride(c->np);
     GL_CUDA(cudaStreamSynchronize(c->s));
     GL_CUDA(cudaStreamSynchronize(c->se));

@@ -95,4 +95,26 @@ struct BatchArgs {
     unsigned long long* steps_done;
 };
 
+// Arguments of one element sample (section 3: osculating elements logged at a
+// fixed interval; libration of a resonant argument).
+struct SampleArgs {
+    int64_t n;                 // live slots
+    int64_t ld;                // leading dimension of the state planes
+    const double* st;          // [6][ld]
+    const int32_t* id;         // [n]
+    const uint8_t* alive;      // [n]
+    const double* planets;     // [np][6] heliocentric planet states at the sample step
+    const PlanetConsts* pc;    // masses, m0, G
+    int32_t frame;             // GLISSE_FRAME_*
+    int32_t res_planet;        // 0-based planet of the resonance, -1: none
+    int32_t res_p, res_q;      // phi = p lambda - q lambda_planet - (p - q) varpi
+    double avoid;              // half-width of the windows around 0 and 180 degrees, radians
+    double* elem;              // [N][6] by id, or null
+    uint8_t* near0;            // [N] by id (res_planet >= 0)
+    uint8_t* near180;          // [N]
+    int32_t* count;            // [N] samples that entered the test
+};
+
+cudaError_t launch_sample(const SampleArgs& a, cudaStream_t s);
+
 }  // namespace glisse
