@@ -13,8 +13,10 @@
 // tangent vectors through n steps (explicit half kicks) and stores the
 // synchronised state every K steps.  Backward: for each K-step segment from
 // the last, the thread recomputes the segment from its checkpoint, keeping the
-// pre-drift state and the post-drift position of every step in a scratch
-// buffer, then runs the adjoint kicks and drifts backwards through it.
+// pre-drift state, the post-drift position and the solved universal anomaly
+// s and reduced time tau of every step in a scratch buffer, then runs the
+// adjoint kicks and drifts backwards through it (the drift's G-functions are
+// re-evaluated from the stored s and tau, without a second solve).
 // A removed particle's output is its frozen state; its derivatives are those
 // of that frozen state (the steps after removal contribute nothing).
 #include <cuda_runtime.h>
@@ -33,6 +35,7 @@ cudaError_t launch_eph_setup(const double*, int, double, double, int, double, Pl
 cudaError_t launch_eph_chunk(const PlanetConsts*, double*, double, int, double*, double*, int*, cudaStream_t);
 
 constexpr int kMaxTangents = 6;
+constexpr int kScratchRows = 11;  // pre-drift state (6), post-drift position (3), s, tau
 constexpr int kDiffBlock = 128;
 
 struct DiffArgs {
@@ -49,7 +52,7 @@ struct DiffArgs {
     int64_t* rstep;         // [n] removal step (-1 live)
     int32_t* reason;        // [n]
     double* ckpt;           // [ceil(nsteps / K)][6][n]
-    double* scratch;        // [K][9][n]
+    double* scratch;        // [K][kScratchRows][n]
     const double* grad1;    // [n][6]
     double* grad0;          // [n][6]
 };
@@ -203,11 +206,13 @@ __global__ void __launch_bounds__(kDiffBlock) diff_backward_kernel(const DiffArg
             for (int64_t k = k0; k < k1; ++k) {
                 const double* L0 = a.log + k * S;
                 kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);
-                double* sc = a.scratch + (k - k0) * 9 * a.n + i;
+                double* sc = a.scratch + (k - k0) * kScratchRows * a.n + i;
                 for (int c = 0; c < 6; ++c) sc[c * a.n] = st[c];
                 if (k == kend - 1 && cut_before_drift) break;
                 DriftScalars d;
                 drift_scalars(pc.mu, pc.dt, st, d);
+                sc[9 * a.n] = d.s;
+                sc[10 * a.n] = d.tau;
                 double pre[6];
                 for (int c = 0; c < 6; ++c) pre[c] = st[c];
                 for (int c = 0; c < 3; ++c) {
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(kDiffBlock) diff_backward_kernel(const DiffArg
             }
             // adjoint sweep, last step first
             for (int64_t k = k1 - 1; k >= k0; --k) {
-                const double* sc = a.scratch + (k - k0) * 9 * a.n + i;
+                const double* sc = a.scratch + (k - k0) * kScratchRows * a.n + i;
                 double pre[6], post[3];
                 for (int c = 0; c < 6; ++c) pre[c] = sc[c * a.n];
                 for (int c = 0; c < 3; ++c) post[c] = sc[(6 + c) * a.n];
@@ -230,7 +235,8 @@ __global__ void __launch_bounds__(kDiffBlock) diff_backward_kernel(const DiffArg
                 }
                 if (!(last && cut_before_drift)) {
                     DriftScalars d;
-                    drift_scalars(pc.mu, pc.dt, pre, d);
+                    drift_restore(pc.mu, pc.dt, pre, sc[9 * a.n], sc[10 * a.n], d);
+                    drift_finish(pc.mu, d);
                     drift_adjoint(pc.mu, pre, d, l);
                 }
                 // opening half kick at t_k: lr += (dt/2) A(pre) lv
@@ -345,7 +351,7 @@ extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const dou
         const int64_t np1 = std::max<int64_t>(n_particles, 1);
         if (cudaMalloc(&d->d_log, sizeof(double) * (size_t)(n_steps + 1) * S) != cudaSuccess ||
             cudaMalloc(&d->d_ckpt, sizeof(double) * (size_t)nck * 6 * np1) != cudaSuccess ||
-            cudaMalloc(&d->d_scratch, sizeof(double) * (size_t)d->K * 9 * np1) != cudaSuccess ||
+            cudaMalloc(&d->d_scratch, sizeof(double) * (size_t)d->K * kScratchRows * np1) != cudaSuccess ||
             cudaMalloc(&d->d_rstep, sizeof(int64_t) * np1) != cudaSuccess ||
             cudaMalloc(&d->d_reason, sizeof(int32_t) * np1) != cudaSuccess) {
             (void)cudaGetLastError();

@@ -405,19 +405,82 @@ struct DriftScalars {
     double R, f, g, fd, gd;
 };
 
-// Drift scalars of one body at its current state (general solver; FP64 throughout).
-__device__ inline bool drift_scalars(double mu, double dt, const double st[6], DriftScalars& d) {
+// Drift scalars of one body at its current state, in two parts: drift_solve
+// finds s (and tau, dtau/dbeta) and drift_finish evaluates the G-functions and
+// f, g from them, so that a caller that stored s and tau can redo the second
+// part alone.  drift_solve starts from the FP32 root of the fast path and
+// takes two full FP64 Newton steps (the FP32 start is good to ~1e-7, so the
+// second step lands at rounding level); orbits outside the FP32 domain, or
+// |z| > 0.1, use the general safeguarded solver.
+__device__ inline bool drift_solve(double mu, double dt, const double st[6], DriftScalars& d) {
     d.r0 = sqrt(st[0] * st[0] + st[1] * st[1] + st[2] * st[2]);
     const double v2 = st[3] * st[3] + st[4] * st[4] + st[5] * st[5];
     d.u = st[0] * st[3] + st[1] * st[4] + st[2] * st[5];
     d.beta = 2.0 * mu / d.r0 - v2;
-    double kper;
-    if (!universal_solve(mu, dt, d.r0, d.u, d.beta, d.s, d.tau, kper)) return false;
     d.dtau_dbeta = 0.0;
-    if (kper != 0.0) {
+    // FP32 start (the fast path's iteration), accepted only well inside its domain
+    const int er = exp_bits(d.r0), ev = exp_bits(v2);
+    bool ok = er > 1023 - 60 && er < 1023 + 60 && ev < 1023 + 120 && ev > 1023 - 200 && dt != 0.0;
+    if (ok) {
+        const float r0f = (float)d.r0, uf = (float)d.u, bf = (float)d.beta, muf = (float)mu, dtf = (float)dt;
+        float sf = dtf / r0f, dsf = 0.f;
+        for (int it = 0; it < 4; ++it) {
+            const float zf = bf * sf * sf;
+            const float c2 = fmaf(zf, fmaf(zf, fmaf(zf, -1.0f / 40320.0f, 1.0f / 720.0f), -1.0f / 24.0f), 0.5f);
+            const float c3 =
+                fmaf(zf, fmaf(zf, fmaf(zf, -1.0f / 362880.0f, 1.0f / 5040.0f), -1.0f / 120.0f), 1.0f / 6.0f);
+            const float G1 = sf * fmaf(-zf, c3, 1.0f), G2 = sf * sf * c2, G3 = sf * sf * sf * c3;
+            const float F = fmaf(r0f, G1, fmaf(uf, G2, fmaf(muf, G3, -dtf)));
+            const float Fp = fmaf(r0f, fmaf(-zf, c2, 1.0f), fmaf(uf, G1, muf * G2));
+            dsf = -F / Fp;
+            sf += dsf;
+        }
+        ok = isfinite(sf) && fabsf(dsf) <= 1e-5f * fabsf(sf) && fabsf(bf * sf * sf) <= 0.09f;
+        if (ok) {
+            double s = (double)sf;
+            for (int it = 0; it < 2; ++it) {
+                double c2, c3;
+                const double z = d.beta * s * s;
+                c23_poly<7>(z, c2, c3);
+                const double G1 = s * fma(-z, c3, 1.0), G2 = s * s * c2, G3 = s * s * s * c3;
+                const double F = d.r0 * G1 + d.u * G2 + mu * G3 - dt;
+                const double Fp = d.r0 * fma(-z, c2, 1.0) + d.u * G1 + mu * G2;
+                s -= F / Fp;
+            }
+            ok = isfinite(s) && fabs(d.beta * s * s) <= 0.1;
+            d.s = s;
+            d.tau = dt;
+        }
+    }
+    if (!ok) {
+        double kper;
+        if (!universal_solve(mu, dt, d.r0, d.u, d.beta, d.s, d.tau, kper)) return false;
+        if (kper != 0.0) {
+            const double period = 6.283185307179586476925286766559 * mu / (d.beta * sqrt(d.beta));
+            d.dtau_dbeta = 1.5 * kper * period / d.beta;
+        }
+    }
+    return true;
+}
+
+// Recover r0, u, beta and dtau/dbeta of a state whose s and tau were stored.
+__device__ inline void drift_restore(double mu, double dt, const double st[6], double s, double tau,
+                                     DriftScalars& d) {
+    d.r0 = sqrt(st[0] * st[0] + st[1] * st[1] + st[2] * st[2]);
+    const double v2 = st[3] * st[3] + st[4] * st[4] + st[5] * st[5];
+    d.u = st[0] * st[3] + st[1] * st[4] + st[2] * st[5];
+    d.beta = 2.0 * mu / d.r0 - v2;
+    d.s = s;
+    d.tau = tau;
+    d.dtau_dbeta = 0.0;
+    if (tau != dt && d.beta > 0.0) {
         const double period = 6.283185307179586476925286766559 * mu / (d.beta * sqrt(d.beta));
+        const double kper = rint((dt - tau) / period);
         d.dtau_dbeta = 1.5 * kper * period / d.beta;
     }
+}
+
+__device__ inline void drift_finish(double mu, DriftScalars& d) {
     double c[6];
     stumpff_all(d.beta * d.s * d.s, c);
     double sp = 1.0;
@@ -431,10 +494,15 @@ __device__ inline bool drift_scalars(double mu, double dt, const double st[6], D
     d.g = d.tau - mu * d.G[3];
     d.fd = -mu * d.G[1] / (d.R * d.r0);
     d.gd = 1.0 - mu * d.G[2] / d.R;
+}
+
+// Drift scalars of one body at its current state.
+__device__ inline bool drift_scalars(double mu, double dt, const double st[6], DriftScalars& d) {
+    if (!drift_solve(mu, dt, st, d)) return false;
+    drift_finish(mu, d);
     return true;
 }
 
-// Tangent of the drift: (dr, dv) at the start -> (dr1, dv1) at the end (in place).
 __device__ inline void drift_tangent(double mu, const double st[6], const DriftScalars& d, double t[6]) {
     const double *r = st, *v = st + 3;
     const double dr0 = (r[0] * t[0] + r[1] * t[1] + r[2] * t[2]) / d.r0;
