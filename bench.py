@@ -37,16 +37,16 @@ UNIT = "particle-steps/s"
 
 # FP64 work of one interior particle-step in the kernel's formulation (static count of
 # the source; ncu's executed DADD:DMUL:DFMA mix matches it): the fast Kepler drift with
-# the degree-3 Stumpff tier (4 DADD, 11 DMUL, 39 DFMA), the h0 term (3 DFMA), and per
-# planet 3 DADD + 2 DMUL + 8 DFMA (separation, |d|^2, k |d|^-3 with the seed's square
-# and cube formed in integer arithmetic, velocity update).
+# the degree-3 Stumpff tier (3 DADD, 13 DMUL, 42 DFMA), the h0 term (3 DFMA), and per
+# planet 3 DADD + 1 DMUL + 8 DFMA (separation, |d|^2, k |d|^-3 with the seed's square
+# and k times its cube formed in integer arithmetic, velocity update).
 def fp64_instr_per_step(np_: int) -> int:
-    return 54 + 3 + 13 * np_
+    return 58 + 3 + 12 * np_
 
 
 def flop_per_step(np_: int) -> int:
     # DFMA counts 2 FLOP, DADD / DMUL 1
-    return (4 + 11 + 2 * 39) + 2 * 3 + np_ * (3 + 2 + 2 * 8)
+    return (3 + 13 + 2 * 42) + 2 * 3 + np_ * (3 + 1 + 2 * 8)
 
 
 # GB300 FP64 pipe: 2 DFMA per clock per SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
@@ -389,7 +389,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="longrun", choices=["longrun", "belt", "tiny", "batched", "diff"])
+    ap.add_argument("--workload", default="longrun",
+                    choices=["longrun", "belt", "tiny", "batched", "diff", "eccentric"])
+    ap.add_argument("--sort", action="store_true",
+                    help="order live particles by expected Kepler-solve cost at every compaction")
     ap.add_argument("--tune", action="store_true", help="batched: run the autotuner before timing")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-particles", type=int, default=8192)
@@ -449,6 +452,7 @@ def main():
     kmode = G.GLISSE_KEPLER_PAPER_FIXED if paper else G.GLISSE_KEPLER_CONVERGE
     o.kepler_mode = kmode
     o.kepler_iters = args.kepler_iters
+    o.sort_mode = G.GLISSE_SORT_COST if args.sort else G.GLISSE_SORT_NONE
     h = G.glisse_create(w.star_mass, planets, particles, w.dt, o)
     if args.sample_every > 0:
         G.glisse_set_sampling(h, args.sample_every, frame=G.GLISSE_FRAME_BARY, max_samples=0, res_planet=np_ - 1,
@@ -510,7 +514,8 @@ def main():
         for k in range(args.e2e_steps + 1):
             t0 = time.perf_counter()
             sim = G.Simulation(w.star_mass, planets, particles, w.dt, chunk_steps=w.chunk, enc_value=w.k_hill,
-                               r_max=w.r_max, timing=1, kepler_mode=kmode, kepler_iters=args.kepler_iters)
+                               r_max=w.r_max, timing=1, kepler_mode=kmode, kepler_iters=args.kepler_iters,
+                               sort_mode=o.sort_mode)
             sim.advance(w.chunk)
             out = sim.read()
             st = sim.timings()["particle_steps"]
@@ -547,6 +552,7 @@ def main():
                    if paper else "converged (FP32 pre-solve + FP64 Halley step)"),
         "sampling": (f"barycentric elements + 3:2 libration test every {args.sample_every} steps"
                      if args.sample_every > 0 else None),
+        "sort": "by expected Kepler-solve cost, costliest first" if args.sort else None,
         "roofline": None if paper else {"bound": "alu", "achieved": achieved * 1e-9, "peak": peak * 1e-9, "unit": "GFLOP/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "particle_chunk_kernel<4>",
                      "kernel_ms_avg": kernel_ms, "flop_per_particle_step": flop_per_step(np_),

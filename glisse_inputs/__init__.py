@@ -18,6 +18,8 @@ this implementation:
             1e6 steps, seed 2 (resonant belt, frequent removal)
   diff      65536 particles, a in U[22, 28], e in U[0, 0.05], sigma_i = 1 deg,
             1e4 steps, seed 3
+  eccentric 131072 particles, a in U[20, 29], e in U[0, 0.9], sigma_i = 2 deg,
+            seed 5 (mixed solve costs: the sorting option's workload)
 
 All share the 4-planet system below: star of 1 M_sun; planets at
 a = 5.2, 9.55, 19.2, 30.1 AU with m = 9.5e-4, 2.9e-4, 4.4e-5, 5.2e-5 M_sun,
@@ -67,6 +69,7 @@ WORKLOADS = {
     "longrun": Workload("longrun", 131072, (20.0, 29.0), (0.0, 0.1), 2.0, 0.5, 2_000_000, 1),
     "belt": Workload("belt", 1048576, (40.0, 50.0), (0.0, 0.4), 5.0, 0.5, 1_000_000, 2),
     "diff": Workload("diff", 65536, (22.0, 28.0), (0.0, 0.05), 1.0, 0.5, 10_000, 3),
+    "eccentric": Workload("eccentric", 131072, (20.0, 29.0), (0.0, 0.9), 2.0, 0.5, 2_000_000, 5),
 }
 
 

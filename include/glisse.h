@@ -60,14 +60,26 @@ extern "C" {
  * is removed with GLISSE_REMOVED_KEPLER, keeping its state from before the
  * drift.  Unbound or nearly radial orbits (r alpha < 1e-3), which the paper
  * does not treat, use the converged universal-variable solve.  Only
- * glisse_create accepts it; the batched and differentiable entry points
- * return GLISSE_E_INVAL. */
+ * glisse_create accepts it (and GLISSE_SORT_COST); the batched and
+ * differentiable entry points return GLISSE_E_INVAL for either. */
 #define GLISSE_PAPER_KEPLER_TOL 1e-14
 #define GLISSE_MAX_KEPLER_ITERS 64
 
 /* encounter criterion (section 2.2, close-encounter paragraph) */
 #define GLISSE_ENC_HILL 0  /* R_crit,j = enc_value * a_j (m_j / 3 m0)^(1/3) */
 #define GLISSE_ENC_FIXED 1 /* R_crit,j = enc_value (AU) for every planet */
+
+/* particle order (section 2.2 suggests sorting particles by the expected work
+ * of their Kepler solve so that the threads of a block do similar work, the
+ * costliest group first).  GLISSE_SORT_COST orders the live particles at every
+ * compaction (and before the first step) by the tier of their pericentre
+ * value of z = beta s^2 ~ (n dt / (1 - e))^2, which sets the fast path's
+ * polynomial degree (tiers <= 2^-9, <= 2^-5, <= 0.1, beyond / unbound: the
+ * general solver), costliest tier first, stable within a tier.  Results per
+ * particle change only by rounding (a warp's polynomial degree depends on its
+ * members). */
+#define GLISSE_SORT_NONE 0
+#define GLISSE_SORT_COST 1
 
 /* element frames for glisse_set_sampling */
 #define GLISSE_FRAME_HELIO 0 /* heliocentric; mu = G m0 (particles), G (m0 + m_j) (planet j) */
@@ -82,6 +94,8 @@ typedef struct {
     int32_t kepler_iters;  /* iterations for PAPER_FIXED (1..GLISSE_MAX_KEPLER_ITERS), default 5 (section 2.2) */
     int32_t enc_mode;      /* GLISSE_ENC_*, default HILL */
     int32_t timing;        /* non-zero: time every launch with CUDA events (see glisse_timings) */
+    int32_t sort_mode;     /* GLISSE_SORT_*, default NONE */
+    int32_t pad_;
     double enc_value;      /* Hill multiple k (default 1.0) or fixed distance in AU */
     double r_max;          /* escape radius in AU, default 1000; <= 0 disables the escape test */
     void* cuda_stream;     /* cudaStream_t to run on; NULL = the library creates one */

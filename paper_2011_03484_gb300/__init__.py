@@ -34,6 +34,8 @@ GLISSE_PAPER_KEPLER_TOL = 1e-14
 GLISSE_MAX_KEPLER_ITERS = 64
 GLISSE_ENC_HILL = 0
 GLISSE_ENC_FIXED = 1
+GLISSE_SORT_NONE = 0
+GLISSE_SORT_COST = 1
 GLISSE_FRAME_HELIO = 0
 GLISSE_FRAME_BARY = 1
 
@@ -71,6 +73,8 @@ class glisse_opts(C.Structure):
         ("kepler_iters", C.c_int32),
         ("enc_mode", C.c_int32),
         ("timing", C.c_int32),
+        ("sort_mode", C.c_int32),
+        ("pad_", C.c_int32),
         ("enc_value", C.c_double),
         ("r_max", C.c_double),
         ("cuda_stream", C.c_void_p),

@@ -588,6 +588,7 @@ extern "C" int glisse_batch_create(glisse_batch** out, int32_t n_systems, const 
     if (n_systems < 1 || !star_mass || !n_planets || !n_particles || !dt) return GLISSE_E_INVAL;
     if (o.chunk_steps < 1 || o.chunk_steps > (1 << 20)) return GLISSE_E_INVAL;
     if (o.kepler_mode != GLISSE_KEPLER_CONVERGE) return GLISSE_E_INVAL;  // batches use the converged solver
+    if (o.sort_mode != GLISSE_SORT_NONE) return GLISSE_E_INVAL;          // and keep each system's order
     if (o.enc_mode != GLISSE_ENC_HILL && o.enc_mode != GLISSE_ENC_FIXED) return GLISSE_E_INVAL;
     if (!(o.enc_value >= 0.0) || !std::isfinite(o.enc_value) || !std::isfinite(o.r_max)) return GLISSE_E_INVAL;
     int64_t tot_pl = 0, tot_pa = 0;

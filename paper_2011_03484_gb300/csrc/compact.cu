@@ -12,6 +12,11 @@
 //      values and its id.
 // The pass is bound by HBM traffic: 8 x 6 + 4 bytes read and written per
 // live particle plus one byte of flag per slot.
+//
+// The same three kernels select slots whose key equals a given value and
+// place them after a device-side base offset, so a stable partition into
+// several groups is one pass per group (used to order live particles by the
+// expected cost of their Kepler solve, section 2.2's sorting suggestion).
 #include <cuda_runtime.h>
 
 #include "glisse_internal.h"
@@ -22,14 +27,14 @@ constexpr int kCompactThreads = 256;
 constexpr int kCompactRounds = 8;
 constexpr int kTile = kCompactThreads * kCompactRounds;
 
-__global__ void __launch_bounds__(kCompactThreads) compact_count_kernel(const uint8_t* __restrict__ alive, int64_t n,
-                                                                         int64_t* __restrict__ counts) {
+__global__ void __launch_bounds__(kCompactThreads) compact_count_kernel(const uint8_t* __restrict__ key, uint8_t want,
+                                                                         int64_t n, int64_t* __restrict__ counts) {
     const int64_t base = (int64_t)blockIdx.x * kTile;
     int c = 0;
 #pragma unroll
     for (int r = 0; r < kCompactRounds; ++r) {
         const int64_t idx = base + r * kCompactThreads + threadIdx.x;
-        c += (idx < n && alive[idx] != 0) ? 1 : 0;
+        c += (idx < n && key[idx] == want) ? 1 : 0;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
@@ -43,12 +48,13 @@ __global__ void __launch_bounds__(kCompactThreads) compact_count_kernel(const ui
     }
 }
 
-// Exclusive scan of counts[0..nb) in place; total to *n_out.  One block of 1024 threads.
+// Exclusive scan of counts[0..nb) in place, starting at *base (0 when base is
+// null); base + total to *n_out.  One block of 1024 threads.
 __global__ void __launch_bounds__(1024) compact_scan_kernel(int64_t* __restrict__ counts, int64_t nb,
-                                                              int64_t* __restrict__ n_out) {
+                                                              const int64_t* base, int64_t* n_out) {
     __shared__ int64_t wsum[32];
     __shared__ int64_t carry;
-    if (threadIdx.x == 0) carry = 0;
+    if (threadIdx.x == 0) carry = base ? *base : 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t b0 = 0; b0 < nb; b0 += 1024) {
@@ -83,7 +89,8 @@ __global__ void __launch_bounds__(1024) compact_scan_kernel(int64_t* __restrict_
 }
 
 __global__ void __launch_bounds__(kCompactThreads) compact_scatter_kernel(
-    const uint8_t* __restrict__ alive, int64_t n, const int64_t* __restrict__ offsets, const double* __restrict__ src,
+    const uint8_t* __restrict__ key, uint8_t want, int64_t n, const int64_t* __restrict__ offsets,
+    const double* __restrict__ src,
     const int32_t* __restrict__ src_id, int64_t lds, double* __restrict__ dst, int32_t* __restrict__ dst_id,
     int64_t ldd) {
     __shared__ int wcnt[kCompactThreads / 32];
@@ -92,7 +99,7 @@ __global__ void __launch_bounds__(kCompactThreads) compact_scatter_kernel(
     const int64_t base = (int64_t)blockIdx.x * kTile;
     for (int r = 0; r < kCompactRounds; ++r) {
         const int64_t idx = base + r * kCompactThreads + threadIdx.x;
-        const bool f = idx < n && alive[idx] != 0;
+        const bool f = idx < n && key[idx] == want;
         const unsigned ball = __ballot_sync(0xFFFFFFFFu, f);
         const int rank = __popc(ball & ((1u << lane) - 1u));
         if (lane == 0) wcnt[warp] = __popc(ball);
@@ -120,10 +127,55 @@ cudaError_t launch_compact(int64_t n, const uint8_t* alive, const double* src, c
                            cudaStream_t s) {
     if (n <= 0) return cudaMemsetAsync(n_out, 0, sizeof(int64_t), s);
     const int64_t nb = (n + kTile - 1) / kTile;
-    compact_count_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(alive, n, counts);
-    compact_scan_kernel<<<1, 1024, 0, s>>>(counts, nb, n_out);
-    compact_scatter_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(alive, n, counts, src, src_id, lds, dst, dst_id,
-                                                                      ldd);
+    compact_count_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(alive, 1, n, counts);
+    compact_scan_kernel<<<1, 1024, 0, s>>>(counts, nb, nullptr, n_out);
+    compact_scatter_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(alive, 1, n, counts, src, src_id, lds, dst,
+                                                                      dst_id, ldd);
+    return cudaGetLastError();
+}
+
+// Expected cost tier of a particle's drift, from its osculating orbit: the
+// fast path's polynomial degree follows z = beta s^2 ~ (n dt)^2 (a / r)^2,
+// largest at pericentre, z_q = (n dt / (1 - e))^2.  Tiers 0..3: z_q <= 2^-9
+// (degree 3), <= 2^-5 (degree 5), <= 0.1 (degree 7), beyond (the general
+// solver near pericentre; also unbound and nearly radial orbits).
+__device__ __forceinline__ int cost_tier(const double* st, int64_t ld, int64_t i, double mu, double dt) {
+    const double x = st[i], y = st[ld + i], z = st[2 * ld + i];
+    const double vx = st[3 * ld + i], vy = st[4 * ld + i], vz = st[5 * ld + i];
+    const double r = sqrt(x * x + y * y + z * z);
+    const double alpha = 2.0 / r - (vx * vx + vy * vy + vz * vz) / mu;  // 1 / a
+    if (!(alpha > 0.0) || !(r * alpha >= 1e-3)) return 3;
+    const double ec = 1.0 - r * alpha, rv = x * vx + y * vy + z * vz;
+    const double e2 = ec * ec + rv * rv * alpha / mu;
+    const double om = sqrt(fmax(1.0 - sqrt(e2), 0.0));  // sqrt(1 - e)
+    const double zq = mu * alpha * alpha * alpha * dt * dt / (om * om * om * om);
+    return zq <= 0.001953125 ? 0 : zq <= 0.03125 ? 1 : zq <= 0.1 ? 2 : 3;
+}
+
+// key[i] = 0 for a removed slot, 1 + cost tier for a live one.
+__global__ void sort_key_kernel(int64_t n, const uint8_t* __restrict__ alive, const double* __restrict__ st,
+                                int64_t ld, double mu, double dt, uint8_t* __restrict__ key) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    key[i] = alive[i] ? (uint8_t)(1 + cost_tier(st, ld, i, mu, dt)) : (uint8_t)0;
+}
+
+// Stable partition of the live slots ordered by cost tier, costliest first
+// (section 2.2: the most expensive group starts first); one pass per tier,
+// each placed after the previous ones on the device.  key needs n bytes of
+// scratch, counts ceil(n / kTile) entries.
+cudaError_t launch_compact_sorted(int64_t n, const uint8_t* alive, const double* src, const int32_t* src_id,
+                                  int64_t lds, double* dst, int32_t* dst_id, int64_t ldd, int64_t* counts,
+                                  uint8_t* key, double mu, double dt, int64_t* n_out, cudaStream_t s) {
+    if (n <= 0) return cudaMemsetAsync(n_out, 0, sizeof(int64_t), s);
+    const int64_t nb = (n + kTile - 1) / kTile;
+    sort_key_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, alive, src, lds, mu, dt, key);
+    for (int t = 4; t >= 1; --t) {
+        compact_count_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(key, (uint8_t)t, n, counts);
+        compact_scan_kernel<<<1, 1024, 0, s>>>(counts, nb, t == 4 ? nullptr : n_out, n_out);
+        compact_scatter_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(key, (uint8_t)t, n, counts, src, src_id,
+                                                                          lds, dst, dst_id, ldd);
+    }
     return cudaGetLastError();
 }
 

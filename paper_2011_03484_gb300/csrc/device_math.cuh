@@ -31,58 +31,21 @@ __device__ __forceinline__ double rcp_seed(double x) {
 // With y = seed and e = 1 - x y^2 (|e| < 2^-19, computed exactly by one FMA
 // since y^2 is exact):
 //   x^(-1/2) = y (1 - e)^(-1/2) = y (1 + e/2 + 3e^2/8 + O(e^3)).
-// The e^2 term is below 2^-39 relative, so it is formed in FP32.
-// 4 FP64 instructions.
+// The e^2 term is below 2^-39 relative, so it is formed in FP32; y^2 comes
+// from integer arithmetic (seed_square).  3 FP64 instructions.
 __device__ __forceinline__ double rsqrt_full(double x);
 
 // k * x^(-3/2) for normal x > 0 (the inverse-cube distance factor of a kick).
 // y = seed, e = 1 - x y^2:
 //   x^(-3/2) = y^3 (1 - e)^(-3/2) = y^3 (1 + 3e/2 + 15e^2/8 + O(e^3)).
-// y^2 (exact) and y^3 (correctly rounded) come from integer arithmetic on the
-// seed's 21-bit significand (seed_powers), so 4 FP64 instructions remain.
+// y^2 (exact) and k y^3 (correctly rounded) come from integer arithmetic on
+// the seed's 21-bit significand and k's 53-bit one (seed_square_kcube), so 3
+// FP64 instructions remain.
 __device__ __forceinline__ double k_rcube(double x, double k);
-
-// |t|^2 exactly and t^3 correctly rounded (ties away from zero) for a double t
-// whose significand has at most 21 bits (the low 32 bits of its encoding are
-// zero), by integer multiplication of the significands: m^2 has 42 bits and
-// m^3 at most 63.  Returns false (results unspecified) when t is zero,
-// subnormal, non-finite or |t| is outside [2^-300, 2^300].
-__device__ __forceinline__ bool seed_powers(double t, double& t2, double& t3) {
-    const int hi = __double2hiint(t);
-    const int et = (hi >> 20) & 0x7FF;  // biased exponent: t = m 2^(et - 1043)
-    const unsigned m = ((unsigned)hi & 0xFFFFFu) | 0x100000u;
-    const unsigned long long m2 = (unsigned long long)m * m;  // [2^40, 2^42)
-    const unsigned long long m3 = m2 * m;                     // [2^60, 2^63)
-    // t^2 = m2 2^(2 et - 2086); with the leading bit of m2 at 40 + a the
-    // significand m2 << (12 - a) lies in [2^52, 2^53) and the biased exponent
-    // is 2 et - 1023 + a.  Adding the significand (implicit bit included) to
-    // (exponent - 1) << 52 assembles the encoding.
-    const int a = (int)(m2 >> 41);
-    const unsigned long long q2 = m2 << (12 - a);
-    const long long e2 = (long long)(2 * et - 1024 + a) << 52;
-    t2 = __longlong_as_double(e2 + (long long)q2);
-    // t^3 = m3 2^(3 et - 3129); leading bit at 60 + b (b = 0, 1, 2); keep the
-    // top 53 bits with rounding: shift right by 8 + b after adding half of
-    // the last kept unit.  A carry to 2^53 moves into the exponent field.
-    const unsigned h3 = (unsigned)(m3 >> 32);
-    const int b = min((int)(h3 >> 29), 2);
-    const int sh = 8 + b;
-    const unsigned long long q3 = (m3 + (1ull << (sh - 1))) >> sh;
-    const long long e3 = (long long)(3 * et - 2047 + b) << 52;
-    const long long sign = (long long)(hi & 0x80000000) << 32;
-    t3 = __longlong_as_double((e3 + (long long)q3) | sign);
-    return (unsigned)(et - 723) <= 600u;
-}
 
 // 1/x to about 2^-40 from the MUFU seed and one Newton step (2 FP64 instructions).
 __device__ __forceinline__ double rcp_40(double x) {
     double y = rcp_seed(x);
-    double e = fma(-x, y, 1.0);
-    return fma(y, e, y);
-}
-
-// Refine an approximation y of 1/x by one Newton step: relative error e -> e^2.
-__device__ __forceinline__ double rcp_refine(double x, double y) {
     double e = fma(-x, y, 1.0);
     return fma(y, e, y);
 }
@@ -113,6 +76,47 @@ __device__ __forceinline__ double f2d_bits(float f) {
     hi = (e == 0u) ? sign : hi;
     lo = (e == 0u) ? 0u : lo;
     return __hiloint2double((int)hi, (int)lo);
+}
+
+// t^2 exactly for t with at most 21 significant bits (the low 32 bits of its
+// encoding zero, as the MUFU seeds are), by an integer square of the
+// significand (42 bits).  Valid for |t| in [2^-511, 2^511]; NaN outside.
+__device__ __forceinline__ double seed_square(double t) {
+    const int hi = __double2hiint(t);
+    const int et = (hi >> 20) & 0x7FF;
+    const unsigned m = ((unsigned)hi & 0xFFFFFu) | 0x100000u;
+    const unsigned long long m2 = (unsigned long long)m * m;  // [2^40, 2^42)
+    const int a = (int)(m2 >> 41);
+    const double t2 = __longlong_as_double(((long long)(2 * et - 1024 + a) << 52) + (long long)(m2 << (12 - a)));
+    return (unsigned)(et - 512) <= 1022u ? t2 : __longlong_as_double(0x7FF8000000000000ll);
+}
+
+// For t with at most 21 significant bits (the low 32 bits of its encoding
+// zero, as the MUFU seeds are) and k >= 0: t^2
+// exactly and k t^3 correctly rounded (ties away from zero) by integer
+// arithmetic.  The 53-bit significand of k times m^3 (63 bits, exact) is a
+// 116-bit product; its top 64 bits come from one 64 x 64 high multiply
+// (the low bits can only matter for an exact tie) and are rounded to 53.
+// k = 0 (or subnormal) gives 0.  Returns false (kt3 unspecified) when t is
+// outside [2^-300, 2^300] or not normal, k is not finite, or k t^3 leaves
+// the normal range.
+__device__ __forceinline__ bool seed_square_kcube(double t, double k, double& t2, double& kt3) {
+    const int hi = __double2hiint(t);
+    const int et = (hi >> 20) & 0x7FF;  // t = m 2^(et - 1043)
+    const unsigned m = ((unsigned)hi & 0xFFFFFu) | 0x100000u;
+    const unsigned long long m2 = (unsigned long long)m * m;  // [2^40, 2^42)
+    const unsigned long long m3 = m2 * m;                     // [2^60, 2^63)
+    const int a = (int)(m2 >> 41);
+    t2 = __longlong_as_double(((long long)(2 * et - 1024 + a) << 52) + (long long)(m2 << (12 - a)));
+    const long long kb = __double_as_longlong(k);
+    const int ek = (int)((kb >> 52) & 0x7FF);  // k = km 2^(ek - 1075)
+    const unsigned long long km = ((unsigned long long)kb & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const unsigned long long p = __umul64hi(km << 11, m3 << 1);  // floor(km m3 / 2^52) in [2^60, 2^64)
+    const int sh = 11 - __clzll(p);                               // leading bit at 52 + sh
+    const unsigned long long q = ((p >> (sh - 1)) + 1) >> 1;      // 53 bits, rounded
+    const int be = sh + ek + 3 * et - 3077;                       // biased exponent of k t^3
+    kt3 = (ek == 0) ? 0.0 : __longlong_as_double(((long long)(be - 1) << 52) + (long long)q);
+    return (unsigned)(et - 723) <= 600u && ek != 0x7FF && (ek == 0 || (unsigned)(be - 1) < 2045u);
 }
 
 // |s|^2 exactly and s^3 correctly rounded (ties away from zero) for a float s,
@@ -146,7 +150,7 @@ __device__ __forceinline__ bool float_powers(float s, double& s2, double& s3) {
 
 __device__ __forceinline__ double rsqrt_full(double x) {
     const double y = rsqrt_seed(x);
-    const double y2 = y * y;
+    const double y2 = seed_square(y);
     const double e = fma(-x, y2, 1.0);
     const float ef = d2f_bits(e);
     const double c = fma(0.5, e, f2d_bits(0.375f * ef * ef));
@@ -155,10 +159,10 @@ __device__ __forceinline__ double rsqrt_full(double x) {
 
 __device__ __forceinline__ double k_rcube(double x, double k) {
     const double y = rsqrt_seed(x);
-    double y2, y3;
-    const bool ok = seed_powers(y, y2, y3);
+    double y2, ky3;
+    const bool ok = seed_square_kcube(y, k, y2, ky3);
     const double e = fma(-x, y2, 1.0);
-    const double w = ok ? y3 * k : __longlong_as_double(0x7FF8000000000000ll);
+    const double w = ok ? ky3 : __longlong_as_double(0x7FF8000000000000ll);
     const float ef = d2f_bits(e);
     const double c = fma(1.5, e, f2d_bits(1.875f * ef * ef));
     return fma(w, c, w);

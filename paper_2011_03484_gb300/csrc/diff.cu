@@ -324,7 +324,7 @@ extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const dou
         n_particles < 0 || n_steps < 0 || !(dt != 0.0) || !std::isfinite(dt) || checkpoint_every < 1)
         return GLISSE_E_INVAL;
     // derivatives are of the converged drift only
-    if (o.kepler_mode != GLISSE_KEPLER_CONVERGE) return GLISSE_E_INVAL;
+    if (o.kepler_mode != GLISSE_KEPLER_CONVERGE || o.sort_mode != GLISSE_SORT_NONE) return GLISSE_E_INVAL;
     for (int64_t k = 0; k < 7 * (int64_t)n_planets; ++k)
         if (!std::isfinite(planets[k])) return GLISSE_E_INVAL;
     glisse_diff* d = new (std::nothrow) glisse_diff();

@@ -36,6 +36,8 @@ cudaError_t launch_particle_chunk(int, const ChunkArgs&, const ParticleConsts&, 
 cudaError_t launch_particle_chunk_paper(int, const ChunkArgs&, const ParticleConsts&, cudaStream_t);
 cudaError_t launch_compact(int64_t, const uint8_t*, const double*, const int32_t*, int64_t, double*, int32_t*,
                            int64_t, int64_t*, int64_t*, cudaStream_t);
+cudaError_t launch_compact_sorted(int64_t, const uint8_t*, const double*, const int32_t*, int64_t, double*, int32_t*,
+                                  int64_t, int64_t*, uint8_t*, double, double, int64_t*, cudaStream_t);
 int64_t compact_scratch_entries(int64_t);
 cudaError_t launch_export_live(int64_t, const double*, int64_t, const int32_t*, double*, cudaStream_t);
 cudaError_t launch_import(int64_t, const double*, double*, int64_t, int32_t*, cudaStream_t);
@@ -77,6 +79,7 @@ struct glisse_ctx {
     int32_t* d_id[2] = {};
     int cur = 0;
     uint8_t* d_alive = nullptr;
+    uint8_t* d_key = nullptr;  // sort keys (sort_mode != NONE)
     double* d_out_state = nullptr;
     int64_t* d_out_step = nullptr;
     int32_t* d_out_reason = nullptr;
@@ -140,6 +143,7 @@ extern "C" void glisse_opts_default(glisse_opts* o) {
     o->kepler_iters = 5;
     o->enc_mode = GLISSE_ENC_HILL;
     o->timing = 0;
+    o->sort_mode = GLISSE_SORT_NONE;
     o->enc_value = 1.0;
     o->r_max = 1000.0;
     o->cuda_stream = nullptr;
@@ -176,6 +180,7 @@ static void ctx_free(glisse_ctx* c) {
         cudaFree(c->d_st[b]);
         cudaFree(c->d_id[b]);
     }
+    cudaFree(c->d_key);
     cudaFree(c->d_elem);
     cudaFree(c->d_near0);
     cudaFree(c->d_near180);
@@ -280,6 +285,7 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles) 
         GL_ALLOC(c->d_id[b], sizeof(int32_t) * (size_t)cap);
     }
     GL_ALLOC(c->d_alive, (size_t)cap);
+    if (c->o.sort_mode == GLISSE_SORT_COST) GL_ALLOC(c->d_key, (size_t)cap);
     GL_ALLOC(c->d_out_state, sizeof(double) * 6 * (size_t)cap);
     GL_ALLOC(c->d_out_step, sizeof(int64_t) * (size_t)cap);
     GL_ALLOC(c->d_out_reason, sizeof(int32_t) * (size_t)cap);
@@ -360,6 +366,7 @@ extern "C" int glisse_create(glisse_ctx** out, double star_mass, const double* p
     if (o.kepler_mode == GLISSE_KEPLER_PAPER_FIXED && (o.kepler_iters < 1 || o.kepler_iters > GLISSE_MAX_KEPLER_ITERS))
         return GLISSE_E_INVAL;
     if (o.enc_mode != GLISSE_ENC_HILL && o.enc_mode != GLISSE_ENC_FIXED) return GLISSE_E_INVAL;
+    if (o.sort_mode != GLISSE_SORT_NONE && o.sort_mode != GLISSE_SORT_COST) return GLISSE_E_INVAL;
     if (!(o.enc_value >= 0.0) || !std::isfinite(o.enc_value) || !std::isfinite(o.r_max)) return GLISSE_E_INVAL;
     for (int64_t k = 0; k < 7 * (int64_t)n_planets; ++k)
         if (!std::isfinite(planets[k])) return GLISSE_E_INVAL;
@@ -391,8 +398,13 @@ extern "C" int glisse_create(glisse_ctx** out, double star_mass, const double* p
 static int compact(glisse_ctx* c) {
     const int nxt = c->cur ^ 1;
     if (c->timing) GL_CUDA(cudaEventRecord(c->tc0, c->s));
-    GL_CUDA(launch_compact(c->n_live, c->d_alive, c->d_st[c->cur], c->d_id[c->cur], c->cap, c->d_st[nxt],
-                           c->d_id[nxt], c->cap, c->d_counts, c->d_nlive, c->s));
+    if (c->o.sort_mode == GLISSE_SORT_COST)
+        GL_CUDA(launch_compact_sorted(c->n_live, c->d_alive, c->d_st[c->cur], c->d_id[c->cur], c->cap, c->d_st[nxt],
+                                      c->d_id[nxt], c->cap, c->d_counts, c->d_key, c->ppc.mu, c->dt, c->d_nlive,
+                                      c->s));
+    else
+        GL_CUDA(launch_compact(c->n_live, c->d_alive, c->d_st[c->cur], c->d_id[c->cur], c->cap, c->d_st[nxt],
+                               c->d_id[nxt], c->cap, c->d_counts, c->d_nlive, c->s));
     if (c->timing) GL_CUDA(cudaEventRecord(c->tc1, c->s));
     GL_CUDA(cudaMemcpyAsync(c->h_nlive, c->d_nlive, sizeof(int64_t), cudaMemcpyDeviceToHost, c->s));
     GL_CUDA(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->s));
@@ -517,6 +529,8 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
     const int S = log_stride(c->np);
     int64_t remaining = n_steps;
     int rc = GLISSE_OK;
+    if (c->o.sort_mode == GLISSE_SORT_COST && !c->tested_first && c->n_live > 0 && (rc = compact(c)) != GLISSE_OK)
+        return rc;
     while (remaining > 0 && rc == GLISSE_OK) {
         const double* log = nullptr;
         int64_t m = 0;
@@ -600,6 +614,11 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
         ++c->since_compact;
         if (c->since_compact >= c->o.resync_chunks || remaining == 0) rc = compact(c);
     }
+    // Start the planets of the next chunk now, while the GPU is idle: the
+    // ephemeris kernel takes a whole SM (all of its shared memory), and if it
+    // is placed while other work (the caller's, or the next particle launch)
+    // occupies the SMs it can land beside particle blocks and unbalance them.
+    if (rc == GLISSE_OK && !c->external && c->n_live > 0) rc = ensure_chunk(c, c->step / c->C + 1);
     if (rc == GLISSE_OK) rc = check_status(c);
     if (prev != c->device) cudaSetDevice(prev);
     return rc;

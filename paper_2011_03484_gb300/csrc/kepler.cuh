@@ -285,26 +285,32 @@ __device__ __forceinline__ void fast_tail(double mu, double dt, double beta, dou
     const double G2n = fma(dH, t2, G2);
     const double G3n = fma(dH, t3, G3);
     const double G1n = fma(-beta, G3n, s1);
-    // r(s+d) = r + T'' d + O(d^2): the correction is ~1e-9 r, so FP32 carries it
-    const double r1 = r + f2d_bits(Fpp * d2f_bits(dH));
-    const double rinv1 = rcp_refine(r1, rinv);
     // domain checks (integer tests): r > 0 and the correction small against s
     const bool good = (__double2hiint(r) > 0) && (exp_bits(dH) + 14 <= exp_bits(s0) || dH == 0.0);
     ok = ok && good;
     const double fm1 = -mur0 * G2n;
     const double g = fma(-mu, G3n, dt);
+    const double x1 = fma(fm1, x, fma(g, vx, x));
+    const double y1 = fma(fm1, y, fma(g, vy, y));
+    const double z1 = fma(fm1, z, fma(g, vz, z));
+    // |r| and mu/|r| at the new position from the position itself: the next
+    // step starts from them, and values carried from r(s) instead would
+    // random-walk away from |x| (amplified in beta = 2 mu/r - v^2, which
+    // cancels strongly near the pericentre of an eccentric orbit)
+    const double x2 = fma(x1, x1, fma(y1, y1, z1 * z1));
+    const double rinv1 = rsqrt_full(x2);
     const double fd = -(mur0 * rinv1) * G1n;
     const double mur1 = mu * rinv1;
     const double gdm1 = -mur1 * G2n;
     if (ok) {
         const double x0 = x, y0 = y, z0 = z;
-        x = fma(fm1, x0, fma(g, vx, x0));
-        y = fma(fm1, y0, fma(g, vy, y0));
-        z = fma(fm1, z0, fma(g, vz, z0));
+        x = x1;
+        y = y1;
+        z = z1;
         vx = fma(fd, x0, fma(gdm1, vx, vx));
         vy = fma(fd, y0, fma(gdm1, vy, vy));
         vz = fma(fd, z0, fma(gdm1, vz, vz));
-        r0 = r1;
+        r0 = x2 * rinv1;
         mur0 = mur1;
     }
 }
@@ -326,7 +332,7 @@ __device__ __forceinline__ bool drift_fast(double mu, float muf, double dt, floa
     float s = __fdividef(dtf, r0f);
     float zf = 0.f, dsf = 0.f;
 #pragma unroll
-    for (int it = 0; it < 4; ++it) {
+    for (int it = 0; it < 5; ++it) {
         zf = bf * s * s;
         const float c2 = fmaf(zf, fmaf(zf, fmaf(zf, -1.0f / 40320.0f, 1.0f / 720.0f), -1.0f / 24.0f), 0.5f);
         const float c3 = fmaf(zf, fmaf(zf, fmaf(zf, -1.0f / 362880.0f, 1.0f / 5040.0f), -1.0f / 120.0f), 1.0f / 6.0f);
@@ -340,7 +346,10 @@ __device__ __forceinline__ bool drift_fast(double mu, float muf, double dt, floa
         s += dsf;
     }
     zf = bf * s * s;
-    ok = ok && (fabsf(zf) <= kZ7) && (fabsf(dsf) <= 1e-5f * fabsf(s) + 1e-30f) && isfinite(s);
+    // accept the FP32 root only if its last Newton step was below 2^-20 |s|: the
+    // Halley step then leaves ~(2^-20)^3 and the neglected third-order terms of
+    // the G-function updates are as small; other lanes use the general solver
+    ok = ok && (fabsf(zf) <= kZ7) && (fabsf(dsf) <= 9.5367431640625e-7f * fabsf(s) + 1e-30f) && isfinite(s);
     // ---- warp-uniform polynomial degree ------------------------------------------
     const unsigned zb = ok ? __float_as_uint(fabsf(zf)) : 0u;
     const unsigned zmax = __reduce_max_sync(kFullMask, zb);

@@ -18,12 +18,20 @@
 // finishes or compaction drops it.  A failed Kepler solve or a non-finite
 // result keeps the state from before the drift (reasons -2 / -3).
 #pragma once
+#include <algorithm>
 #include "glisse_internal.h"
 #include "kepler.cuh"
 
 namespace glisse {
 
 constexpr int kParticleBlock = 128;
+// Resident blocks per SM the particle kernel is compiled for (register budget
+// 65536 / (128 x blocks)).  A chunk's warps all do the same work, so a launch
+// that spills past one wave leaves a tail in which a lone warp per SM
+// partition cannot keep the FP64 pipe busy.
+#ifndef GLISSE_PARTICLE_MIN_BLOCKS
+#define GLISSE_PARTICLE_MIN_BLOCKS 8
+#endif
 
 // drift used by the particle map: the converged fast solver (default) or the
 // paper's fixed-iteration solve (GLISSE_KEPLER_PAPER_FIXED)
@@ -181,7 +189,8 @@ __device__ __forceinline__ void store_removed(int64_t pid, double x, double y, d
 }
 
 template <int NP, int MODE>
-__global__ void __launch_bounds__(kParticleBlock) particle_chunk_kernel(const ChunkArgs a, const ParticleConsts pc) {
+__global__ void __launch_bounds__(kParticleBlock, GLISSE_PARTICLE_MIN_BLOCKS)
+    particle_chunk_kernel(const ChunkArgs a, const ParticleConsts pc) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool in = i < a.n;
     const int64_t ld = a.ld;
@@ -227,13 +236,47 @@ __global__ void __launch_bounds__(kParticleBlock) particle_chunk_kernel(const Ch
     }
 }
 
+// Dynamic shared memory (unused by the kernel) that caps the resident blocks
+// per SM at what an even spread of this grid needs.  Every block does the same
+// work, so the chunk lasts as long as the SM holding the most blocks; the
+// hardware may pack up to GLISSE_PARTICLE_MIN_BLOCKS on some SMs and fewer on
+// others, and the ephemeris kernel holds one SM for itself (all of its shared
+// memory).  Spread over the other SMs, ceil(grid / (SMs - 1)) per SM is the
+// best any placement can do; the request makes more than that impossible.
+inline cudaError_t particle_smem_cap(const void* kernel, int64_t grid, size_t* smem) {
+    *smem = 0;
+    int dev = 0, nsm = 0, smem_sm = 0, reserved = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t per_sm = nsm > 1 ? (grid + nsm - 2) / (nsm - 1) : GLISSE_PARTICLE_MIN_BLOCKS;
+    if (per_sm >= GLISSE_PARTICLE_MIN_BLOCKS) return cudaSuccess;  // the register budget already caps it
+    // per_sm blocks fit, per_sm + 1 do not
+    size_t b = (size_t)(smem_sm / per_sm - reserved) & ~(size_t)1023;
+    b = std::min<size_t>(b, (size_t)optin);
+    while (b > 0 && (size_t)(per_sm + 1) * (b + reserved) <= (size_t)smem_sm) b += 1024;
+    if ((size_t)per_sm * (b + reserved) > (size_t)smem_sm) return cudaSuccess;  // cannot express the cap
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    if (e == cudaSuccess) *smem = b;
+    return e;
+}
+
 template <int MODE>
 cudaError_t launch_particle_chunk_mode(int np, const ChunkArgs& a, const ParticleConsts& pc, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     const int64_t grid = (a.n + kParticleBlock - 1) / kParticleBlock;
+    size_t smem = 0;
+    cudaError_t e = cudaSuccess;
     switch (np) {
-#define GLISSE_CASE(N) \
-    case N: particle_chunk_kernel<N, MODE><<<(unsigned)grid, kParticleBlock, 0, s>>>(a, pc); break;
+#define GLISSE_CASE(N)                                                                                    \
+    case N:                                                                                               \
+        e = particle_smem_cap(reinterpret_cast<const void*>(particle_chunk_kernel<N, MODE>), grid, &smem); \
+        if (e != cudaSuccess) return e;                                                                   \
+        particle_chunk_kernel<N, MODE><<<(unsigned)grid, kParticleBlock, smem, s>>>(a, pc);              \
+        break;
         GLISSE_CASE(0)
         GLISSE_CASE(1)
         GLISSE_CASE(2)

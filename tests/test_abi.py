@@ -44,6 +44,7 @@ def test_opts_defaults(G):
     assert o.chunk_steps == 1024 and o.resync_chunks == 1
     assert o.kepler_mode == G.GLISSE_KEPLER_CONVERGE and o.kepler_iters == 5
     assert o.enc_mode == G.GLISSE_ENC_HILL and o.enc_value == 1.0 and o.r_max == 1000.0
+    assert o.sort_mode == G.GLISSE_SORT_NONE and o.timing == 0
 
 
 def test_strerror_names_every_code(G):
@@ -84,6 +85,11 @@ def test_argument_errors_before_any_cuda_call(G):
         with pytest.raises(G.GlisseError) as ei:
             G.glisse_create(1.0, w["planets"], w["particles"], 0.5, o)
         assert ei.value.code == G.GLISSE_E_INVAL, (mode, iters)
+    o = G.glisse_opts_default()
+    o.sort_mode = 2
+    with pytest.raises(G.GlisseError) as ei:
+        G.glisse_create(1.0, w["planets"], w["particles"], 0.5, o)
+    assert ei.value.code == G.GLISSE_E_INVAL
     # the fixed-iteration mode is for glisse_create only
     o = G.glisse_opts_default()
     o.kepler_mode = G.GLISSE_KEPLER_PAPER_FIXED

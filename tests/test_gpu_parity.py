@@ -98,7 +98,9 @@ def test_tiny_workload_parity(G, orc):
     print(rep)
     assert_parity(rep)
     assert rep["removed"] > 0  # the workload exercises removal
-    assert rep["regular"] > 0.2 * rep["n"]
+    # regular = insensitive to one ulp and never within 5 R_crit (~15% of this workload over 1e4 steps);
+    # the far-only criterion below covers the ~500 particles that never came within 5 R_crit
+    assert rep["regular"] > 0.1 * rep["n"]
     # without the sensitivity reruns: never within 5 R_crit -> 1e-10
     rep5 = compare(g, o, n)
     assert rep5["regular_over_tol"] == 0, rep5
@@ -265,6 +267,46 @@ def test_external_ephemeris_cr3bp(G, orc):
 # ---------------------------------------------------------------------------
 # full-size workloads in the benchmark's launch configuration, sampled
 # ---------------------------------------------------------------------------
+def test_eccentric_two_body_against_the_oracle(G, orc):
+    """No planets, e in [0.3, 0.95]: the map is the exact Kepler flow, which the oracle follows
+    to ~1e-13 median / 6e-11 worst after 2000 steps (its two-body pins).  A drift that lets
+    |r| or 1/|r| drift away from the position shows here first: beta = 2 mu/r - v^2 cancels
+    by up to 1/(1 - e) near the pericentre (an earlier carried radius gave 2e-9)."""
+    rng = np.random.default_rng(11)
+    n = 400
+    a = rng.uniform(20, 29, n)
+    e = rng.uniform(0.3, 0.95, n)
+    pa = gi.elements_to_cartesian(gi.G, a, e, np.radians(rng.uniform(0, 5, n)), *rng.uniform(0, 2 * np.pi, (3, n)))
+    sim = G.Simulation(1.0, np.zeros((0, 7)), pa, 0.5, chunk_steps=512)
+    sim.advance(2000)
+    g = sim.read()["state"]
+    sim.close()
+    o = orc.run(1.0, np.zeros((0, 7)), pa, 0.5, 2000, r_max=0.0)["state"]
+    err = parity.rel_err(g, o)
+    print("eccentric two-body: median", np.median(err), "max", err.max())
+    assert np.median(err) < 1e-12 and err.max() < 2e-10
+
+
+def test_eccentric_workload_parity(G, orc):
+    """e up to 0.9: pericentre passages where the fast path's FP32 root needs several
+    iterations, lanes that fall back to the general solver, frequent removals."""
+    w = gi.make("eccentric")
+    ids = gi.subset_ids("eccentric", 3000)
+    pa = w["particles"][ids]
+    n = 2000
+    sim = G.Simulation(1.0, w["planets"], pa, w["dt"], chunk_steps=512)
+    sim.advance(n)
+    g = sim.read()
+    sim.close()
+    base = orc.run(1.0, w["planets"], pa, w["dt"], n)
+    runs = [orc.run(1.0, w["planets"], p, w["dt"], n) for p in parity.perturbed_inputs(pa)]
+    sens, unstable = parity.sensitivity(base, runs)
+    rep = parity.compare(g, base, n, sens, unstable, ecc=parity.eccentricity(pa, gi.G))
+    print(rep)
+    parity.assert_parity(rep)
+    assert rep["removed"] > 100
+
+
 @pytest.mark.parametrize("name,n_steps,k", [("longrun", 10_000, 2048), ("belt", 4096, 1024)])
 def test_full_size_sampled_parity(G, orc, name, n_steps, k):
     w = gi.make(name)
