@@ -10,8 +10,11 @@
 // Planet positions are data (no derivative with respect to the planets).
 //
 // Forward: one thread per particle carries the state and up to kMaxTangents
-// tangent vectors through n steps (explicit half kicks) and stores the
-// synchronised state every K steps.  Backward: for each K-step segment from
+// tangent vectors through n steps and stores the synchronised state every K
+// steps.  Inside a K-step segment the closing half kick of a step and the
+// opening half kick of the next use the same planet positions and are one
+// kick of dt (their Jacobians, tau A(r) at the same r, merge the same way);
+// at a segment boundary and at the end they stay half kicks.  Backward: for each K-step segment from
 // the last, the thread recomputes the segment from its checkpoint, keeping the
 // pre-drift state, the post-drift position and the solved universal anomaly
 // s and reduced time tau of every step in a scratch buffer, then runs the
@@ -88,23 +91,28 @@ __device__ __forceinline__ void kick_jac(const double r[3], const double* __rest
         const double dx = r[0] - L[kRec * j], dy = r[1] - L[kRec * j + 1], dz = r[2] - L[kRec * j + 2];
         const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const double s = k_rcube(d2, tgm[j]);
-        const double c = 3.0 * (dx * w[0] + dy * w[1] + dz * w[2]) / d2;
+        const double c = 3.0 * (dx * w[0] + dy * w[1] + dz * w[2]) * rcp_full(d2);
         out[0] -= s * (w[0] - c * dx);
         out[1] -= s * (w[1] - c * dy);
         out[2] -= s * (w[2] - c * dz);
     }
 }
 
-template <int NP>
+// TMAX: compile-time tangent capacity (0, 1 or kMaxTangents) so that the
+// tangent vectors stay in registers; tangents a.ntan..TMAX-1 are zero.
+template <int NP, int TMAX>
 __global__ void __launch_bounds__(kDiffBlock) diff_forward_kernel(const DiffArgs a, const ParticleConsts pc) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const int S = log_stride(NP);
-    const int T = a.ntan;
-    double st[6], t[kMaxTangents][6];
+    constexpr int T = TMAX;
+    constexpr int TA = TMAX > 0 ? TMAX : 1;
+    double st[6], t[TA][6];
     for (int c = 0; c < 6; ++c) st[c] = a.state0[6 * i + c];
-    for (int k = 0; k < kMaxTangents; ++k)
-        for (int c = 0; c < 6; ++c) t[k][c] = (k < T) ? a.tan0[((int64_t)k * a.n + i) * 6 + c] : 0.0;
+#pragma unroll
+    for (int k = 0; k < TA; ++k)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) t[k][c] = (k < a.ntan) ? a.tan0[((int64_t)k * a.n + i) * 6 + c] : 0.0;
     double n0 = 0.0;
     for (int c = 0; c < 6; ++c) n0 += t[0][c] * t[0][c];
     int64_t rstep = -1;
@@ -122,6 +130,7 @@ __global__ void __launch_bounds__(kDiffBlock) diff_forward_kernel(const DiffArgs
             reason = hit ? hit : esc;
         }
     }
+    bool opened = false;  // this step's opening kick was merged into the previous closing kick
     for (int64_t k = 0; k < a.nsteps && rstep < 0; ++k) {
         if (k % a.K == 0) {
             double* cp = a.ckpt + (k / a.K) * 6 * a.n;
@@ -130,8 +139,11 @@ __global__ void __launch_bounds__(kDiffBlock) diff_forward_kernel(const DiffArgs
         const double* L0 = a.log + k * S;
         const double* L1 = L0 + S;
         // opening half kick (tangents first: A is evaluated at r, which the kick leaves unchanged)
-        for (int q = 0; q < T; ++q) kick_jac<NP>(st, L0, pc.tgm_half, t[q], t[q] + 3);
-        kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);
+        if (!opened) {
+#pragma unroll
+            for (int q = 0; q < T; ++q) kick_jac<NP>(st, L0, pc.tgm_half, t[q], t[q] + 3);
+            kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);
+        }
         double pre[6];
         for (int c = 0; c < 6; ++c) pre[c] = st[c];
         DriftScalars d;
@@ -152,29 +164,38 @@ __global__ void __launch_bounds__(kDiffBlock) diff_forward_kernel(const DiffArgs
             reason = GLISSE_REMOVED_NONFINITE;
             break;
         }
+#pragma unroll
         for (int q = 0; q < T; ++q) drift_tangent(pc.mu, pre, d, t[q]);
-        // tests at t_{k+1}, then the closing half kick
+        // tests at t_{k+1}, then the closing kick (merged with the next opening one
+        // inside a segment)
+        const bool merge = (k + 1 < a.nsteps) && ((k + 1) % a.K != 0);
+        const double tau = merge ? pc.dt : pc.half_dt;
+        const double(&tgm)[kMaxPlanets] = merge ? pc.tgm_full : pc.tgm_half;
         const double r2 = st[0] * st[0] + st[1] * st[1] + st[2] * st[2];
         int hit = (has_rmax && lt_nonneg(pc.rmax2, r2)) ? GLISSE_REMOVED_ESCAPE : 0;
         double nst[6];
         for (int c = 0; c < 6; ++c) nst[c] = st[c];
-        const int enc = kick_state<NP>(nst, L1, pc.half_dt, pc.tgm_half, pc.rc2);
+        const int enc = kick_state<NP>(nst, L1, tau, tgm, pc.rc2);
         hit = enc ? enc : hit;
         if (hit) {
             rstep = k + 1;
             reason = hit;
             break;
         }
-        for (int q = 0; q < T; ++q) kick_jac<NP>(st, L1, pc.tgm_half, t[q], t[q] + 3);
+#pragma unroll
+        for (int q = 0; q < T; ++q) kick_jac<NP>(st, L1, tgm, t[q], t[q] + 3);
         for (int c = 0; c < 6; ++c) st[c] = nst[c];
+        opened = merge;
     }
     for (int c = 0; c < 6; ++c) a.state1[6 * i + c] = st[c];
+#pragma unroll
     for (int q = 0; q < T; ++q)
-        for (int c = 0; c < 6; ++c) a.tan1[((int64_t)q * a.n + i) * 6 + c] = t[q][c];
+        if (q < a.ntan)
+            for (int c = 0; c < 6; ++c) a.tan1[((int64_t)q * a.n + i) * 6 + c] = t[q][c];
     if (a.log_growth) {
         double n1 = 0.0;
         for (int c = 0; c < 6; ++c) n1 += t[0][c] * t[0][c];
-        a.log_growth[i] = (T > 0 && n0 > 0.0) ? 0.5 * log(n1 / n0) : 0.0;
+        a.log_growth[i] = (a.ntan > 0 && n0 > 0.0) ? 0.5 * log(n1 / n0) : 0.0;
     }
     a.rstep[i] = rstep;
     a.reason[i] = reason;
@@ -205,7 +226,7 @@ __global__ void __launch_bounds__(kDiffBlock) diff_backward_kernel(const DiffArg
             // recompute the segment: pre-drift state (6) and post-drift position (3) per step
             for (int64_t k = k0; k < k1; ++k) {
                 const double* L0 = a.log + k * S;
-                kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);
+                if (k == k0) kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);  // else merged below
                 double* sc = a.scratch + (k - k0) * kScratchRows * a.n + i;
                 for (int c = 0; c < 6; ++c) sc[c * a.n] = st[c];
                 if (k == kend - 1 && cut_before_drift) break;
@@ -220,7 +241,8 @@ __global__ void __launch_bounds__(kDiffBlock) diff_backward_kernel(const DiffArg
                     st[3 + c] = d.fd * pre[c] + d.gd * pre[3 + c];
                 }
                 for (int c = 0; c < 3; ++c) sc[(6 + c) * a.n] = st[c];
-                if (k + 1 < k1) kick_state<NP>(st, a.log + (k + 1) * S, pc.half_dt, pc.tgm_half, pc.rc2);
+                // closing kick of step k merged with the opening kick of step k + 1 (as in the forward pass)
+                if (k + 1 < k1) kick_state<NP>(st, a.log + (k + 1) * S, pc.dt, pc.tgm_full, pc.rc2);
             }
             // adjoint sweep, last step first
             for (int64_t k = k1 - 1; k >= k0; --k) {
@@ -230,8 +252,9 @@ __global__ void __launch_bounds__(kDiffBlock) diff_backward_kernel(const DiffArg
                 for (int c = 0; c < 3; ++c) post[c] = sc[(6 + c) * a.n];
                 const bool last = (k == kend - 1);
                 if (!(last && (cut_after_drift || cut_before_drift))) {
-                    // closing half kick at t_{k+1}: lr += (dt/2) A(post) lv
-                    kick_jac<NP>(post, a.log + (k + 1) * S, pc.tgm_half, l + 3, l);
+                    // closing kick at t_{k+1}: lr += tau A(post) lv, tau = dt inside the segment
+                    // (merged with the opening kick of step k + 1), dt/2 at its end
+                    kick_jac<NP>(post, a.log + (k + 1) * S, (k + 1 < k1) ? pc.tgm_full : pc.tgm_half, l + 3, l);
                 }
                 if (!(last && cut_before_drift)) {
                     DriftScalars d;
@@ -239,8 +262,9 @@ __global__ void __launch_bounds__(kDiffBlock) diff_backward_kernel(const DiffArg
                     drift_finish(pc.mu, d);
                     drift_adjoint(pc.mu, pre, d, l);
                 }
-                // opening half kick at t_k: lr += (dt/2) A(pre) lv
-                kick_jac<NP>(pre, a.log + k * S, pc.tgm_half, l + 3, l);
+                // opening half kick at t_k (only at the segment start; inside, it is part of
+                // the previous step's merged closing kick): lr += (dt/2) A(pre) lv
+                if (k == k0) kick_jac<NP>(pre, a.log + k * S, pc.tgm_half, l + 3, l);
             }
         }
     }
@@ -261,11 +285,32 @@ __global__ void __launch_bounds__(kDiffBlock) diff_backward_kernel(const DiffArg
         default: return cudaErrorInvalidValue;                             \
     }
 
+template <int TMAX>
+static cudaError_t launch_diff_forward_t(int np, const DiffArgs& a, const ParticleConsts& pc, cudaStream_t s) {
+    const unsigned grid = (unsigned)((a.n + kDiffBlock - 1) / kDiffBlock);
+    switch (np) {
+#define GLISSE_FWD_CASE(N) \
+    case N: diff_forward_kernel<N, TMAX><<<grid, kDiffBlock, 0, s>>>(a, pc); break;
+        GLISSE_FWD_CASE(0)
+        GLISSE_FWD_CASE(1)
+        GLISSE_FWD_CASE(2)
+        GLISSE_FWD_CASE(3)
+        GLISSE_FWD_CASE(4)
+        GLISSE_FWD_CASE(5)
+        GLISSE_FWD_CASE(6)
+        GLISSE_FWD_CASE(7)
+        GLISSE_FWD_CASE(8)
+#undef GLISSE_FWD_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 static cudaError_t launch_diff_forward(int np, const DiffArgs& a, const ParticleConsts& pc, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
-    const unsigned grid = (unsigned)((a.n + kDiffBlock - 1) / kDiffBlock);
-    GLISSE_DIFF_SWITCH(diff_forward_kernel)
-    return cudaGetLastError();
+    if (a.ntan == 0) return launch_diff_forward_t<0>(np, a, pc, s);
+    if (a.ntan == 1) return launch_diff_forward_t<1>(np, a, pc, s);
+    return launch_diff_forward_t<kMaxTangents>(np, a, pc, s);
 }
 
 static cudaError_t launch_diff_backward(int np, const DiffArgs& a, const ParticleConsts& pc, cudaStream_t s) {

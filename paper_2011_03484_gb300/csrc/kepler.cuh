@@ -412,6 +412,7 @@ struct DriftScalars {
     double r0, u, beta, tau, dtau_dbeta, s;
     double G[6], Gb[4];  // G_0..G_5 and dG_n/dbeta, n = 0..3
     double R, f, g, fd, gd;
+    double inv_r0, inv_R;  // 1/r0 and 1/R (MUFU seed + one correction: no divisions downstream)
 };
 
 // Drift scalars of one body at its current state, in two parts: drift_solve
@@ -422,10 +423,12 @@ struct DriftScalars {
 // second step lands at rounding level); orbits outside the FP32 domain, or
 // |z| > 0.1, use the general safeguarded solver.
 __device__ inline bool drift_solve(double mu, double dt, const double st[6], DriftScalars& d) {
-    d.r0 = sqrt(st[0] * st[0] + st[1] * st[1] + st[2] * st[2]);
-    const double v2 = st[3] * st[3] + st[4] * st[4] + st[5] * st[5];
-    d.u = st[0] * st[3] + st[1] * st[4] + st[2] * st[5];
-    d.beta = 2.0 * mu / d.r0 - v2;
+    const double x2 = fma(st[0], st[0], fma(st[1], st[1], st[2] * st[2]));
+    d.inv_r0 = rsqrt_full(x2);
+    d.r0 = x2 * d.inv_r0;
+    const double v2 = fma(st[3], st[3], fma(st[4], st[4], st[5] * st[5]));
+    d.u = fma(st[0], st[3], fma(st[1], st[4], st[2] * st[5]));
+    d.beta = fma(2.0 * mu, d.inv_r0, -v2);
     d.dtau_dbeta = 0.0;
     // FP32 start (the fast path's iteration), accepted only well inside its domain
     const int er = exp_bits(d.r0), ev = exp_bits(v2);
@@ -475,10 +478,12 @@ __device__ inline bool drift_solve(double mu, double dt, const double st[6], Dri
 // Recover r0, u, beta and dtau/dbeta of a state whose s and tau were stored.
 __device__ inline void drift_restore(double mu, double dt, const double st[6], double s, double tau,
                                      DriftScalars& d) {
-    d.r0 = sqrt(st[0] * st[0] + st[1] * st[1] + st[2] * st[2]);
-    const double v2 = st[3] * st[3] + st[4] * st[4] + st[5] * st[5];
-    d.u = st[0] * st[3] + st[1] * st[4] + st[2] * st[5];
-    d.beta = 2.0 * mu / d.r0 - v2;
+    const double x2 = fma(st[0], st[0], fma(st[1], st[1], st[2] * st[2]));
+    d.inv_r0 = rsqrt_full(x2);
+    d.r0 = x2 * d.inv_r0;
+    const double v2 = fma(st[3], st[3], fma(st[4], st[4], st[5] * st[5]));
+    d.u = fma(st[0], st[3], fma(st[1], st[4], st[2] * st[5]));
+    d.beta = fma(2.0 * mu, d.inv_r0, -v2);
     d.s = s;
     d.tau = tau;
     d.dtau_dbeta = 0.0;
@@ -499,10 +504,11 @@ __device__ inline void drift_finish(double mu, DriftScalars& d) {
     }
     for (int n = 0; n < 4; ++n) d.Gb[n] = -0.5 * (d.s * d.G[n + 1] - n * d.G[n + 2]);
     d.R = d.r0 * d.G[0] + d.u * d.G[1] + mu * d.G[2];
-    d.f = 1.0 - mu * d.G[2] / d.r0;
+    d.inv_R = rcp_full(d.R);
+    d.f = 1.0 - mu * d.G[2] * d.inv_r0;
     d.g = d.tau - mu * d.G[3];
-    d.fd = -mu * d.G[1] / (d.R * d.r0);
-    d.gd = 1.0 - mu * d.G[2] / d.R;
+    d.fd = -mu * d.G[1] * (d.inv_R * d.inv_r0);
+    d.gd = 1.0 - mu * d.G[2] * d.inv_R;
 }
 
 // Drift scalars of one body at its current state.
@@ -514,21 +520,21 @@ __device__ inline bool drift_scalars(double mu, double dt, const double st[6], D
 
 __device__ inline void drift_tangent(double mu, const double st[6], const DriftScalars& d, double t[6]) {
     const double *r = st, *v = st + 3;
-    const double dr0 = (r[0] * t[0] + r[1] * t[1] + r[2] * t[2]) / d.r0;
+    const double dr0 = (r[0] * t[0] + r[1] * t[1] + r[2] * t[2]) * d.inv_r0;
     const double du = (t[0] * v[0] + t[1] * v[1] + t[2] * v[2]) + (r[0] * t[3] + r[1] * t[4] + r[2] * t[5]);
-    const double dbeta = -2.0 * mu * dr0 / (d.r0 * d.r0) - 2.0 * (v[0] * t[3] + v[1] * t[4] + v[2] * t[5]);
+    const double dbeta = -2.0 * mu * dr0 * (d.inv_r0 * d.inv_r0) - 2.0 * (v[0] * t[3] + v[1] * t[4] + v[2] * t[5]);
     const double dtau = d.dtau_dbeta * dbeta;
     const double Tb = d.r0 * d.Gb[1] + d.u * d.Gb[2] + mu * d.Gb[3];
-    const double ds = (dtau - d.G[1] * dr0 - d.G[2] * du - Tb * dbeta) / d.R;
+    const double ds = (dtau - d.G[1] * dr0 - d.G[2] * du - Tb * dbeta) * d.inv_R;
     const double dG0 = -d.beta * d.G[1] * ds + d.Gb[0] * dbeta;
     const double dG1 = d.G[0] * ds + d.Gb[1] * dbeta;
     const double dG2 = d.G[1] * ds + d.Gb[2] * dbeta;
     const double dG3 = d.G[2] * ds + d.Gb[3] * dbeta;
-    const double df = -mu * (dG2 - d.G[2] * dr0 / d.r0) / d.r0;
+    const double df = -mu * (dG2 - d.G[2] * dr0 * d.inv_r0) * d.inv_r0;
     const double dg = dtau - mu * dG3;
     const double dR = dr0 * d.G[0] + d.r0 * dG0 + du * d.G[1] + d.u * dG1 + mu * dG2;
-    const double dfd = -mu * (dG1 - d.G[1] * (dR / d.R + dr0 / d.r0)) / (d.R * d.r0);
-    const double dgd = -mu * (dG2 - d.G[2] * dR / d.R) / d.R;
+    const double dfd = -mu * (dG1 - d.G[1] * (dR * d.inv_R + dr0 * d.inv_r0)) * (d.inv_R * d.inv_r0);
+    const double dgd = -mu * (dG2 - d.G[2] * dR * d.inv_R) * d.inv_R;
     double o[6];
     for (int i = 0; i < 3; ++i) {
         o[i] = df * r[i] + d.f * t[i] + dg * v[i] + d.g * t[3 + i];
@@ -552,14 +558,14 @@ __device__ inline void drift_adjoint(double mu, const double st[6], const DriftS
     // f = 1 - mu G2 / r0;  g = tau - mu G3;  fd = -mu G1 / (R r0);  gd = 1 - mu G2 / R
     double lG0 = 0.0, lG1 = 0.0, lG2 = 0.0, lG3 = 0.0, lR = 0.0, lr0 = 0.0, lu = 0.0, lbeta = 0.0;
     double ltau = lg;
-    lG2 += -mu * lf / d.r0;
-    lr0 += mu * d.G[2] * lf / (d.r0 * d.r0);
+    lG2 += -mu * lf * d.inv_r0;
+    lr0 += mu * d.G[2] * lf * (d.inv_r0 * d.inv_r0);
     lG3 += -mu * lg;
-    lG1 += -mu * lfd / (d.R * d.r0);
-    lR += -d.fd * lfd / d.R;
-    lr0 += -d.fd * lfd / d.r0;
-    lG2 += -mu * lgd / d.R;
-    lR += mu * d.G[2] * lgd / (d.R * d.R);
+    lG1 += -mu * lfd * (d.inv_R * d.inv_r0);
+    lR += -d.fd * lfd * d.inv_R;
+    lr0 += -d.fd * lfd * d.inv_r0;
+    lG2 += -mu * lgd * d.inv_R;
+    lR += mu * d.G[2] * lgd * (d.inv_R * d.inv_R);
     // R = r0 G0 + u G1 + mu G2
     lr0 += d.G[0] * lR;
     lG0 += d.r0 * lR;
@@ -571,18 +577,19 @@ __device__ inline void drift_adjoint(double mu, const double st[6], const DriftS
     lbeta += d.Gb[0] * lG0 + d.Gb[1] * lG1 + d.Gb[2] * lG2 + d.Gb[3] * lG3;
     // s(tau, r0, u, beta)
     const double Tb = d.r0 * d.Gb[1] + d.u * d.Gb[2] + mu * d.Gb[3];
-    ltau += ls / d.R;
-    lr0 += -d.G[1] * ls / d.R;
-    lu += -d.G[2] * ls / d.R;
-    lbeta += -Tb * ls / d.R;
+    const double lsR = ls * d.inv_R;
+    ltau += lsR;
+    lr0 += -d.G[1] * lsR;
+    lu += -d.G[2] * lsR;
+    lbeta += -Tb * lsR;
     // tau(beta)
     lbeta += d.dtau_dbeta * ltau;
     // beta(r0, v) = 2 mu / r0 - v.v
-    lr0 += -2.0 * mu * lbeta / (d.r0 * d.r0);
+    lr0 += -2.0 * mu * lbeta * (d.inv_r0 * d.inv_r0);
     for (int i = 0; i < 3; ++i) lv[i] += -2.0 * lbeta * v[i];
     // u = r . v ; r0 = |r|
     for (int i = 0; i < 3; ++i) {
-        lr[i] += lu * v[i] + lr0 * r[i] / d.r0;
+        lr[i] += lu * v[i] + lr0 * r[i] * d.inv_r0;
         lv[i] += lu * r[i];
     }
     for (int i = 0; i < 3; ++i) {

@@ -123,6 +123,9 @@ def test_adjoint_is_the_transpose_of_the_tangent(G):
 
 
 def test_gradient_independent_of_checkpoint_interval(G):
+    """Interior kicks merge inside a checkpoint segment and stay half kicks at its
+    boundaries, so the trajectory, and with it the gradient, depends on K only by
+    rounding (chaotic particles amplify it, as they do state differences)."""
     w, pl, s0 = _workload(256)
     n = 700
     g = np.random.default_rng(6).normal(size=s0.shape)
@@ -133,7 +136,14 @@ def test_gradient_independent_of_checkpoint_interval(G):
         outs.append(dm.backward(_cuda(g)).cpu().numpy())
         dm.close()
     for o in outs[1:]:
-        np.testing.assert_array_equal(o, outs[0])
+        rel = np.abs(o - outs[0]).max(axis=1) / np.abs(outs[0]).max(axis=1)
+        assert np.median(rel) < 1e-12 and np.quantile(rel, 0.99) < 1e-8, (np.median(rel), rel.max())
+    # the same K twice: bit-identical (the backward pass recomputes the forward trajectory exactly)
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n, 7)
+    dm.forward(_cuda(s0))
+    again = dm.backward(_cuda(g)).cpu().numpy()
+    dm.close()
+    np.testing.assert_array_equal(again, outs[1])
 
 
 def test_autograd_function(G):
