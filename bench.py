@@ -396,7 +396,7 @@ def main():
     ap.add_argument("--tune", action="store_true", help="batched: run the autotuner before timing")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-particles", type=int, default=8192)
-    ap.add_argument("--cpu-particles", type=int, default=16384)
+    ap.add_argument("--cpu-particles", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kepler", default="converge", choices=["converge", "paper"],
                     help="paper: the paper's fixed-iteration Kepler solve (GLISSE_KEPLER_PAPER_FIXED)")
@@ -507,17 +507,27 @@ def main():
     pipe = fp64_instr_per_step(np_) * steps_per_launch / (kernel_ms * 1e-3) / dfma_peak
     traffic = profile_traffic()
 
-    # end to end through the C ABI with host buffers: create (H2D) + one chunk + read (D2H)
+    # end to end through the C ABI with host buffers in pinned memory: create (H2D of the
+    # planets and particles) + one chunk + read (D2H of states, flags, steps, reasons)
     e2e = None
     if args.e2e_steps > 0:
+        def pinned(shape, dtype):
+            return torch.empty(shape, dtype=dtype).pin_memory().numpy()
+
+        pl_h = pinned(planets.shape, torch.float64)
+        pl_h[...] = planets
+        pa_h = pinned(particles.shape, torch.float64)
+        pa_h[...] = particles
+        out_h = {"state": pinned((n, 6), torch.float64), "alive": pinned((n,), torch.uint8),
+                 "removal_step": pinned((n,), torch.int64), "removal_reason": pinned((n,), torch.int32)}
         times, done = [], 0
         for k in range(args.e2e_steps + 1):
             t0 = time.perf_counter()
-            sim = G.Simulation(w.star_mass, planets, particles, w.dt, chunk_steps=w.chunk, enc_value=w.k_hill,
+            sim = G.Simulation(w.star_mass, pl_h, pa_h, w.dt, chunk_steps=w.chunk, enc_value=w.k_hill,
                                r_max=w.r_max, timing=1, kepler_mode=kmode, kepler_iters=args.kepler_iters,
                                sort_mode=o.sort_mode)
             sim.advance(w.chunk)
-            out = sim.read()
+            out = sim.read(out_h)
             st = sim.timings()["particle_steps"]
             sim.close()
             dt_ = time.perf_counter() - t0
@@ -527,7 +537,8 @@ def main():
         e2e = {"value": done / sum(times), "unit": UNIT,
                "h2d_bytes_per_step": int(particles.nbytes + planets.nbytes),
                "d2h_bytes_per_step": int(out["state"].nbytes + out["removal_step"].nbytes +
-                                         out["removal_reason"].nbytes)}
+                                         out["removal_reason"].nbytes + n),
+               "host_buffers": "pinned"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -219,12 +219,19 @@ def glisse_advance(h, n_steps: int):
     _check(load().glisse_advance(h, int(n_steps)), "glisse_advance")
 
 
-def glisse_read(h, n: int):
-    """Returns dict(state [n][6], alive [n] bool, removal_step [n], removal_reason [n])."""
-    st = np.empty((n, 6))
-    alive = np.empty(n, dtype=np.uint8)
-    steps = np.empty(n, dtype=np.int64)
-    rsn = np.empty(n, dtype=np.int32)
+def glisse_read(h, n: int, out=None):
+    """Returns dict(state [n][6], alive [n] bool, removal_step [n], removal_reason [n]).
+    out: optional dict of preallocated host arrays (state float64 [n][6], alive uint8 [n],
+    removal_step int64 [n], removal_reason int32 [n]), e.g. in pinned memory, written in place."""
+    if out is not None:
+        st, alive, steps, rsn = out["state"], out["alive"], out["removal_step"], out["removal_reason"]
+        assert st.dtype == np.float64 and st.shape == (n, 6) and st.flags.c_contiguous
+        assert alive.dtype == np.uint8 and steps.dtype == np.int64 and rsn.dtype == np.int32
+    else:
+        st = np.empty((n, 6))
+        alive = np.empty(n, dtype=np.uint8)
+        steps = np.empty(n, dtype=np.int64)
+        rsn = np.empty(n, dtype=np.int32)
     rc = load().glisse_read(h, _dp(st), alive.ctypes.data_as(C.POINTER(C.c_uint8)),
                             steps.ctypes.data_as(C.POINTER(C.c_int64)), rsn.ctypes.data_as(C.POINTER(C.c_int32)))
     _check(rc, "glisse_read")
@@ -428,8 +435,8 @@ class Simulation:
         glisse_advance(self.h, n_steps)
         return self
 
-    def read(self):
-        return glisse_read(self.h, self.n)
+    def read(self, out=None):
+        return glisse_read(self.h, self.n, out)
 
     def status(self):
         return glisse_status(self.h)
