@@ -230,6 +230,25 @@ int glisse_partition_device_noalloc(int64_t n, int64_t ld, const uint8_t* alive,
                                     const int32_t* src_id, double* dst, int32_t* dst_id, int64_t* n_out,
                                     void* stream);
 
+/* Test hook: evaluate one of the device arithmetic helpers elementwise,
+ * out[i] = fn(a[i], b[i]) for device arrays of n doubles (b may be NULL:
+ * 1.0).  The helpers stand in for library division and square root on the
+ * hot path, so the tests check each against exact arithmetic:
+ *   RSQRT  a^(-1/2) (MUFU seed, one correction);  RCP  1/a (same);
+ *   RCP40  1/a to about 2^-40;  KRCUBE  b a^(-3/2) (integer seed powers);
+ *   FLOAT_SQUARE / FLOAT_CUBE  s^2 / s^3 of s = (float)a (integer products);
+ *   D2F  a truncated to float by bit operations.
+ * Not part of the method (the paper has no counterpart).  Synchronises the
+ * stream.  Errors: INVAL, CUDA. */
+#define GLISSE_MATH_RSQRT 0
+#define GLISSE_MATH_RCP 1
+#define GLISSE_MATH_RCP40 2
+#define GLISSE_MATH_KRCUBE 3
+#define GLISSE_MATH_FLOAT_SQUARE 4
+#define GLISSE_MATH_FLOAT_CUBE 5
+#define GLISSE_MATH_D2F 6
+int glisse_selftest_math(int32_t fn, const double* a, const double* b, double* out, int64_t n, void* stream);
+
 /*
  * FP64 throughput probe: runs independent chains of fused multiply-adds on
  * every SM for about `iterations` x 8 operations per thread and reports the

@@ -36,6 +36,8 @@ GLISSE_ENC_HILL = 0
 GLISSE_ENC_FIXED = 1
 GLISSE_SORT_NONE = 0
 GLISSE_SORT_COST = 1
+GLISSE_MATH_RSQRT, GLISSE_MATH_RCP, GLISSE_MATH_RCP40, GLISSE_MATH_KRCUBE = 0, 1, 2, 3
+GLISSE_MATH_FLOAT_SQUARE, GLISSE_MATH_FLOAT_CUBE, GLISSE_MATH_D2F = 4, 5, 6
 GLISSE_FRAME_HELIO = 0
 GLISSE_FRAME_BARY = 1
 
@@ -47,7 +49,7 @@ EXPORTED = (
     "glisse_batch_create", "glisse_batch_advance", "glisse_batch_read", "glisse_batch_status",
     "glisse_batch_timings", "glisse_batch_tune", "glisse_batch_destroy",
     "glisse_diff_create", "glisse_diff_forward", "glisse_diff_backward", "glisse_diff_destroy",
-    "glisse_set_sampling", "glisse_read_elements", "glisse_read_libration",
+    "glisse_set_sampling", "glisse_read_elements", "glisse_read_libration", "glisse_selftest_math",
 )
 
 GLISSE_PARTITION_NOALLOC_MAX = 67108864
@@ -176,6 +178,8 @@ def load(build_if_missing: bool = False):
     L.glisse_read_elements.restype = C.c_int
     L.glisse_read_libration.argtypes = [vp, u8p, u8p, i32p]
     L.glisse_read_libration.restype = C.c_int
+    L.glisse_selftest_math.argtypes = [C.c_int32, vp, vp, vp, C.c_int64, vp]
+    L.glisse_selftest_math.restype = C.c_int
     _lib = L
     return L
 
@@ -270,6 +274,19 @@ def glisse_read_libration(h, n: int):
                                         cnt.ctypes.data_as(C.POINTER(C.c_int32))), "glisse_read_libration")
     return {"near0": n0.astype(bool), "near180": n1.astype(bool), "count": cnt,
             "librating": (cnt > 0) & ~(n0.astype(bool) & n1.astype(bool))}
+
+
+def glisse_selftest_math(fn, a, b=None):
+    """Evaluate a device arithmetic helper on CUDA float64 tensors a (and b); returns a tensor."""
+    import torch
+
+    a = a.contiguous()
+    out = torch.empty_like(a)
+    bp = b.contiguous().data_ptr() if b is not None else None
+    stream = torch.cuda.current_stream(a.device).cuda_stream
+    _check(load().glisse_selftest_math(int(fn), a.data_ptr(), bp, out.data_ptr(), a.numel(), stream),
+           "glisse_selftest_math")
+    return out
 
 
 def glisse_status(h):
