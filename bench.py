@@ -364,6 +364,16 @@ def diff_arm(args):
     tan = G._growth_seed(x0)
     ms_fwd_t, _ = timed(lambda: dm.forward(x0, tan))
     dm.close()
+    # tape mode: the forward pass records every step, the backward pass only sweeps back
+    tape = None
+    need = 88 * n * n_steps
+    if torch.cuda.mem_get_info(dev)[0] > need + (8 << 30):
+        dt_ = G.DiffMap(1.0, pl, n, w.dt, n_steps, 0)
+        ms_fwd_tape, _ = timed(lambda: dt_.forward(x0))
+        ms_bwd_tape, _ = timed(lambda: dt_.backward(torch.ones_like(x0)))
+        dt_.close()
+        tape = {"forward_ms": ms_fwd_tape, "adjoint_ms": ms_bwd_tape, "tape_bytes": need,
+                "forward_plus_adjoint_ratio": (ms_fwd_tape + ms_bwd_tape) / ms_map}
     ps = n * n_steps  # particle-steps of the differentiable run (removed particles stop early)
     line = {
         "metric": "FP64 particle-steps/s of the differentiable map (forward, adjoint) vs the plain map",
@@ -378,6 +388,7 @@ def diff_arm(args):
         "adjoint": {"ms": ms_bwd, "particle_steps_per_s": ps / (ms_bwd * 1e-3)},
         "cost_ratio_to_plain_map": {"forward": ms_fwd / ms_map, "forward_with_tangent": ms_fwd_t / ms_map,
                                     "forward_plus_adjoint": (ms_fwd + ms_bwd) / ms_map},
+        "tape_mode": tape,
     }
     print(json.dumps(line), flush=True)
     return 0

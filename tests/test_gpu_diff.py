@@ -146,6 +146,24 @@ def test_gradient_independent_of_checkpoint_interval(G):
     np.testing.assert_array_equal(again, outs[1])
 
 
+def test_tape_mode_equals_one_recomputed_segment(G):
+    """checkpoint_every = 0 records every step in the forward pass; the backward pass then
+    skips the recompute.  With a single segment (K = n) the recompute produces the same
+    record, so the two gradients are bit-identical."""
+    w, pl, s0 = _workload(512)
+    n = 900
+    g = np.random.default_rng(8).normal(size=s0.shape)
+    outs = []
+    for K in (0, n):
+        dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n, K)
+        s1, _, _, rstep, _ = dm.forward(_cuda(s0))
+        outs.append((s1.cpu().numpy(), dm.backward(_cuda(g)).cpu().numpy(), rstep.cpu().numpy()))
+        dm.close()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    assert (outs[0][2] >= 0).sum() > 0  # removals on the way (frozen-state derivatives on the tape)
+
+
 def test_autograd_function(G):
     import torch
 
