@@ -324,6 +324,13 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles) 
     p.kepler_tol = GLISSE_PAPER_KEPLER_TOL;
     p.rmax = c->o.r_max > 0.0 ? c->o.r_max : 0.0;
 
+    // the first chunk of planets now, on the side stream: it overlaps the
+    // particle upload below and whatever the caller does before advancing
+    if (c->n_total > 0) {
+        const int er = ensure_chunk(c, 0);
+        if (er != GLISSE_OK) return er;
+    }
+
     // particles -> device SoA, ids, flags
     if (c->n_total > 0) {
         double* d_aos = nullptr;
@@ -614,11 +621,6 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
         ++c->since_compact;
         if (c->since_compact >= c->o.resync_chunks || remaining == 0) rc = compact(c);
     }
-    // Start the planets of the next chunk now, while the GPU is idle: the
-    // ephemeris kernel takes a whole SM (all of its shared memory), and if it
-    // is placed while other work (the caller's, or the next particle launch)
-    // occupies the SMs it can land beside particle blocks and unbalance them.
-    if (rc == GLISSE_OK && !c->external && c->n_live > 0) rc = ensure_chunk(c, c->step / c->C + 1);
     if (rc == GLISSE_OK) rc = check_status(c);
     if (prev != c->device) cudaSetDevice(prev);
     return rc;
