@@ -39,7 +39,8 @@
 namespace glisse {
 cudaError_t launch_eph_setup(const double*, int, double, double, int, double, PlanetConsts*, double*, int*,
                              cudaStream_t);
-cudaError_t launch_eph_chunk(const PlanetConsts*, double*, double, int, double*, double*, int*, cudaStream_t);
+cudaError_t launch_eph_chunk(const PlanetConsts*, double*, double, int, double*, double*, int*, cudaStream_t,
+                             int* progress = nullptr);
 
 constexpr int kMaxTangents = 6;
 constexpr int kScratchRows = 11;  // pre-drift state (6), post-drift position (3), s, tau

@@ -193,10 +193,14 @@ __device__ __forceinline__ void emit_step(int k, int np, int S, int lane, bool o
 // Advance the planets nsteps steps from the Jacobi state `jac` (in place).
 // Writes log steps 0..nsteps (positions + h0, broadcast layout) and the
 // synchronised heliocentric states hist[0..nsteps][np][6].
+// progress (optional, host-mapped): after every kProgressEvery-th step and the
+// last, the number of steps whose log entries are written, published with a
+// system-scope fence so that the host may launch work on them while this runs.
 // status: set to GLISSE_E_KEPLER if a planet's drift fails.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void eph_advance(const PlanetConsts& pc, double* jac, double dt, int nsteps,
-                                            double* __restrict__ log, double* __restrict__ hist, int* status) {
+                                            double* __restrict__ log, double* __restrict__ hist, int* status,
+                                            int* progress = nullptr) {
     const int np = pc.np;
     const int lane = threadIdx.x;
     const bool on = lane < np;
@@ -242,6 +246,11 @@ __device__ __forceinline__ void eph_advance(const PlanetConsts& pc, double* jac,
 #pragma unroll
         for (int d = 0; d < 3; ++d) w[d] = fma(hdt, acc[d], w[d]);
         emit_step(k + 1, np, S, lane, on, m_over_eta, r, w, h0, log, hist);
+        if (progress && (((k + 1) % kProgressEvery) == 0 || k + 1 == nsteps)) {
+            __threadfence_system();  // every lane's log entries before the count
+            __syncwarp();
+            if (lane == 0) *reinterpret_cast<volatile int*>(progress) = k + 1;
+        }
     }
     if (on) {
 #pragma unroll
@@ -255,8 +264,8 @@ __device__ __forceinline__ void eph_advance(const PlanetConsts& pc, double* jac,
 
 __global__ void __launch_bounds__(32) eph_chunk_kernel(const PlanetConsts* __restrict__ pcp, double* jac, double dt,
                                                          int nsteps, double* __restrict__ log,
-                                                         double* __restrict__ hist, int* status) {
-    eph_advance(*pcp, jac, dt, nsteps, log, hist, status);
+                                                         double* __restrict__ hist, int* status, int* progress) {
+    eph_advance(*pcp, jac, dt, nsteps, log, hist, status, progress);
 }
 
 // Many independent systems: block b advances system b (one warp each).
@@ -312,14 +321,14 @@ cudaError_t launch_eph_setup(const double* planets, int np, double m0, double G,
 // its block asks for the largest dynamic shared-memory allocation a block may
 // have: no other block fits on that SM while it runs (the memory is unused).
 cudaError_t launch_eph_chunk(const PlanetConsts* pc, double* jac, double dt, int nsteps, double* log, double* hist,
-                             int* status, cudaStream_t s) {
+                             int* status, cudaStream_t s, int* progress) {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(eph_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
-    eph_chunk_kernel<<<1, 32, (size_t)optin, s>>>(pc, jac, dt, nsteps, log, hist, status);
+    eph_chunk_kernel<<<1, 32, (size_t)optin, s>>>(pc, jac, dt, nsteps, log, hist, status, progress);
     return cudaGetLastError();
 }
 

@@ -15,8 +15,13 @@
 // run.  The ephemeris kernel for chunk j+1 runs on a high-priority side stream
 // while the particle kernel works through chunk j on the main stream (section
 // 2.2 computes the planets one chunk ahead in the same way); events order the
-// ring-buffer reuse.  After each segment (a particle launch over at most one
-// chunk) live particles are compacted every resync_chunks segments.
+// ring-buffer reuse.  The first chunk has nothing to overlap with: its planet
+// kernel starts in glisse_create, publishes its progress to host-mapped memory,
+// and the particles of that chunk run in segments launched as their planet steps
+// appear (the segments pass the open kick between them, so the cuts leave no
+// trace in the results).  After each segment (a particle launch over at most one
+// chunk) live particles are compacted every resync_chunks segments; the cuts in
+// the first chunk do not count as segments.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,7 +35,8 @@
 namespace glisse {
 cudaError_t launch_eph_setup(const double*, int, double, double, int, double, PlanetConsts*, double*, int*,
                              cudaStream_t);
-cudaError_t launch_eph_chunk(const PlanetConsts*, double*, double, int, double*, double*, int*, cudaStream_t);
+cudaError_t launch_eph_chunk(const PlanetConsts*, double*, double, int, double*, double*, int*, cudaStream_t,
+                             int* progress = nullptr);
 cudaError_t launch_eph_external(const PlanetConsts*, const double*, int64_t, double*, cudaStream_t);
 cudaError_t launch_particle_chunk(int, const ChunkArgs&, const ParticleConsts&, cudaStream_t);
 cudaError_t launch_particle_chunk_paper(int, const ChunkArgs&, const ParticleConsts&, cudaStream_t);
@@ -43,12 +49,22 @@ cudaError_t launch_export_live(int64_t, const double*, int64_t, const int32_t*, 
 cudaError_t launch_import(int64_t, const double*, double*, int64_t, int32_t*, cudaStream_t);
 }  // namespace glisse
 
+#include <chrono>
+#include <thread>
 #include <vector>
 
 using namespace glisse;
 
 namespace {
 constexpr int kRing = 3;
+// The first chunk of planets has no particle work to overlap with.  Its kernel
+// publishes its step count to host-mapped memory, and the particles of that chunk
+// run in segments ending at steps kFirstPiece * 2^k, each launched once the host
+// sees its planet steps written: the particles follow the planets from the first
+// piece on, while the planet kernel keeps its SM.
+constexpr int kMaxPieces = 8;
+constexpr int64_t kFirstPiece = kProgressEvery;
+constexpr double kProgressWaitSeconds = 60.0;
 constexpr double kG = 4.0 * 3.14159265358979323846 * 3.14159265358979323846;
 }  // namespace
 
@@ -75,6 +91,10 @@ struct glisse_ctx {
     cudaEvent_t ev_use[kRing] = {};
     bool used[kRing] = {};
     int64_t next_chunk = 0;
+    int64_t piece_end[kMaxPieces] = {};     // first chunk: step each particle segment may end at
+    int n_pieces = 0;
+    int* h_prog = nullptr;                  // host-mapped: planet steps of the first chunk written
+    int* d_prog = nullptr;
     double* d_st[2] = {};
     int32_t* d_id[2] = {};
     int cur = 0;
@@ -176,6 +196,7 @@ static void ctx_free(glisse_ctx* c) {
     }
     for (cudaEvent_t e : {c->tp0, c->tp1, c->tc0, c->tc1})
         if (e) cudaEventDestroy(e);
+    if (c->h_prog) cudaFreeHost(c->h_prog);
     for (int b = 0; b < 2; ++b) {
         cudaFree(c->d_st[b]);
         cudaFree(c->d_id[b]);
@@ -219,7 +240,16 @@ static int ensure_chunk(glisse_ctx* c, int64_t j) {
         const int slot = (int)(c->next_chunk % kRing);
         if (c->used[slot]) GL_CUDA(cudaStreamWaitEvent(c->se, c->ev_use[slot], 0));
         if (c->timing) GL_CUDA(cudaEventRecord(c->te0[slot], c->se));
-        GL_CUDA(launch_eph_chunk(c->d_pc, c->d_jac, c->dt, c->C, c->d_log[slot], c->d_hist[slot], c->d_status, c->se));
+        int* prog = nullptr;
+        if (c->next_chunk == 0) {
+            c->n_pieces = 0;
+            for (int64_t b = 0; b < c->C; b = c->piece_end[c->n_pieces++])
+                c->piece_end[c->n_pieces] =
+                    c->n_pieces == kMaxPieces - 1 ? c->C : std::min<int64_t>(c->C, kFirstPiece << c->n_pieces);
+            prog = c->d_prog;
+        }
+        GL_CUDA(launch_eph_chunk(c->d_pc, c->d_jac, c->dt, c->C, c->d_log[slot], c->d_hist[slot], c->d_status, c->se,
+                                 prog));
         if (c->timing) {
             GL_CUDA(cudaEventRecord(c->te1[slot], c->se));
             c->eph_pending[slot] = true;
@@ -230,6 +260,24 @@ static int ensure_chunk(glisse_ctx* c, int64_t j) {
         ++c->next_chunk;
     }
     return GLISSE_OK;
+}
+
+// Wait until the first chunk's planet kernel has written `steps` steps (host-mapped
+// count); fails if the side stream stops or errs first, or after kProgressWaitSeconds.
+static int wait_progress(glisse_ctx* c, int64_t steps) {
+    const volatile int* p = c->h_prog;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (unsigned it = 0;; ++it) {
+        if (*p >= steps) return GLISSE_OK;
+        if ((it & 255u) == 255u) {
+            const cudaError_t q = cudaStreamQuery(c->se);
+            if (q == cudaSuccess) return *p >= steps ? GLISSE_OK : GLISSE_E_CUDA;
+            if (q != cudaErrorNotReady) return GLISSE_E_CUDA;
+            const std::chrono::duration<double> el = std::chrono::steady_clock::now() - t0;
+            if (el.count() > kProgressWaitSeconds) return GLISSE_E_CUDA;
+        }
+        std::this_thread::yield();
+    }
 }
 
 static int check_status(glisse_ctx* c) {
@@ -254,6 +302,9 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles) 
         GL_CUDA(cudaEventCreateWithFlags(&c->ev_eph[r], cudaEventDisableTiming));
         GL_CUDA(cudaEventCreateWithFlags(&c->ev_use[r], cudaEventDisableTiming));
     }
+    GL_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&c->h_prog), sizeof(int), cudaHostAllocMapped));
+    *c->h_prog = 0;
+    GL_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->d_prog), c->h_prog, 0));
     if (c->timing) {
         for (int r = 0; r < kRing; ++r) {
             GL_CUDA(cudaEventCreate(&c->te0[r]));
@@ -331,15 +382,13 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles) 
         if (er != GLISSE_OK) return er;
     }
 
-    // particles -> device SoA, ids, flags
+    // particles -> device SoA, ids, flags.  The [N][6] per-id output buffer stages
+    // the upload (it is cleared right after on the same stream): a temporary buffer
+    // would have to be freed, and cudaFree waits for the planet kernel started above.
     if (c->n_total > 0) {
-        double* d_aos = nullptr;
-        GL_ALLOC(d_aos, sizeof(double) * 6 * (size_t)c->n_total);
-        e = cudaMemcpyAsync(d_aos, particles, sizeof(double) * 6 * (size_t)c->n_total, cudaMemcpyHostToDevice, c->s);
-        if (e == cudaSuccess) e = launch_import(c->n_total, d_aos, c->d_st[0], cap, c->d_id[0], c->s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
-        cudaFree(d_aos);
-        if (e != cudaSuccess) return GLISSE_E_CUDA;
+        GL_CUDA(cudaMemcpyAsync(c->d_out_state, particles, sizeof(double) * 6 * (size_t)c->n_total,
+                                cudaMemcpyHostToDevice, c->s));
+        GL_CUDA(launch_import(c->n_total, c->d_out_state, c->d_st[0], cap, c->d_id[0], c->s));
     }
     GL_CUDA(cudaMemsetAsync(c->d_alive, 1, (size_t)cap, c->s));
     GL_CUDA(cudaMemsetAsync(c->d_out_state, 0, sizeof(double) * 6 * (size_t)cap, c->s));
@@ -538,10 +587,12 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
     int rc = GLISSE_OK;
     if (c->o.sort_mode == GLISSE_SORT_COST && !c->tested_first && c->n_live > 0 && (rc = compact(c)) != GLISSE_OK)
         return rc;
+    bool open = false;  // the live velocities hold an opening half kick (between pieces)
     while (remaining > 0 && rc == GLISSE_OK) {
         const double* log = nullptr;
         int64_t m = 0;
         int slot = -1;
+        bool piece_cut = false;
         if (c->external) {
             m = std::min<int64_t>(remaining, c->C);
             log = c->d_ext_log + (size_t)c->ext_off * S;
@@ -554,15 +605,27 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
                 rc = GLISSE_E_STATE;
                 break;
             }
-            GL_CUDA(cudaStreamWaitEvent(c->s, c->ev_eph[slot], 0));
             m = std::min<int64_t>(remaining, c->C - off);
+            int k = 0;
+            while (j == 0 && c->piece_end[k] <= off && k < c->n_pieces - 1) ++k;
+            if (j == 0 && k < c->n_pieces - 1) {
+                // first chunk: wait (on the host) only for the planet steps of this piece
+                if ((rc = wait_progress(c, c->piece_end[k])) != GLISSE_OK) break;
+                m = std::min<int64_t>(m, c->piece_end[k] - off);
+                piece_cut = off + m == c->piece_end[k];
+            } else {
+                GL_CUDA(cudaStreamWaitEvent(c->s, c->ev_eph[slot], 0));
+            }
             log = c->d_log[slot] + (size_t)off * S;
             if (c->samp_on) {
                 // end the segment at the next sample step
                 const int64_t next = (c->step / c->samp.every + 1) * c->samp.every;
+                if (next - c->step <= m) piece_cut = false;
                 m = std::min<int64_t>(m, next - c->step);
             }
         }
+        // a segment cut only by a piece end, with more steps to come, leaves the state open
+        const bool close = !(piece_cut && m < remaining);
         if (c->n_live > 0) {
             ChunkArgs a;
             a.pc = nullptr;
@@ -575,6 +638,8 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
             a.step0 = c->step;
             a.nsteps = (int32_t)m;
             a.test_first = c->tested_first ? 0 : 1;
+            a.open_in = open ? 1 : 0;
+            a.close_out = close ? 1 : 0;
             a.out_state = c->d_out_state;
             a.out_step = c->d_out_step;
             a.out_reason = c->d_out_reason;
@@ -618,6 +683,8 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
         c->step += m;
         remaining -= m;
         if (c->external) c->ext_off += m;
+        open = !close;
+        if (open) continue;  // no compaction between pieces: warps keep their members
         ++c->since_compact;
         if (c->since_compact >= c->o.resync_chunks || remaining == 0) rc = compact(c);
     }

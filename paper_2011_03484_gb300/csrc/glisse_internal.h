@@ -14,6 +14,8 @@ constexpr int kMaxPlanets = GLISSE_MAX_PLANETS;
 // warp fetch a whole record with two 16-byte broadcast loads.
 constexpr int kRec = 4;
 __host__ __device__ constexpr int log_stride(int np) { return kRec * (np + 1); }
+// The ephemeris kernel of a context's first chunk publishes its step count this often.
+constexpr int kProgressEvery = 64;
 
 // Planet system constants (written once by the set-up kernel, read by all kernels).
 struct PlanetConsts {
@@ -55,6 +57,9 @@ struct ChunkArgs {
     int64_t step0;        // global index of the segment's first step
     int32_t nsteps;       // steps in the segment (>= 1)
     int32_t test_first;   // apply the removal test at the segment's step 0 first
+    int32_t open_in;      // the velocities already hold the opening half kick of step 0
+    int32_t close_out;    // 1: end with the closing half kick (synchronised state);
+                          // 0: end with the full kick that also opens the next segment
     // per-id outputs for particles removed during the segment
     double* out_state;    // [N][6]
     int64_t* out_step;    // [N]

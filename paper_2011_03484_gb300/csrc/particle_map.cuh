@@ -93,11 +93,16 @@ __device__ __forceinline__ int test_only(double x, double y, double z, const dou
 
 // The map for one lane over nsteps steps of the log L (L step 0 = the lane's
 // current time).  State in registers; act / reason / rstep record removal.
+// open_in: the velocities already carry the opening half kick of step 0.
+// close_out: false leaves the state open, ending with the full kick that a
+// single longer launch would apply there (the next segment then has open_in).
+// A split with open_in / close_out is bit-identical to no split.
 // pc may live in the constant bank (kernel parameter) or in shared memory.
 template <int NP, int MODE = kDriftConverge>
 __device__ __forceinline__ void advance_lane(const ParticleConsts& pc, const double* __restrict__ L, int64_t step0,
                                              int nsteps, bool test_first, double& x, double& y, double& z, double& vx,
-                                             double& vy, double& vz, bool& act, int& reason, int64_t& rstep) {
+                                             double& vy, double& vz, bool& act, int& reason, int64_t& rstep,
+                                             bool open_in = false, bool close_out = true) {
     const float muf = d2f_bits(pc.mu), dtf = d2f_bits(pc.dt);
     const bool has_rmax = __double_as_longlong(pc.rmax) != 0;
     const int S = log_stride(NP);
@@ -110,7 +115,7 @@ __device__ __forceinline__ void advance_lane(const ParticleConsts& pc, const dou
             rstep = step0;
         }
     }
-    if (act) kick_test<NP>(x, y, z, vx, vy, vz, L, pc.half_dt, pc.tgm_half, pc.rc2);
+    if (act && !open_in) kick_test<NP>(x, y, z, vx, vy, vz, L, pc.half_dt, pc.tgm_half, pc.rc2);
     double r0, mur0;
     radius_of(x, y, z, r0, mur0);
     mur0 *= pc.mu;
@@ -151,7 +156,7 @@ __device__ __forceinline__ void advance_lane(const ParticleConsts& pc, const dou
         }
         // escape: |r| > r_max, with |r| from the drift (integer compare of positive doubles)
         int hit = (has_rmax && lt_nonneg(pc.rmax, r0)) ? GLISSE_REMOVED_ESCAPE : 0;
-        const bool last = (k + 1 == nsteps);
+        const bool last = close_out && (k + 1 == nsteps);
         double nvx = vx, nvy = vy, nvz = vz;
         int enc;
         if (last)
@@ -216,7 +221,7 @@ __global__ void __launch_bounds__(kParticleBlock, GLISSE_PARTICLE_MIN_BLOCKS)
     int reason = 0;
     int64_t rstep = -1;
     advance_lane<NP, MODE>(pc, a.log, a.step0, a.nsteps, a.test_first != 0, x, y, z, vx, vy, vz, act, reason,
-                           rstep);
+                           rstep, a.open_in != 0, a.close_out != 0);
     if (a.steps_done) {
         // steps this particle actually advanced in the segment (exact work count)
         const unsigned adv = !started ? 0u : (rstep >= 0 ? (unsigned)(rstep - a.step0) : (unsigned)a.nsteps);

@@ -86,6 +86,18 @@ def test_planet_log_chunking_is_exact(G):
     np.testing.assert_array_equal(outs[0], outs[2])
 
 
+def test_first_chunk_pieces_are_exact(G):
+    """The first chunk's planets run in pieces ending at 64 * 2^k steps (the last piece
+    takes the rest); the planet sequence matches chunks too short to be split."""
+    w = gi.make("tiny", n=4)
+    n = 9000
+    ref = run_gpu(G, w, n, splits=[100] * 90, chunk_steps=50)
+    for c in (9000, 300, 4097):
+        g = run_gpu(G, w, n, splits=[100] * 90, chunk_steps=c)
+        np.testing.assert_array_equal(g["planets"], ref["planets"])
+        np.testing.assert_array_equal(g["removal_step"], ref["removal_step"])
+
+
 # ---------------------------------------------------------------------------
 # the tiny workload, whole set, 10^4 steps
 # ---------------------------------------------------------------------------
