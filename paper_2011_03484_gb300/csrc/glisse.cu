@@ -176,7 +176,7 @@ extern "C" const char* glisse_strerror(int code) {
         case GLISSE_E_NOMEM: return "out of memory";
         case GLISSE_E_CUDA: return "CUDA error";
         case GLISSE_E_KEPLER: return "Kepler solve did not converge";
-        case GLISSE_E_TIMEOUT: return "device wait timed out";
+        case GLISSE_E_TIMEOUT: return "wait for device work timed out";
         case GLISSE_E_STATE: return "invalid in the current state";
         default: return "unknown status";
     }
@@ -274,7 +274,7 @@ static int wait_progress(glisse_ctx* c, int64_t steps) {
             if (q == cudaSuccess) return *p >= steps ? GLISSE_OK : GLISSE_E_CUDA;
             if (q != cudaErrorNotReady) return GLISSE_E_CUDA;
             const std::chrono::duration<double> el = std::chrono::steady_clock::now() - t0;
-            if (el.count() > kProgressWaitSeconds) return GLISSE_E_CUDA;
+            if (el.count() > kProgressWaitSeconds) return GLISSE_E_TIMEOUT;
         }
         std::this_thread::yield();
     }
