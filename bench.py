@@ -366,7 +366,7 @@ def diff_arm(args):
     dm.close()
     # tape mode: the forward pass records every step, the backward pass only sweeps back
     tape = None
-    need = 88 * n * n_steps
+    need = 112 * n * n_steps
     if torch.cuda.mem_get_info(dev)[0] > need + (8 << 30):
         dt_ = G.DiffMap(1.0, pl, n, w.dt, n_steps, 0)
         ms_fwd_tape, _ = timed(lambda: dt_.forward(x0))

@@ -278,9 +278,9 @@ typedef struct glisse_diff glisse_diff; /* opaque; owned by the library */
 /* Planets as in glisse_create; n_particles states per forward call; the planet
  * log of n_steps steps is computed on the device here.  checkpoint_every >= 1:
  * the backward pass recomputes that many steps per segment (storage: 48 B per
- * particle per checkpoint plus 88 B per particle per step of one segment).
- * checkpoint_every = 0 (tape mode): the forward pass records every step (88 B
- * per particle per step, e.g. 58 GB for 65536 particles over 10^4 steps) and
+ * particle per checkpoint plus 112 B per particle per step of one segment).
+ * checkpoint_every = 0 (tape mode): the forward pass records every step (112 B
+ * per particle per step, e.g. 73 GB for 65536 particles over 10^4 steps) and
  * the backward pass does not recompute; NOMEM if the device cannot hold it.
  * opts: enc_mode, enc_value and r_max apply.  Errors: INVAL, NOMEM, CUDA, KEPLER. */
 int glisse_diff_create(glisse_diff** out, double star_mass, const double* planets, int32_t n_planets,

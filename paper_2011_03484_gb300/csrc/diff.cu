@@ -16,13 +16,14 @@
 // kick of dt (their Jacobians, tau A(r) at the same r, merge the same way);
 // at a segment boundary and at the end they stay half kicks.  Backward: for each K-step segment from
 // the last, the thread recomputes the segment from its checkpoint, keeping the
-// pre-drift state, the post-drift position and the solved universal anomaly
-// s and reduced time tau of every step in a scratch buffer, then runs the
-// adjoint kicks and drifts backwards through it (the drift's G-functions are
-// re-evaluated from the stored s and tau, without a second solve).
+// pre-drift state, the post-drift position, the solved universal anomaly s,
+// the reduced time tau, G_4, G_5 and 1/R of every step in a scratch buffer,
+// then runs the adjoint kicks and drifts backwards through it (the other
+// G-functions follow from G_4, G_5 by their recurrence: no second solve and no
+// second series).
 // Tape mode (checkpoint_every = 0) keeps that record for every step of the
 // run, written by the forward pass itself: the backward pass is the reverse
-// sweep alone, at 88 B per particle-step of device memory (58 GB for 65536
+// sweep alone, at 112 B per particle-step of device memory (73 GB for 65536
 // particles over 10^4 steps, which HBM holds).
 // A removed particle's output is its frozen state; its derivatives are those
 // of that frozen state (the steps after removal contribute nothing).
@@ -43,7 +44,7 @@ cudaError_t launch_eph_chunk(const PlanetConsts*, double*, double, int, double*,
                              int* progress = nullptr);
 
 constexpr int kMaxTangents = 6;
-constexpr int kScratchRows = 11;  // pre-drift state (6), post-drift position (3), s, tau
+constexpr int kScratchRows = 14;  // pre-drift state (6), post-drift position (3), s, tau, G_4, G_5, 1/R
 constexpr int kDiffBlock = 128;
 
 struct DiffArgs {
@@ -88,7 +89,10 @@ __device__ __forceinline__ int kick_state(double st[6], const double* __restrict
     return hit;
 }
 
-// out += tau A(r) w  (tgm = tau G m_j)
+// out += tau A(r) w  (tgm = tau G m_j), A(r) = sum_j -G m_j (I - 3 d d^T / |d|^2) / |d|^3.
+// A is symmetric, so the same routine serves the tangent and the adjoint map.
+// 1/|d|^2 takes the 40-bit reciprocal: it scales a term that is itself
+// ~tau G m_j / |d|^3 (1e-4 or less) of the step's Jacobian.
 template <int NP>
 __device__ __forceinline__ void kick_jac(const double r[3], const double* __restrict__ L,
                                          const double (&tgm)[kMaxPlanets], const double w[3], double out[3]) {
@@ -97,17 +101,17 @@ __device__ __forceinline__ void kick_jac(const double r[3], const double* __rest
         const double dx = r[0] - L[kRec * j], dy = r[1] - L[kRec * j + 1], dz = r[2] - L[kRec * j + 2];
         const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const double s = k_rcube(d2, tgm[j]);
-        const double c = 3.0 * (dx * w[0] + dy * w[1] + dz * w[2]) * rcp_full(d2);
-        out[0] -= s * (w[0] - c * dx);
-        out[1] -= s * (w[1] - c * dy);
-        out[2] -= s * (w[2] - c * dz);
+        const double c = (3.0 * fma(dx, w[0], fma(dy, w[1], dz * w[2]))) * rcp_40(d2);
+        out[0] = fma(-s, fma(-c, dx, w[0]), out[0]);
+        out[1] = fma(-s, fma(-c, dy, w[1]), out[1]);
+        out[2] = fma(-s, fma(-c, dz, w[2]), out[2]);
     }
 }
 
 // TMAX: compile-time tangent capacity (0, 1 or kMaxTangents) so that the
 // tangent vectors stay in registers; tangents a.ntan..TMAX-1 are zero.
 template <int NP, int TMAX>
-__global__ void __launch_bounds__(kDiffBlock) diff_forward_kernel(const DiffArgs a, const ParticleConsts pc) {
+__global__ void __launch_bounds__(kDiffBlock, TMAX == 0 ? 7 : 1) diff_forward_kernel(const DiffArgs a, const ParticleConsts pc) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const int S = log_stride(NP);
@@ -169,6 +173,9 @@ __global__ void __launch_bounds__(kDiffBlock) diff_forward_kernel(const DiffArgs
             for (int c = 0; c < 3; ++c) tp[(6 + c) * a.n] = st[c];
             tp[9 * a.n] = d.s;
             tp[10 * a.n] = d.tau;
+            tp[11 * a.n] = d.G[4];
+            tp[12 * a.n] = d.G[5];
+            tp[13 * a.n] = d.inv_R;
         }
         bool bad = false;
         for (int c = 0; c < 6; ++c) bad |= nonfinite_bits(st[c]);
@@ -250,6 +257,9 @@ __global__ void __launch_bounds__(kDiffBlock, 4) diff_backward_kernel(const Diff
                 drift_scalars(pc.mu, pc.dt, st, d);
                 sc[9 * a.n] = d.s;
                 sc[10 * a.n] = d.tau;
+                sc[11 * a.n] = d.G[4];
+                sc[12 * a.n] = d.G[5];
+                sc[13 * a.n] = d.inv_R;
                 double pre[6];
                 for (int c = 0; c < 6; ++c) pre[c] = st[c];
                 for (int c = 0; c < 3; ++c) {
@@ -275,7 +285,7 @@ __global__ void __launch_bounds__(kDiffBlock, 4) diff_backward_kernel(const Diff
                 if (!(last && cut_before_drift)) {
                     DriftScalars d;
                     drift_restore(pc.mu, pc.dt, pre, sc[9 * a.n], sc[10 * a.n], d);
-                    drift_finish(pc.mu, d);
+                    drift_finish_stored(pc.mu, d, sc[11 * a.n], sc[12 * a.n], sc[13 * a.n]);
                     drift_adjoint(pc.mu, pre, d, l);
                 }
                 // opening half kick at t_k (only at the segment start; inside, it is part of
