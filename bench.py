@@ -333,7 +333,9 @@ def diff_arm(args):
     w = gi.WORKLOADS["diff"]
     full = gi.make("diff")
     pl, s0 = full["planets"], full["particles"]
-    n, n_steps, K = s0.shape[0], w.n_steps, 256
+    if args.diff_particles > 0:
+        s0 = s0[: args.diff_particles]  # a prefix of the same seeded set (small cases for ncu)
+    n, n_steps, K = s0.shape[0], (args.diff_steps if args.diff_steps > 0 else w.n_steps), 256
     stream = torch.cuda.current_stream(dev)
 
     def timed(fn):
@@ -406,6 +408,8 @@ def main():
                     help="order live particles by expected Kepler-solve cost at every compaction")
     ap.add_argument("--tune", action="store_true", help="batched: run the autotuner before timing")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--diff-particles", type=int, default=0, help="diff: first N particles only (0 = all)")
+    ap.add_argument("--diff-steps", type=int, default=0, help="diff: steps (0 = the workload's)")
     ap.add_argument("--ref-particles", type=int, default=8192)
     ap.add_argument("--cpu-particles", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
