@@ -365,6 +365,8 @@ def diff_arm(args):
     ms_bwd, _ = timed(lambda: dm.backward(torch.ones_like(x0)))
     tan = G._growth_seed(x0)
     ms_fwd_t, _ = timed(lambda: dm.forward(x0, tan))
+    # gradient of the growth indicator: forward mode over 6 state directions
+    ms_grow, _ = timed(lambda: dm.growth_gradient(x0, tan[0].contiguous()))
     dm.close()
     # tape mode: the forward pass records every step, the backward pass only sweeps back
     tape = None
@@ -388,6 +390,8 @@ def diff_arm(args):
         "diff_forward": {"ms": ms_fwd, "particle_steps_per_s": ps / (ms_fwd * 1e-3)},
         "diff_forward_with_tangent": {"ms": ms_fwd_t, "particle_steps_per_s": ps / (ms_fwd_t * 1e-3)},
         "adjoint": {"ms": ms_bwd, "particle_steps_per_s": ps / (ms_bwd * 1e-3)},
+        "growth_gradient": {"ms": ms_grow, "particle_steps_per_s": ps / (ms_grow * 1e-3),
+                            "ratio_to_plain_map": ms_grow / ms_map},
         "cost_ratio_to_plain_map": {"forward": ms_fwd / ms_map, "forward_with_tangent": ms_fwd_t / ms_map,
                                     "forward_plus_adjoint": (ms_fwd + ms_bwd) / ms_map},
         "tape_mode": tape,

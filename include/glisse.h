@@ -301,6 +301,21 @@ int glisse_diff_forward(glisse_diff* d, const double* state0, double* state1, in
  * particle's own map).  Errors: STATE before any forward call, INVAL, CUDA. */
 int glisse_diff_backward(glisse_diff* d, const double* grad_state1, double* grad_state0, void* stream);
 
+/* Gradient of the tangent-growth indicator g = log(|J t_0| / |t_0|) with respect to
+ * the initial state, the tangent seed t_0 held fixed (the part through t_0 is
+ * J^T (J t_0) / |J t_0|^2 - t_0 / |t_0|^2, which glisse_diff_backward gives).
+ *   state0, tangent0 : device [n][6]; grad_state0 : device [n][6] out,
+ *                      grad_state0[i][c] = dg_i / d state0[i][c]
+ *   log_growth       : device [n] out, g_i (may be NULL)
+ * Forward mode: for each particle and each of the 6 state coordinates, the map,
+ * its tangent along that coordinate and the growth tangent with its derivative
+ * (the second derivative of the map contracted with t_0) run through the same
+ * steps, kick merging and removals as glisse_diff_forward; about 6 forward
+ * passes with two tangents, one of them in dual numbers.  Independent of any
+ * forward call.  Synchronises `stream`.  Errors: INVAL, CUDA. */
+int glisse_diff_growth_gradient(glisse_diff* d, const double* state0, const double* tangent0,
+                                double* grad_state0, double* log_growth, void* stream);
+
 /* Release the object (NULL is ignored). */
 void glisse_diff_destroy(glisse_diff* d);
 

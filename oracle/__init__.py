@@ -247,6 +247,44 @@ def particles_jvp(star_mass, planet_masses, log, dt, state0, direction, rcrit_, 
     return s1, jv, rs, rn
 
 
+def growth(star_mass, planet_masses, log, dt, state0, tangent0, rcrit_, r_max, nthreads=0):
+    """Tangent-growth indicator g = log(|J t0| / |t0|) per particle, J t0 from the
+    complex-step tangent map; also the removal steps of that run."""
+    t0 = _f64(tangent0).reshape(-1, 6)
+    _, jv, rs, _ = particles_jvp(star_mass, planet_masses, log, dt, state0, t0, rcrit_, r_max, nthreads=nthreads)
+    return 0.5 * np.log((jv * jv).sum(axis=1) / (t0 * t0).sum(axis=1)), rs
+
+
+def growth_gradient(star_mass, planet_masses, log, dt, state0, tangent0, rcrit_, r_max, h_pos=1e-5, h_vel=1e-6,
+                    nthreads=0):
+    """d g / d state0 [n][6] at fixed tangent0, by central differences of growth()
+    with steps h and h/2 per coordinate (h_pos AU for positions, h_vel AU/yr for
+    velocities) combined by Richardson extrapolation, (4 D(h/2) - D(h)) / 3.
+
+    Returns (gradient, error estimate |R - D(h/2)| per entry, ok [n]); ok is False
+    for particles whose removal step differs between the perturbed runs (there
+    the difference quotient is not a derivative)."""
+    s0 = _f64(state0).reshape(-1, 6)
+    n = s0.shape[0]
+    _, rs0 = growth(star_mass, planet_masses, log, dt, s0, tangent0, rcrit_, r_max, nthreads)
+    ok = np.ones(n, dtype=bool)
+    grad = np.empty((n, 6))
+    err = np.empty((n, 6))
+    for c in range(6):
+        h = h_pos if c < 3 else h_vel
+        d = []
+        for hh in (h, 0.5 * h):
+            e = np.zeros_like(s0)
+            e[:, c] = hh
+            gp, rp = growth(star_mass, planet_masses, log, dt, s0 + e, tangent0, rcrit_, r_max, nthreads)
+            gm, rm = growth(star_mass, planet_masses, log, dt, s0 - e, tangent0, rcrit_, r_max, nthreads)
+            ok &= (rp == rs0) & (rm == rs0)
+            d.append((gp - gm) / (2.0 * hh))
+        grad[:, c] = (4.0 * d[1] - d[0]) / 3.0
+        err[:, c] = np.abs(grad[:, c] - d[1])
+    return grad, err, ok
+
+
 def particles_jacobian(star_mass, planet_masses, log, dt, state0, rcrit_, r_max, nthreads=0):
     """Full 6x6 Jacobian per particle [n][6][6] (column c = derivative along input coordinate c)."""
     s0 = _f64(state0).reshape(-1, 6)

@@ -48,7 +48,8 @@ EXPORTED = (
     "glisse_partition_device", "glisse_fp64_peak", "glisse_timings", "glisse_partition_device_noalloc",
     "glisse_batch_create", "glisse_batch_advance", "glisse_batch_read", "glisse_batch_status",
     "glisse_batch_timings", "glisse_batch_tune", "glisse_batch_destroy",
-    "glisse_diff_create", "glisse_diff_forward", "glisse_diff_backward", "glisse_diff_destroy",
+    "glisse_diff_create", "glisse_diff_forward", "glisse_diff_backward", "glisse_diff_growth_gradient",
+    "glisse_diff_destroy",
     "glisse_set_sampling", "glisse_read_elements", "glisse_read_libration", "glisse_selftest_math",
 )
 
@@ -170,6 +171,8 @@ def load(build_if_missing: bool = False):
     L.glisse_diff_forward.restype = C.c_int
     L.glisse_diff_backward.argtypes = [vp, vp, vp, vp]
     L.glisse_diff_backward.restype = C.c_int
+    L.glisse_diff_growth_gradient.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.glisse_diff_growth_gradient.restype = C.c_int
     L.glisse_diff_destroy.argtypes = [vp]
     L.glisse_diff_destroy.restype = None
     L.glisse_set_sampling.argtypes = [vp, C.POINTER(glisse_sampling)]
@@ -516,6 +519,11 @@ def glisse_diff_backward(h, grad_state1, grad_state0, stream=0):
     _check(load().glisse_diff_backward(h, grad_state1, grad_state0, stream), "glisse_diff_backward")
 
 
+def glisse_diff_growth_gradient(h, state0, tangent0, grad_state0, log_growth=None, stream=0):
+    _check(load().glisse_diff_growth_gradient(h, state0, tangent0, grad_state0, log_growth, stream),
+           "glisse_diff_growth_gradient")
+
+
 def glisse_diff_destroy(h):
     if h:
         load().glisse_diff_destroy(h)
@@ -572,6 +580,22 @@ class DiffMap:
         glisse_diff_backward(self.h, g.data_ptr(), out.data_ptr(), stream)
         return out
 
+    def growth_gradient(self, state0, tangent0):
+        """(d g / d state0 [n, 6] with the seed held fixed, g [n]) for
+        g = log(|J t0| / |t0|); independent of forward()."""
+        import torch
+
+        state0 = state0.contiguous()
+        tangent0 = tangent0.contiguous()
+        assert state0.is_cuda and state0.dtype == torch.float64 and state0.shape == (self.n, 6)
+        assert tangent0.shape == (self.n, 6) and tangent0.dtype == torch.float64
+        grad = torch.empty_like(state0)
+        growth = torch.empty(self.n, dtype=torch.float64, device=state0.device)
+        stream = torch.cuda.current_stream(state0.device).cuda_stream
+        glisse_diff_growth_gradient(self.h, state0.data_ptr(), tangent0.data_ptr(), grad.data_ptr(),
+                                    growth.data_ptr(), stream)
+        return grad, growth
+
     def close(self):
         if self.h:
             glisse_diff_destroy(self.h)
@@ -597,26 +621,53 @@ def _make_autograd():
     import torch
 
     class GlisseMap(torch.autograd.Function):
-        """state1, log_growth = GlisseMap.apply(state0, diff_map).
+        """state1, log_growth = GlisseMap.apply(state0, diff_map[, tangent0]).
 
-        Differentiable with respect to state0 through the hand-written adjoint
-        kernel (glisse_diff_backward); log_growth (log |J t| / |t| for the
-        default tangent along r and v) is returned as a non-differentiable
-        stability indicator."""
+        Both outputs are differentiable with respect to state0 (and tangent0).
+        log_growth = log(|J t0| / |t0|) for the seed tangent0 [n, 6], by default
+        unit vectors along r and v (_growth_seed, whose own dependence on state0
+        is included).  Gradients: J^T from the hand-written adjoint kernel
+        (glisse_diff_backward); the growth's gradient with respect to state0 at
+        fixed seed from the second-order kernel (glisse_diff_growth_gradient),
+        and with respect to the seed from the adjoint, J^T (J t0) / |J t0|^2 -
+        t0 / |t0|^2."""
 
         @staticmethod
-        def forward(ctx, state0, dmap):
-            state1, _, growth, _, _ = dmap.forward(state0, _growth_seed(state0))
+        def forward(ctx, state0, dmap, *rest):
+            tangent0 = rest[0] if rest else None
+            ctx.n_inputs = 2 + len(rest)
+            ctx.default_seed = tangent0 is None
+            seed = _growth_seed(state0.detach())[0] if tangent0 is None else tangent0.detach()
+            state1, tan1, growth, _, _ = dmap.forward(state0.detach(), seed.unsqueeze(0).contiguous())
             ctx.dmap = dmap
             ctx.call = dmap.forward_calls
-            ctx.mark_non_differentiable(growth)
+            ctx.save_for_backward(state0.detach(), seed, tan1[0])
             return state1, growth
 
         @staticmethod
         def backward(ctx, grad_state1, grad_growth):
             if ctx.dmap.forward_calls != ctx.call:
                 raise RuntimeError("DiffMap was run forward again before this backward; use one DiffMap per use")
-            return ctx.dmap.backward(grad_state1), None
+            state0, seed, tn = ctx.saved_tensors
+            g1 = torch.zeros_like(state0) if grad_state1 is None else grad_state1
+            grad_state0 = ctx.dmap.backward(g1)
+            grad_seed = None
+            if grad_growth is not None and bool((grad_growth != 0).any()):
+                gg = grad_growth.unsqueeze(1)
+                H, _ = ctx.dmap.growth_gradient(state0, seed)
+                grad_state0 = grad_state0 + gg * H
+                if ctx.default_seed or ctx.needs_input_grad[2]:
+                    nn = (tn * tn).sum(dim=1, keepdim=True)
+                    u = torch.where(nn > 0, tn / torch.where(nn > 0, nn, torch.ones_like(nn)), torch.zeros_like(tn))
+                    n0 = (seed * seed).sum(dim=1, keepdim=True)
+                    grad_seed = ctx.dmap.backward((gg * u).contiguous()) - gg * seed / n0
+                if ctx.default_seed and grad_seed is not None:
+                    with torch.enable_grad():
+                        s0 = state0.clone().requires_grad_(True)
+                        (gs,) = torch.autograd.grad(_growth_seed(s0)[0], s0, grad_seed)
+                    grad_state0 = grad_state0 + gs
+                    grad_seed = None
+            return (grad_state0, None, grad_seed)[: ctx.n_inputs]
 
     return GlisseMap
 

@@ -35,7 +35,7 @@
 #include <new>
 
 #include "glisse_internal.h"
-#include "kepler.cuh"
+#include "drift_diff.cuh"
 
 namespace glisse {
 cudaError_t launch_eph_setup(const double*, int, double, double, int, double, PlanetConsts*, double*, int*,
@@ -93,15 +93,17 @@ __device__ __forceinline__ int kick_state(double st[6], const double* __restrict
 // A is symmetric, so the same routine serves the tangent and the adjoint map.
 // 1/|d|^2 takes the 40-bit reciprocal: it scales a term that is itself
 // ~tau G m_j / |d|^3 (1e-4 or less) of the step's Jacobian.
-template <int NP>
-__device__ __forceinline__ void kick_jac(const double r[3], const double* __restrict__ L,
-                                         const double (&tgm)[kMaxPlanets], const double w[3], double out[3]) {
+// Generic over the scalar type: with ad::Dual components (r, dr) and (w, dw) it
+// also gives d(tau A(r) w) = tau A(r) dw + tau (dA(r)[dr]) w.
+template <int NP, class T>
+__device__ __forceinline__ void kick_jac(const T r[3], const double* __restrict__ L,
+                                         const double (&tgm)[kMaxPlanets], const T w[3], T out[3]) {
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
-        const double dx = r[0] - L[kRec * j], dy = r[1] - L[kRec * j + 1], dz = r[2] - L[kRec * j + 2];
-        const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
-        const double s = k_rcube(d2, tgm[j]);
-        const double c = (3.0 * fma(dx, w[0], fma(dy, w[1], dz * w[2]))) * rcp_40(d2);
+        const T dx = r[0] - L[kRec * j], dy = r[1] - L[kRec * j + 1], dz = r[2] - L[kRec * j + 2];
+        const T d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        const T s = k_rcube(d2, tgm[j]);
+        const T c = (3.0 * fma(dx, w[0], fma(dy, w[1], dz * w[2]))) * rcp_40(d2);
         out[0] = fma(-s, fma(-c, dx, w[0]), out[0]);
         out[1] = fma(-s, fma(-c, dy, w[1]), out[1]);
         out[2] = fma(-s, fma(-c, dz, w[2]), out[2]);
@@ -220,6 +222,101 @@ __global__ void __launch_bounds__(kDiffBlock, TMAX == 0 ? 7 : 1) diff_forward_ke
     }
     a.rstep[i] = rstep;
     a.reason[i] = reason;
+}
+
+// Gradient of the tangent-growth indicator g = log(|J t0| / |t0|) with respect
+// to the initial state, the seed t0 held fixed: thread (i, c) carries particle
+// i's state x, the first-order tangent dx along coordinate c of the initial
+// state, and the growth tangent t as dual numbers (t, dt) with
+// dt = d(J t0)/dx0 [e_c], through the same steps, kick merging and removals as
+// the forward pass.  Then dg/dx0_c = (J t0) . dt / |J t0|^2.
+// a.grad0[6 i + c] <- dg/dx0_c; a.log_growth[i] <- g (from the c = 0 thread).
+template <int NP>
+__global__ void __launch_bounds__(kDiffBlock) diff_growth_kernel(const DiffArgs a, const ParticleConsts pc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (i >= a.n) return;
+    const int S = log_stride(NP);
+    double st[6], dx[6];
+    Dual t[6];
+    for (int k = 0; k < 6; ++k) {
+        st[k] = a.state0[6 * i + k];
+        dx[k] = (k == c) ? 1.0 : 0.0;
+        t[k] = {a.tan0[6 * i + k], 0.0};
+    }
+    double n0 = 0.0;
+    for (int k = 0; k < 6; ++k) n0 = fma(t[k].v, t[k].v, n0);
+    bool removed = false;
+    const bool has_rmax = __double_as_longlong(pc.rmax) != 0;
+    {
+        double tmp[6];
+        for (int k = 0; k < 6; ++k) tmp[k] = st[k];
+        const int hit = kick_state<NP>(tmp, a.log, 0.0, pc.tgm_half, pc.rc2);
+        const double r2 = st[0] * st[0] + st[1] * st[1] + st[2] * st[2];
+        removed = hit != 0 || (has_rmax && lt_nonneg(pc.rmax2, r2));
+    }
+    bool opened = false;
+    for (int64_t k = 0; k < a.nsteps && !removed; ++k) {
+        const double* L0 = a.log + k * S;
+        const double* L1 = L0 + S;
+        if (!opened) {
+            const Dual rd[3] = {{st[0], dx[0]}, {st[1], dx[1]}, {st[2], dx[2]}};
+            kick_jac<NP>(rd, L0, pc.tgm_half, t, t + 3);
+            kick_jac<NP>(st, L0, pc.tgm_half, dx, dx + 3);
+            kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);
+        }
+        double pre[6], pdx[6];
+        for (int q = 0; q < 6; ++q) {
+            pre[q] = st[q];
+            pdx[q] = dx[q];
+        }
+        DriftScalars d;
+        if (!drift_scalars(pc.mu, pc.dt, pre, d)) {
+            removed = true;
+            break;
+        }
+        for (int q = 0; q < 3; ++q) {
+            st[q] = d.f * pre[q] + d.g * pre[3 + q];
+            st[3 + q] = d.fd * pre[q] + d.gd * pre[3 + q];
+        }
+        bool bad = false;
+        for (int q = 0; q < 6; ++q) bad |= nonfinite_bits(st[q]);
+        if (bad) {
+            for (int q = 0; q < 6; ++q) st[q] = pre[q];
+            removed = true;
+            break;
+        }
+        drift_tangent(pc.mu, pre, d, dx);
+        {
+            const DriftScalarsT<Dual> e = drift_lift(pc.mu, pre, pdx, d);
+            Dual pd[6];
+            for (int q = 0; q < 6; ++q) pd[q] = {pre[q], pdx[q]};
+            drift_tangent(pc.mu, pd, e, t);
+        }
+        const bool merge = (k + 1 < a.nsteps) && ((k + 1) % a.K != 0);
+        const double tau = merge ? pc.dt : pc.half_dt;
+        const double(&tgm)[kMaxPlanets] = merge ? pc.tgm_full : pc.tgm_half;
+        const double r2 = st[0] * st[0] + st[1] * st[1] + st[2] * st[2];
+        double nst[6];
+        for (int q = 0; q < 6; ++q) nst[q] = st[q];
+        const int enc = kick_state<NP>(nst, L1, tau, tgm, pc.rc2);
+        if (enc != 0 || (has_rmax && lt_nonneg(pc.rmax2, r2))) {
+            removed = true;
+            break;
+        }
+        const Dual rd[3] = {{st[0], dx[0]}, {st[1], dx[1]}, {st[2], dx[2]}};
+        kick_jac<NP>(rd, L1, tgm, t, t + 3);
+        kick_jac<NP>(st, L1, tgm, dx, dx + 3);
+        for (int q = 0; q < 6; ++q) st[q] = nst[q];
+        opened = merge;
+    }
+    double n1 = 0.0, p1 = 0.0;
+    for (int k = 0; k < 6; ++k) {
+        n1 = fma(t[k].v, t[k].v, n1);
+        p1 = fma(t[k].v, t[k].d, p1);
+    }
+    a.grad0[6 * i + c] = n1 > 0.0 ? p1 / n1 : 0.0;
+    if (c == 0 && a.log_growth) a.log_growth[i] = (n0 > 0.0 && n1 > 0.0) ? 0.5 * log(n1 / n0) : 0.0;
 }
 
 template <int NP>
@@ -343,6 +440,13 @@ static cudaError_t launch_diff_backward(int np, const DiffArgs& a, const Particl
     if (a.n <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)((a.n + kDiffBlock - 1) / kDiffBlock);
     GLISSE_DIFF_SWITCH(diff_backward_kernel)
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_diff_growth(int np, const DiffArgs& a, const ParticleConsts& pc, cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((a.n + kDiffBlock - 1) / kDiffBlock), 6);
+    GLISSE_DIFF_SWITCH(diff_growth_kernel)
     return cudaGetLastError();
 }
 
@@ -536,6 +640,29 @@ extern "C" int glisse_diff_backward(glisse_diff* d, const double* grad_state1, d
     a.grad1 = grad_state1;
     a.grad0 = grad_state0;
     cudaError_t e = launch_diff_backward(d->np, a, d->pc, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GLISSE_E_CUDA;
+    }
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_diff_growth_gradient(glisse_diff* d, const double* state0, const double* tangent0,
+                                           double* grad_state0, double* log_growth, void* stream) {
+    if (!d) return GLISSE_E_INVAL;
+    if (d->n > 0 && (!state0 || !tangent0 || !grad_state0)) return GLISSE_E_INVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DiffArgs a{};
+    a.log = d->d_log;
+    a.n = d->n;
+    a.nsteps = d->nsteps;
+    a.K = d->K;
+    a.state0 = state0;
+    a.tan0 = tangent0;
+    a.grad0 = grad_state0;
+    a.log_growth = log_growth;
+    cudaError_t e = launch_diff_growth(d->np, a, d->pc, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();

@@ -26,9 +26,9 @@ def _mp():
     return pytest.importorskip("mpmath")
 
 
-def analytic_state(mu, a, e, inc, node, peri, M, dps=40):
-    """Cartesian state [6] (float64) of a two-body orbit; hyperbolic orbits take a = |a| and e > 1,
-    with M the hyperbolic mean anomaly e sinh F - F."""
+def analytic_state(mu, a, e, inc, node, peri, M, dps=40, as_mp=False):
+    """Cartesian state [6] (float64, or mpmath numbers with as_mp) of a two-body orbit; hyperbolic
+    orbits take a = |a| and e > 1, with M the hyperbolic mean anomaly e sinh F - F."""
     mp = _mp()
     with mp.workdps(dps):
         mu, a, e, inc, node, peri, M = (mp.mpf(v) for v in (mu, a, e, inc, node, peri, M))
@@ -62,6 +62,8 @@ def analytic_state(mu, a, e, inc, node, peri, M, dps=40):
         p32 = cw * si
         out = [p11 * xo + p12 * yo, p21 * xo + p22 * yo, p31 * xo + p32 * yo,
                p11 * vxo + p12 * vyo, p21 * vxo + p22 * vyo, p31 * vxo + p32 * vyo]
+        if as_mp:
+            return out
         return np.array([float(v) for v in out])
 
 
@@ -72,8 +74,8 @@ def state_to_elements(mu, state, dps=40):
     starts from precisely the input the integrator sees.  Needs inc > 0."""
     mp = _mp()
     with mp.workdps(dps):
-        r = [mp.mpf(float(x)) for x in state[:3]]
-        v = [mp.mpf(float(x)) for x in state[3:6]]
+        r = [x if isinstance(x, mp.mpf) else mp.mpf(float(x)) for x in state[:3]]
+        v = [x if isinstance(x, mp.mpf) else mp.mpf(float(x)) for x in state[3:6]]
         mu = mp.mpf(mu)
 
         def cross(p, q):
@@ -112,6 +114,15 @@ def propagate_exact(mu, state, dt, dps=40):
         a, e, inc, node, peri, M = state_to_elements(mu, state, dps)
         n = mp.sqrt(mp.mpf(mu) / a**3)
         return analytic_state(mu, a, e, inc, node, peri, M + n * mp.mpf(dt), dps)
+
+
+def propagate_exact_mp(mu, state, dt, dps=60):
+    """propagate_exact for a state of mpmath numbers (or doubles), returning mpmath numbers."""
+    mp = _mp()
+    with mp.workdps(dps):
+        a, e, inc, node, peri, M = state_to_elements(mu, state, dps)
+        n = mp.sqrt(mp.mpf(mu) / a**3)
+        return analytic_state(mu, a, e, inc, node, peri, M + n * mp.mpf(dt), dps, as_mp=True)
 
 
 def condition(mu, state, dt):

@@ -2,7 +2,9 @@
 
 Checked against the oracle's complex-step tangent map, central finite
 differences (h = 1e-7 AU), the symplectic structure of the Jacobian, the
-dot-product identity <g, J t> = <J^T g, t> between the two kernels, and the
+dot-product identity <g, J t> = <J^T g, t> between the two kernels, the
+gradient of the tangent-growth indicator against the oracle's difference
+quotients and the GPU's own, and the
 independence of the gradient from the checkpoint interval; the
 torch.autograd.Function is checked against the tangent kernel.
 """
@@ -179,7 +181,7 @@ def test_autograd_function(G):
     got = x.grad.cpu().numpy()
     err = np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)
     assert err.max() < 1e-10, err.max()
-    assert torch.isfinite(growth).all() and growth.requires_grad is False
+    assert torch.isfinite(growth).all() and growth.requires_grad  # differentiable too (tests below)
     dm.close()
 
 
@@ -194,3 +196,118 @@ def test_removed_particles_have_frozen_state_derivatives(G, orc):
     assert rstep[0] == 0 and reason[0] == 3
     np.testing.assert_array_equal(s1[0], s0[0])
     np.testing.assert_array_equal(J[0], np.eye(6))
+
+
+# ---------------------------------------------------------------------------
+# gradient of the tangent-growth indicator (glisse_diff_growth_gradient)
+# ---------------------------------------------------------------------------
+def _seed(s0):
+    r = s0[:, :3] / np.linalg.norm(s0[:, :3], axis=1, keepdims=True)
+    v = s0[:, 3:] / np.linalg.norm(s0[:, 3:], axis=1, keepdims=True)
+    return np.ascontiguousarray(np.hstack([r, v]) / 2**0.5)
+
+
+def test_growth_gradient_matches_oracle(G, orc):
+    """d log(|J t0| / |t0|) / d state0 at fixed t0 on 32 particles over 2000 steps,
+    against the oracle's Richardson-extrapolated difference quotients of its
+    complex-step growth (good to ~1e-8 relative on regular orbits)."""
+    w, pl, s0 = _workload(32)
+    n = 2000
+    t0 = _seed(s0)
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n)
+    grad, growth = dm.growth_gradient(_cuda(s0), _cuda(t0))
+    _, _, g_fwd, rstep, _ = dm.forward(_cuda(s0), _cuda(t0[None]))
+    # the value part of the dual tangent is the forward pass's tangent, bit for bit
+    np.testing.assert_array_equal(growth.cpu().numpy(), g_fwd.cpu().numpy())
+    dm.close()
+    _, log, _ = orc.planet_wh(1.0, pl, w["dt"], n)
+    rc = orc.rcrit(1.0, pl)
+    ref, err, ok = orc.growth_gradient(1.0, pl[:, 0], log, w["dt"], s0, t0, rc, 1000.0)
+    o = orc.run(1.0, pl, s0, w["dt"], n)
+    regular = ok & (o["closest"] >= 25.0) & (o["removal_step"] < 0)
+    got = grad.cpu().numpy()
+    rel = np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)
+    print("growth gradient rel err: regular max", rel[regular].max(), "median", np.median(rel), "regular",
+          int(regular.sum()))
+    assert regular.sum() >= 16
+    assert rel[regular].max() < 1e-6
+
+
+def test_growth_gradient_gives_the_directional_derivative(G):
+    """grad . a against difference quotients of the GPU's own growth along a random a."""
+    w, pl, s0 = _workload(128)
+    n = 1000
+    t0 = _seed(s0)
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n)
+    grad, g0 = dm.growth_gradient(_cuda(s0), _cuda(t0))
+    a = np.random.default_rng(8).normal(size=s0.shape) * [1e-5, 1e-5, 1e-5, 1e-6, 1e-6, 1e-6]
+    d, same = [], None
+    _, _, _, r0, _ = dm.forward(_cuda(s0), _cuda(t0[None]))
+    r0 = r0.cpu().numpy()
+    for hh in (1.0, 0.5):
+        gs = []
+        for sg in (1.0, -1.0):
+            _, _, g, rs, _ = dm.forward(_cuda(s0 + sg * hh * a), _cuda(t0[None]))
+            gs.append(g.cpu().numpy())
+            eq = rs.cpu().numpy() == r0
+            same = eq if same is None else same & eq
+        d.append((gs[0] - gs[1]) / (2 * hh))
+    dm.close()
+    fd = (4 * d[1] - d[0]) / 3
+    pred = (grad.cpu().numpy() * a).sum(axis=1)
+    scale = np.abs(grad.cpu().numpy() * a).sum(axis=1)
+    rel = np.abs(pred - fd) / scale
+    print("directional: max", rel[same].max(), "median", np.median(rel[same]))
+    assert same.sum() > 100
+    assert np.median(rel[same]) < 1e-7 and rel[same].max() < 1e-4
+
+
+def test_autograd_growth_gradient(G):
+    """(s1 . w + growth).sum() through glisse_map() with the default seed (unit
+    vectors along r and v, whose dependence on the state is part of the
+    gradient), against difference quotients of the same loss."""
+    import torch
+
+    w, pl, s0 = _workload(64)
+    n = 1000
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n)
+    wgt = _cuda(np.random.default_rng(9).normal(size=s0.shape))
+    x = _cuda(s0).requires_grad_(True)
+    s1, growth = G.glisse_map().apply(x, dm)
+    assert growth.requires_grad
+    ((s1 * wgt).sum(dim=1) + growth).sum().backward()
+    got = x.grad.cpu().numpy()
+
+    def loss(xx):
+        y, _, g, rs, _ = dm.forward(xx, G._growth_seed(xx).contiguous())
+        return ((y * wgt).sum(dim=1) + g).cpu().numpy(), rs.cpu().numpy()
+
+    a = np.random.default_rng(10).normal(size=s0.shape) * [1e-5, 1e-5, 1e-5, 1e-6, 1e-6, 1e-6]
+    base, r0 = loss(_cuda(s0))
+    d, same = [], np.ones(len(s0), dtype=bool)
+    for hh in (1.0, 0.5):
+        lp, rp = loss(_cuda(s0 + hh * a))
+        lm, rm = loss(_cuda(s0 - hh * a))
+        same &= (rp == r0) & (rm == r0)
+        d.append((lp - lm) / (2 * hh))
+    dm.close()
+    fd = (4 * d[1] - d[0]) / 3
+    pred = (got * a).sum(axis=1)
+    rel = np.abs(pred - fd) / np.abs(got * a).sum(axis=1)
+    print("autograd growth: max", rel[same].max(), "median", np.median(rel[same]))
+    assert same.sum() > 50
+    assert np.median(rel[same]) < 1e-7 and rel[same].max() < 1e-4
+
+
+def test_growth_gradient_of_particle_removed_at_t0(G, orc):
+    w, pl, s0 = _workload(8)
+    rc = orc.rcrit(1.0, pl)
+    s0 = s0.copy()
+    s0[0, :3] = pl[2, 1:4] + [0.3 * rc[2], 0, 0]
+    s0[0, 3:] = pl[2, 4:7]
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], 300)
+    grad, growth = dm.growth_gradient(_cuda(s0), _cuda(_seed(s0)))
+    dm.close()
+    assert growth[0].item() == 0.0
+    np.testing.assert_array_equal(grad[0].cpu().numpy(), np.zeros(6))
+    assert np.isfinite(grad.cpu().numpy()).all() and np.abs(grad[1:].cpu().numpy()).max() > 0
