@@ -301,6 +301,25 @@ int glisse_diff_forward(glisse_diff* d, const double* state0, double* state1, in
  * particle's own map).  Errors: STATE before any forward call, INVAL, CUDA. */
 int glisse_diff_backward(glisse_diff* d, const double* grad_state1, double* grad_state0, void* stream);
 
+/* Reverse pass for the map extended by the tangent of the last forward call's
+ * tangent 0 (the growth seed t_0): one sweep back through the checkpoints gives
+ *   grad_state0   = J^T grad_state1 + grad_growth * dg/dstate0 (t_0 held fixed)
+ *   grad_tangent0 = grad_growth * dg/dt_0 = grad_growth * (J^T (J t_0) / |J t_0|^2 - t_0 / |t_0|^2)
+ * for g = log(|J t_0| / |t_0|) (per particle).  Each kick and drift runs its
+ * adjoint in dual numbers, the state carrying the tangent and the cotangent
+ * (growth part, state part): the second-order term is (dM[t])^T of the step's
+ * Jacobian M, by the symmetry of the map's second derivative.
+ *   grad_state1   : device [n][6] or NULL (zero)
+ *   grad_growth   : device [n] or NULL (zero)
+ *   tangent1      : device [n][6], J t_0 as returned by that forward call
+ *   grad_state0, grad_tangent0 : device [n][6] out
+ * Needs checkpoints (checkpoint_every >= 1) and a forward call with at least one
+ * tangent; the extended recompute takes 184 B per particle per step of one
+ * segment on first use.  Errors: STATE (no such forward call, or tape mode),
+ * INVAL, NOMEM, CUDA. */
+int glisse_diff_backward_growth(glisse_diff* d, const double* grad_state1, const double* grad_growth,
+                                const double* tangent1, double* grad_state0, double* grad_tangent0, void* stream);
+
 /* Gradient of the tangent-growth indicator g = log(|J t_0| / |t_0|) with respect to
  * the initial state, the tangent seed t_0 held fixed (the part through t_0 is
  * J^T (J t_0) / |J t_0|^2 - t_0 / |t_0|^2, which glisse_diff_backward gives).

@@ -48,7 +48,8 @@ EXPORTED = (
     "glisse_partition_device", "glisse_fp64_peak", "glisse_timings", "glisse_partition_device_noalloc",
     "glisse_batch_create", "glisse_batch_advance", "glisse_batch_read", "glisse_batch_status",
     "glisse_batch_timings", "glisse_batch_tune", "glisse_batch_destroy",
-    "glisse_diff_create", "glisse_diff_forward", "glisse_diff_backward", "glisse_diff_growth_gradient",
+    "glisse_diff_create", "glisse_diff_forward", "glisse_diff_backward", "glisse_diff_backward_growth",
+    "glisse_diff_growth_gradient",
     "glisse_diff_destroy",
     "glisse_set_sampling", "glisse_read_elements", "glisse_read_libration", "glisse_selftest_math",
 )
@@ -171,6 +172,8 @@ def load(build_if_missing: bool = False):
     L.glisse_diff_forward.restype = C.c_int
     L.glisse_diff_backward.argtypes = [vp, vp, vp, vp]
     L.glisse_diff_backward.restype = C.c_int
+    L.glisse_diff_backward_growth.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.glisse_diff_backward_growth.restype = C.c_int
     L.glisse_diff_growth_gradient.argtypes = [vp, vp, vp, vp, vp, vp]
     L.glisse_diff_growth_gradient.restype = C.c_int
     L.glisse_diff_destroy.argtypes = [vp]
@@ -519,6 +522,11 @@ def glisse_diff_backward(h, grad_state1, grad_state0, stream=0):
     _check(load().glisse_diff_backward(h, grad_state1, grad_state0, stream), "glisse_diff_backward")
 
 
+def glisse_diff_backward_growth(h, grad_state1, grad_growth, tangent1, grad_state0, grad_tangent0, stream=0):
+    _check(load().glisse_diff_backward_growth(h, grad_state1, grad_growth, tangent1, grad_state0, grad_tangent0,
+                                              stream), "glisse_diff_backward_growth")
+
+
 def glisse_diff_growth_gradient(h, state0, tangent0, grad_state0, log_growth=None, stream=0):
     _check(load().glisse_diff_growth_gradient(h, state0, tangent0, grad_state0, log_growth, stream),
            "glisse_diff_growth_gradient")
@@ -541,6 +549,7 @@ class DiffMap:
         for k, v in opt.items():
             setattr(o, k, v)
         self.n = int(n_particles)
+        self.tape = int(checkpoint_every) == 0
         self.h = glisse_diff_create(star_mass, planets, n_particles, dt, n_steps, checkpoint_every, o)
         self.forward_calls = 0
 
@@ -579,6 +588,23 @@ class DiffMap:
         stream = torch.cuda.current_stream(g.device).cuda_stream
         glisse_diff_backward(self.h, g.data_ptr(), out.data_ptr(), stream)
         return out
+
+    def backward_growth(self, grad_state1, grad_growth, tangent1):
+        """One reverse sweep for the last forward call (which carried tangent 0 = t0):
+        (J^T grad_state1 + grad_growth dg/dstate0, grad_growth dg/dt0) for
+        g = log(|J t0| / |t0|); tangent1 = J t0 from that call [n, 6].  Needs
+        checkpoints (not tape mode).  grad_state1 / grad_growth may be None."""
+        import torch
+
+        t1 = tangent1.contiguous()
+        g1 = None if grad_state1 is None else grad_state1.contiguous()
+        gg = None if grad_growth is None else grad_growth.contiguous()
+        gs0 = torch.empty_like(t1)
+        gt0 = torch.empty_like(t1)
+        stream = torch.cuda.current_stream(t1.device).cuda_stream
+        glisse_diff_backward_growth(self.h, self._ptr(g1), self._ptr(gg), t1.data_ptr(), gs0.data_ptr(),
+                                    gt0.data_ptr(), stream)
+        return gs0, gt0
 
     def growth_gradient(self, state0, tangent0):
         """(d g / d state0 [n, 6] with the seed held fixed, g [n]) for
@@ -626,11 +652,12 @@ def _make_autograd():
         Both outputs are differentiable with respect to state0 (and tangent0).
         log_growth = log(|J t0| / |t0|) for the seed tangent0 [n, 6], by default
         unit vectors along r and v (_growth_seed, whose own dependence on state0
-        is included).  Gradients: J^T from the hand-written adjoint kernel
-        (glisse_diff_backward); the growth's gradient with respect to state0 at
-        fixed seed from the second-order kernel (glisse_diff_growth_gradient),
-        and with respect to the seed from the adjoint, J^T (J t0) / |J t0|^2 -
-        t0 / |t0|^2."""
+        is included).  Gradients: with checkpoints, one reverse sweep of the map
+        extended by its tangent (glisse_diff_backward_growth) gives both parts;
+        without the growth, or in tape mode, J^T from the adjoint kernel
+        (glisse_diff_backward), the growth's gradient at fixed seed from the
+        forward-mode second-order kernel (glisse_diff_growth_gradient), and with
+        respect to the seed J^T (J t0) / |J t0|^2 - t0 / |t0|^2 from the adjoint."""
 
         @staticmethod
         def forward(ctx, state0, dmap, *rest):
@@ -650,9 +677,20 @@ def _make_autograd():
                 raise RuntimeError("DiffMap was run forward again before this backward; use one DiffMap per use")
             state0, seed, tn = ctx.saved_tensors
             g1 = torch.zeros_like(state0) if grad_state1 is None else grad_state1
-            grad_state0 = ctx.dmap.backward(g1)
             grad_seed = None
-            if grad_growth is not None and bool((grad_growth != 0).any()):
+            has_growth = grad_growth is not None and bool((grad_growth != 0).any())
+            if has_growth and not ctx.dmap.tape:
+                # one reverse sweep of the map extended by its tangent
+                grad_state0, grad_seed = ctx.dmap.backward_growth(g1, grad_growth, tn)
+                if ctx.default_seed:
+                    with torch.enable_grad():
+                        s0 = state0.clone().requires_grad_(True)
+                        (gs,) = torch.autograd.grad(_growth_seed(s0)[0], s0, grad_seed)
+                    grad_state0 = grad_state0 + gs
+                    grad_seed = None
+                return (grad_state0, None, grad_seed)[: ctx.n_inputs]
+            grad_state0 = ctx.dmap.backward(g1)
+            if has_growth:
                 gg = grad_growth.unsqueeze(1)
                 H, _ = ctx.dmap.growth_gradient(state0, seed)
                 grad_state0 = grad_state0 + gg * H

@@ -65,6 +65,11 @@ struct DiffArgs {
     double* scratch;        // [K][kScratchRows][n]
     const double* grad1;    // [n][6]
     double* grad0;          // [n][6]
+    // growth indicator of tangent 0 (glisse_diff_backward_growth)
+    double* ckpt_t;         // [ceil(nsteps / K)][6][n] tangent 0 at each checkpoint (written by forward)
+    const double* gradg;    // [n] cotangent of the growth log(|J t0| / |t0|), or null
+    const double* tanN;     // [n][6] J t0 from the forward pass
+    double* gradt0;         // [n][6] out: gradient with respect to t0
 };
 
 // v += tau a(r) for the log step L; returns the lowest planet index whose encounter test fires.
@@ -147,6 +152,10 @@ __global__ void __launch_bounds__(kDiffBlock, TMAX == 0 ? 7 : 1) diff_forward_ke
         if (k % a.K == 0) {
             double* cp = a.ckpt + (k / a.K) * 6 * a.n;
             for (int c = 0; c < 6; ++c) cp[c * a.n + i] = st[c];
+            if (T > 0 && a.ckpt_t) {
+                double* ct = a.ckpt_t + (k / a.K) * 6 * a.n;
+                for (int c = 0; c < 6; ++c) ct[c * a.n + i] = t[0][c];
+            }
         }
         const double* L0 = a.log + k * S;
         const double* L1 = L0 + S;
@@ -394,6 +403,117 @@ __global__ void __launch_bounds__(kDiffBlock, 4) diff_backward_kernel(const Diff
     for (int c = 0; c < 6; ++c) a.grad0[6 * i + c] = l[c];
 }
 
+// Scratch rows of the extended recompute: the kScratchRows of the plain one,
+// then tangent 0 before the drift (6) and its position part after the drift (3).
+constexpr int kScratchRowsG = kScratchRows + 9;
+
+// One reverse sweep of the map extended by its tangent, z = (x, t) with
+// t_{k+1} = M_k(x_k) t_k, for the cotangent (lx, lt) = (grad_state1,
+// grad_growth (J t0) / |J t0|^2) at the end.  Each piece (kick, drift) runs its
+// adjoint in dual numbers: state (x, t), cotangent (lt, lx) -> (M^T lt,
+// (dM[t])^T lt + M^T lx); see drift_adjoint.  Segments are recomputed from the
+// state and tangent checkpoints, as the plain backward pass does.
+// a.grad0 <- lx at t_0 (= J^T grad_state1 + grad_growth dg/dstate0 at fixed t0);
+// a.gradt0 <- lt at t_0 minus grad_growth t0 / |t0|^2 (= dg/dt0 times grad_growth).
+template <int NP>
+__global__ void __launch_bounds__(kDiffBlock, 2) diff_backward_growth_kernel(const DiffArgs a, const ParticleConsts pc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int S = log_stride(NP);
+    const double gg = a.gradg ? a.gradg[i] : 0.0;
+    double nn = 0.0;
+    for (int c = 0; c < 6; ++c) nn = fma(a.tanN[6 * i + c], a.tanN[6 * i + c], nn);
+    const double w = nn > 0.0 ? gg / nn : 0.0;
+    Dual l[6];
+    for (int c = 0; c < 6; ++c) l[c] = {w * a.tanN[6 * i + c], a.grad1 ? a.grad1[6 * i + c] : 0.0};
+    const int64_t rstep = a.rstep[i];
+    const int reason = a.reason[i];
+    const int64_t kend = rstep >= 0 ? rstep : a.nsteps;
+    const bool cut_after_drift = rstep > 0 && reason != GLISSE_REMOVED_KEPLER && reason != GLISSE_REMOVED_NONFINITE;
+    const bool cut_before_drift = rstep > 0 && !cut_after_drift;
+    if (kend > 0) {
+        const int64_t nseg = (kend + a.K - 1) / a.K;
+        for (int64_t cseg = nseg - 1; cseg >= 0; --cseg) {
+            const int64_t k0 = cseg * a.K;
+            const int64_t k1 = min(k0 + (int64_t)a.K, kend);
+            double st[6], t[6];
+            const double* cp = a.ckpt + cseg * 6 * a.n;
+            const double* ct = a.ckpt_t + cseg * 6 * a.n;
+            for (int c = 0; c < 6; ++c) {
+                st[c] = cp[c * a.n + i];
+                t[c] = ct[c * a.n + i];
+            }
+            for (int64_t k = k0; k < k1; ++k) {
+                const double* L0 = a.log + k * S;
+                if (k == k0) {
+                    kick_jac<NP>(st, L0, pc.tgm_half, t, t + 3);
+                    kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);
+                }
+                double* sc = a.scratch + (k - k0) * kScratchRowsG * a.n + i;
+                for (int c = 0; c < 6; ++c) {
+                    sc[c * a.n] = st[c];
+                    sc[(kScratchRows + c) * a.n] = t[c];
+                }
+                if (k == kend - 1 && cut_before_drift) break;
+                DriftScalars d;
+                drift_scalars(pc.mu, pc.dt, st, d);
+                sc[9 * a.n] = d.s;
+                sc[10 * a.n] = d.tau;
+                sc[11 * a.n] = d.G[4];
+                sc[12 * a.n] = d.G[5];
+                sc[13 * a.n] = d.inv_R;
+                double pre[6];
+                for (int c = 0; c < 6; ++c) pre[c] = st[c];
+                for (int c = 0; c < 3; ++c) {
+                    st[c] = d.f * pre[c] + d.g * pre[3 + c];
+                    st[3 + c] = d.fd * pre[c] + d.gd * pre[3 + c];
+                }
+                drift_tangent(pc.mu, pre, d, t);
+                for (int c = 0; c < 3; ++c) {
+                    sc[(6 + c) * a.n] = st[c];
+                    sc[(kScratchRows + 6 + c) * a.n] = t[c];
+                }
+                if (k + 1 < k1) {
+                    kick_jac<NP>(st, a.log + (k + 1) * S, pc.tgm_full, t, t + 3);
+                    kick_state<NP>(st, a.log + (k + 1) * S, pc.dt, pc.tgm_full, pc.rc2);
+                }
+            }
+            for (int64_t k = k1 - 1; k >= k0; --k) {
+                const double* sc = a.scratch + (k - k0) * kScratchRowsG * a.n + i;
+                double pre[6];
+                Dual pd[6], qd[3];
+                for (int c = 0; c < 6; ++c) {
+                    pre[c] = sc[c * a.n];
+                    pd[c] = {pre[c], sc[(kScratchRows + c) * a.n]};
+                }
+                for (int c = 0; c < 3; ++c) qd[c] = {sc[(6 + c) * a.n], sc[(kScratchRows + 6 + c) * a.n]};
+                const bool last = (k == kend - 1);
+                if (!(last && (cut_after_drift || cut_before_drift)))
+                    kick_jac<NP>(qd, a.log + (k + 1) * S, (k + 1 < k1) ? pc.tgm_full : pc.tgm_half, l + 3, l);
+                if (!(last && cut_before_drift)) {
+                    DriftScalars d;
+                    drift_restore(pc.mu, pc.dt, pre, sc[9 * a.n], sc[10 * a.n], d);
+                    drift_finish_stored(pc.mu, d, sc[11 * a.n], sc[12 * a.n], sc[13 * a.n]);
+                    const double tp[6] = {pd[0].d, pd[1].d, pd[2].d, pd[3].d, pd[4].d, pd[5].d};
+                    const DriftScalarsT<Dual> e = drift_lift(pc.mu, pre, tp, d);
+                    drift_adjoint(pc.mu, pd, e, l);
+                }
+                if (k == k0) kick_jac<NP>(pd, a.log + k * S, pc.tgm_half, l + 3, l);
+            }
+        }
+    }
+    double n0 = 0.0, t0[6];
+    for (int c = 0; c < 6; ++c) {
+        t0[c] = a.ckpt_t[c * a.n + i];
+        n0 = fma(t0[c], t0[c], n0);
+    }
+    const double w0 = n0 > 0.0 ? gg / n0 : 0.0;
+    for (int c = 0; c < 6; ++c) {
+        a.grad0[6 * i + c] = l[c].d;
+        a.gradt0[6 * i + c] = fma(-w0, t0[c], l[c].v);
+    }
+}
+
 #define GLISSE_DIFF_SWITCH(KERNEL)                                         \
     switch (np) {                                                          \
         case 0: KERNEL<0><<<grid, kDiffBlock, 0, s>>>(a, pc); break;       \
@@ -443,6 +563,14 @@ static cudaError_t launch_diff_backward(int np, const DiffArgs& a, const Particl
     return cudaGetLastError();
 }
 
+static cudaError_t launch_diff_backward_growth(int np, const DiffArgs& a, const ParticleConsts& pc,
+                                               cudaStream_t s) {
+    if (a.n <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((a.n + kDiffBlock - 1) / kDiffBlock);
+    GLISSE_DIFF_SWITCH(diff_backward_growth_kernel)
+    return cudaGetLastError();
+}
+
 static cudaError_t launch_diff_growth(int np, const DiffArgs& a, const ParticleConsts& pc, cudaStream_t s) {
     if (a.n <= 0) return cudaSuccess;
     const dim3 grid((unsigned)((a.n + kDiffBlock - 1) / kDiffBlock), 6);
@@ -464,14 +592,17 @@ struct glisse_diff {
     double* d_log = nullptr;
     double* d_ckpt = nullptr;
     double* d_scratch = nullptr;
+    double* d_ckpt_t = nullptr;     // tangent 0 at each checkpoint
+    double* d_scratch_g = nullptr;  // extended recompute (glisse_diff_backward_growth), on first use
     int64_t* d_rstep = nullptr;
     int32_t* d_reason = nullptr;
     bool have_forward = false;
+    int32_t last_ntan = 0;
 };
 
 static void diff_free(glisse_diff* d) {
     if (!d) return;
-    void* ptrs[] = {d->d_log, d->d_ckpt, d->d_scratch, d->d_rstep, d->d_reason};
+    void* ptrs[] = {d->d_log, d->d_ckpt, d->d_scratch, d->d_ckpt_t, d->d_scratch_g, d->d_rstep, d->d_reason};
     for (void* p : ptrs) cudaFree(p);
     delete d;
 }
@@ -532,6 +663,7 @@ extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const dou
         const int64_t np1 = std::max<int64_t>(n_particles, 1);
         if (cudaMalloc(&d->d_log, sizeof(double) * (size_t)(n_steps + 1) * S) != cudaSuccess ||
             cudaMalloc(&d->d_ckpt, sizeof(double) * (size_t)nck * 6 * np1) != cudaSuccess ||
+            cudaMalloc(&d->d_ckpt_t, sizeof(double) * (size_t)nck * 6 * np1) != cudaSuccess ||
             cudaMalloc(&d->d_scratch, sizeof(double) * (size_t)d->K * kScratchRows * np1) != cudaSuccess ||
             cudaMalloc(&d->d_rstep, sizeof(int64_t) * np1) != cudaSuccess ||
             cudaMalloc(&d->d_reason, sizeof(int32_t) * np1) != cudaSuccess) {
@@ -608,6 +740,7 @@ extern "C" int glisse_diff_forward(glisse_diff* d, const double* state0, double*
     a.rstep = d->d_rstep;
     a.reason = d->d_reason;
     a.ckpt = d->d_ckpt;
+    a.ckpt_t = d->d_ckpt_t;
     cudaError_t e = launch_diff_forward(d->np, a, d->pc, s);
     if (e == cudaSuccess && removal_step && d->n > 0)
         e = cudaMemcpyAsync(removal_step, d->d_rstep, sizeof(int64_t) * d->n, cudaMemcpyDeviceToDevice, s);
@@ -619,6 +752,7 @@ extern "C" int glisse_diff_forward(glisse_diff* d, const double* state0, double*
         return GLISSE_E_CUDA;
     }
     d->have_forward = true;
+    d->last_ntan = n_tangents;
     return GLISSE_OK;
 }
 
@@ -640,6 +774,45 @@ extern "C" int glisse_diff_backward(glisse_diff* d, const double* grad_state1, d
     a.grad1 = grad_state1;
     a.grad0 = grad_state0;
     cudaError_t e = launch_diff_backward(d->np, a, d->pc, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GLISSE_E_CUDA;
+    }
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_diff_backward_growth(glisse_diff* d, const double* grad_state1, const double* grad_growth,
+                                           const double* tangent1, double* grad_state0, double* grad_tangent0,
+                                           void* stream) {
+    if (!d) return GLISSE_E_INVAL;
+    if (!d->have_forward || d->last_ntan < 1 || d->tape) return GLISSE_E_STATE;
+    if (d->n > 0 && (!tangent1 || !grad_state0 || !grad_tangent0)) return GLISSE_E_INVAL;
+    if (!d->d_scratch_g && d->n > 0) {
+        const size_t bytes = sizeof(double) * (size_t)d->K * kScratchRowsG * (size_t)d->n;
+        if (cudaMalloc(&d->d_scratch_g, bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            d->d_scratch_g = nullptr;
+            return GLISSE_E_NOMEM;
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DiffArgs a{};
+    a.log = d->d_log;
+    a.n = d->n;
+    a.nsteps = d->nsteps;
+    a.K = d->K;
+    a.rstep = d->d_rstep;
+    a.reason = d->d_reason;
+    a.ckpt = d->d_ckpt;
+    a.ckpt_t = d->d_ckpt_t;
+    a.scratch = d->d_scratch_g;
+    a.grad1 = grad_state1;
+    a.gradg = grad_growth;
+    a.tanN = tangent1;
+    a.grad0 = grad_state0;
+    a.gradt0 = grad_tangent0;
+    cudaError_t e = launch_diff_backward_growth(d->np, a, d->pc, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();

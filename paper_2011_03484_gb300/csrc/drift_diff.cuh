@@ -421,47 +421,52 @@ __device__ inline void drift_tangent(double mu, const T st[6], const DriftScalar
 // the G's through s(tau, r0, u, beta) (implicit differentiation) and beta, then
 // r0 = |r|, u = r . v, beta = 2 mu / r0 - v . v.  Every accumulator starts from
 // its first term (an add to 0.0 is not free under IEEE rules).
-__device__ inline void drift_adjoint(double mu, const double st[6], const DriftScalars& d, double l[6]) {
-    const double *r = st, *v = st + 3;
-    const double lf = fma(l[0], r[0], fma(l[1], r[1], l[2] * r[2]));
-    const double lg = fma(l[0], v[0], fma(l[1], v[1], l[2] * v[2]));
-    const double lfd = fma(l[3], r[0], fma(l[4], r[1], l[5] * r[2]));
-    const double lgd = fma(l[3], v[0], fma(l[4], v[1], l[5] * v[2]));
-    double lr[3], lv[3];
+// With T = ad::Dual, the state carrying a tangent t as its derivative and the
+// cotangent (lt, lx) as (value, derivative), the result is (M^T lt,
+// (dM[t])^T lt + M^T lx): one reverse step of the map extended by its tangent
+// (the second derivative of the map is symmetric, so d(M t)/dx^T lt = (dM[t])^T lt).
+template <class T>
+__device__ inline void drift_adjoint(double mu, const T st[6], const DriftScalarsT<T>& d, T l[6]) {
+    const T *r = st, *v = st + 3;
+    const T lf = fma(l[0], r[0], fma(l[1], r[1], l[2] * r[2]));
+    const T lg = fma(l[0], v[0], fma(l[1], v[1], l[2] * v[2]));
+    const T lfd = fma(l[3], r[0], fma(l[4], r[1], l[5] * r[2]));
+    const T lgd = fma(l[3], v[0], fma(l[4], v[1], l[5] * v[2]));
+    T lr[3], lv[3];
     for (int i = 0; i < 3; ++i) {
         lr[i] = fma(d.f, l[i], d.fd * l[3 + i]);
         lv[i] = fma(d.g, l[i], d.gd * l[3 + i]);
     }
     // through f, g, fd, gd
-    const double a = lf * d.inv_r0;
-    const double e = d.fd * lfd;
-    double lG2 = -mu * fma(lgd, d.inv_R, a);
-    const double lG3 = -mu * lg;
-    double lG1 = (-mu * d.irR) * lfd;
-    const double lR = d.inv_R * fma(d.mg2R, lgd, -e);
-    double lr0 = fma(d.mg2r, a, -e * d.inv_r0);
+    const T a = lf * d.inv_r0;
+    const T e = d.fd * lfd;
+    T lG2 = -mu * fma(lgd, d.inv_R, a);
+    const T lG3 = -mu * lg;
+    T lG1 = (-mu * d.irR) * lfd;
+    const T lR = d.inv_R * fma(d.mg2R, lgd, -e);
+    T lr0 = fma(d.mg2r, a, -e * d.inv_r0);
     // through R
     lr0 = fma(d.G[0], lR, lr0);
-    const double lG0 = d.r0 * lR;
-    double lu = d.G[1] * lR;
+    const T lG0 = d.r0 * lR;
+    T lu = d.G[1] * lR;
     lG1 = fma(d.u, lR, lG1);
     lG2 = fma(mu, lR, lG2);
     // through the G's: s and beta
-    const double ls = fma(-d.beta * d.G[1], lG0, fma(d.G[0], lG1, fma(d.G[1], lG2, d.G[2] * lG3)));
-    double lbeta = fma(d.Gb[0], lG0, fma(d.Gb[1], lG1, fma(d.Gb[2], lG2, d.Gb[3] * lG3)));
+    const T ls = fma(-d.beta * d.G[1], lG0, fma(d.G[0], lG1, fma(d.G[1], lG2, d.G[2] * lG3)));
+    T lbeta = fma(d.Gb[0], lG0, fma(d.Gb[1], lG1, fma(d.Gb[2], lG2, d.Gb[3] * lG3)));
     // s(tau, r0, u, beta): ds = (dtau - G1 dr0 - G2 du - Tb dbeta) / R
-    const double Tb = fma(d.r0, d.Gb[1], fma(d.u, d.Gb[2], mu * d.Gb[3]));
-    const double lsR = ls * d.inv_R;
-    const double ltau = lg + lsR;
+    const T Tb = fma(d.r0, d.Gb[1], fma(d.u, d.Gb[2], mu * d.Gb[3]));
+    const T lsR = ls * d.inv_R;
+    const T ltau = lg + lsR;
     lr0 = fma(-d.G[1], lsR, lr0);
     lu = fma(-d.G[2], lsR, lu);
     lbeta = fma(-Tb, lsR, lbeta);
     lbeta = fma(d.dtau_dbeta, ltau, lbeta);
     // beta = 2 mu / r0 - v . v
-    const double tb = 2.0 * lbeta;
+    const T tb = 2.0 * lbeta;
     lr0 = fma(-tb, mu * (d.inv_r0 * d.inv_r0), lr0);
     // u = r . v ; r0 = |r|
-    const double c = lr0 * d.inv_r0;
+    const T c = lr0 * d.inv_r0;
     for (int i = 0; i < 3; ++i) {
         l[i] = fma(lu, v[i], fma(c, r[i], lr[i]));
         l[3 + i] = fma(lu, r[i], fma(-tb, v[i], lv[i]));

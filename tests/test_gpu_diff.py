@@ -311,3 +311,73 @@ def test_growth_gradient_of_particle_removed_at_t0(G, orc):
     assert growth[0].item() == 0.0
     np.testing.assert_array_equal(grad[0].cpu().numpy(), np.zeros(6))
     assert np.isfinite(grad.cpu().numpy()).all() and np.abs(grad[1:].cpu().numpy()).max() > 0
+
+
+def test_reverse_growth_sweep_matches_forward_mode(G):
+    """glisse_diff_backward_growth (one reverse sweep of the map extended by its
+    tangent, dual-number adjoints) against the forward-mode growth gradient plus
+    the plain adjoint: J^T g1 + gg dg/dx0, and gg (J^T (J t0)/|J t0|^2 - t0/|t0|^2)."""
+    import torch
+
+    w, pl, s0 = _workload(256)
+    n = 1500
+    t0 = _seed(s0)
+    rng = np.random.default_rng(11)
+    g1 = _cuda(rng.normal(size=s0.shape))
+    gg = _cuda(rng.normal(size=len(s0)))
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n, 128)
+    _, tan1, _, rstep, _ = dm.forward(_cuda(s0), _cuda(t0[None]))
+    gs_rev, gt_rev = dm.backward_growth(g1, gg, tan1[0])
+    H, _ = dm.growth_gradient(_cuda(s0), _cuda(t0))
+    ref_s = dm.backward(g1) + gg[:, None] * H
+    tn = tan1[0]
+    u = tn / (tn * tn).sum(dim=1, keepdim=True)
+    tt = _cuda(t0)
+    ref_t = dm.backward((gg[:, None] * u).contiguous()) - gg[:, None] * tt / (tt * tt).sum(dim=1, keepdim=True)
+    dm.close()
+    a, b = gs_rev.cpu().numpy(), ref_s.cpu().numpy()
+    rel_s = np.abs(a - b).max(axis=1) / np.abs(b).max(axis=1)
+    c, d = gt_rev.cpu().numpy(), ref_t.cpu().numpy()
+    rel_t = np.abs(c - d).max(axis=1) / np.maximum(np.abs(d).max(axis=1), 1e-300)
+    print("reverse vs forward mode: state median", np.median(rel_s), "max", rel_s.max(), "seed median",
+          np.median(rel_t), "max", rel_t.max(), "removed", int((rstep.cpu().numpy() >= 0).sum()))
+    assert np.median(rel_s) < 1e-11 and np.median(rel_t) < 1e-11
+    assert np.mean(rel_s < 1e-8) > 0.95 and np.mean(rel_t < 1e-8) > 0.95
+
+
+def test_autograd_growth_tape_mode_matches_checkpoints(G):
+    """Tape mode takes the forward-mode route for the growth; the gradient agrees with
+    the checkpointed reverse sweep."""
+    import torch
+
+    w, pl, s0 = _workload(64)
+    n = 800
+    out = []
+    for K in (100, 0):
+        dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n, K)
+        x = _cuda(s0).requires_grad_(True)
+        s1, growth = G.glisse_map().apply(x, dm)
+        (s1.sum(dim=1) + 2.0 * growth).sum().backward()
+        out.append(x.grad.cpu().numpy())
+        dm.close()
+    rel = np.abs(out[0] - out[1]).max(axis=1) / np.abs(out[1]).max(axis=1)
+    assert np.median(rel) < 1e-11 and rel.max() < 1e-7, (np.median(rel), rel.max())
+
+
+def test_reverse_growth_sweep_needs_a_tangent_and_checkpoints(G):
+    import torch
+
+    w, pl, s0 = _workload(8)
+    t = _cuda(_seed(s0))
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], 100, 50)
+    with pytest.raises(RuntimeError):
+        dm.backward_growth(None, None, t)  # no forward call yet
+    dm.forward(_cuda(s0))
+    with pytest.raises(RuntimeError):
+        dm.backward_growth(None, None, t)  # the forward call carried no tangent
+    dm.close()
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], 100, 0)
+    dm.forward(_cuda(s0), t[None])
+    with pytest.raises(RuntimeError):
+        dm.backward_growth(None, None, t)  # tape mode
+    dm.close()
