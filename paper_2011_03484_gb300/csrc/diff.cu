@@ -118,7 +118,7 @@ __device__ __forceinline__ void kick_jac(const T r[3], const double* __restrict_
 // TMAX: compile-time tangent capacity (0, 1 or kMaxTangents) so that the
 // tangent vectors stay in registers; tangents a.ntan..TMAX-1 are zero.
 template <int NP, int TMAX>
-__global__ void __launch_bounds__(kDiffBlock, TMAX == 0 ? 7 : 1) diff_forward_kernel(const DiffArgs a, const ParticleConsts pc) {
+__global__ void __launch_bounds__(kDiffBlock, TMAX == 0 ? 7 : (TMAX == 1 ? 4 : 1)) diff_forward_kernel(const DiffArgs a, const ParticleConsts pc) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const int S = log_stride(NP);
