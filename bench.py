@@ -496,19 +496,25 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    chunk_live, chunk_steps = [], []  # host-side counters, read between chunks (no GPU work)
     with ClockSampler(dev.index or 0) as clocks:
         t_wall0 = time.perf_counter()
         for k in range(args.steps):
             flush_l2()
+            chunk_live.append(G.glisse_status(h)[0])
             starts[k].record(stream)
             G.glisse_advance(h, w.chunk)
             ends[k].record(stream)
+            chunk_steps.append(G.glisse_timings(h)["particle_steps"])
         torch.cuda.synchronize(dev)
         t_wall = time.perf_counter() - t_wall0
     if dist:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
+    # particle-steps/s of each chunk against the fraction of particles live at its start
+    done = [b - a for a, b in zip([0] + chunk_steps[:-1], chunk_steps)]
+    vs_alive = [[round(lv / n, 5), round(ps / (ms * 1e-3), 1)] for lv, ps, ms in zip(chunk_live, done, step_ms)]
     tm = G.glisse_timings(h)
     live_after = G.glisse_status(h)[0]
     G.glisse_destroy(h)
@@ -599,6 +605,8 @@ def main():
                      "probe_frac_of_peak": probe_rate / dfma_peak},
         "stage_ms_per_step": {"particle": tm["particle_ms"] / args.steps, "ephemeris": tm["ephemeris_ms"] / args.steps,
                               "compaction": tm["compact_ms"] / args.steps},
+        "throughput_vs_alive": {"columns": ["fraction live at chunk start", "particle-steps/s of the chunk"],
+                                "chunks": vs_alive},
         "e2e": e2e,
         "cpu_baseline": cpu,
         "gpu_launches": int(launches),

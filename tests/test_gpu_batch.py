@@ -101,18 +101,22 @@ def test_batch_matches_oracle_system_by_system(G, orc):
     assert g["n_live"] == int(g["alive"].sum()) and g["step"] == n
 
 
-def test_batch_equals_single_system_runs(G):
+@pytest.mark.parametrize("chunk", [128, 1024])
+def test_batch_equals_single_system_runs(G, chunk):
     """Each system of a batch evolves as the single-system path evolves it: same removal
     steps, and bit-identical states except on lanes that needed the general Kepler
     solver, whose plain expressions the compiler may contract into FMAs differently
-    in the two kernels (rounding-level differences)."""
+    in the two kernels (rounding-level differences).  The single-system path runs its
+    first chunk in segments (cut at steps 64, 128, 256, 512) that pass the open kick
+    between them; the batch path does not cut, so this also checks that the cuts leave
+    no trace."""
     b = small_batch(n_systems=6, seed=8)
     n = 700
-    g = run_batch(G, b, n, chunk_steps=128)
+    g = run_batch(G, b, n, chunk_steps=chunk)
     po, ao = offsets(b)
     for s in range(len(b["star_mass"])):
         sim = G.Simulation(b["star_mass"][s], b["planets"][po[s]:po[s + 1]], b["particles"][ao[s]:ao[s + 1]],
-                           b["dt"][s], chunk_steps=128)
+                           b["dt"][s], chunk_steps=chunk)
         sim.advance(n)
         r = sim.read()
         sim.close()
