@@ -15,7 +15,7 @@ constexpr int kMaxPlanets = GLISSE_MAX_PLANETS;
 constexpr int kRec = 4;
 __host__ __device__ constexpr int log_stride(int np) { return kRec * (np + 1); }
 // The ephemeris kernel of a context's first chunk publishes its step count this often.
-constexpr int kProgressEvery = 64;
+constexpr int kProgressEvery = 16;
 
 // Planet system constants (written once by the set-up kernel, read by all kernels).
 struct PlanetConsts {
