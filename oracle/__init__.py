@@ -6,6 +6,15 @@ path (the CUDA library and its binding) never imports, links or calls it.
 
 ``build()`` compiles the C file with gcc (no FMA contraction, no fast-math,
 OpenMP over particles) into ``oracle/_build/liboracle.so``.
+
+Every function here is pinned to something other than itself: closed forms,
+exact two-body motion, reversibility, the Jacobi constant, convergence
+against an N-body integration and the paper's statements
+(tests/test_oracle_pins.py, planted mistakes in tests/test_oracle_mutants.py);
+the tangent map (tests/test_oracle_tangent.py); the growth gradient
+(tests/test_oracle_growth.py); the fixed-iteration solve
+(tests/test_oracle_paper_mode.py); elements and the libration test
+(tests/test_oracle_elements.py).
 """
 from __future__ import annotations
 
