@@ -41,7 +41,7 @@ extern "C" {
 #define GLISSE_E_NOMEM -2   /* device or host allocation failed */
 #define GLISSE_E_CUDA -3    /* a CUDA call failed (no device, launch error, ...) */
 #define GLISSE_E_KEPLER -4  /* a planet's Kepler solve did not converge */
-#define GLISSE_E_TIMEOUT -5 /* a bounded wait for device work gave up */
+#define GLISSE_E_TIMEOUT -5 /* a bounded wait gave up (reserved; no current call returns it) */
 #define GLISSE_E_STATE -6   /* call not valid in the context's current state */
 
 /* removal reasons reported by glisse_read() */
@@ -126,10 +126,10 @@ int glisse_create(glisse_ctx** out, double star_mass, const double* planets, int
  * kick(dt/2) (section 2.2), integrating the planets on the GPU one chunk ahead.
  * Returns after the work has finished on the context's stream.  In the first
  * chunk the host launches the particles' segments as the planet kernel (started
- * by glisse_create) reports its progress through host-mapped memory; that wait
- * is bounded (60 s).
- * Errors: INVAL (n_steps < 0), STATE (external ephemeris too short), KEPLER, CUDA,
- * TIMEOUT (the first chunk's planet kernel reported no progress within the bound).
+ * by glisse_create) reports its progress through host-mapped memory; if that
+ * progress does not come within 0.5 s (the GPU busy with other work), the rest
+ * of the chunk waits for the whole planet chunk instead.
+ * Errors: INVAL (n_steps < 0), STATE (external ephemeris too short), KEPLER, CUDA.
  */
 int glisse_advance(glisse_ctx* ctx, int64_t n_steps);
 

@@ -64,7 +64,12 @@ constexpr int kRing = 3;
 // piece on, while the planet kernel keeps its SM.
 constexpr int kMaxPieces = 8;
 constexpr int64_t kFirstPiece = kProgressEvery;
-constexpr double kProgressWaitSeconds = 60.0;
+// A count that has not arrived after this long means the GPU is busy with other
+// work (the planet kernel has not started): the rest of the chunk then waits for
+// the planet kernel's completion event instead.  The longest piece the host polls
+// for is 1024 planet steps, ~10-20 ms of planet kernel.
+constexpr double kProgressPollSeconds = 0.5;
+constexpr int kPollGaveUp = 1;
 constexpr double kG = 4.0 * 3.14159265358979323846 * 3.14159265358979323846;
 }  // namespace
 
@@ -263,7 +268,8 @@ static int ensure_chunk(glisse_ctx* c, int64_t j) {
 }
 
 // Wait until the first chunk's planet kernel has written `steps` steps (host-mapped
-// count); fails if the side stream stops or errs first, or after kProgressWaitSeconds.
+// count).  GLISSE_OK; GLISSE_E_CUDA if the side stream errs or stops short of the
+// count; kPollGaveUp after kProgressPollSeconds without it.
 static int wait_progress(glisse_ctx* c, int64_t steps) {
     const volatile int* p = c->h_prog;
     const auto t0 = std::chrono::steady_clock::now();
@@ -274,7 +280,7 @@ static int wait_progress(glisse_ctx* c, int64_t steps) {
             if (q == cudaSuccess) return *p >= steps ? GLISSE_OK : GLISSE_E_CUDA;
             if (q != cudaErrorNotReady) return GLISSE_E_CUDA;
             const std::chrono::duration<double> el = std::chrono::steady_clock::now() - t0;
-            if (el.count() > kProgressWaitSeconds) return GLISSE_E_TIMEOUT;
+            if (el.count() > kProgressPollSeconds) return kPollGaveUp;
         }
         std::this_thread::yield();
     }
@@ -608,12 +614,20 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
             m = std::min<int64_t>(remaining, c->C - off);
             int k = 0;
             while (j == 0 && c->piece_end[k] <= off && k < c->n_pieces - 1) ++k;
+            int w = kPollGaveUp;
             if (j == 0 && k < c->n_pieces - 1) {
                 // first chunk: wait (on the host) only for the planet steps of this piece
-                if ((rc = wait_progress(c, c->piece_end[k])) != GLISSE_OK) break;
+                w = wait_progress(c, c->piece_end[k]);
+                if (w < 0) {
+                    rc = w;
+                    break;
+                }
+            }
+            if (w == GLISSE_OK) {
                 m = std::min<int64_t>(m, c->piece_end[k] - off);
                 piece_cut = off + m == c->piece_end[k];
             } else {
+                if (j == 0) c->n_pieces = 1;  // no more cuts in this chunk
                 GL_CUDA(cudaStreamWaitEvent(c->s, c->ev_eph[slot], 0));
             }
             log = c->d_log[slot] + (size_t)off * S;
