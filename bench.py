@@ -243,7 +243,7 @@ def batched_arm(args):
     torch.cuda.set_device(dev)
     G._build.build()
     G.load()
-    b = gi.make_batched(seed=4 + 1000 * rank)
+    b = gi.make_batched(seed=4 + 1000 * rank, n_systems=args.batched_systems)
     C = 1024
     stream = torch.cuda.current_stream(dev)
     args_b = (b["star_mass"], b["n_planets"], b["planets"], b["n_particles"], b["particles"], b["dt"])
@@ -417,6 +417,7 @@ def main():
                     help="order live particles by expected Kepler-solve cost at every compaction")
     ap.add_argument("--tune", action="store_true", help="batched: run the autotuner before timing")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--batched-systems", type=int, default=256, help="batched: number of systems (small cases for ncu)")
     ap.add_argument("--diff-particles", type=int, default=0, help="diff: first N particles only (0 = all)")
     ap.add_argument("--diff-steps", type=int, default=0, help="diff: steps (0 = the workload's)")
     ap.add_argument("--ref-particles", type=int, default=8192)
