@@ -254,20 +254,18 @@ def batched_arm(args):
         sim.advance(C_run)
     torch.cuda.synchronize(dev)
     live0 = sim.status()[0]
+    steps0 = sim.steps_done()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     with ClockSampler(dev.index or 0) as clocks:
-        done = 0
         for k in range(args.steps):
             flush.zero_()
-            n_before = sim.status()[0]
             starts[k].record(stream)
             sim.advance(C_run)
             ends[k].record(stream)
-            n_after = sim.status()[0]
-            done += (n_before + n_after) // 2 * C_run
         torch.cuda.synchronize(dev)
+    done = sim.steps_done() - steps0  # exact: each particle counts the steps it advanced
     total_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
     live1 = sim.status()[0]
     sim.close()

@@ -422,6 +422,11 @@ int glisse_batch_read(glisse_batch* b, double* state, uint8_t* alive, int64_t* r
 /* Live particles over all systems and the step index (pointers may be NULL). */
 int glisse_batch_status(glisse_batch* b, int64_t* n_live, int64_t* step);
 
+/* Particle-steps advanced since creation over all systems (each particle counts
+ * the steps it actually advanced; exact in every mode).  Synchronises the batch's
+ * stream.  Errors: INVAL, CUDA. */
+int glisse_batch_steps_done(glisse_batch* b, int64_t* steps);
+
 /* Stage timings of the batch (opts.timing != 0), as glisse_timings. */
 int glisse_batch_timings(glisse_batch* b, glisse_timing* out, int32_t reset);
 

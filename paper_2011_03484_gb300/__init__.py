@@ -47,7 +47,7 @@ EXPORTED = (
     "glisse_read_planets", "glisse_set_ephemeris", "glisse_destroy", "glisse_strerror",
     "glisse_partition_device", "glisse_fp64_peak", "glisse_timings", "glisse_partition_device_noalloc",
     "glisse_batch_create", "glisse_batch_advance", "glisse_batch_read", "glisse_batch_status",
-    "glisse_batch_timings", "glisse_batch_tune", "glisse_batch_destroy",
+    "glisse_batch_timings", "glisse_batch_steps_done", "glisse_batch_tune", "glisse_batch_destroy",
     "glisse_diff_create", "glisse_diff_forward", "glisse_diff_backward", "glisse_diff_backward_growth",
     "glisse_diff_growth_gradient",
     "glisse_diff_destroy",
@@ -161,6 +161,8 @@ def load(build_if_missing: bool = False):
     L.glisse_batch_status.restype = C.c_int
     L.glisse_batch_timings.argtypes = [vp, C.POINTER(glisse_timing), C.c_int32]
     L.glisse_batch_timings.restype = C.c_int
+    L.glisse_batch_steps_done.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.glisse_batch_steps_done.restype = C.c_int
     L.glisse_batch_tune.argtypes = [vp, C.c_int32, i32p, i32p]
     L.glisse_batch_tune.restype = C.c_int
     L.glisse_batch_destroy.argtypes = [vp]
@@ -388,6 +390,12 @@ def glisse_batch_status(h):
     return nl.value, st.value
 
 
+def glisse_batch_steps_done(h) -> int:
+    v = C.c_int64()
+    _check(load().glisse_batch_steps_done(h, C.byref(v)), "glisse_batch_steps_done")
+    return v.value
+
+
 def glisse_batch_timings(h, reset: bool = False) -> dict:
     t = glisse_timing()
     _check(load().glisse_batch_timings(h, C.byref(t), 1 if reset else 0), "glisse_batch_timings")
@@ -427,6 +435,10 @@ class BatchSimulation:
 
     def timings(self, reset=False):
         return glisse_batch_timings(self.h, reset)
+
+    def steps_done(self):
+        """Particle-steps advanced since creation over all systems (exact)."""
+        return glisse_batch_steps_done(self.h)
 
     def tune(self, trial_steps=256):
         return glisse_batch_tune(self.h, trial_steps)

@@ -669,6 +669,15 @@ extern "C" int glisse_batch_status(glisse_batch* b, int64_t* n_live, int64_t* st
     return GLISSE_OK;
 }
 
+extern "C" int glisse_batch_steps_done(glisse_batch* b, int64_t* steps) {
+    if (!b || !steps) return GLISSE_E_INVAL;
+    unsigned long long st = 0;
+    GB_CUDA(cudaStreamSynchronize(b->s));
+    GB_CUDA(cudaMemcpy(&st, b->d_steps, sizeof(st), cudaMemcpyDeviceToHost));
+    *steps = (int64_t)st;
+    return GLISSE_OK;
+}
+
 extern "C" int glisse_batch_timings(glisse_batch* b, glisse_timing* out, int32_t reset) {
     if (!b) return GLISSE_E_INVAL;
     if (!b->timing) return GLISSE_E_STATE;

@@ -183,3 +183,20 @@ def test_full_batched_workload_sampled(G, orc):
     parity.assert_parity(rep)
     assert g["n_live"] == int(g["alive"].sum())
     assert np.all((g["removal_step"] >= 0) == ~g["alive"])
+
+
+def test_steps_done_counts_each_particles_steps(G):
+    """glisse_batch_steps_done (graph-replayed chunks) equals the particle-steps implied
+    by the removal steps: a removed particle advanced removal_step steps, a live one all."""
+    b = small_batch(n_systems=5, seed=12)
+    n = 1300
+    sim = G.BatchSimulation(b["star_mass"], b["n_planets"], b["planets"], b["n_particles"], b["particles"], b["dt"],
+                            chunk_steps=256)
+    sim.advance(700)
+    sim.advance(600)
+    done = sim.steps_done()
+    g = sim.read()
+    sim.close()
+    rs = g["removal_step"]
+    assert done == int(np.where(rs >= 0, rs, n).sum())
+    assert (rs >= 0).sum() > 0
