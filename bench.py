@@ -272,6 +272,8 @@ def batched_arm(args):
     value = done / (total_ms * 1e-3)
     # per-stage device times from a timing-mode copy (direct launches with events)
     simt = G.BatchSimulation(*args_b, chunk_steps=C_run, timing=1, cuda_stream=stream.cuda_stream)
+    if tuned:
+        simt.set_launch(tuned[1], tuned[2])
     for _ in range(args.warmup):
         simt.advance(C_run)
     simt.timings(reset=True)

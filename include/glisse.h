@@ -431,13 +431,25 @@ int glisse_batch_steps_done(glisse_batch* b, int64_t* steps);
 int glisse_batch_timings(glisse_batch* b, glisse_timing* out, int32_t reset);
 
 /*
- * Autotuner: tries chunk lengths {256, 512, 1024, 2048} and particle-kernel
- * block sizes {64, 128, 256} on a scratch copy of the batch (trial_steps steps
- * each, <= 0 for 256) and keeps the fastest in live particle-steps per second.
- * The batch itself does not move.  *chunk_steps and *block_threads (may be
- * NULL) receive the choice.  Errors: INVAL, NOMEM, CUDA.
+ * Autotuner: tries particle-kernel block sizes {64, 128, 256}, then 2 lanes per
+ * particle instead of 1 at the best block size, then chunk lengths {256, 512,
+ * 1024, 2048} (up to the creation chunk), on a scratch copy of the batch
+ * (trial_steps steps each, <= 0 for 256), and keeps the fastest in live
+ * particle-steps per second.  The batch itself does not move.  *chunk_steps,
+ * *block_threads and *threads_per_particle (may be NULL) receive the choice.
+ * Errors: INVAL, NOMEM, CUDA.
  */
-int glisse_batch_tune(glisse_batch* b, int32_t trial_steps, int32_t* chunk_steps, int32_t* block_threads);
+int glisse_batch_tune(glisse_batch* b, int32_t trial_steps, int32_t* chunk_steps, int32_t* block_threads,
+                      int32_t* threads_per_particle);
+
+/*
+ * Set the particle kernel's launch shape directly: block_threads in {32, 64,
+ * ..., 256}, threads_per_particle 1 (one lane per particle) or 2 (a lane pair
+ * per particle, each lane taking half of the planets in the kick: shorter steps
+ * per particle, more FP64 work in all, for batches too small to fill the GPU).
+ * Errors: INVAL.
+ */
+int glisse_batch_set_launch(glisse_batch* b, int32_t block_threads, int32_t threads_per_particle);
 
 /* Release the batch (NULL is ignored). */
 void glisse_batch_destroy(glisse_batch* b);

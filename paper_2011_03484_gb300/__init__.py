@@ -47,7 +47,8 @@ EXPORTED = (
     "glisse_read_planets", "glisse_set_ephemeris", "glisse_destroy", "glisse_strerror",
     "glisse_partition_device", "glisse_fp64_peak", "glisse_timings", "glisse_partition_device_noalloc",
     "glisse_batch_create", "glisse_batch_advance", "glisse_batch_read", "glisse_batch_status",
-    "glisse_batch_timings", "glisse_batch_steps_done", "glisse_batch_tune", "glisse_batch_destroy",
+    "glisse_batch_timings", "glisse_batch_steps_done", "glisse_batch_tune", "glisse_batch_set_launch",
+    "glisse_batch_destroy",
     "glisse_diff_create", "glisse_diff_forward", "glisse_diff_backward", "glisse_diff_backward_growth",
     "glisse_diff_growth_gradient",
     "glisse_diff_destroy",
@@ -163,8 +164,10 @@ def load(build_if_missing: bool = False):
     L.glisse_batch_timings.restype = C.c_int
     L.glisse_batch_steps_done.argtypes = [vp, C.POINTER(C.c_int64)]
     L.glisse_batch_steps_done.restype = C.c_int
-    L.glisse_batch_tune.argtypes = [vp, C.c_int32, i32p, i32p]
+    L.glisse_batch_tune.argtypes = [vp, C.c_int32, i32p, i32p, i32p]
     L.glisse_batch_tune.restype = C.c_int
+    L.glisse_batch_set_launch.argtypes = [vp, C.c_int32, C.c_int32]
+    L.glisse_batch_set_launch.restype = C.c_int
     L.glisse_batch_destroy.argtypes = [vp]
     L.glisse_batch_destroy.restype = None
     L.glisse_diff_create.argtypes = [C.POINTER(vp), C.c_double, dp, C.c_int32, C.c_int64, C.c_double, C.c_int64,
@@ -403,9 +406,14 @@ def glisse_batch_timings(h, reset: bool = False) -> dict:
 
 
 def glisse_batch_tune(h, trial_steps: int = 256):
-    c, t = C.c_int32(), C.c_int32()
-    _check(load().glisse_batch_tune(h, int(trial_steps), C.byref(c), C.byref(t)), "glisse_batch_tune")
-    return c.value, t.value
+    """(chunk steps, block threads, threads per particle) chosen by the autotuner."""
+    c, t, p = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().glisse_batch_tune(h, int(trial_steps), C.byref(c), C.byref(t), C.byref(p)), "glisse_batch_tune")
+    return c.value, t.value, p.value
+
+
+def glisse_batch_set_launch(h, block_threads: int, threads_per_particle: int = 1):
+    _check(load().glisse_batch_set_launch(h, int(block_threads), int(threads_per_particle)), "glisse_batch_set_launch")
 
 
 def glisse_batch_destroy(h):
@@ -442,6 +450,9 @@ class BatchSimulation:
 
     def tune(self, trial_steps=256):
         return glisse_batch_tune(self.h, trial_steps)
+
+    def set_launch(self, block_threads, threads_per_particle=1):
+        glisse_batch_set_launch(self.h, block_threads, threads_per_particle)
 
     def close(self):
         if self.h:

@@ -29,8 +29,8 @@ cudaError_t launch_eph_setup(const double*, int, double, double, int, double, Pl
                              cudaStream_t);
 cudaError_t launch_eph_batch(const PlanetConsts*, int, double*, const double*, int, double*, const int64_t*, int*,
                              cudaStream_t);
-cudaError_t launch_batch_particles(const BatchArgs&, int, int, cudaStream_t);
-cudaError_t batch_particles_occupancy(int, int*);
+cudaError_t launch_batch_particles(const BatchArgs&, int, int, int, cudaStream_t);
+cudaError_t batch_particles_occupancy(int, int, int*);
 cudaError_t launch_export_live(int64_t, const double*, int64_t, const int32_t*, double*, cudaStream_t);
 cudaError_t launch_import(int64_t, const double*, double*, int64_t, int32_t*, cudaStream_t);
 
@@ -226,6 +226,7 @@ struct glisse_batch {
     int C = 1024;
     int threads = 128;
     int blocks = 0;
+    int tpp = 1;  // lanes per particle in the particle kernel (1 or 2)
     int n_sm = 0;
     int64_t n_total = 0, cap = 0, n_live = 0, step = 0;
     std::vector<int> np_host;       // internal system order
@@ -317,11 +318,13 @@ extern "C" void glisse_batch_destroy(glisse_batch* b) {
     cudaSetDevice(prev);
 }
 
-static int set_launch_shape(glisse_batch* b, int threads) {
+static int set_launch_shape(glisse_batch* b, int threads, int tpp) {
+    if (threads < 32 || threads > 256 || threads % 32 || (tpp != 1 && tpp != 2)) return GLISSE_E_INVAL;
     int per_sm = 0;
-    GB_CUDA(batch_particles_occupancy(threads, &per_sm));
+    GB_CUDA(batch_particles_occupancy(threads, tpp, &per_sm));
     if (per_sm < 1) return GLISSE_E_INVAL;
     b->threads = threads;
+    b->tpp = tpp;
     b->blocks = per_sm * b->n_sm;
     return GLISSE_OK;
 }
@@ -355,7 +358,7 @@ static int enqueue_chunk(glisse_batch* b, int m) {
     a.out_step = b->d_out_step;
     a.out_reason = b->d_out_reason;
     a.steps_done = b->d_steps;
-    GB_CUDA(launch_batch_particles(a, b->blocks, b->threads, s));
+    GB_CUDA(launch_batch_particles(a, b->blocks, b->threads, b->tpp, s));
     if (b->timing) GB_CUDA(cudaEventRecord(b->ev[2], s));
     const unsigned tiles = (unsigned)((b->cap + kBTile - 1) / kBTile);
     bpart_count_kernel<<<tiles, kBThreads, 0, s>>>(b->d_alive, b->d_nlive, b->d_counts);
@@ -571,7 +574,7 @@ static int batch_setup(glisse_batch* b, const double* star_mass, const int32_t* 
     batch_tasks_kernel<<<1, 1024, 0, b->s>>>(n, b->d_cnt, b->d_task_sys, b->d_task_start, b->d_task_count,
                                               b->d_n_tasks, b->d_nlive, nullptr, b->d_counter, b->d_clock, 0);
     GB_CUDA(cudaGetLastError());
-    int rc = set_launch_shape(b, 128);
+    int rc = set_launch_shape(b, 128, 1);
     if (rc) return rc;
     rc = refresh_host_counts(b);
     return rc;
@@ -743,7 +746,8 @@ __global__ void batch_counts_from_tasks(const int32_t* __restrict__ task_sys, co
         atomicAdd(reinterpret_cast<unsigned long long*>(cnt + task_sys[t]), (unsigned long long)task_count[t]);
 }
 
-extern "C" int glisse_batch_tune(glisse_batch* b, int32_t trial_steps, int32_t* chunk_steps, int32_t* block_threads) {
+extern "C" int glisse_batch_tune(glisse_batch* b, int32_t trial_steps, int32_t* chunk_steps, int32_t* block_threads,
+                                 int32_t* threads_per_particle) {
     if (!b) return GLISSE_E_INVAL;
     if (trial_steps <= 0) trial_steps = 256;
     Snapshot sn;
@@ -755,16 +759,16 @@ extern "C" int glisse_batch_tune(glisse_batch* b, int32_t trial_steps, int32_t* 
     GB_CUDA(cudaMemsetAsync(sn.cnt, 0, sizeof(int64_t) * b->n_sys, b->s));
     batch_counts_from_tasks<<<2 * b->n_sm, 256, 0, b->s>>>(b->d_task_sys, b->d_task_count, b->d_n_tasks, sn.cnt);
     rc = snap_copy(b, sn, true);
-    const int cur0 = b->cur, C0 = b->C, T0 = b->threads;
+    const int cur0 = b->cur, C0 = b->C, T0 = b->threads, P0 = b->tpp;
     const int64_t step0 = b->step;
     const bool timing0 = b->timing;
     b->timing = false;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = GLISSE_E_CUDA;
     double best = -1.0;
-    int bestC = C0, bestT = T0;
-    auto trial = [&](int C, int T, int64_t steps, double* rate) -> int {
-        int r = set_launch_shape(b, T);
+    int bestC = C0, bestT = T0, bestP = P0;
+    auto trial = [&](int C, int T, int P, int64_t steps, double* rate) -> int {
+        int r = set_launch_shape(b, T, P);
         if (r) return r;
         r = snap_copy(b, sn, false);
         if (r) return r;
@@ -787,14 +791,23 @@ extern "C" int glisse_batch_tune(glisse_batch* b, int32_t trial_steps, int32_t* 
         *rate = (double)(s1 - s0) / (ms * 1e-3);
         return GLISSE_OK;
     };
-    // block shape at the current chunk length, then the chunk length
+    // block size and lanes per particle at the current chunk length, then the chunk length
     const int Ts[3] = {64, 128, 256};
     for (int k = 0; k < 3 && !rc; ++k) {
         double rate = 0;
-        rc = trial(C0, Ts[k], trial_steps, &rate);
+        rc = trial(C0, Ts[k], 1, trial_steps, &rate);
         if (!rc && rate > best) {
             best = rate;
             bestT = Ts[k];
+            bestP = 1;
+        }
+    }
+    if (!rc) {
+        double rate = 0;
+        rc = trial(C0, bestT, 2, trial_steps, &rate);
+        if (!rc && rate > best) {
+            best = rate;
+            bestP = 2;
         }
     }
     best = -1.0;
@@ -805,7 +818,7 @@ extern "C" int glisse_batch_tune(glisse_batch* b, int32_t trial_steps, int32_t* 
             continue;
         }
         double rate = 0;
-        rc = trial(Cs[k], bestT, std::max<int64_t>(2 * Cs[k], trial_steps), &rate);
+        rc = trial(Cs[k], bestT, bestP, std::max<int64_t>(2 * Cs[k], trial_steps), &rate);
         if (!rc && rate > best) {
             best = rate;
             bestC = Cs[k];
@@ -816,7 +829,7 @@ extern "C" int glisse_batch_tune(glisse_batch* b, int32_t trial_steps, int32_t* 
     b->cur = cur0;
     b->step = step0;
     b->timing = timing0;
-    if (!rc) rc = set_launch_shape(b, bestT);
+    if (!rc) rc = set_launch_shape(b, bestT, bestP);
     if (!rc) {
         b->C = bestC;
         drop_graphs(b);
@@ -827,5 +840,13 @@ extern "C" int glisse_batch_tune(glisse_batch* b, int32_t trial_steps, int32_t* 
     snap_free(sn);
     if (chunk_steps) *chunk_steps = b->C;
     if (block_threads) *block_threads = b->threads;
+    if (threads_per_particle) *threads_per_particle = b->tpp;
+    return rc;
+}
+
+extern "C" int glisse_batch_set_launch(glisse_batch* b, int32_t block_threads, int32_t threads_per_particle) {
+    if (!b) return GLISSE_E_INVAL;
+    const int rc = set_launch_shape(b, block_threads, threads_per_particle);
+    if (rc == GLISSE_OK) drop_graphs(b);
     return rc;
 }

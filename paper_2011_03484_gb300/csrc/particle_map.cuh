@@ -73,6 +73,56 @@ __device__ __forceinline__ int kick_test(double x, double y, double z, double& v
     return hit;
 }
 
+// kick_test with the planets split over a lane pair (two lanes per particle,
+// both holding the same state): lane parity p takes planets p, p + 2, ...,
+// each lane sums its partial kick, and the pair adds the two partial sums (the
+// same sum on both lanes: addition commutes) and takes the lower encounter
+// index.  The h0 term is applied by both lanes as in kick_test.
+template <int NP>
+__device__ __forceinline__ int kick_test_pair(double x, double y, double z, double& vx, double& vy, double& vz,
+                                              const double* __restrict__ L, double tau,
+                                              const double (&tgm)[kMaxPlanets], const double (&rc2)[kMaxPlanets]) {
+    const int parity = threadIdx.x & 1;
+    double hx, hy, hz;
+    load_rec(L + kRec * NP, hx, hy, hz);
+    vx = fma(tau, hx, vx);
+    vy = fma(tau, hy, vy);
+    vz = fma(tau, hz, vz);
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    int hit = 0;
+#pragma unroll
+    for (int jj = (NP + 1) / 2 - 1; jj >= 0; --jj) {
+        const int j = 2 * jj + parity;
+        if (j < NP) {
+            double px, py, pz;
+            load_rec(L + kRec * j, px, py, pz);
+            const double dx = x - px, dy = y - py, dz = z - pz;
+            const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            hit = lt_nonneg(d2, rc2[j]) ? (j + 1) : hit;
+            const double s = k_rcube(d2, tgm[j]);
+            ax = fma(-s, dx, ax);
+            ay = fma(-s, dy, ay);
+            az = fma(-s, dz, az);
+        }
+    }
+    vx += ax + __shfl_xor_sync(kFullMask, ax, 1);
+    vy += ay + __shfl_xor_sync(kFullMask, ay, 1);
+    vz += az + __shfl_xor_sync(kFullMask, az, 1);
+    const int other = __shfl_xor_sync(kFullMask, hit, 1);
+    return (hit != 0 && other != 0) ? min(hit, other) : (hit | other);
+}
+
+// The kick of a particle held by TPP lanes (1, or 2: kick_test_pair).
+template <int NP, int TPP>
+__device__ __forceinline__ int kick_lanes(double x, double y, double z, double& vx, double& vy, double& vz,
+                                          const double* __restrict__ L, double tau, const double (&tgm)[kMaxPlanets],
+                                          const double (&rc2)[kMaxPlanets]) {
+    if constexpr (TPP == 2)
+        return kick_test_pair<NP>(x, y, z, vx, vy, vz, L, tau, tgm, rc2);
+    else
+        return kick_test<NP>(x, y, z, vx, vy, vz, L, tau, tgm, rc2);
+}
+
 // Removal test without a kick (used at t_0).
 template <int NP>
 __device__ __forceinline__ int test_only(double x, double y, double z, const double* __restrict__ L,
@@ -98,7 +148,9 @@ __device__ __forceinline__ int test_only(double x, double y, double z, const dou
 // single longer launch would apply there (the next segment then has open_in).
 // A split with open_in / close_out is bit-identical to no split.
 // pc may live in the constant bank (kernel parameter) or in shared memory.
-template <int NP, int MODE = kDriftConverge>
+// TPP = 2: the particle is held by a lane pair (batched kernel), each lane
+// running the same state with half of the planets in the kicks.
+template <int NP, int MODE = kDriftConverge, int TPP = 1>
 __device__ __forceinline__ void advance_lane(const ParticleConsts& pc, const double* __restrict__ L, int64_t step0,
                                              int nsteps, bool test_first, double& x, double& y, double& z, double& vx,
                                              double& vy, double& vz, bool& act, int& reason, int64_t& rstep,
@@ -115,7 +167,20 @@ __device__ __forceinline__ void advance_lane(const ParticleConsts& pc, const dou
             rstep = step0;
         }
     }
-    if (act && !open_in) kick_test<NP>(x, y, z, vx, vy, vz, L, pc.half_dt, pc.tgm_half, pc.rc2);
+    if (!open_in) {
+        if constexpr (TPP == 2) {
+            // the pair kick shuffles across the warp: every lane runs it, active lanes keep it
+            double nvx = vx, nvy = vy, nvz = vz;
+            kick_test_pair<NP>(x, y, z, nvx, nvy, nvz, L, pc.half_dt, pc.tgm_half, pc.rc2);
+            if (act) {
+                vx = nvx;
+                vy = nvy;
+                vz = nvz;
+            }
+        } else if (act) {
+            kick_test<NP>(x, y, z, vx, vy, vz, L, pc.half_dt, pc.tgm_half, pc.rc2);
+        }
+    }
     double r0, mur0;
     radius_of(x, y, z, r0, mur0);
     mur0 *= pc.mu;
@@ -160,9 +225,9 @@ __device__ __forceinline__ void advance_lane(const ParticleConsts& pc, const dou
         double nvx = vx, nvy = vy, nvz = vz;
         int enc;
         if (last)
-            enc = kick_test<NP>(x, y, z, nvx, nvy, nvz, Ln, pc.half_dt, pc.tgm_half, pc.rc2);
+            enc = kick_lanes<NP, TPP>(x, y, z, nvx, nvy, nvz, Ln, pc.half_dt, pc.tgm_half, pc.rc2);
         else
-            enc = kick_test<NP>(x, y, z, nvx, nvy, nvz, Ln, pc.dt, pc.tgm_full, pc.rc2);
+            enc = kick_lanes<NP, TPP>(x, y, z, nvx, nvy, nvz, Ln, pc.dt, pc.tgm_full, pc.rc2);
         hit = enc ? enc : hit;
         if (act) {
             if (hit != 0) {

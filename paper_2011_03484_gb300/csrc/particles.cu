@@ -9,11 +9,16 @@ namespace glisse {
 // the work counter, stages its system's constants in a warp-private slot of
 // shared memory and runs advance_lane with that system's planet count.
 // ---------------------------------------------------------------------------
-template <int NP>
+// TPP = 1: lane k holds particle start + k.  TPP = 2: the lane pair (2k, 2k + 1)
+// holds particle start + k (half of the task's 32 particles per call; `half`
+// picks which), and only its even lane writes results and counts.
+template <int NP, int TPP>
 __device__ __forceinline__ void batch_task(const BatchArgs& a, const ParticleConsts& pc, int s, int64_t start,
-                                           int cnt, int lane, int64_t step0, bool test_first) {
-    const int64_t i = start + lane;
-    const bool in = lane < cnt;
+                                           int cnt, int lane, int64_t step0, bool test_first, int half = 0) {
+    const int slot = TPP == 2 ? 16 * half + (lane >> 1) : lane;
+    const bool owner = TPP == 1 || (lane & 1) == 0;
+    const int64_t i = start + slot;
+    const bool in = slot < cnt;
     const int64_t ld = a.ld;
     double x = 1.0, y = 0.0, z = 0.0, vx = 0.0, vy = 6.283185307179586, vz = 0.0;
     if (in) {
@@ -28,15 +33,17 @@ __device__ __forceinline__ void batch_task(const BatchArgs& a, const ParticleCon
     const bool started = act;
     int reason = 0;
     int64_t rstep = -1;
-    advance_lane<NP>(pc, a.log + a.log_off[s], step0, a.nsteps, test_first, x, y, z, vx, vy, vz, act, reason, rstep);
-    const unsigned live = __reduce_add_sync(kFullMask, act ? 1u : 0u);
+    advance_lane<NP, kDriftConverge, TPP>(pc, a.log + a.log_off[s], step0, a.nsteps, test_first, x, y, z, vx, vy, vz,
+                                          act, reason, rstep);
+    const unsigned live = __reduce_add_sync(kFullMask, (act && owner) ? 1u : 0u);
     if (lane == 0 && live) atomicAdd(reinterpret_cast<unsigned long long*>(a.cnt_new + s), (unsigned long long)live);
     if (a.steps_done) {
-        const unsigned adv = !started ? 0u : (rstep >= 0 ? (unsigned)(rstep - step0) : (unsigned)a.nsteps);
+        const unsigned adv =
+            (!started || !owner) ? 0u : (rstep >= 0 ? (unsigned)(rstep - step0) : (unsigned)a.nsteps);
         const unsigned wsum = __reduce_add_sync(kFullMask, adv);
         if (lane == 0 && wsum) atomicAdd(a.steps_done, (unsigned long long)wsum);
     }
-    if (in) {
+    if (in && owner) {
         a.st[i] = x;
         a.st[ld + i] = y;
         a.st[2 * ld + i] = z;
@@ -51,6 +58,7 @@ __device__ __forceinline__ void batch_task(const BatchArgs& a, const ParticleCon
 
 constexpr int kBatchMaxWarps = 8;  // largest block of the batched kernel: 256 threads
 
+template <int TPP>
 __global__ void __launch_bounds__(32 * kBatchMaxWarps) batch_particle_kernel(const BatchArgs a) {
     __shared__ ParticleConsts s_pc[kBatchMaxWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -73,8 +81,10 @@ __global__ void __launch_bounds__(32 * kBatchMaxWarps) batch_particle_kernel(con
         __syncwarp();
         const ParticleConsts& pc = s_pc[warp];
         switch (a.np_of[s]) {
-#define GLISSE_BCASE(N) \
-    case N: batch_task<N>(a, pc, s, start, cnt, lane, step0, test_first); break;
+#define GLISSE_BCASE(N)                                                          \
+    case N:                                                                      \
+        for (int h = 0; h < TPP; ++h) batch_task<N, TPP>(a, pc, s, start, cnt, lane, step0, test_first, h); \
+        break;
             GLISSE_BCASE(0)
             GLISSE_BCASE(1)
             GLISSE_BCASE(2)
@@ -91,15 +101,23 @@ __global__ void __launch_bounds__(32 * kBatchMaxWarps) batch_particle_kernel(con
     }
 }
 
-// Persistent launch: `blocks` blocks of `threads` threads (a multiple of 32, <= 256).
-cudaError_t launch_batch_particles(const BatchArgs& a, int blocks, int threads, cudaStream_t s) {
+// Persistent launch: `blocks` blocks of `threads` threads (a multiple of 32, <= 256),
+// tpp (1 or 2) lanes per particle.
+cudaError_t launch_batch_particles(const BatchArgs& a, int blocks, int threads, int tpp, cudaStream_t s) {
     if (threads < 32 || threads > 32 * kBatchMaxWarps || threads % 32) return cudaErrorInvalidValue;
-    batch_particle_kernel<<<blocks, threads, 0, s>>>(a);
+    if (tpp == 2)
+        batch_particle_kernel<2><<<blocks, threads, 0, s>>>(a);
+    else if (tpp == 1)
+        batch_particle_kernel<1><<<blocks, threads, 0, s>>>(a);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-cudaError_t batch_particles_occupancy(int threads, int* blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_particle_kernel, threads, 0);
+cudaError_t batch_particles_occupancy(int threads, int tpp, int* blocks_per_sm) {
+    if (tpp == 2)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_particle_kernel<2>, threads, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_particle_kernel<1>, threads, 0);
 }
 
 cudaError_t launch_particle_chunk(int np, const ChunkArgs& a, const ParticleConsts& pc, cudaStream_t s) {

@@ -151,8 +151,8 @@ def test_autotuner_keeps_the_state(G, orc):
     sim = G.BatchSimulation(b["star_mass"], b["n_planets"], b["planets"], b["n_particles"], b["particles"], b["dt"])
     sim.advance(100)
     before = sim.read()
-    c, t = sim.tune(trial_steps=64)
-    assert c in (256, 512, 1024) and t in (64, 128, 256)
+    c, t, p = sim.tune(trial_steps=64)
+    assert c in (256, 512, 1024) and t in (64, 128, 256) and p in (1, 2)
     after = sim.read()
     for k in ("state", "removal_step", "removal_reason"):
         np.testing.assert_array_equal(before[k], after[k])
@@ -200,3 +200,53 @@ def test_steps_done_counts_each_particles_steps(G):
     rs = g["removal_step"]
     assert done == int(np.where(rs >= 0, rs, n).sum())
     assert (rs >= 0).sum() > 0
+
+
+def test_two_lanes_per_particle_match_the_oracle(G, orc):
+    """The lane-pair kernel (threads_per_particle = 2: each lane of the pair takes half of
+    the planets in the kick) against the oracle, system by system."""
+    b = small_batch()
+    n = 1500
+    sim = G.BatchSimulation(b["star_mass"], b["n_planets"], b["planets"], b["n_particles"], b["particles"], b["dt"],
+                            chunk_steps=256)
+    sim.set_launch(128, 2)
+    sim.advance(n)
+    g = sim.read()
+    g["n_live"], g["step"] = sim.status()
+    done = sim.steps_done()
+    sim.close()
+    o, sens, unst, ids, ph = oracle_batch(orc, b, n)
+    rep = parity.compare(sub(g, ids), o, n, sens, unst, ph)
+    print(rep)
+    parity.assert_parity(rep)
+    assert rep["removed"] > 0
+    rs = g["removal_step"]
+    assert done == int(np.where(rs >= 0, rs, n).sum())  # each particle counted once
+
+
+def test_two_lanes_equal_one_lane_up_to_rounding(G):
+    """The pair sums its two partial kicks, so states differ from the one-lane kernel by
+    rounding only; removal steps agree."""
+    b = small_batch(n_systems=5, seed=13)
+    n = 800
+    out = []
+    for tpp in (1, 2):
+        sim = G.BatchSimulation(b["star_mass"], b["n_planets"], b["planets"], b["n_particles"], b["particles"],
+                                b["dt"], chunk_steps=256)
+        sim.set_launch(64, tpp)
+        sim.advance(n)
+        out.append(sim.read())
+        sim.close()
+    assert np.mean(out[0]["removal_step"] == out[1]["removal_step"]) > 0.999
+    both = out[0]["alive"] & out[1]["alive"]
+    e = parity.rel_err(out[0]["state"][both], out[1]["state"][both])
+    assert np.median(e) < 1e-12 and e.max() < parity.state_tol(n), (np.median(e), e.max())
+
+
+def test_set_launch_rejects_bad_shapes(G):
+    b = small_batch(n_systems=2, seed=14)
+    sim = G.BatchSimulation(b["star_mass"], b["n_planets"], b["planets"], b["n_particles"], b["particles"], b["dt"])
+    for bad in ((48, 1), (512, 1), (128, 3), (128, 0)):
+        with pytest.raises(RuntimeError):
+            sim.set_launch(*bad)
+    sim.close()
