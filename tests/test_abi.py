@@ -107,6 +107,36 @@ def test_argument_errors_before_any_cuda_call(G):
     L.glisse_destroy(None)
 
 
+def test_null_handles_are_rejected(G):
+    """Every call that takes a context returns GLISSE_E_INVAL for a NULL one (no CUDA call)."""
+    L = G.load()
+    E = G.GLISSE_E_INVAL
+    calls = [
+        lambda: L.glisse_status(None, None, None, None),
+        lambda: L.glisse_read_planets(None, None, None),
+        lambda: L.glisse_set_ephemeris(None, None, 1),
+        lambda: L.glisse_timings(None, None, 0),
+        lambda: L.glisse_set_sampling(None, None),
+        lambda: L.glisse_read_elements(None, None, None, 0, None),
+        lambda: L.glisse_read_libration(None, None, None, None),
+        lambda: L.glisse_batch_advance(None, 1),
+        lambda: L.glisse_batch_read(None, None, None, None, None),
+        lambda: L.glisse_batch_status(None, None, None),
+        lambda: L.glisse_batch_timings(None, None, 0),
+        lambda: L.glisse_batch_steps_done(None, None),
+        lambda: L.glisse_batch_tune(None, 0, None, None, None),
+        lambda: L.glisse_batch_set_launch(None, 128, 1),
+        lambda: L.glisse_diff_forward(None, None, None, 0, None, None, None, None, None, None),
+        lambda: L.glisse_diff_backward(None, None, None, None),
+        lambda: L.glisse_diff_backward_growth(None, None, None, None, None, None, None),
+        lambda: L.glisse_diff_growth_gradient(None, None, None, None, None, None),
+    ]
+    for k, call in enumerate(calls):
+        assert call() == E, k
+    L.glisse_batch_destroy(None)
+    L.glisse_diff_destroy(None)
+
+
 def test_no_cpu_fallback_without_a_device(G):
     """On a machine without a usable GPU a valid create fails with GLISSE_E_CUDA instead of computing."""
     import torch
