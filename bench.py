@@ -418,6 +418,8 @@ def main():
     ap.add_argument("--tune", action="store_true", help="batched: run the autotuner before timing")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--batched-systems", type=int, default=256, help="batched: number of systems (small cases for ncu)")
+    ap.add_argument("--one-call", action="store_true",
+                    help="single-system: time the whole run as one glisse_advance call of steps x chunk steps")
     ap.add_argument("--diff-particles", type=int, default=0, help="diff: first N particles only (0 = all)")
     ap.add_argument("--diff-steps", type=int, default=0, help="diff: steps (0 = the workload's)")
     ap.add_argument("--ref-particles", type=int, default=8192)
@@ -500,13 +502,24 @@ def main():
     chunk_live, chunk_steps = [], []  # host-side counters, read between chunks (no GPU work)
     with ClockSampler(dev.index or 0) as clocks:
         t_wall0 = time.perf_counter()
-        for k in range(args.steps):
+        if args.one_call:
+            # the whole timed run as one glisse_advance call (the planets may run ahead of
+            # the particles up to its last chunk)
             flush_l2()
             chunk_live.append(G.glisse_status(h)[0])
-            starts[k].record(stream)
-            G.glisse_advance(h, w.chunk)
-            ends[k].record(stream)
+            starts[0].record(stream)
+            G.glisse_advance(h, w.chunk * args.steps)
+            ends[0].record(stream)
             chunk_steps.append(G.glisse_timings(h)["particle_steps"])
+            starts, ends = starts[:1], ends[:1]
+        else:
+            for k in range(args.steps):
+                flush_l2()
+                chunk_live.append(G.glisse_status(h)[0])
+                starts[k].record(stream)
+                G.glisse_advance(h, w.chunk)
+                ends[k].record(stream)
+                chunk_steps.append(G.glisse_timings(h)["particle_steps"])
         torch.cuda.synchronize(dev)
         t_wall = time.perf_counter() - t_wall0
     if dist:

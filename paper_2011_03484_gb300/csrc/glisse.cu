@@ -15,7 +15,8 @@
 // run.  The ephemeris kernel for chunk j+1 runs on a high-priority side stream
 // while the particle kernel works through chunk j on the main stream (section
 // 2.2 computes the planets one chunk ahead in the same way); events order the
-// ring-buffer reuse.  The first chunk has nothing to overlap with: its planet
+// ring-buffer reuse.  Within a long glisse_advance call the ring grows and the
+// planets run further ahead, up to the call's last chunk (grow_ring, kEphQueue).  The first chunk has nothing to overlap with: its planet
 // kernel starts in glisse_create, publishes its progress to host-mapped memory,
 // and the particles of that chunk run in segments launched as their planet steps
 // appear (the segments pass the open kick between them, so the cuts leave no
@@ -56,7 +57,16 @@ cudaError_t launch_import(int64_t, const double*, double*, int64_t, int32_t*, cu
 using namespace glisse;
 
 namespace {
-constexpr int kRing = 3;
+// Planet-log ring: 3 slots (the chunk the particles run, the next one, one
+// spare), more for a long glisse_advance call, so that the planets can run ahead
+// of the particles up to the call's last step (see grow_ring), within this budget.
+constexpr size_t kRingMin = 3;
+constexpr size_t kRingBudgetBytes = size_t(512) << 20;
+// Planet kernels enqueued beyond the last one known complete: enough that the
+// side stream never runs dry between two particle chunks (it completes ~3
+// chunks of planets per chunk of 131072 particles), few enough that the launch
+// queue never fills (a full queue blocks the host in the launch call).
+constexpr int64_t kEphQueue = 8;
 // The first chunk of planets has no particle work to overlap with.  Its kernel
 // publishes its step count to host-mapped memory, and the particles of that chunk
 // run in segments ending at steps kFirstPiece * 2^k, each launched once the host
@@ -72,6 +82,18 @@ constexpr double kProgressPollSeconds = 0.5;
 constexpr int kPollGaveUp = 1;
 constexpr double kG = 4.0 * 3.14159265358979323846 * 3.14159265358979323846;
 }  // namespace
+
+// One chunk of planets on the device: log [(C+1)][4 (N_p+1)] (positions + h0)
+// and history [(C+1)][N_p][6] (synchronised heliocentric states).
+struct Slot {
+    double* log = nullptr;
+    double* hist = nullptr;
+    int64_t chunk = -1;           // chunk held (-1: none)
+    cudaEvent_t ev_eph = nullptr;  // planet kernel done (side stream)
+    cudaEvent_t ev_use = nullptr;  // particles done with it (main stream)
+    cudaEvent_t te0 = nullptr, te1 = nullptr;  // timing mode
+    bool used = false, pending = false;
+};
 
 struct glisse_ctx {
     int device = 0;
@@ -89,13 +111,10 @@ struct glisse_ctx {
     double* d_jac = nullptr;
     int* d_status = nullptr;
     int* h_status = nullptr;
-    double* d_log[kRing] = {};
-    double* d_hist[kRing] = {};
-    int64_t chunk_of[kRing] = {-1, -1, -1};
-    cudaEvent_t ev_eph[kRing] = {};
-    cudaEvent_t ev_use[kRing] = {};
-    bool used[kRing] = {};
+    std::vector<Slot> ring;  // planet-log slots; chunk j lives in ring[j % ring.size()]
+    cudaEvent_t ev_order = nullptr;
     int64_t next_chunk = 0;
+    int64_t eph_done = 0;  // chunks whose planet kernel is known complete (host view)
     int64_t piece_end[kMaxPieces] = {};     // first chunk: step each particle segment may end at
     int n_pieces = 0;
     int* h_prog = nullptr;                  // host-mapped: planet steps of the first chunk written
@@ -120,8 +139,7 @@ struct glisse_ctx {
     // optional per-launch timing
     bool timing = false;
     cudaEvent_t tp0 = nullptr, tp1 = nullptr, tc0 = nullptr, tc1 = nullptr;
-    cudaEvent_t te0[kRing] = {}, te1[kRing] = {};
-    bool eph_pending[kRing] = {};
+
     glisse_timing acc{};
     // element sampling / libration test (glisse_set_sampling)
     bool samp_on = false;
@@ -187,19 +205,39 @@ extern "C" const char* glisse_strerror(int code) {
     }
 }
 
+static void free_slot(Slot& sl) {
+    cudaFree(sl.log);
+    cudaFree(sl.hist);
+    for (cudaEvent_t e : {sl.ev_eph, sl.ev_use, sl.te0, sl.te1})
+        if (e) cudaEventDestroy(e);
+    sl = Slot{};
+}
+
+static size_t slot_bytes(const glisse_ctx* c) {
+    return sizeof(double) * (size_t)(c->C + 1) * (size_t)(log_stride(c->np) + 6 * std::max(c->np, 1));
+}
+
+// Buffers and events of an empty slot; false (nothing left allocated) on failure.
+static bool alloc_slot(const glisse_ctx* c, Slot& sl) {
+    const int S = log_stride(c->np);
+    bool ok = cudaMalloc(&sl.log, sizeof(double) * (size_t)(c->C + 1) * S) == cudaSuccess &&
+              cudaMalloc(&sl.hist, sizeof(double) * (size_t)(c->C + 1) * 6 * std::max(c->np, 1)) == cudaSuccess &&
+              cudaEventCreateWithFlags(&sl.ev_eph, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&sl.ev_use, cudaEventDisableTiming) == cudaSuccess;
+    if (ok && c->timing) ok = cudaEventCreate(&sl.te0) == cudaSuccess && cudaEventCreate(&sl.te1) == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();
+        free_slot(sl);
+    }
+    return ok;
+}
+
 static void ctx_free(glisse_ctx* c) {
     if (!c) return;
     if (c->s) cudaStreamSynchronize(c->s);
     if (c->se) cudaStreamSynchronize(c->se);
-    for (int r = 0; r < kRing; ++r) {
-        cudaFree(c->d_log[r]);
-        cudaFree(c->d_hist[r]);
-        if (c->ev_eph[r]) cudaEventDestroy(c->ev_eph[r]);
-        if (c->ev_use[r]) cudaEventDestroy(c->ev_use[r]);
-        if (c->te0[r]) cudaEventDestroy(c->te0[r]);
-        if (c->te1[r]) cudaEventDestroy(c->te1[r]);
-    }
-    for (cudaEvent_t e : {c->tp0, c->tp1, c->tc0, c->tc1})
+    for (Slot& sl : c->ring) free_slot(sl);
+    for (cudaEvent_t e : {c->tp0, c->tp1, c->tc0, c->tc1, c->ev_order})
         if (e) cudaEventDestroy(e);
     if (c->h_prog) cudaFreeHost(c->h_prog);
     for (int b = 0; b < 2; ++b) {
@@ -242,9 +280,9 @@ extern "C" void glisse_destroy(glisse_ctx* c) {
 // Enqueue the ephemeris for chunk j (and every earlier chunk not yet enqueued).
 static int ensure_chunk(glisse_ctx* c, int64_t j) {
     while (c->next_chunk <= j) {
-        const int slot = (int)(c->next_chunk % kRing);
-        if (c->used[slot]) GL_CUDA(cudaStreamWaitEvent(c->se, c->ev_use[slot], 0));
-        if (c->timing) GL_CUDA(cudaEventRecord(c->te0[slot], c->se));
+        Slot& sl = c->ring[(size_t)(c->next_chunk % (int64_t)c->ring.size())];
+        if (sl.used) GL_CUDA(cudaStreamWaitEvent(c->se, sl.ev_use, 0));
+        if (c->timing) GL_CUDA(cudaEventRecord(sl.te0, c->se));
         int* prog = nullptr;
         if (c->next_chunk == 0) {
             c->n_pieces = 0;
@@ -253,17 +291,56 @@ static int ensure_chunk(glisse_ctx* c, int64_t j) {
                     c->n_pieces == kMaxPieces - 1 ? c->C : std::min<int64_t>(c->C, kFirstPiece << c->n_pieces);
             prog = c->d_prog;
         }
-        GL_CUDA(launch_eph_chunk(c->d_pc, c->d_jac, c->dt, c->C, c->d_log[slot], c->d_hist[slot], c->d_status, c->se,
-                                 prog));
+        GL_CUDA(launch_eph_chunk(c->d_pc, c->d_jac, c->dt, c->C, sl.log, sl.hist, c->d_status, c->se, prog));
         if (c->timing) {
-            GL_CUDA(cudaEventRecord(c->te1[slot], c->se));
-            c->eph_pending[slot] = true;
+            GL_CUDA(cudaEventRecord(sl.te1, c->se));
+            sl.pending = true;
         }
-        GL_CUDA(cudaEventRecord(c->ev_eph[slot], c->se));
-        c->chunk_of[slot] = c->next_chunk;
-        c->used[slot] = false;
+        GL_CUDA(cudaEventRecord(sl.ev_eph, c->se));
+        sl.chunk = c->next_chunk;
+        sl.used = false;
         ++c->next_chunk;
     }
+    return GLISSE_OK;
+}
+
+// Give the ring at least `want` slots (capped by kRingBudgetBytes), so that a long
+// glisse_advance call can enqueue the planets of all its chunks at once: the
+// planet kernel then runs ahead while the particles are the slower stage and
+// has the log ready when they become the faster one (few live particles).
+// Between calls nothing of the main stream is in flight; the side stream is
+// drained, and slots holding chunks move (pointers and events) to the position
+// of their chunk in the larger ring.  An allocation failure keeps the ring as
+// it is (the lookahead is an optimisation).
+static int grow_ring(glisse_ctx* c, size_t want) {
+    const size_t cap = std::max(kRingMin, kRingBudgetBytes / std::max<size_t>(slot_bytes(c), 1));
+    want = std::min(want, cap);
+    const size_t R = c->ring.size();
+    if (want <= R) return GLISSE_OK;
+    std::vector<Slot> fresh(want - R);
+    for (size_t k = 0; k < fresh.size(); ++k) {
+        if (!alloc_slot(c, fresh[k])) {
+            for (Slot& f : fresh) free_slot(f);
+            return GLISSE_OK;
+        }
+    }
+    GL_CUDA(cudaStreamSynchronize(c->se));
+    std::vector<Slot> next(want);
+    std::vector<Slot> spare;
+    for (Slot& old : c->ring) {
+        if (old.chunk >= 0 && next[(size_t)(old.chunk % (int64_t)want)].log == nullptr)
+            next[(size_t)(old.chunk % (int64_t)want)] = old;
+        else
+            spare.push_back(old);
+    }
+    for (Slot& f : fresh) spare.push_back(f);
+    for (Slot& n : next) {
+        if (n.log) continue;
+        n = spare.back();
+        spare.pop_back();
+        n.chunk = -1;
+    }
+    c->ring.swap(next);
     return GLISSE_OK;
 }
 
@@ -304,18 +381,10 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles) 
     int lo = 0, hi = 0;
     GL_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     GL_CUDA(cudaStreamCreateWithPriority(&c->se, cudaStreamNonBlocking, hi));
-    for (int r = 0; r < kRing; ++r) {
-        GL_CUDA(cudaEventCreateWithFlags(&c->ev_eph[r], cudaEventDisableTiming));
-        GL_CUDA(cudaEventCreateWithFlags(&c->ev_use[r], cudaEventDisableTiming));
-    }
     GL_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&c->h_prog), sizeof(int), cudaHostAllocMapped));
     *c->h_prog = 0;
     GL_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->d_prog), c->h_prog, 0));
     if (c->timing) {
-        for (int r = 0; r < kRing; ++r) {
-            GL_CUDA(cudaEventCreate(&c->te0[r]));
-            GL_CUDA(cudaEventCreate(&c->te1[r]));
-        }
         GL_CUDA(cudaEventCreate(&c->tp0));
         GL_CUDA(cudaEventCreate(&c->tp1));
         GL_CUDA(cudaEventCreate(&c->tc0));
@@ -331,10 +400,9 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles) 
     GL_ALLOC(c->d_pc, sizeof(PlanetConsts));
     GL_ALLOC(c->d_jac, sizeof(double) * 6 * std::max(np, 1));
     GL_ALLOC(c->d_status, sizeof(int));
-    for (int r = 0; r < kRing; ++r) {
-        GL_ALLOC(c->d_log[r], sizeof(double) * (size_t)(c->C + 1) * S);
-        GL_ALLOC(c->d_hist[r], sizeof(double) * (size_t)(c->C + 1) * 6 * std::max(np, 1));
-    }
+    c->ring.resize(kRingMin);
+    for (Slot& sl : c->ring)
+        if (!alloc_slot(c, sl)) return GLISSE_E_NOMEM;
     const int64_t cap = std::max<int64_t>(c->n_total, 1);
     c->cap = cap;
     for (int b = 0; b < 2; ++b) {
@@ -402,8 +470,9 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles) 
     GL_CUDA(cudaMemsetAsync(c->d_out_reason, 0, sizeof(int32_t) * (size_t)cap, c->s));
     c->n_live = c->n_total;
     // the first two planet chunks
-    GL_CUDA(cudaEventRecord(c->ev_use[0], c->s));  // order the side stream after the set-up
-    GL_CUDA(cudaStreamWaitEvent(c->se, c->ev_use[0], 0));
+    GL_CUDA(cudaEventCreateWithFlags(&c->ev_order, cudaEventDisableTiming));
+    GL_CUDA(cudaEventRecord(c->ev_order, c->s));  // order the side stream after the set-up
+    GL_CUDA(cudaStreamWaitEvent(c->se, c->ev_order, 0));
     int rc = ensure_chunk(c, 1);
     if (rc) return rc;
     GL_CUDA(cudaStreamSynchronize(c->s));
@@ -594,10 +663,13 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
     if (c->o.sort_mode == GLISSE_SORT_COST && !c->tested_first && c->n_live > 0 && (rc = compact(c)) != GLISSE_OK)
         return rc;
     bool open = false;  // the live velocities hold an opening half kick (between pieces)
+    // the planets may run ahead of the particles up to the call's last chunk (+1)
+    const int64_t j_last = c->external ? 0 : (c->step + n_steps - 1) / c->C;
+    if (!c->external && (rc = grow_ring(c, (size_t)(j_last - c->step / c->C + kRingMin))) != GLISSE_OK) return rc;
     while (remaining > 0 && rc == GLISSE_OK) {
         const double* log = nullptr;
         int64_t m = 0;
-        int slot = -1;
+        Slot* sl = nullptr;
         bool piece_cut = false;
         if (c->external) {
             m = std::min<int64_t>(remaining, c->C);
@@ -605,9 +677,13 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
         } else {
             const int64_t j = c->step / c->C;
             const int64_t off = c->step - j * c->C;
-            if ((rc = ensure_chunk(c, j + 1)) != GLISSE_OK) break;
-            slot = (int)(j % kRing);
-            if (c->chunk_of[slot] != j) {
+            while (c->eph_done < c->next_chunk &&
+                   cudaEventQuery(c->ring[(size_t)(c->eph_done % (int64_t)c->ring.size())].ev_eph) == cudaSuccess)
+                ++c->eph_done;
+            const int64_t ahead = std::min({j + (int64_t)c->ring.size() - 1, j_last + 1, c->eph_done + kEphQueue});
+            if ((rc = ensure_chunk(c, std::max<int64_t>(ahead, j + 1))) != GLISSE_OK) break;
+            sl = &c->ring[(size_t)(j % (int64_t)c->ring.size())];
+            if (sl->chunk != j) {
                 rc = GLISSE_E_STATE;
                 break;
             }
@@ -628,9 +704,9 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
                 piece_cut = off + m == c->piece_end[k];
             } else {
                 if (j == 0) c->n_pieces = 1;  // no more cuts in this chunk
-                GL_CUDA(cudaStreamWaitEvent(c->s, c->ev_eph[slot], 0));
+                GL_CUDA(cudaStreamWaitEvent(c->s, sl->ev_eph, 0));
             }
-            log = c->d_log[slot] + (size_t)off * S;
+            log = sl->log + (size_t)off * S;
             if (c->samp_on) {
                 // end the segment at the next sample step
                 const int64_t next = (c->step / c->samp.every + 1) * c->samp.every;
@@ -674,25 +750,25 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
                 c->acc.particle_steps = (int64_t)*c->h_steps;
             }
         }
-        if (c->timing && slot >= 0 && c->eph_pending[slot]) {
+        if (c->timing && sl && sl->pending) {
             // the main stream has waited for this chunk's ephemeris: its events are complete
-            GL_CUDA(cudaEventSynchronize(c->te1[slot]));
+            GL_CUDA(cudaEventSynchronize(sl->te1));
             float ms = 0.f;
-            GL_CUDA(cudaEventElapsedTime(&ms, c->te0[slot], c->te1[slot]));
+            GL_CUDA(cudaEventElapsedTime(&ms, sl->te0, sl->te1));
             c->acc.ephemeris_ms += ms;
             ++c->acc.ephemeris_launches;
-            c->eph_pending[slot] = false;
+            sl->pending = false;
         }
         c->tested_first = true;
-        if (c->samp_on && slot >= 0 && (c->step + m) % c->samp.every == 0) {
+        if (c->samp_on && sl && (c->step + m) % c->samp.every == 0) {
             // sample the particles live at step + m, with the planets of that step
             const int64_t off = c->step - (c->step / c->C) * c->C;
-            if ((rc = take_sample(c, c->d_hist[slot] + (size_t)(off + m) * 6 * c->np, c->step + m)) != GLISSE_OK)
+            if ((rc = take_sample(c, sl->hist + (size_t)(off + m) * 6 * c->np, c->step + m)) != GLISSE_OK)
                 break;
         }
-        if (slot >= 0) {
-            GL_CUDA(cudaEventRecord(c->ev_use[slot], c->s));
-            c->used[slot] = true;
+        if (sl) {
+            GL_CUDA(cudaEventRecord(sl->ev_use, c->s));
+            sl->used = true;
         }
         c->step += m;
         remaining -= m;
@@ -750,11 +826,11 @@ extern "C" int glisse_read_planets(glisse_ctx* c, double* planets, double* t) {
     const int64_t off = c->step - j * c->C;
     int rc = ensure_chunk(c, j);
     if (rc) return rc;
-    const int slot = (int)(j % kRing);
-    if (c->chunk_of[slot] != j) return GLISSE_E_STATE;
+    const Slot& sl = c->ring[(size_t)(j % (int64_t)c->ring.size())];
+    if (sl.chunk != j) return GLISSE_E_STATE;
     GL_CUDA(cudaStreamSynchronize(c->se));
     double buf[6 * GLISSE_MAX_PLANETS];
-    GL_CUDA(cudaMemcpy(buf, c->d_hist[slot] + (size_t)off * 6 * c->np, sizeof(double) * 6 * c->np,
+    GL_CUDA(cudaMemcpy(buf, sl.hist + (size_t)off * 6 * c->np, sizeof(double) * 6 * c->np,
                        cudaMemcpyDeviceToHost));
     for (int p = 0; p < c->np; ++p) {
         planets[7 * p] = c->hpc.m[p];
