@@ -98,6 +98,22 @@ def test_first_chunk_pieces_are_exact(G):
         np.testing.assert_array_equal(g["removal_step"], ref["removal_step"])
 
 
+def test_long_call_equals_chunk_sized_calls(G):
+    """A long glisse_advance call grows the planet ring and lets the planets run ahead of
+    the particles; its segments are the same as those of chunk-sized calls, so the
+    results are bit-identical (a mid-run growth, 192 then 2808 steps, included; the
+    call boundaries fall on chunk boundaries, where every run closes its segment)."""
+    w = gi.make("tiny", n=1024)
+    n, C = 3000, 64
+    one = run_gpu(G, w, n, chunk_steps=C)
+    many = run_gpu(G, w, n, splits=[C] * (n // C) + [n % C], chunk_steps=C)
+    grown = run_gpu(G, w, n, splits=[192, 2808], chunk_steps=C)
+    for g in (many, grown):
+        for k in ("state", "removal_step", "removal_reason", "planets"):
+            np.testing.assert_array_equal(g[k], one[k], err_msg=k)
+    assert (one["removal_step"] >= 0).sum() > 0
+
+
 # ---------------------------------------------------------------------------
 # the tiny workload, whole set, 10^4 steps
 # ---------------------------------------------------------------------------
