@@ -128,7 +128,10 @@ int glisse_create(glisse_ctx** out, double star_mass, const double* planets, int
  * chunk the host launches the particles' segments as the planet kernel (started
  * by glisse_create) reports its progress through host-mapped memory; if that
  * progress does not come within 0.5 s (the GPU busy with other work), the rest
- * of the chunk waits for the whole planet chunk instead.
+ * of the chunk waits for the whole planet chunk instead.  A call longer than a
+ * few chunks lets the planets run ahead of the particles up to its last chunk:
+ * the planet-log buffers then grow (once, kept until glisse_destroy) to up to
+ * 512 MB, (C + 1) x (4 (N_p + 1) + 6 N_p) doubles per chunk held.
  * Errors: INVAL (n_steps < 0), STATE (external ephemeris too short), KEPLER, CUDA.
  */
 int glisse_advance(glisse_ctx* ctx, int64_t n_steps);
