@@ -93,6 +93,7 @@ struct Slot {
     cudaEvent_t ev_use = nullptr;  // particles done with it (main stream)
     cudaEvent_t te0 = nullptr, te1 = nullptr;  // timing mode
     bool used = false, pending = false;
+    bool in_arena = false;  // buffers carved from the context's arena (not freed one by one)
 };
 
 struct glisse_ctx {
@@ -117,6 +118,8 @@ struct glisse_ctx {
     int64_t eph_done = 0;  // chunks whose planet kernel is known complete (host view)
     int64_t piece_end[kMaxPieces] = {};     // first chunk: step each particle segment may end at
     int n_pieces = 0;
+    void* d_arena = nullptr;                // the fixed-size device buffers, in one allocation
+    void* h_block = nullptr;                // the pinned host words below, in one mapped allocation
     int* h_prog = nullptr;                  // host-mapped: planet steps of the first chunk written
     int* d_prog = nullptr;
     double* d_st[2] = {};
@@ -206,8 +209,10 @@ extern "C" const char* glisse_strerror(int code) {
 }
 
 static void free_slot(Slot& sl) {
-    cudaFree(sl.log);
-    cudaFree(sl.hist);
+    if (!sl.in_arena) {
+        cudaFree(sl.log);
+        cudaFree(sl.hist);
+    }
     for (cudaEvent_t e : {sl.ev_eph, sl.ev_use, sl.te0, sl.te1})
         if (e) cudaEventDestroy(e);
     sl = Slot{};
@@ -217,12 +222,14 @@ static size_t slot_bytes(const glisse_ctx* c) {
     return sizeof(double) * (size_t)(c->C + 1) * (size_t)(log_stride(c->np) + 6 * std::max(c->np, 1));
 }
 
-// Buffers and events of an empty slot; false (nothing left allocated) on failure.
+// Buffers (unless the slot already has arena buffers) and events of an empty
+// slot; false (nothing of its own left allocated) on failure.
 static bool alloc_slot(const glisse_ctx* c, Slot& sl) {
     const int S = log_stride(c->np);
-    bool ok = cudaMalloc(&sl.log, sizeof(double) * (size_t)(c->C + 1) * S) == cudaSuccess &&
-              cudaMalloc(&sl.hist, sizeof(double) * (size_t)(c->C + 1) * 6 * std::max(c->np, 1)) == cudaSuccess &&
-              cudaEventCreateWithFlags(&sl.ev_eph, cudaEventDisableTiming) == cudaSuccess &&
+    bool ok = sl.in_arena ||
+              (cudaMalloc(&sl.log, sizeof(double) * (size_t)(c->C + 1) * S) == cudaSuccess &&
+               cudaMalloc(&sl.hist, sizeof(double) * (size_t)(c->C + 1) * 6 * std::max(c->np, 1)) == cudaSuccess);
+    ok = ok && cudaEventCreateWithFlags(&sl.ev_eph, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&sl.ev_use, cudaEventDisableTiming) == cudaSuccess;
     if (ok && c->timing) ok = cudaEventCreate(&sl.te0) == cudaSuccess && cudaEventCreate(&sl.te1) == cudaSuccess;
     if (!ok) {
@@ -239,30 +246,13 @@ static void ctx_free(glisse_ctx* c) {
     for (Slot& sl : c->ring) free_slot(sl);
     for (cudaEvent_t e : {c->tp0, c->tp1, c->tc0, c->tc1, c->ev_order})
         if (e) cudaEventDestroy(e);
-    if (c->h_prog) cudaFreeHost(c->h_prog);
-    for (int b = 0; b < 2; ++b) {
-        cudaFree(c->d_st[b]);
-        cudaFree(c->d_id[b]);
-    }
-    cudaFree(c->d_key);
+    if (c->h_block) cudaFreeHost(c->h_block);
+    cudaFree(c->d_arena);
     cudaFree(c->d_elem);
     cudaFree(c->d_near0);
     cudaFree(c->d_near180);
     cudaFree(c->d_count);
-    cudaFree(c->d_pc);
-    cudaFree(c->d_jac);
-    cudaFree(c->d_status);
-    cudaFree(c->d_alive);
-    cudaFree(c->d_out_state);
-    cudaFree(c->d_out_step);
-    cudaFree(c->d_out_reason);
-    cudaFree(c->d_counts);
-    cudaFree(c->d_nlive);
     cudaFree(c->d_ext_log);
-    cudaFree(c->d_steps);
-    if (c->h_steps) cudaFreeHost(c->h_steps);
-    if (c->h_status) cudaFreeHost(c->h_status);
-    if (c->h_nlive) cudaFreeHost(c->h_nlive);
     if (c->se) cudaStreamDestroy(c->se);
     if (c->own_s && c->s) cudaStreamDestroy(c->s);
     delete c;
@@ -381,45 +371,82 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles) 
     int lo = 0, hi = 0;
     GL_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     GL_CUDA(cudaStreamCreateWithPriority(&c->se, cudaStreamNonBlocking, hi));
-    GL_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&c->h_prog), sizeof(int), cudaHostAllocMapped));
-    *c->h_prog = 0;
+    // pinned host words: progress count (mapped), status, live count, step counter
+    GL_CUDA(cudaHostAlloc(&c->h_block, 64, cudaHostAllocMapped));
+    std::memset(c->h_block, 0, 64);
+    char* hb = static_cast<char*>(c->h_block);
+    c->h_prog = reinterpret_cast<int*>(hb);
+    c->h_status = reinterpret_cast<int*>(hb + 8);
+    c->h_nlive = reinterpret_cast<int64_t*>(hb + 16);
+    c->h_steps = reinterpret_cast<unsigned long long*>(hb + 24);
     GL_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->d_prog), c->h_prog, 0));
     if (c->timing) {
         GL_CUDA(cudaEventCreate(&c->tp0));
         GL_CUDA(cudaEventCreate(&c->tp1));
         GL_CUDA(cudaEventCreate(&c->tc0));
         GL_CUDA(cudaEventCreate(&c->tc1));
-        GL_ALLOC(c->d_steps, sizeof(unsigned long long));
-        GL_CUDA(cudaMemset(c->d_steps, 0, sizeof(unsigned long long)));
-        GL_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&c->h_steps), sizeof(unsigned long long),
-                              cudaHostAllocDefault));
     }
-    GL_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&c->h_status), sizeof(int), cudaHostAllocDefault));
-    GL_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&c->h_nlive), sizeof(int64_t), cudaHostAllocDefault));
     const int S = log_stride(np);
-    GL_ALLOC(c->d_pc, sizeof(PlanetConsts));
-    GL_ALLOC(c->d_jac, sizeof(double) * 6 * std::max(np, 1));
-    GL_ALLOC(c->d_status, sizeof(int));
-    c->ring.resize(kRingMin);
-    for (Slot& sl : c->ring)
-        if (!alloc_slot(c, sl)) return GLISSE_E_NOMEM;
     const int64_t cap = std::max<int64_t>(c->n_total, 1);
     c->cap = cap;
-    for (int b = 0; b < 2; ++b) {
-        GL_ALLOC(c->d_st[b], sizeof(double) * 6 * (size_t)cap);
-        GL_ALLOC(c->d_id[b], sizeof(int32_t) * (size_t)cap);
+    // the fixed-size device buffers in one allocation, each at a 256-byte boundary
+    // (one cudaMalloc and one cudaFree per context instead of ~20 of each)
+    c->ring.resize(kRingMin);
+    double* d_in = nullptr;  // planets [np][7] for the set-up kernel
+    {
+        size_t off = 0;
+        auto take = [&off](size_t bytes) {
+            const size_t o = off;
+            off += (std::max<size_t>(bytes, 16) + 255) & ~size_t(255);
+            return o;
+        };
+        const size_t o_pc = take(sizeof(PlanetConsts)), o_jac = take(sizeof(double) * 6 * std::max(np, 1)),
+                     o_status = take(sizeof(int)), o_in = take(sizeof(double) * 7 * std::max(np, 1));
+        size_t o_log[kRingMin], o_hist[kRingMin];
+        for (size_t r = 0; r < kRingMin; ++r) {
+            o_log[r] = take(sizeof(double) * (size_t)(c->C + 1) * S);
+            o_hist[r] = take(sizeof(double) * (size_t)(c->C + 1) * 6 * std::max(np, 1));
+        }
+        size_t o_st[2], o_id[2];
+        for (int b = 0; b < 2; ++b) {
+            o_st[b] = take(sizeof(double) * 6 * (size_t)cap);
+            o_id[b] = take(sizeof(int32_t) * (size_t)cap);
+        }
+        const size_t o_alive = take((size_t)cap), o_key = c->o.sort_mode == GLISSE_SORT_COST ? take((size_t)cap) : 0,
+                     o_out_state = take(sizeof(double) * 6 * (size_t)cap), o_out_step = take(sizeof(int64_t) * (size_t)cap),
+                     o_out_reason = take(sizeof(int32_t) * (size_t)cap),
+                     o_counts = take(sizeof(int64_t) * (size_t)compact_scratch_entries(cap)),
+                     o_nlive = take(sizeof(int64_t)), o_steps = take(sizeof(unsigned long long));
+        GL_ALLOC(c->d_arena, off);
+        char* base = static_cast<char*>(c->d_arena);
+        c->d_pc = reinterpret_cast<PlanetConsts*>(base + o_pc);
+        c->d_jac = reinterpret_cast<double*>(base + o_jac);
+        c->d_status = reinterpret_cast<int*>(base + o_status);
+        d_in = reinterpret_cast<double*>(base + o_in);
+        for (size_t r = 0; r < kRingMin; ++r) {
+            c->ring[r].log = reinterpret_cast<double*>(base + o_log[r]);
+            c->ring[r].hist = reinterpret_cast<double*>(base + o_hist[r]);
+            c->ring[r].in_arena = true;
+        }
+        for (int b = 0; b < 2; ++b) {
+            c->d_st[b] = reinterpret_cast<double*>(base + o_st[b]);
+            c->d_id[b] = reinterpret_cast<int32_t*>(base + o_id[b]);
+        }
+        c->d_alive = reinterpret_cast<uint8_t*>(base + o_alive);
+        if (c->o.sort_mode == GLISSE_SORT_COST) c->d_key = reinterpret_cast<uint8_t*>(base + o_key);
+        c->d_out_state = reinterpret_cast<double*>(base + o_out_state);
+        c->d_out_step = reinterpret_cast<int64_t*>(base + o_out_step);
+        c->d_out_reason = reinterpret_cast<int32_t*>(base + o_out_reason);
+        c->d_counts = reinterpret_cast<int64_t*>(base + o_counts);
+        c->d_nlive = reinterpret_cast<int64_t*>(base + o_nlive);
+        // the exact particle-step counter exists in timing mode only (the kernel skips a null one)
+        c->d_steps = c->timing ? reinterpret_cast<unsigned long long*>(base + o_steps) : nullptr;
     }
-    GL_ALLOC(c->d_alive, (size_t)cap);
-    if (c->o.sort_mode == GLISSE_SORT_COST) GL_ALLOC(c->d_key, (size_t)cap);
-    GL_ALLOC(c->d_out_state, sizeof(double) * 6 * (size_t)cap);
-    GL_ALLOC(c->d_out_step, sizeof(int64_t) * (size_t)cap);
-    GL_ALLOC(c->d_out_reason, sizeof(int32_t) * (size_t)cap);
-    GL_ALLOC(c->d_counts, sizeof(int64_t) * (size_t)compact_scratch_entries(cap));
-    GL_ALLOC(c->d_nlive, sizeof(int64_t));
+    for (Slot& sl : c->ring)
+        if (!alloc_slot(c, sl)) return GLISSE_E_NOMEM;
+    if (c->timing) GL_CUDA(cudaMemsetAsync(c->d_steps, 0, sizeof(unsigned long long), c->s));
 
     // planets -> device, set-up kernel (Jacobi state, constants, encounter radii)
-    double* d_in = nullptr;
-    GL_ALLOC(d_in, sizeof(double) * 7 * std::max(np, 1));
     cudaError_t e = cudaSuccess;
     if (np > 0) e = cudaMemcpyAsync(d_in, planets, sizeof(double) * 7 * np, cudaMemcpyHostToDevice, c->s);
     if (e == cudaSuccess)
@@ -429,7 +456,6 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles) 
         e = cudaMemcpyAsync(&c->hpc, c->d_pc, sizeof(PlanetConsts), cudaMemcpyDeviceToHost, c->s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
-    cudaFree(d_in);
     if (e != cudaSuccess) return GLISSE_E_CUDA;
     if (*c->h_status != 0) return *c->h_status;
 
