@@ -381,3 +381,26 @@ def test_reverse_growth_sweep_needs_a_tangent_and_checkpoints(G):
     with pytest.raises(RuntimeError):
         dm.backward_growth(None, None, t)  # tape mode
     dm.close()
+
+
+@pytest.mark.parametrize("K", [256, 0])
+def test_forward_pass_reproduces_the_map(G, orc, K):
+    """The differentiable forward pass (its own drift arithmetic: one Halley step from the
+    FP32 root, the G-functions from two series and their recurrence; half kicks at the
+    checkpoint boundaries) meets the plain map's parity criteria against the oracle:
+    256 particles over 10^4 steps, with checkpoints and in tape mode."""
+    import parity
+
+    w, pl, s0 = _workload(256)
+    n = 10_000
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n, K)
+    s1, _, _, rstep, reason = dm.forward(_cuda(s0))
+    dm.close()
+    rs = rstep.cpu().numpy()
+    g = {"state": s1.cpu().numpy(), "alive": rs < 0, "removal_step": rs, "removal_reason": reason.cpu().numpy()}
+    base = orc.run(1.0, pl, s0, w["dt"], n)
+    runs = [orc.run(1.0, pl, p, w["dt"], n) for p in parity.perturbed_inputs(s0)]
+    sens, unstable = parity.sensitivity(base, runs)
+    rep = parity.compare(g, base, n, sens, unstable)
+    print(rep)
+    parity.assert_parity(rep)
