@@ -164,15 +164,17 @@ __device__ __forceinline__ void planet_accel(const PlanetConsts& pc, bool on, in
 __device__ __forceinline__ void emit_step(int k, int np, int S, int lane, bool on, double m_over_eta, const double r[3],
                                           const double w[3], const double h0[3], double* __restrict__ log,
                                           double* __restrict__ hist) {
-    double vh[3];
-    jac_to_helio(w, m_over_eta, lane, np, vh);
     double* L = log + (size_t)k * S;
     if (on) {
         L[kRec * lane + 0] = r[0];
         L[kRec * lane + 1] = r[1];
         L[kRec * lane + 2] = r[2];
         L[kRec * lane + 3] = 0.0;
-        if (hist) {
+    }
+    if (hist) {  // the same pointer on every lane: the warp takes this branch together
+        double vh[3];
+        jac_to_helio(w, m_over_eta, lane, np, vh);
+        if (on) {
             double* H = hist + (size_t)k * 6 * np;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
