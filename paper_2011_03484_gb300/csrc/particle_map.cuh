@@ -10,7 +10,14 @@
 // closing half kick of step k and the opening half kick of step k+1 use the
 // same planet positions, so they are applied as one kick of dt; the segment's
 // first and last kicks are half kicks so that the stored state is the
-// synchronised one.
+// synchronised one.  The exception is the cuts of a context's first chunk
+// (launched as the planets of that chunk appear): a segment may end with the
+// full kick and leave the state open, and the next one then skips its opening
+// half kick (open_in / close_out), so that those cuts leave no trace.
+//
+// The batched kernel may hold one particle in a lane pair (TPP = 2): both
+// lanes run the same state and drift, each takes half of the planets in the
+// kick, and the pair adds its two partial kicks (kick_test_pair).
 //
 // A removed particle keeps the state it had after the drift and before the
 // closing kick, gets removal_step = k+1 and the reason (planet 1..N_p, lowest
