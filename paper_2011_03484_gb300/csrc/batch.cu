@@ -5,7 +5,8 @@
 // decreasing planet count (the costliest tasks are handed out first, which
 // keeps the persistent kernel's tail short).  One chunk is:
 //   1. eph_batch_kernel      planet chunk of every system (block = system)
-//   2. batch_particle_kernel persistent; warps take 32-particle tasks
+//   2. batch_particle_kernel persistent; warps take 32-particle tasks, one lane
+//                            (or, chosen by the autotuner, a lane pair) per particle
 //   3. stable partition      count / scan / scatter, sizes read on the device
 //   4. flags + task rebuild  per-system live counts -> offsets -> task table,
 //                            clock advanced

@@ -3,7 +3,7 @@
 //
 // The map of one step is K(t_{k+1}, dt/2) o D(dt) o K(t_k, dt/2) with
 //   kick  K(tau): v += tau a(r),  a(r) = h0 - sum_j G m_j d_j / |d_j|^3, d_j = r - r_j
-//   drift D(dt):  the two-body flow (kepler.cuh), derivatives in drift_tangent / drift_adjoint.
+//   drift D(dt):  the two-body flow, derivatives in drift_tangent / drift_adjoint (drift_diff.cuh).
 // The kick's Jacobian is dv'/dr = tau A(r) with the symmetric tidal matrix
 //   tau A w = -sum_j s_j (w - 3 d_j (d_j . w) / |d_j|^2),  s_j = tau G m_j / |d_j|^3,
 // so the tangent adds tau A dr to dv and the adjoint adds tau A lv to lr.
@@ -27,6 +27,14 @@
 // particles over 10^4 steps, which HBM holds).
 // A removed particle's output is its frozen state; its derivatives are those
 // of that frozen state (the steps after removal contribute nothing).
+//
+// Tangent growth g = log(|J t0| / |t0|): its gradient with respect to the
+// initial state needs the second derivative of the map contracted with t0.
+// diff_backward_growth_kernel gets it in one reverse sweep of the map extended
+// by its tangent (checkpoints of the state and of t), running each kick's and
+// drift's adjoint in dual numbers (state (x, t), cotangent (lt, lx));
+// diff_growth_kernel gets the part at fixed t0 in forward mode, one thread per
+// particle and state coordinate (used in tape mode, and as a cross-check).
 #include <cuda_runtime.h>
 
 #include <algorithm>
