@@ -14,7 +14,10 @@ against an N-body integration and the paper's statements
 the tangent map (tests/test_oracle_tangent.py); the growth gradient
 (tests/test_oracle_growth.py); the fixed-iteration solve
 (tests/test_oracle_paper_mode.py); elements and the libration test
-(tests/test_oracle_elements.py).
+(tests/test_oracle_elements.py); the integrated map, elements and libration
+test together against the resonance locations, the 3:1 resonance and the
+solver range that the paper prints (tests/golden/paper_values.txt,
+tests/test_oracle_golden.py).
 """
 from __future__ import annotations
 

@@ -10,14 +10,30 @@ the mathematics directly.
   tolerance (a library integrator used as one step of the reference).
 * ``jacobi_constant``: the Jacobi integral of the circular restricted
   three-body problem in the rotating barycentric frame.
+* ``paper_values``: the numbers the paper prints (``tests/golden/paper_values.txt``,
+  each section with the passage it comes from).
 """
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 
 G = 4.0 * math.pi * math.pi
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def paper_values(section: str) -> dict:
+    """One section of ``golden/paper_values.txt`` as a dict of strings."""
+    import configparser
+
+    cp = configparser.ConfigParser(inline_comment_prefixes=("#",))
+    with open(os.path.join(GOLDEN, "paper_values.txt")) as fh:
+        cp.read_file(fh)
+    return dict(cp[section])
 
 
 def _mp():

@@ -27,17 +27,21 @@ def _random_states(n, a_range, e_range, seed):
 
 
 def test_five_iterations_reach_the_papers_convergence(orc):
-    """e < 0.8, 20 < a < 70 AU, dt = 120 days: five iterations converge within 1e-14."""
-    st = _random_states(3000, (20.0, 70.0), (0.0, 0.8), 1)
-    dt = 120.0 / 365.25
+    """The paper's printed claim (tests/golden/paper_values.txt): e < 0.8, 20 < a < 70 AU,
+    steps up to 120 days: five iterations converge within 1e-14."""
+    v = pins.paper_values("kepler_fixed_iterations")
+    iters, tol = int(v["iterations"]), float(v["tolerance"])
+    assert tol == orc.PAPER_KEPLER_TOL
+    st = _random_states(3000, (float(v["a_min"]), float(v["a_max"])), (0.0, float(v["e_max"])), 1)
+    dt = float(v["dt_max_days"]) / 365.25
     worst = 0.0
     for p in range(len(st)):
         s = st[p]
         for _ in range(2):
-            s, rc, ldx = orc.kepler_drift_fixed(MU, s, dt, 5)
+            s, rc, ldx = orc.kepler_drift_fixed(MU, s, dt, iters)
             assert rc == 0, (p, ldx)
             worst = max(worst, ldx)
-    assert worst <= orc.PAPER_KEPLER_TOL, worst
+    assert worst <= tol, worst
     # fewer iterations do not: the criterion is live on this range
     fails = sum(orc.kepler_drift_fixed(MU, st[p], dt, 2)[1] != 0 for p in range(len(st)))
     assert fails > len(st) // 2
