@@ -213,9 +213,9 @@ int glisse_partition_device(int64_t n, int64_t ld, const uint8_t* alive, const d
 
 /*
  * Same stable partition as glisse_partition_device, for callers that must not
- * allocate device memory (for example while a CUDA graph is being captured,
- * under a framework or pool allocator that owns all device memory, or in a
- * loop that cannot afford an allocation's synchronisation or its failure).
+ * allocate device memory (for example under a framework or pool allocator that
+ * owns all device memory, with a memory budget fixed at start-up, or in a loop
+ * that cannot afford an allocation's synchronisation or its failure).
  * The paper has no counterpart; this is a property of this library only.
  *   - Allocates nothing: no cudaMalloc / cudaFree or allocating library call.
  *     Its scratch is a fixed array of GLISSE_PARTITION_NOALLOC_MAX / 2048
@@ -224,7 +224,7 @@ int glisse_partition_device(int64_t n, int64_t ld, const uint8_t* alive, const d
  *   - n above GLISSE_PARTITION_NOALLOC_MAX returns GLISSE_E_INVAL.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
- *     outside any stream capture.
+ *     before any stream capture.
  *   - All calls on a device share the one array (its contents are left over
  *     from the previous call and are never assumed to be zero).  Calls whose
  *     GPU work overlaps -- e.g. from two host threads on two streams -- race on

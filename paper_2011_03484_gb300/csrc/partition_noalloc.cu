@@ -1,10 +1,11 @@
 // partition_noalloc.cu -- stable partition with no memory allocation.
 //
 // glisse_partition_device allocates its scratch (one int64 per 2048-slot tile)
-// with cudaMalloc on every call.  Some callers cannot allow that: code running
-// while a CUDA graph is being captured, allocators or frameworks that own all
-// device memory and forbid other allocations, real-time loops where an
-// allocation's implicit synchronisation or failure is not acceptable.  This
+// with cudaMalloc on every call.  Some callers cannot allow that: programs
+// whose device memory is all handed out by a framework or pool allocator that
+// forbids allocations behind its back, programs that reserve a fixed memory
+// budget at start-up, and loops where an allocation's implicit synchronisation
+// or its failure part-way through a run is not acceptable.  This
 // entry point runs the same three kernels but takes its scratch from a
 // fixed-size array that lives in the library's device image: it is created
 // when the library's module is loaded on a device and stays allocated there

@@ -1,7 +1,7 @@
 """glisse_partition_device_noalloc: the partition for callers that cannot allocate.
 
-Callers that run under CUDA graph capture, or inside a framework or pool
-allocator that owns all device memory, cannot let a library call cudaMalloc.
+Callers whose device memory is all owned by a framework or pool allocator, or
+that fix their memory budget at start-up, cannot let a library call cudaMalloc.
 This entry point takes its scratch from a fixed array in the library's device
 image instead.  The test calls it through the C ABI and checks, on two calls
 in a row with different data, that its output equals the allocating entry
