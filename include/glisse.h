@@ -188,6 +188,41 @@ typedef struct {
  * Errors: STATE when the context was created without opts.timing. */
 int glisse_timings(glisse_ctx* ctx, glisse_timing* out, int32_t reset);
 
+/*
+ * Checkpoint and resume.  The paper continues runs from their output states
+ * (sections 4.2.2 and 4.3.2: the librating particles integrated for another
+ * 1 Myr from the states a 4 Gyr run left).  A checkpoint holds everything the
+ * map needs to go on exactly as the context would have: the star, dt and the
+ * map options, the planet constants
+ * (masses, encounter radii fixed at create), the planets' Jacobi state at the
+ * start of the current planet chunk (the chunk is recomputed on resume, bit
+ * for bit), the step counter, and the particle arrays as laid out on the device
+ * (so warps keep their members), with every removed particle's frozen state,
+ * step and reason.  A context resumed from it and advanced gives results
+ * identical to the original context advanced by the same calls.
+ *
+ * glisse_checkpoint_size: *bytes receives the size of a checkpoint of ctx now.
+ * glisse_checkpoint: write it to the caller's host buffer `buf` of `bytes`
+ *   bytes (at least the size above).  Synchronises the context's streams.
+ * glisse_resume: create a context from a checkpoint (host buffer, not kept).
+ *   opts may be NULL; only its cuda_stream and timing fields are used (every
+ *   option that shapes the map comes from the checkpoint).  Runs on the
+ *   current device.
+ * The buffer is plain bytes in the byte order of the machine that wrote it
+ * (little-endian on every supported host).
+ * Errors: INVAL (NULL pointers, a buffer too small, or not a checkpoint of this
+ *   format: wrong magic, version or inconsistent sizes), STATE (element
+ *   sampling set, or an external ephemeris installed: neither is saved),
+ *   NOMEM, CUDA.
+ */
+int glisse_checkpoint_size(glisse_ctx* ctx, int64_t* bytes);
+int glisse_checkpoint(glisse_ctx* ctx, void* buf, int64_t bytes);
+int glisse_resume(glisse_ctx** out, const void* buf, int64_t bytes, const glisse_opts* opts);
+
+/* Sizes fixed at create (or resume): particles (all ids, live or not) and
+ * planets; pointers may be NULL. */
+int glisse_sizes(glisse_ctx* ctx, int64_t* n_particles, int32_t* n_planets);
+
 /* Release all device and host resources of the context (NULL is ignored). */
 void glisse_destroy(glisse_ctx* ctx);
 

@@ -53,6 +53,7 @@ EXPORTED = (
     "glisse_diff_growth_gradient",
     "glisse_diff_destroy",
     "glisse_set_sampling", "glisse_read_elements", "glisse_read_libration", "glisse_selftest_math",
+    "glisse_checkpoint_size", "glisse_checkpoint", "glisse_resume", "glisse_sizes",
 )
 
 GLISSE_PARTITION_NOALLOC_MAX = 67108864
@@ -142,6 +143,14 @@ def load(build_if_missing: bool = False):
     L.glisse_set_ephemeris.restype = C.c_int
     L.glisse_destroy.argtypes = [vp]
     L.glisse_destroy.restype = None
+    L.glisse_checkpoint_size.argtypes = [vp, i64p]
+    L.glisse_checkpoint_size.restype = C.c_int
+    L.glisse_checkpoint.argtypes = [vp, vp, C.c_int64]
+    L.glisse_checkpoint.restype = C.c_int
+    L.glisse_resume.argtypes = [C.POINTER(vp), vp, C.c_int64, C.POINTER(glisse_opts)]
+    L.glisse_resume.restype = C.c_int
+    L.glisse_sizes.argtypes = [vp, i64p, i32p]
+    L.glisse_sizes.restype = C.c_int
     L.glisse_strerror.argtypes = [C.c_int]
     L.glisse_strerror.restype = C.c_char_p
     L.glisse_partition_device.argtypes = [C.c_int64, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
@@ -324,6 +333,34 @@ def glisse_destroy(h):
         load().glisse_destroy(h)
 
 
+def glisse_checkpoint(h) -> np.ndarray:
+    """The context's checkpoint as a uint8 array (host bytes; see glisse_resume)."""
+    L = load()
+    n = C.c_int64()
+    _check(L.glisse_checkpoint_size(h, C.byref(n)), "glisse_checkpoint_size")
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(L.glisse_checkpoint(h, buf.ctypes.data, n.value), "glisse_checkpoint")
+    return buf
+
+
+def glisse_resume(buf, opts: glisse_opts | None = None):
+    """A new context from a checkpoint (bytes or uint8 array); returns a handle.  Of opts
+    only cuda_stream and timing are used."""
+    b = np.ascontiguousarray(np.frombuffer(buf, dtype=np.uint8) if isinstance(buf, (bytes, bytearray)) else buf,
+                             dtype=np.uint8)
+    h = C.c_void_p()
+    rc = load().glisse_resume(C.byref(h), b.ctypes.data, b.size, C.byref(opts) if opts is not None else None)
+    _check(rc, "glisse_resume")
+    return h
+
+
+def glisse_sizes(h):
+    """(number of particles, number of planets) of a context."""
+    n, npl = C.c_int64(), C.c_int32()
+    _check(load().glisse_sizes(h, C.byref(n), C.byref(npl)), "glisse_sizes")
+    return n.value, npl.value
+
+
 def glisse_partition_device(n, ld, alive_ptr, src_ptr, src_id_ptr, dst_ptr, dst_id_ptr, n_out_ptr, stream=0):
     """Device-level stable partition; all pointers are device addresses (ints)."""
     rc = load().glisse_partition_device(int(n), int(ld), alive_ptr, src_ptr, src_id_ptr, dst_ptr, dst_id_ptr,
@@ -492,6 +529,22 @@ class Simulation:
 
     def set_ephemeris(self, log):
         glisse_set_ephemeris(self.h, log)
+
+    def checkpoint(self) -> np.ndarray:
+        """Everything needed to go on exactly from here (see Simulation.resume)."""
+        return glisse_checkpoint(self.h)
+
+    @classmethod
+    def resume(cls, buf, **opt):
+        """A Simulation continuing from a checkpoint; opt may set cuda_stream and timing."""
+        o = glisse_opts_default()
+        for k, v in opt.items():
+            setattr(o, k, v)
+        self = cls.__new__(cls)
+        self.h = None
+        self.h = glisse_resume(buf, o)
+        self.n, self.n_planets = glisse_sizes(self.h)
+        return self
 
     def timings(self, reset=False):
         return glisse_timings(self.h, reset)

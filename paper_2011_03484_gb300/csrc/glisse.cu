@@ -84,7 +84,10 @@ constexpr double kG = 4.0 * 3.14159265358979323846 * 3.14159265358979323846;
 }  // namespace
 
 // One chunk of planets on the device: log [(C+1)][4 (N_p+1)] (positions + h0)
-// and history [(C+1)][N_p][6] (synchronised heliocentric states).
+// and history [(C+2)][N_p][6]: rows 0..C the synchronised heliocentric states,
+// row C+1 the planets' Jacobi state at the chunk's first step (what the planet
+// kernel started from; a checkpoint saves it so that resume recomputes the
+// chunk bit for bit).
 struct Slot {
     double* log = nullptr;
     double* hist = nullptr;
@@ -218,8 +221,10 @@ static void free_slot(Slot& sl) {
     sl = Slot{};
 }
 
+static size_t hist_doubles(const glisse_ctx* c) { return (size_t)(c->C + 2) * 6 * std::max(c->np, 1); }
+
 static size_t slot_bytes(const glisse_ctx* c) {
-    return sizeof(double) * (size_t)(c->C + 1) * (size_t)(log_stride(c->np) + 6 * std::max(c->np, 1));
+    return sizeof(double) * ((size_t)(c->C + 1) * (size_t)log_stride(c->np) + hist_doubles(c));
 }
 
 // Buffers (unless the slot already has arena buffers) and events of an empty
@@ -228,7 +233,7 @@ static bool alloc_slot(const glisse_ctx* c, Slot& sl) {
     const int S = log_stride(c->np);
     bool ok = sl.in_arena ||
               (cudaMalloc(&sl.log, sizeof(double) * (size_t)(c->C + 1) * S) == cudaSuccess &&
-               cudaMalloc(&sl.hist, sizeof(double) * (size_t)(c->C + 1) * 6 * std::max(c->np, 1)) == cudaSuccess);
+               cudaMalloc(&sl.hist, sizeof(double) * hist_doubles(c)) == cudaSuccess);
     ok = ok && cudaEventCreateWithFlags(&sl.ev_eph, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&sl.ev_use, cudaEventDisableTiming) == cudaSuccess;
     if (ok && c->timing) ok = cudaEventCreate(&sl.te0) == cudaSuccess && cudaEventCreate(&sl.te1) == cudaSuccess;
@@ -281,6 +286,9 @@ static int ensure_chunk(glisse_ctx* c, int64_t j) {
                     c->n_pieces == kMaxPieces - 1 ? c->C : std::min<int64_t>(c->C, kFirstPiece << c->n_pieces);
             prog = c->d_prog;
         }
+        if (c->np > 0)
+            GL_CUDA(cudaMemcpyAsync(sl.hist + (size_t)(c->C + 1) * 6 * c->np, c->d_jac, sizeof(double) * 6 * c->np,
+                                    cudaMemcpyDeviceToDevice, c->se));
         GL_CUDA(launch_eph_chunk(c->d_pc, c->d_jac, c->dt, c->C, sl.log, sl.hist, c->d_status, c->se, prog));
         if (c->timing) {
             GL_CUDA(cudaEventRecord(sl.te1, c->se));
@@ -359,7 +367,22 @@ static int check_status(glisse_ctx* c) {
     return *c->h_status;
 }
 
-static int setup(glisse_ctx* c, const double* planets, const double* particles) {
+// A context's state as a checkpoint holds it (host pointers into the caller's
+// buffer), installed by setup() in place of the initial conditions.
+struct Restore {
+    PlanetConsts pc;
+    const double* jac0;         // [np][6] Jacobi state at the first step of chunk step / C
+    const double* st;           // [6][n_live] particle slots as laid out on the device
+    const int32_t* id;          // [n_live]
+    const uint8_t* alive;       // [n_live]
+    const double* out_state;    // [n_total][6] by id
+    const int64_t* out_step;    // [n_total]
+    const int32_t* out_reason;  // [n_total]
+    int64_t n_live = 0, step = 0, since_compact = 0;
+    bool tested_first = false;
+};
+
+static int setup(glisse_ctx* c, const double* planets, const double* particles, const Restore* r = nullptr) {
     const int np = c->np;
     GL_CUDA(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
     c->own_s = true;
@@ -405,7 +428,7 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles) 
         size_t o_log[kRingMin], o_hist[kRingMin];
         for (size_t r = 0; r < kRingMin; ++r) {
             o_log[r] = take(sizeof(double) * (size_t)(c->C + 1) * S);
-            o_hist[r] = take(sizeof(double) * (size_t)(c->C + 1) * 6 * std::max(np, 1));
+            o_hist[r] = take(sizeof(double) * hist_doubles(c));
         }
         size_t o_st[2], o_id[2];
         for (int b = 0; b < 2; ++b) {
@@ -446,18 +469,30 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles) 
         if (!alloc_slot(c, sl)) return GLISSE_E_NOMEM;
     if (c->timing) GL_CUDA(cudaMemsetAsync(c->d_steps, 0, sizeof(unsigned long long), c->s));
 
-    // planets -> device, set-up kernel (Jacobi state, constants, encounter radii)
     cudaError_t e = cudaSuccess;
-    if (np > 0) e = cudaMemcpyAsync(d_in, planets, sizeof(double) * 7 * np, cudaMemcpyHostToDevice, c->s);
-    if (e == cudaSuccess)
-        e = launch_eph_setup(d_in, np, c->m0, kG, c->o.enc_mode, c->o.enc_value, c->d_pc, c->d_jac, c->d_status,
-                             c->s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&c->hpc, c->d_pc, sizeof(PlanetConsts), cudaMemcpyDeviceToHost, c->s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
-    if (e != cudaSuccess) return GLISSE_E_CUDA;
-    if (*c->h_status != 0) return *c->h_status;
+    if (r) {
+        // restore: the saved constants and the Jacobi state the current chunk starts from
+        c->hpc = r->pc;
+        e = cudaMemcpyAsync(c->d_pc, &c->hpc, sizeof(PlanetConsts), cudaMemcpyHostToDevice, c->s);
+        if (e == cudaSuccess && np > 0)
+            e = cudaMemcpyAsync(c->d_jac, r->jac0, sizeof(double) * 6 * np, cudaMemcpyHostToDevice, c->s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+        if (e != cudaSuccess) return GLISSE_E_CUDA;
+    } else {
+        // planets -> device, set-up kernel (Jacobi state, constants, encounter radii)
+        if (np > 0) e = cudaMemcpyAsync(d_in, planets, sizeof(double) * 7 * np, cudaMemcpyHostToDevice, c->s);
+        if (e == cudaSuccess)
+            e = launch_eph_setup(d_in, np, c->m0, kG, c->o.enc_mode, c->o.enc_value, c->d_pc, c->d_jac, c->d_status,
+                                 c->s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&c->hpc, c->d_pc, sizeof(PlanetConsts), cudaMemcpyDeviceToHost, c->s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+        if (e != cudaSuccess) return GLISSE_E_CUDA;
+        if (*c->h_status != 0) return *c->h_status;
+    }
 
     // particle constants (kernel parameters)
     ParticleConsts& p = c->ppc;
@@ -476,30 +511,59 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles) 
     p.rmax = c->o.r_max > 0.0 ? c->o.r_max : 0.0;
 
     // the first chunk of planets now, on the side stream: it overlaps the
-    // particle upload below and whatever the caller does before advancing
+    // particle upload below and whatever the caller does before advancing.  A
+    // resumed context starts at the chunk holding its step, from that chunk's
+    // saved Jacobi state.
+    const int64_t j0 = r ? r->step / c->C : 0;
+    c->next_chunk = j0;
+    c->eph_done = j0;
     if (c->n_total > 0) {
-        const int er = ensure_chunk(c, 0);
+        const int er = ensure_chunk(c, j0);
         if (er != GLISSE_OK) return er;
     }
 
-    // particles -> device SoA, ids, flags.  The [N][6] per-id output buffer stages
-    // the upload (it is cleared right after on the same stream): a temporary buffer
-    // would have to be freed, and cudaFree waits for the planet kernel started above.
-    if (c->n_total > 0) {
-        GL_CUDA(cudaMemcpyAsync(c->d_out_state, particles, sizeof(double) * 6 * (size_t)c->n_total,
-                                cudaMemcpyHostToDevice, c->s));
-        GL_CUDA(launch_import(c->n_total, c->d_out_state, c->d_st[0], cap, c->d_id[0], c->s));
+    if (r) {
+        // particle slots exactly as the checkpointed context held them, per-id results
+        if (r->n_live > 0) {
+            GL_CUDA(cudaMemcpy2DAsync(c->d_st[0], sizeof(double) * (size_t)cap, r->st,
+                                      sizeof(double) * (size_t)r->n_live, sizeof(double) * (size_t)r->n_live, 6,
+                                      cudaMemcpyHostToDevice, c->s));
+            GL_CUDA(cudaMemcpyAsync(c->d_id[0], r->id, sizeof(int32_t) * (size_t)r->n_live, cudaMemcpyHostToDevice,
+                                    c->s));
+            GL_CUDA(cudaMemcpyAsync(c->d_alive, r->alive, (size_t)r->n_live, cudaMemcpyHostToDevice, c->s));
+        }
+        if (c->n_total > 0) {
+            GL_CUDA(cudaMemcpyAsync(c->d_out_state, r->out_state, sizeof(double) * 6 * (size_t)c->n_total,
+                                    cudaMemcpyHostToDevice, c->s));
+            GL_CUDA(cudaMemcpyAsync(c->d_out_step, r->out_step, sizeof(int64_t) * (size_t)c->n_total,
+                                    cudaMemcpyHostToDevice, c->s));
+            GL_CUDA(cudaMemcpyAsync(c->d_out_reason, r->out_reason, sizeof(int32_t) * (size_t)c->n_total,
+                                    cudaMemcpyHostToDevice, c->s));
+        }
+        c->n_live = r->n_live;
+        c->step = r->step;
+        c->since_compact = r->since_compact;
+        c->tested_first = r->tested_first;
+    } else {
+        // particles -> device SoA, ids, flags.  The [N][6] per-id output buffer stages
+        // the upload (it is cleared right after on the same stream): a temporary buffer
+        // would have to be freed, and cudaFree waits for the planet kernel started above.
+        if (c->n_total > 0) {
+            GL_CUDA(cudaMemcpyAsync(c->d_out_state, particles, sizeof(double) * 6 * (size_t)c->n_total,
+                                    cudaMemcpyHostToDevice, c->s));
+            GL_CUDA(launch_import(c->n_total, c->d_out_state, c->d_st[0], cap, c->d_id[0], c->s));
+        }
+        GL_CUDA(cudaMemsetAsync(c->d_alive, 1, (size_t)cap, c->s));
+        GL_CUDA(cudaMemsetAsync(c->d_out_state, 0, sizeof(double) * 6 * (size_t)cap, c->s));
+        GL_CUDA(cudaMemsetAsync(c->d_out_step, 0xFF, sizeof(int64_t) * (size_t)cap, c->s));  // -1
+        GL_CUDA(cudaMemsetAsync(c->d_out_reason, 0, sizeof(int32_t) * (size_t)cap, c->s));
+        c->n_live = c->n_total;
     }
-    GL_CUDA(cudaMemsetAsync(c->d_alive, 1, (size_t)cap, c->s));
-    GL_CUDA(cudaMemsetAsync(c->d_out_state, 0, sizeof(double) * 6 * (size_t)cap, c->s));
-    GL_CUDA(cudaMemsetAsync(c->d_out_step, 0xFF, sizeof(int64_t) * (size_t)cap, c->s));  // -1
-    GL_CUDA(cudaMemsetAsync(c->d_out_reason, 0, sizeof(int32_t) * (size_t)cap, c->s));
-    c->n_live = c->n_total;
     // the first two planet chunks
     GL_CUDA(cudaEventCreateWithFlags(&c->ev_order, cudaEventDisableTiming));
     GL_CUDA(cudaEventRecord(c->ev_order, c->s));  // order the side stream after the set-up
     GL_CUDA(cudaStreamWaitEvent(c->se, c->ev_order, 0));
-    int rc = ensure_chunk(c, 1);
+    int rc = ensure_chunk(c, j0 + 1);
     if (rc) return rc;
     GL_CUDA(cudaStreamSynchronize(c->s));
     return GLISSE_OK;
@@ -862,6 +926,227 @@ extern "C" int glisse_read_planets(glisse_ctx* c, double* planets, double* t) {
         planets[7 * p] = c->hpc.m[p];
         for (int d = 0; d < 6; ++d) planets[7 * p + 1 + d] = buf[6 * p + d];
     }
+    return GLISSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume.  Buffer: a fixed header, then the arrays, each at an
+// 8-byte offset: the chunk-start Jacobi state [np][6], the particle slots
+// [6][n_live], the per-id frozen states [n_total][6], removal steps [n_total],
+// slot ids [n_live], reasons [n_total], slot flags [n_live].
+// ---------------------------------------------------------------------------
+namespace {
+constexpr char kCkptMagic[8] = {'G', 'L', 'I', 'S', 'S', 'E', 'C', 'K'};
+constexpr int32_t kCkptVersion = 1;
+
+struct CkptHeader {
+    char magic[8];
+    int32_t version;
+    int32_t header_bytes;
+    int32_t np;
+    int32_t chunk_steps, resync_chunks, kepler_mode, kepler_iters, enc_mode, sort_mode;
+    int32_t tested_first;
+    double m0, dt, enc_value, r_max;
+    int64_t n_total, n_live, step, since_compact;
+    int64_t total_bytes;
+    PlanetConsts pc;
+};
+
+struct CkptLayout {
+    size_t jac0, st, out_state, out_step, id, out_reason, alive, total;
+};
+
+CkptLayout ckpt_layout(int np, int64_t n_total, int64_t n_live) {
+    CkptLayout L{};
+    size_t off = (sizeof(CkptHeader) + 7) & ~size_t(7);
+    auto take = [&off](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 7) & ~size_t(7);
+        return o;
+    };
+    L.jac0 = take(sizeof(double) * 6 * (size_t)np);
+    L.st = take(sizeof(double) * 6 * (size_t)n_live);
+    L.out_state = take(sizeof(double) * 6 * (size_t)n_total);
+    L.out_step = take(sizeof(int64_t) * (size_t)n_total);
+    L.id = take(sizeof(int32_t) * (size_t)n_live);
+    L.out_reason = take(sizeof(int32_t) * (size_t)n_total);
+    L.alive = take((size_t)n_live);
+    L.total = off;
+    return L;
+}
+
+int ckpt_state_ok(const glisse_ctx* c) {
+    if (c->samp_on || c->external || !c->planets_valid) return GLISSE_E_STATE;
+    return GLISSE_OK;
+}
+}  // namespace
+
+extern "C" int glisse_sizes(glisse_ctx* c, int64_t* n_particles, int32_t* n_planets) {
+    if (!c) return GLISSE_E_INVAL;
+    if (n_particles) *n_particles = c->n_total;
+    if (n_planets) *n_planets = c->np;
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_checkpoint_size(glisse_ctx* c, int64_t* bytes) {
+    if (!c || !bytes) return GLISSE_E_INVAL;
+    const int st = ckpt_state_ok(c);
+    if (st != GLISSE_OK) return st;
+    *bytes = (int64_t)ckpt_layout(c->np, c->n_total, c->n_live).total;
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_checkpoint(glisse_ctx* c, void* buf, int64_t bytes) {
+    if (!c || !buf) return GLISSE_E_INVAL;
+    const int st = ckpt_state_ok(c);
+    if (st != GLISSE_OK) return st;
+    const CkptLayout L = ckpt_layout(c->np, c->n_total, c->n_live);
+    if (bytes < (int64_t)L.total) return GLISSE_E_INVAL;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != c->device) GL_CUDA(cudaSetDevice(c->device));
+    int rc = GLISSE_OK;
+    char* out = static_cast<char*>(buf);
+    std::memset(out, 0, L.total);  // the gaps between arrays too: equal contexts, equal bytes
+    // the Jacobi state the current chunk's planet kernel started from
+    const int64_t j = c->step / c->C;
+    if ((rc = ensure_chunk(c, j)) == GLISSE_OK) {
+        const Slot& sl = c->ring[(size_t)(j % (int64_t)c->ring.size())];
+        cudaError_t e = sl.chunk == j ? cudaSuccess : cudaErrorInvalidValue;
+        if (sl.chunk != j) rc = GLISSE_E_STATE;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->se);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+        if (e == cudaSuccess && c->np > 0)
+            e = cudaMemcpy(out + L.jac0, sl.hist + (size_t)(c->C + 1) * 6 * c->np, sizeof(double) * 6 * c->np,
+                           cudaMemcpyDeviceToHost);
+        const int64_t n = c->n_live, N = c->n_total;
+        if (e == cudaSuccess && n > 0)
+            e = cudaMemcpy2D(out + L.st, sizeof(double) * (size_t)n, c->d_st[c->cur], sizeof(double) * (size_t)c->cap,
+                             sizeof(double) * (size_t)n, 6, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && n > 0)
+            e = cudaMemcpy(out + L.id, c->d_id[c->cur], sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && n > 0) e = cudaMemcpy(out + L.alive, c->d_alive, (size_t)n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && N > 0)
+            e = cudaMemcpy(out + L.out_state, c->d_out_state, sizeof(double) * 6 * (size_t)N, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && N > 0)
+            e = cudaMemcpy(out + L.out_step, c->d_out_step, sizeof(int64_t) * (size_t)N, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && N > 0)
+            e = cudaMemcpy(out + L.out_reason, c->d_out_reason, sizeof(int32_t) * (size_t)N, cudaMemcpyDeviceToHost);
+        if (rc == GLISSE_OK && e != cudaSuccess) {
+            (void)cudaGetLastError();
+            rc = GLISSE_E_CUDA;
+        }
+    }
+    if (rc == GLISSE_OK) {
+        CkptHeader h;
+        std::memset(&h, 0, sizeof(h));
+        std::memcpy(h.magic, kCkptMagic, sizeof(kCkptMagic));
+        h.version = kCkptVersion;
+        h.header_bytes = (int32_t)sizeof(CkptHeader);
+        h.np = c->np;
+        h.chunk_steps = c->o.chunk_steps;
+        h.resync_chunks = c->o.resync_chunks;
+        h.kepler_mode = c->o.kepler_mode;
+        h.kepler_iters = c->o.kepler_iters;
+        h.enc_mode = c->o.enc_mode;
+        h.sort_mode = c->o.sort_mode;
+        h.tested_first = c->tested_first ? 1 : 0;
+        h.m0 = c->m0;
+        h.dt = c->dt;
+        h.enc_value = c->o.enc_value;
+        h.r_max = c->o.r_max;
+        h.n_total = c->n_total;
+        h.n_live = c->n_live;
+        h.step = c->step;
+        h.since_compact = c->since_compact;
+        h.total_bytes = (int64_t)L.total;
+        h.pc = c->hpc;
+        std::memcpy(out, &h, sizeof(h));
+    }
+    if (prev != c->device) cudaSetDevice(prev);
+    return rc;
+}
+
+extern "C" int glisse_resume(glisse_ctx** out, const void* buf, int64_t bytes, const glisse_opts* opts) {
+    if (!out) return GLISSE_E_INVAL;
+    *out = nullptr;
+    if (!buf || bytes < (int64_t)sizeof(CkptHeader)) return GLISSE_E_INVAL;
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, kCkptMagic, sizeof(kCkptMagic)) != 0 || h.version != kCkptVersion ||
+        h.header_bytes != (int32_t)sizeof(CkptHeader))
+        return GLISSE_E_INVAL;
+    if (h.np < 0 || h.np > GLISSE_MAX_PLANETS || h.pc.np != h.np) return GLISSE_E_INVAL;
+    if (h.n_total < 0 || h.n_total > INT32_MAX || h.n_live < 0 || h.n_live > h.n_total) return GLISSE_E_INVAL;
+    if (h.step < 0 || h.since_compact < 0 || (h.tested_first != 0 && h.tested_first != 1)) return GLISSE_E_INVAL;
+    if (!(h.m0 > 0.0) || !std::isfinite(h.m0) || !(h.dt != 0.0) || !std::isfinite(h.dt)) return GLISSE_E_INVAL;
+    if (h.chunk_steps < 1 || h.chunk_steps > (1 << 20) || h.resync_chunks < 1) return GLISSE_E_INVAL;
+    if (h.kepler_mode != GLISSE_KEPLER_CONVERGE && h.kepler_mode != GLISSE_KEPLER_PAPER_FIXED) return GLISSE_E_INVAL;
+    if (h.kepler_mode == GLISSE_KEPLER_PAPER_FIXED && (h.kepler_iters < 1 || h.kepler_iters > GLISSE_MAX_KEPLER_ITERS))
+        return GLISSE_E_INVAL;
+    if (h.enc_mode != GLISSE_ENC_HILL && h.enc_mode != GLISSE_ENC_FIXED) return GLISSE_E_INVAL;
+    if (h.sort_mode != GLISSE_SORT_NONE && h.sort_mode != GLISSE_SORT_COST) return GLISSE_E_INVAL;
+    if (!(h.enc_value >= 0.0) || !std::isfinite(h.enc_value) || !std::isfinite(h.r_max)) return GLISSE_E_INVAL;
+    const CkptLayout L = ckpt_layout(h.np, h.n_total, h.n_live);
+    if (h.total_bytes != (int64_t)L.total || bytes < h.total_bytes) return GLISSE_E_INVAL;
+    const char* in = static_cast<const char*>(buf);
+    // every slot id must name a distinct particle: the kernels write per-id outputs through them
+    {
+        std::vector<bool> seen((size_t)h.n_total, false);
+        for (int64_t k = 0; k < h.n_live; ++k) {
+            int32_t id = 0;
+            std::memcpy(&id, in + L.id + sizeof(int32_t) * (size_t)k, sizeof(id));
+            if (id < 0 || (int64_t)id >= h.n_total || seen[(size_t)id]) return GLISSE_E_INVAL;
+            seen[(size_t)id] = true;
+        }
+    }
+    glisse_opts o;
+    glisse_opts_default(&o);
+    o.chunk_steps = h.chunk_steps;
+    o.resync_chunks = h.resync_chunks;
+    o.kepler_mode = h.kepler_mode;
+    o.kepler_iters = h.kepler_iters;
+    o.enc_mode = h.enc_mode;
+    o.sort_mode = h.sort_mode;
+    o.enc_value = h.enc_value;
+    o.r_max = h.r_max;
+    if (opts) {
+        o.cuda_stream = opts->cuda_stream;
+        o.timing = opts->timing;
+    }
+    glisse_ctx* c = new (std::nothrow) glisse_ctx();
+    if (!c) return GLISSE_E_NOMEM;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete c;
+        return GLISSE_E_CUDA;
+    }
+    c->o = o;
+    c->np = h.np;
+    c->m0 = h.m0;
+    c->dt = h.dt;
+    c->C = o.chunk_steps;
+    c->n_total = h.n_total;
+    c->timing = o.timing != 0;
+    Restore r;
+    r.pc = h.pc;
+    r.jac0 = reinterpret_cast<const double*>(in + L.jac0);
+    r.st = reinterpret_cast<const double*>(in + L.st);
+    r.id = reinterpret_cast<const int32_t*>(in + L.id);
+    r.alive = reinterpret_cast<const uint8_t*>(in + L.alive);
+    r.out_state = reinterpret_cast<const double*>(in + L.out_state);
+    r.out_step = reinterpret_cast<const int64_t*>(in + L.out_step);
+    r.out_reason = reinterpret_cast<const int32_t*>(in + L.out_reason);
+    r.n_live = h.n_live;
+    r.step = h.step;
+    r.since_compact = h.since_compact;
+    r.tested_first = h.tested_first != 0;
+    const int rc = setup(c, nullptr, nullptr, &r);
+    if (rc != GLISSE_OK) {
+        ctx_free(c);
+        return rc;
+    }
+    *out = c;
     return GLISSE_OK;
 }
 

@@ -130,6 +130,9 @@ def test_null_handles_are_rejected(G):
         lambda: L.glisse_diff_backward(None, None, None, None),
         lambda: L.glisse_diff_backward_growth(None, None, None, None, None, None, None),
         lambda: L.glisse_diff_growth_gradient(None, None, None, None, None, None),
+        lambda: L.glisse_checkpoint_size(None, None),
+        lambda: L.glisse_checkpoint(None, None, 0),
+        lambda: L.glisse_sizes(None, None, None),
     ]
     for k, call in enumerate(calls):
         assert call() == E, k
@@ -158,3 +161,21 @@ def test_package_does_not_reference_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.lower(), f
+
+
+def test_resume_rejects_what_is_not_a_checkpoint(G):
+    """glisse_resume validates the buffer on the host before any CUDA call."""
+    import ctypes as C
+
+    L = G.load()
+    h = C.c_void_p()
+    E = G.GLISSE_E_INVAL
+    assert L.glisse_resume(None, None, 0, None) == E
+    assert L.glisse_resume(C.byref(h), None, 0, None) == E
+    for buf in (b"", b"GLISSECK", bytes(4096), b"GLISSECK" + bytes(4088), np.random.default_rng(0).bytes(4096)):
+        arr = np.frombuffer(buf, dtype=np.uint8).copy() if buf else np.zeros(1, dtype=np.uint8)
+        assert L.glisse_resume(C.byref(h), arr.ctypes.data, len(buf), None) == E
+        assert not h.value
+    with pytest.raises(G.GlisseError) as ei:
+        G.glisse_resume(bytes(64))
+    assert ei.value.code == E
