@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "glisse_internal.h"
+#include "nvtx_range.h"
 
 namespace glisse {
 cudaError_t launch_eph_setup(const double*, int, double, double, int, double, PlanetConsts*, double*, int*,
@@ -584,6 +585,7 @@ static int batch_setup(glisse_batch* b, const double* star_mass, const int32_t* 
 extern "C" int glisse_batch_create(glisse_batch** out, int32_t n_systems, const double* star_mass,
                                    const int32_t* n_planets, const double* planets, const int64_t* n_particles,
                                    const double* particles, const double* dt, const glisse_opts* opts) {
+    glisse::NvtxRange range("glisse_batch_create");
     if (!out) return GLISSE_E_INVAL;
     *out = nullptr;
     glisse_opts o;
@@ -631,6 +633,7 @@ extern "C" int glisse_batch_create(glisse_batch** out, int32_t n_systems, const 
 }
 
 extern "C" int glisse_batch_advance(glisse_batch* b, int64_t n_steps) {
+    glisse::NvtxRange range("glisse_batch_advance");
     if (!b || n_steps < 0) return GLISSE_E_INVAL;
     int64_t remaining = n_steps;
     while (remaining > 0) {
@@ -749,6 +752,7 @@ __global__ void batch_counts_from_tasks(const int32_t* __restrict__ task_sys, co
 
 extern "C" int glisse_batch_tune(glisse_batch* b, int32_t trial_steps, int32_t* chunk_steps, int32_t* block_threads,
                                  int32_t* threads_per_particle) {
+    glisse::NvtxRange range("glisse_batch_tune");
     if (!b) return GLISSE_E_INVAL;
     if (trial_steps <= 0) trial_steps = 256;
     Snapshot sn;

@@ -43,6 +43,7 @@
 #include <new>
 
 #include "glisse_internal.h"
+#include "nvtx_range.h"
 #include "drift_diff.cuh"
 
 namespace glisse {
@@ -630,6 +631,7 @@ extern "C" void glisse_diff_destroy(glisse_diff* d) { diff_free(d); }
 extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const double* planets, int32_t n_planets,
                                   int64_t n_particles, double dt, int64_t n_steps, int32_t checkpoint_every,
                                   const glisse_opts* opts) {
+    glisse::NvtxRange range("glisse_diff_create");
     if (!out) return GLISSE_E_INVAL;
     *out = nullptr;
     glisse_opts o;
@@ -728,6 +730,7 @@ fail:
 extern "C" int glisse_diff_forward(glisse_diff* d, const double* state0, double* state1, int32_t n_tangents,
                                    const double* tangent0, double* tangent1, double* log_growth,
                                    int64_t* removal_step, int32_t* removal_reason, void* stream) {
+    glisse::NvtxRange range("glisse_diff_forward");
     if (!d || n_tangents < 0 || n_tangents > kMaxTangents) return GLISSE_E_INVAL;
     if (d->n > 0 && (!state0 || !state1)) return GLISSE_E_INVAL;
     if (n_tangents > 0 && (!tangent0 || !tangent1)) return GLISSE_E_INVAL;
@@ -765,6 +768,7 @@ extern "C" int glisse_diff_forward(glisse_diff* d, const double* state0, double*
 }
 
 extern "C" int glisse_diff_backward(glisse_diff* d, const double* grad_state1, double* grad_state0, void* stream) {
+    glisse::NvtxRange range("glisse_diff_backward");
     if (!d) return GLISSE_E_INVAL;
     if (!d->have_forward) return GLISSE_E_STATE;
     if (d->n > 0 && (!grad_state1 || !grad_state0)) return GLISSE_E_INVAL;
@@ -793,6 +797,7 @@ extern "C" int glisse_diff_backward(glisse_diff* d, const double* grad_state1, d
 extern "C" int glisse_diff_backward_growth(glisse_diff* d, const double* grad_state1, const double* grad_growth,
                                            const double* tangent1, double* grad_state0, double* grad_tangent0,
                                            void* stream) {
+    glisse::NvtxRange range("glisse_diff_backward_growth");
     if (!d) return GLISSE_E_INVAL;
     if (!d->have_forward || d->last_ntan < 1 || d->tape) return GLISSE_E_STATE;
     if (d->n > 0 && (!tangent1 || !grad_state0 || !grad_tangent0)) return GLISSE_E_INVAL;
@@ -831,6 +836,7 @@ extern "C" int glisse_diff_backward_growth(glisse_diff* d, const double* grad_st
 
 extern "C" int glisse_diff_growth_gradient(glisse_diff* d, const double* state0, const double* tangent0,
                                            double* grad_state0, double* log_growth, void* stream) {
+    glisse::NvtxRange range("glisse_diff_growth_gradient");
     if (!d) return GLISSE_E_INVAL;
     if (d->n > 0 && (!state0 || !tangent0 || !grad_state0)) return GLISSE_E_INVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

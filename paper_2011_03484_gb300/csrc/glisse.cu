@@ -32,6 +32,7 @@
 #include <new>
 
 #include "glisse_internal.h"
+#include "nvtx_range.h"
 
 namespace glisse {
 cudaError_t launch_eph_setup(const double*, int, double, double, int, double, PlanetConsts*, double*, int*,
@@ -274,6 +275,7 @@ extern "C" void glisse_destroy(glisse_ctx* c) {
 
 // Enqueue the ephemeris for chunk j (and every earlier chunk not yet enqueued).
 static int ensure_chunk(glisse_ctx* c, int64_t j) {
+    NvtxRange range("glisse: enqueue planet chunks");
     while (c->next_chunk <= j) {
         Slot& sl = c->ring[(size_t)(c->next_chunk % (int64_t)c->ring.size())];
         if (sl.used) GL_CUDA(cudaStreamWaitEvent(c->se, sl.ev_use, 0));
@@ -607,6 +609,7 @@ extern "C" int glisse_create(glisse_ctx** out, double star_mass, const double* p
     c->C = o.chunk_steps;
     c->n_total = n_particles;
     c->timing = o.timing != 0;
+    NvtxRange range("glisse_create");
     int rc = setup(c, planets, particles);
     if (rc != GLISSE_OK) {
         ctx_free(c);
@@ -617,6 +620,7 @@ extern "C" int glisse_create(glisse_ctx** out, double star_mass, const double* p
 }
 
 static int compact(glisse_ctx* c) {
+    NvtxRange range("glisse: compaction");
     const int nxt = c->cur ^ 1;
     if (c->timing) GL_CUDA(cudaEventRecord(c->tc0, c->s));
     if (c->o.sort_mode == GLISSE_SORT_COST)
@@ -741,6 +745,7 @@ extern "C" int glisse_read_libration(glisse_ctx* c, uint8_t* near0, uint8_t* nea
 
 extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
     if (!c || n_steps < 0) return GLISSE_E_INVAL;
+    NvtxRange range("glisse_advance");
     if (n_steps == 0) return GLISSE_OK;
     if (c->external && n_steps > c->ext_n - c->ext_off) return GLISSE_E_STATE;
     if (!c->external && !c->planets_valid) return GLISSE_E_STATE;
@@ -824,6 +829,7 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
             a.out_step = c->d_out_step;
             a.out_reason = c->d_out_reason;
             a.steps_done = c->d_steps;
+            NvtxRange seg("glisse: particle segment");
             if (c->timing) GL_CUDA(cudaEventRecord(c->tp0, c->s));
             if (c->o.kepler_mode == GLISSE_KEPLER_PAPER_FIXED)
                 GL_CUDA(launch_particle_chunk_paper(c->np, a, c->ppc, c->s));
@@ -876,6 +882,7 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
 extern "C" int glisse_read(glisse_ctx* c, double* state, uint8_t* alive, int64_t* removal_step,
                            int32_t* removal_reason) {
     if (!c) return GLISSE_E_INVAL;
+    NvtxRange range("glisse_read");
     const int64_t n = c->n_total;
     if (n == 0) return GLISSE_OK;
     GL_CUDA(launch_export_live(c->n_live, c->d_st[c->cur], c->cap, c->d_id[c->cur], c->d_out_state, c->s));
@@ -1005,6 +1012,7 @@ extern "C" int glisse_checkpoint(glisse_ctx* c, void* buf, int64_t bytes) {
     int prev = 0;
     cudaGetDevice(&prev);
     if (prev != c->device) GL_CUDA(cudaSetDevice(c->device));
+    NvtxRange range("glisse_checkpoint");
     int rc = GLISSE_OK;
     char* out = static_cast<char*>(buf);
     std::memset(out, 0, L.total);  // the gaps between arrays too: equal contexts, equal bytes
@@ -1141,6 +1149,7 @@ extern "C" int glisse_resume(glisse_ctx** out, const void* buf, int64_t bytes, c
     r.step = h.step;
     r.since_compact = h.since_compact;
     r.tested_first = h.tested_first != 0;
+    NvtxRange range("glisse_resume");
     const int rc = setup(c, nullptr, nullptr, &r);
     if (rc != GLISSE_OK) {
         ctx_free(c);
