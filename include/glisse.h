@@ -320,6 +320,7 @@ typedef struct glisse_diff glisse_diff; /* opaque; owned by the library */
  * checkpoint_every = 0 (tape mode): the forward pass records every step (112 B
  * per particle per step, e.g. 73 GB for 65536 particles over 10^4 steps) and
  * the backward pass does not recompute; NOMEM if the device cannot hold it.
+ * n_steps <= INT32_MAX (the planet log is one chunk of that many steps).
  * opts: enc_mode, enc_value and r_max apply.  Errors: INVAL, NOMEM, CUDA, KEPLER. */
 int glisse_diff_create(glisse_diff** out, double star_mass, const double* planets, int32_t n_planets,
                        int64_t n_particles, double dt, int64_t n_steps, int32_t checkpoint_every,

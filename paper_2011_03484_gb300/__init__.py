@@ -512,6 +512,7 @@ class Simulation:
             setattr(o, k, v)
         self.n = int(np.asarray(particles).reshape(-1, 6).shape[0])
         self.n_planets = int(np.asarray(planets).reshape(-1, 7).shape[0])
+        self.h = None
         self.h = glisse_create(star_mass, planets, particles, dt, o)
 
     def advance(self, n_steps):
@@ -626,6 +627,7 @@ class DiffMap:
             setattr(o, k, v)
         self.n = int(n_particles)
         self.tape = int(checkpoint_every) == 0
+        self.h = None
         self.h = glisse_diff_create(star_mass, planets, n_particles, dt, n_steps, checkpoint_every, o)
         self.forward_calls = 0
 

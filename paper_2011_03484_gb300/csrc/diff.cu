@@ -638,7 +638,8 @@ extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const dou
     glisse_opts_default(&o);
     if (opts) o = *opts;
     if (!(star_mass > 0.0) || n_planets < 0 || n_planets > GLISSE_MAX_PLANETS || (n_planets > 0 && !planets) ||
-        n_particles < 0 || n_steps < 0 || !(dt != 0.0) || !std::isfinite(dt) || checkpoint_every < 0)
+        n_particles < 0 || n_steps < 0 || n_steps > INT32_MAX || !(dt != 0.0) || !std::isfinite(dt) ||
+        checkpoint_every < 0)
         return GLISSE_E_INVAL;
     // derivatives are of the converged drift only
     if (o.kepler_mode != GLISSE_KEPLER_CONVERGE || o.sort_mode != GLISSE_SORT_NONE) return GLISSE_E_INVAL;

@@ -376,6 +376,31 @@ def test_partition_device_stable(G, n):
     np.testing.assert_array_equal(d_did.cpu().numpy()[:m], ids.numpy()[keep])
 
 
+def test_allocation_failures_return_nomem(G):
+    """Device allocations that cannot be had return GLISSE_E_NOMEM, with no fault, and leave the
+    context usable: element storage for 2^30 samples of 1024 particles (48 TiB), then the same
+    run as a context that never asked (bit for bit); a differentiable map of 2^24 particles
+    with checkpoints every 256 of 10^6 steps (3 TB of checkpoints).  A run longer than the
+    planet log's int32 step count is an argument error."""
+    w = gi.make("tiny", n=1024)
+    ref = run_gpu(G, w, 300, chunk_steps=128)
+    sim = G.Simulation(w["star_mass"], w["planets"], w["particles"], w["dt"], chunk_steps=128)
+    with pytest.raises(G.GlisseError) as ei:
+        sim.set_sampling(16, max_samples=1 << 30)
+    assert ei.value.code == G.GLISSE_E_NOMEM
+    sim.advance(300)
+    out = sim.read()
+    sim.close()
+    for k in ("state", "alive", "removal_step", "removal_reason"):
+        assert np.array_equal(out[k], ref[k]), k
+    with pytest.raises(G.GlisseError) as ei:
+        G.DiffMap(1.0, w["planets"], 1 << 24, w["dt"], 10**6, 256)
+    assert ei.value.code == G.GLISSE_E_NOMEM
+    with pytest.raises(G.GlisseError) as ei:
+        G.DiffMap(1.0, w["planets"], 1024, w["dt"], 1 << 31, 256)
+    assert ei.value.code == G.GLISSE_E_INVAL
+
+
 def test_fp64_peak_probe(G):
     rate, mhz = G.glisse_fp64_peak(4000)
     assert 1e11 < rate < 4e12

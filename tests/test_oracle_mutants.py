@@ -25,6 +25,7 @@ MUTANTS = [
     ("planet_mu_jacobi", "double mu = ORC_G * P->m0 * P->eta[i + 1] / P->eta[i];", "double mu = ORC_G * P->m0;",
      "brute"),
     ("particle_kick_transposed", "dir[1] -= Gm[j] * dy / d3;", "dir[1] -= Gm[j] * dz / d3;", "brute"),
+    ("planet_interaction_transposed", "gh[i][1] += Gmj * dy / d3;", "gh[i][1] += Gmj * dz / d3;", "angmom"),
     ("closing_kick_old_planets", "particle_accel(np, Gm, P1, st, a);", "particle_accel(np, Gm, P0, st, a);",
      "brute"),
     ("drift_dE_g_sign", "double g = (dM - (x - s)) / n;", "double g = (dM - (x + s)) / n;", "two_body"),
@@ -86,6 +87,8 @@ def _run_pin(name):
         PE.test_elements_invert_the_generator(oracle)
     elif name == "barycentre":
         PE.test_barycentre_has_zero_momentum(oracle)
+    elif name == "angmom":
+        P.test_planet_angular_momentum(oracle)
     elif name == "libration":
         PE.test_resonant_particles_librate_and_others_circulate(oracle)
     else:
@@ -108,6 +111,6 @@ def test_pin_catches_planted_mistake(tmp_path, mid, orig, planted, pin):
 
 def test_unmutated_oracle_passes_the_same_pins():
     for pin in ["two_body", "two_body_hyp", "tie", "escape", "hill", "energy", "tangent_sym", "tangent_fd",
-                "paper_newton", "paper_claim", "elements", "barycentre", "libration"]:
+                "paper_newton", "paper_claim", "elements", "barycentre", "libration", "angmom"]:
         _run_pin(pin)
     assert os.path.exists(oracle.build())
