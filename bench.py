@@ -281,6 +281,46 @@ def batched_arm(args):
         simt.advance(C_run)
     tm = simt.timings()
     simt.close()
+    # end to end through the C ABI with host buffers in pinned memory: create (H2D of every
+    # system's planets and particles) + one chunk + read (D2H of states, flags, steps, reasons)
+    e2e = None
+    if args.e2e_steps > 0:
+        def pinned(a, dtype):
+            t = torch.empty(np.shape(a), dtype=dtype).pin_memory().numpy()
+            t[...] = a
+            return t
+
+        pl_h = pinned(b["planets"], torch.float64)
+        pa_h = pinned(b["particles"], torch.float64)
+        n_all = int(np.sum(b["n_particles"]))
+        out_h = {"state": pinned(np.zeros((n_all, 6)), torch.float64),
+                 "alive": pinned(np.zeros(n_all), torch.uint8),
+                 "removal_step": pinned(np.zeros(n_all), torch.int64),
+                 "removal_reason": pinned(np.zeros(n_all), torch.int32)}
+        times, done_e = [], 0
+        for k in range(args.e2e_steps + 1):
+            t0 = time.perf_counter()
+            se = G.BatchSimulation(b["star_mass"], b["n_planets"], pl_h, b["n_particles"], pa_h, b["dt"],
+                                   chunk_steps=C_run, cuda_stream=stream.cuda_stream)
+            if tuned:
+                se.set_launch(tuned[1], tuned[2])
+            se.advance(C_run)
+            se.read(out_h)
+            steps_k = se.steps_done()
+            se.close()
+            el = time.perf_counter() - t0
+            if k > 0:
+                times.append(el)
+                done_e += steps_k
+        e2e = {"value": done_e / sum(times), "unit": UNIT,
+               "h2d_bytes_per_step": int(pl_h.nbytes + pa_h.nbytes),
+               "d2h_bytes_per_step": int(sum(a.nbytes for a in out_h.values())),
+               "host_buffers": "pinned"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = batched_cpu_baseline(b, C_run)
+
     csum = clocks.summary()
     mhz = csum["sm_mhz"] if csum else 2070.0
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -309,10 +349,43 @@ def batched_arm(args):
                               "compaction": tm["compact_ms"] / max(tm["compact_launches"], 1)},
         "gpu_launches": 7 * args.steps,
         "clocks": csum,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def batched_cpu_baseline(b, n_steps, n_sys=64, per_sys=2048, seed=0):
+    """The oracle on the host cores over a bounded sample of the batched workload: n_sys
+    random systems, up to per_sys random particles of each, n_steps steps of each system's
+    own map (its planets integrated by the oracle too)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    n_systems = len(b["star_mass"])
+    pl_off = np.concatenate([[0], np.cumsum(b["n_planets"])])
+    pa_off = np.concatenate([[0], np.cumsum(b["n_particles"])])
+    done, busy, taken = 0, 0.0, 0
+    for s in sorted(rng.choice(n_systems, size=min(n_sys, n_systems), replace=False)):
+        pl = b["planets"][pl_off[s]:pl_off[s + 1]]
+        pa = b["particles"][pa_off[s]:pa_off[s + 1]]
+        if len(pa) > per_sys:
+            pa = pa[np.sort(rng.choice(len(pa), size=per_sys, replace=False))]
+        t0 = time.perf_counter()
+        o = oracle.run(float(b["star_mass"][s]), pl, pa, float(b["dt"][s]), n_steps)
+        busy += time.perf_counter() - t0
+        rs = o["removal_step"]
+        done += int(np.where(rs >= 0, rs, n_steps).sum())
+        taken += len(pa)
+    cores = oracle.max_threads()
+    return {"value": done / busy, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{min(n_sys, n_systems)} random systems, {taken} particles (up to {per_sys} per system), "
+                      f"{n_steps} steps each ({busy:.1f} s wall on {cores} threads)"}
 
 
 def diff_arm(args):

@@ -412,11 +412,20 @@ def glisse_batch_advance(h, n_steps: int):
     _check(load().glisse_batch_advance(h, int(n_steps)), "glisse_batch_advance")
 
 
-def glisse_batch_read(h, n: int):
-    st = np.empty((n, 6))
-    alive = np.empty(n, dtype=np.uint8)
-    steps = np.empty(n, dtype=np.int64)
-    rsn = np.empty(n, dtype=np.int32)
+def glisse_batch_read(h, n: int, out=None):
+    """Returns dict(state [n][6], alive [n] bool, removal_step [n], removal_reason [n]) in the
+    batch's particle order.  out: optional dict of preallocated host arrays (as for glisse_read,
+    e.g. in pinned memory), written in place."""
+    if out is not None:
+        st, alive, steps, rsn = out["state"], out["alive"], out["removal_step"], out["removal_reason"]
+        assert st.shape == (n, 6) and st.dtype == np.float64 and st.flags.c_contiguous
+        assert alive.shape == (n,) and alive.dtype == np.uint8 and steps.dtype == np.int64
+        assert rsn.dtype == np.int32
+    else:
+        st = np.empty((n, 6))
+        alive = np.empty(n, dtype=np.uint8)
+        steps = np.empty(n, dtype=np.int64)
+        rsn = np.empty(n, dtype=np.int32)
     rc = load().glisse_batch_read(h, _dp(st), alive.ctypes.data_as(C.POINTER(C.c_uint8)),
                                   steps.ctypes.data_as(C.POINTER(C.c_int64)),
                                   rsn.ctypes.data_as(C.POINTER(C.c_int32)))
@@ -472,8 +481,8 @@ class BatchSimulation:
         glisse_batch_advance(self.h, n_steps)
         return self
 
-    def read(self):
-        return glisse_batch_read(self.h, self.n)
+    def read(self, out=None):
+        return glisse_batch_read(self.h, self.n, out)
 
     def status(self):
         return glisse_batch_status(self.h)
