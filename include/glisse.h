@@ -490,6 +490,28 @@ int glisse_batch_tune(glisse_batch* b, int32_t trial_steps, int32_t* chunk_steps
  */
 int glisse_batch_set_launch(glisse_batch* b, int32_t block_threads, int32_t threads_per_particle);
 
+/*
+ * Checkpoint and resume of a batch (the continuation runs of sections 4.2.2
+ * and 4.3.2, as for glisse_checkpoint): every system's constants, dt and
+ * current Jacobi planet state, the live particles per system, the particle
+ * slots as laid out on the device, the per-id results, the step and the
+ * removal test at t_0 still pending or not, the chunk length and the launch
+ * shape.  A batch resumed from it and advanced by the same calls gives
+ * results identical to the original.  glisse_batch_checkpoint writes to the
+ * caller's host buffer (at least glisse_batch_checkpoint_size bytes) and
+ * synchronises the batch's stream; glisse_batch_resume creates a batch on the
+ * current device, taking only cuda_stream and timing from opts (may be NULL).
+ * Errors: INVAL (NULL pointers, a buffer too small or not a batch checkpoint:
+ * wrong magic, version or inconsistent sizes, ids or counts), NOMEM, CUDA.
+ */
+int glisse_batch_checkpoint_size(glisse_batch* b, int64_t* bytes);
+int glisse_batch_checkpoint(glisse_batch* b, void* buf, int64_t bytes);
+int glisse_batch_resume(glisse_batch** out, const void* buf, int64_t bytes, const glisse_opts* opts);
+
+/* Sizes fixed at create (or resume): particles over all systems and systems;
+ * pointers may be NULL. */
+int glisse_batch_sizes(glisse_batch* b, int64_t* n_particles, int32_t* n_systems);
+
 /* Release the batch (NULL is ignored). */
 void glisse_batch_destroy(glisse_batch* b);
 

@@ -54,6 +54,7 @@ EXPORTED = (
     "glisse_diff_destroy",
     "glisse_set_sampling", "glisse_read_elements", "glisse_read_libration", "glisse_selftest_math",
     "glisse_checkpoint_size", "glisse_checkpoint", "glisse_resume", "glisse_sizes",
+    "glisse_batch_checkpoint_size", "glisse_batch_checkpoint", "glisse_batch_resume", "glisse_batch_sizes",
 )
 
 GLISSE_PARTITION_NOALLOC_MAX = 67108864
@@ -151,6 +152,14 @@ def load(build_if_missing: bool = False):
     L.glisse_resume.restype = C.c_int
     L.glisse_sizes.argtypes = [vp, i64p, i32p]
     L.glisse_sizes.restype = C.c_int
+    L.glisse_batch_checkpoint_size.argtypes = [vp, i64p]
+    L.glisse_batch_checkpoint_size.restype = C.c_int
+    L.glisse_batch_checkpoint.argtypes = [vp, vp, C.c_int64]
+    L.glisse_batch_checkpoint.restype = C.c_int
+    L.glisse_batch_resume.argtypes = [C.POINTER(vp), vp, C.c_int64, C.POINTER(glisse_opts)]
+    L.glisse_batch_resume.restype = C.c_int
+    L.glisse_batch_sizes.argtypes = [vp, i64p, i32p]
+    L.glisse_batch_sizes.restype = C.c_int
     L.glisse_strerror.argtypes = [C.c_int]
     L.glisse_strerror.restype = C.c_char_p
     L.glisse_partition_device.argtypes = [C.c_int64, C.c_int64, vp, vp, vp, vp, vp, vp, vp]
@@ -354,6 +363,34 @@ def glisse_resume(buf, opts: glisse_opts | None = None):
     return h
 
 
+def glisse_batch_checkpoint(h) -> np.ndarray:
+    """The batch's checkpoint as a uint8 array (host bytes; see glisse_batch_resume)."""
+    L = load()
+    n = C.c_int64()
+    _check(L.glisse_batch_checkpoint_size(h, C.byref(n)), "glisse_batch_checkpoint_size")
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(L.glisse_batch_checkpoint(h, buf.ctypes.data, n.value), "glisse_batch_checkpoint")
+    return buf
+
+
+def glisse_batch_resume(buf, opts: glisse_opts | None = None):
+    """A new batch from a checkpoint (bytes or uint8 array); returns a handle.  Of opts only
+    cuda_stream and timing are used."""
+    b = np.ascontiguousarray(np.frombuffer(buf, dtype=np.uint8) if isinstance(buf, (bytes, bytearray)) else buf,
+                             dtype=np.uint8)
+    h = C.c_void_p()
+    rc = load().glisse_batch_resume(C.byref(h), b.ctypes.data, b.size, C.byref(opts) if opts is not None else None)
+    _check(rc, "glisse_batch_resume")
+    return h
+
+
+def glisse_batch_sizes(h):
+    """(number of particles, number of systems) of a batch."""
+    n, ns = C.c_int64(), C.c_int32()
+    _check(load().glisse_batch_sizes(h, C.byref(n), C.byref(ns)), "glisse_batch_sizes")
+    return n.value, ns.value
+
+
 def glisse_sizes(h):
     """(number of particles, number of planets) of a context."""
     n, npl = C.c_int64(), C.c_int32()
@@ -475,6 +512,7 @@ class BatchSimulation:
         for k, v in opt.items():
             setattr(o, k, v)
         self.n = int(np.sum(n_particles))
+        self.h = None
         self.h = glisse_batch_create(star_mass, n_planets, planets, n_particles, particles, dt, o)
 
     def advance(self, n_steps):
@@ -499,6 +537,24 @@ class BatchSimulation:
 
     def set_launch(self, block_threads, threads_per_particle=1):
         glisse_batch_set_launch(self.h, block_threads, threads_per_particle)
+
+    def checkpoint(self) -> np.ndarray:
+        """Everything needed to go on exactly from here (see BatchSimulation.resume)."""
+        return glisse_batch_checkpoint(self.h)
+
+    @classmethod
+    def resume(cls, buf, **opt):
+        """A BatchSimulation continuing from a checkpoint; opt may set cuda_stream and timing."""
+        o = glisse_opts_default()
+        for k, v in opt.items():
+            setattr(o, k, v)
+        self = cls.__new__(cls)
+        self.h = None
+        b = np.ascontiguousarray(np.frombuffer(buf, dtype=np.uint8) if isinstance(buf, (bytes, bytearray))
+                                 else buf, dtype=np.uint8)
+        self.h = glisse_batch_resume(b, o)
+        self.n = glisse_batch_sizes(self.h)[0]
+        return self
 
     def close(self):
         if self.h:

@@ -429,9 +429,8 @@ static int refresh_host_counts(glisse_batch* b) {
     return status;
 }
 
-static int batch_setup(glisse_batch* b, const double* star_mass, const int32_t* n_planets, const double* planets,
-                       const int64_t* n_particles, const double* particles, const double* dt) {
-    const int n = b->n_sys;
+// Stream (the caller's or an own one), SM count and timing events of a batch.
+static int batch_streams(glisse_batch* b) {
     GB_CUDA(cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking));
     b->own_s = true;
     if (b->o.cuda_stream) {
@@ -442,20 +441,16 @@ static int batch_setup(glisse_batch* b, const double* star_mass, const int32_t* 
     GB_CUDA(cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device));
     if (b->timing)
         for (auto& e : b->ev) GB_CUDA(cudaEventCreate(&e));
-    // internal order: decreasing planet count (stable)
-    std::vector<int64_t> pl_off(n + 1, 0), pa_off(n + 1, 0);
-    for (int i = 0; i < n; ++i) {
-        pl_off[i + 1] = pl_off[i] + n_planets[i];
-        pa_off[i + 1] = pa_off[i] + n_particles[i];
-    }
-    b->order.resize(n);
-    std::iota(b->order.begin(), b->order.end(), 0);
-    std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return n_planets[a] > n_planets[c]; });
-    b->np_host.resize(n);
-    for (int k = 0; k < n; ++k) b->np_host[k] = n_planets[b->order[k]];
+    return GLISSE_OK;
+}
+
+// Device buffers of a batch whose n_sys, np_host (internal order), C and n_total are
+// set; log_off receives each system's offset in the planet log (doubles).
+static int batch_alloc(glisse_batch* b, std::vector<int64_t>& log_off) {
+    const int n = b->n_sys;
     // buffers
     b->cap = std::max<int64_t>(b->n_total, 1);
-    std::vector<int64_t> log_off(n);
+    log_off.assign(n, 0);
     int64_t L = 0;
     for (int k = 0; k < n; ++k) {
         log_off[k] = L;
@@ -492,6 +487,28 @@ static int batch_setup(glisse_batch* b, const double* star_mass, const int32_t* 
     GB_ALLOC(b->d_steps, sizeof(unsigned long long));
     GB_CUDA(cudaMemsetAsync(b->d_steps, 0, sizeof(unsigned long long), b->s));
     GB_CUDA(cudaMemsetAsync(b->d_status, 0, sizeof(int) * (n + 1), b->s));
+    return GLISSE_OK;
+}
+
+static int batch_setup(glisse_batch* b, const double* star_mass, const int32_t* n_planets, const double* planets,
+                       const int64_t* n_particles, const double* particles, const double* dt) {
+    const int n = b->n_sys;
+    const int src = batch_streams(b);
+    if (src) return src;
+    // internal order: decreasing planet count (stable)
+    std::vector<int64_t> pl_off(n + 1, 0), pa_off(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        pl_off[i + 1] = pl_off[i] + n_planets[i];
+        pa_off[i + 1] = pa_off[i] + n_particles[i];
+    }
+    b->order.resize(n);
+    std::iota(b->order.begin(), b->order.end(), 0);
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return n_planets[a] > n_planets[c]; });
+    b->np_host.resize(n);
+    for (int k = 0; k < n; ++k) b->np_host[k] = n_planets[b->order[k]];
+    std::vector<int64_t> log_off;
+    int arc = batch_alloc(b, log_off);
+    if (arc) return arc;
 
     // planets: set-up kernel per system (constants, Jacobi state, encounter radii)
     std::vector<double> hpl(std::max<int64_t>(pl_off[n], 1) * 7);
@@ -854,4 +871,256 @@ extern "C" int glisse_batch_set_launch(glisse_batch* b, int32_t block_threads, i
     const int rc = set_launch_shape(b, block_threads, threads_per_particle);
     if (rc == GLISSE_OK) drop_graphs(b);
     return rc;
+}
+
+// ---- checkpoint / resume ----------------------------------------------------------
+// Buffer: a fixed header, then (each at an 8-byte offset) the internal system
+// order [n_sys] and planet counts [n_sys] (int32), the planet and particle
+// constants [n_sys], the steps dt [n_sys], the planets' Jacobi states
+// [n_sys][kMaxPlanets][6], the live particles per system [n_sys] (int64), the
+// particle slots [6][n_live], slot ids [n_live], slot flags [n_live], and the
+// per-id frozen states [n_total][6], removal steps and reasons.  Between calls
+// the planets and particles of every system are at the same step (the planet
+// chunks run inside each chunk), so the Jacobi states are the current ones.
+namespace {
+constexpr char kBCkptMagic[8] = {'G', 'L', 'I', 'S', 'S', 'E', 'B', 'K'};
+constexpr int32_t kBCkptVersion = 1;
+
+struct BCkptHeader {
+    char magic[8];
+    int32_t version, header_bytes;
+    int32_t n_sys, chunk_steps, threads, tpp, enc_mode, pad;
+    double enc_value, r_max;
+    int64_t n_total, n_live, step, total_bytes;
+    BatchClock clock;
+};
+
+struct BCkptLayout {
+    size_t order, np, pcs, ppcs, dt, jac, cnt, st, id, alive, out_state, out_step, out_reason, total;
+};
+
+BCkptLayout bckpt_layout(int n_sys, int64_t n_total, int64_t n_live) {
+    BCkptLayout L{};
+    size_t off = (sizeof(BCkptHeader) + 7) & ~size_t(7);
+    auto take = [&off](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 7) & ~size_t(7);
+        return o;
+    };
+    const size_t n = (size_t)n_sys;
+    L.order = take(sizeof(int32_t) * n);
+    L.np = take(sizeof(int32_t) * n);
+    L.pcs = take(sizeof(PlanetConsts) * n);
+    L.ppcs = take(sizeof(ParticleConsts) * n);
+    L.dt = take(sizeof(double) * n);
+    L.jac = take(sizeof(double) * 6 * kMaxPlanets * n);
+    L.cnt = take(sizeof(int64_t) * n);
+    L.st = take(sizeof(double) * 6 * (size_t)n_live);
+    L.id = take(sizeof(int32_t) * (size_t)n_live);
+    L.alive = take((size_t)n_live);
+    L.out_state = take(sizeof(double) * 6 * (size_t)n_total);
+    L.out_step = take(sizeof(int64_t) * (size_t)n_total);
+    L.out_reason = take(sizeof(int32_t) * (size_t)n_total);
+    L.total = off;
+    return L;
+}
+}  // namespace
+
+extern "C" int glisse_batch_sizes(glisse_batch* b, int64_t* n_particles, int32_t* n_systems) {
+    if (!b) return GLISSE_E_INVAL;
+    if (n_particles) *n_particles = b->n_total;
+    if (n_systems) *n_systems = b->n_sys;
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_batch_checkpoint_size(glisse_batch* b, int64_t* bytes) {
+    if (!b || !bytes) return GLISSE_E_INVAL;
+    *bytes = (int64_t)bckpt_layout(b->n_sys, b->n_total, b->n_live).total;
+    return GLISSE_OK;
+}
+
+extern "C" int glisse_batch_checkpoint(glisse_batch* b, void* buf, int64_t bytes) {
+    glisse::NvtxRange range("glisse_batch_checkpoint");
+    if (!b || !buf) return GLISSE_E_INVAL;
+    const int n = b->n_sys;
+    const BCkptLayout L = bckpt_layout(n, b->n_total, b->n_live);
+    if (bytes < (int64_t)L.total) return GLISSE_E_INVAL;
+    char* out = static_cast<char*>(buf);
+    std::memset(out, 0, L.total);  // the gaps between arrays too: equal batches, equal bytes
+    // live particles per system in the current layout, from the task table
+    int64_t* d_cnt = nullptr;
+    GB_ALLOC(d_cnt, sizeof(int64_t) * n);
+    cudaError_t e = cudaMemsetAsync(d_cnt, 0, sizeof(int64_t) * n, b->s);
+    if (e == cudaSuccess) {
+        batch_counts_from_tasks<<<2 * b->n_sm, 256, 0, b->s>>>(b->d_task_sys, b->d_task_count, b->d_n_tasks, d_cnt);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+    BCkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    auto d2h = [&](size_t off, const void* src, size_t nbytes) {
+        if (e == cudaSuccess && nbytes > 0) e = cudaMemcpy(out + off, src, nbytes, cudaMemcpyDeviceToHost);
+    };
+    d2h(L.cnt, d_cnt, sizeof(int64_t) * n);
+    d2h(L.pcs, b->d_pcs, sizeof(PlanetConsts) * n);
+    d2h(L.ppcs, b->d_ppcs, sizeof(ParticleConsts) * n);
+    d2h(L.dt, b->d_dt, sizeof(double) * n);
+    d2h(L.jac, b->d_jac, sizeof(double) * 6 * kMaxPlanets * n);
+    d2h(L.id, b->d_id[b->cur], sizeof(int32_t) * (size_t)b->n_live);
+    d2h(L.alive, b->d_alive, (size_t)b->n_live);
+    d2h(L.out_state, b->d_out_state, sizeof(double) * 6 * (size_t)b->n_total);
+    d2h(L.out_step, b->d_out_step, sizeof(int64_t) * (size_t)b->n_total);
+    d2h(L.out_reason, b->d_out_reason, sizeof(int32_t) * (size_t)b->n_total);
+    if (e == cudaSuccess && b->n_live > 0)
+        e = cudaMemcpy2D(out + L.st, sizeof(double) * (size_t)b->n_live, b->d_st[b->cur], sizeof(double) * b->cap,
+                         sizeof(double) * (size_t)b->n_live, 6, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&h.clock, b->d_clock, sizeof(BatchClock), cudaMemcpyDeviceToHost);
+    cudaFree(d_cnt);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GLISSE_E_CUDA;
+    }
+    std::vector<int32_t> np32(b->np_host.begin(), b->np_host.end());
+    std::memcpy(out + L.order, b->order.data(), sizeof(int32_t) * n);
+    std::memcpy(out + L.np, np32.data(), sizeof(int32_t) * n);
+    std::memcpy(h.magic, kBCkptMagic, sizeof(kBCkptMagic));
+    h.version = kBCkptVersion;
+    h.header_bytes = (int32_t)sizeof(BCkptHeader);
+    h.n_sys = n;
+    h.chunk_steps = b->C;
+    h.threads = b->threads;
+    h.tpp = b->tpp;
+    h.enc_mode = b->o.enc_mode;
+    h.enc_value = b->o.enc_value;
+    h.r_max = b->o.r_max;
+    h.n_total = b->n_total;
+    h.n_live = b->n_live;
+    h.step = b->step;
+    h.total_bytes = (int64_t)L.total;
+    std::memcpy(out, &h, sizeof(h));
+    return GLISSE_OK;
+}
+
+static int batch_restore(glisse_batch* b, const BCkptHeader& h, const char* in, const BCkptLayout& L) {
+    const int n = b->n_sys;
+    const int src = batch_streams(b);
+    if (src) return src;
+    b->order.resize(n);
+    std::memcpy(b->order.data(), in + L.order, sizeof(int32_t) * n);
+    std::vector<int32_t> np32(n);
+    std::memcpy(np32.data(), in + L.np, sizeof(int32_t) * n);
+    b->np_host.assign(np32.begin(), np32.end());
+    std::vector<int64_t> log_off;
+    const int arc = batch_alloc(b, log_off);
+    if (arc) return arc;
+    auto h2d = [&](void* dst, size_t off, size_t nbytes) {
+        return nbytes ? cudaMemcpyAsync(dst, in + off, nbytes, cudaMemcpyHostToDevice, b->s) : cudaSuccess;
+    };
+    GB_CUDA(h2d(b->d_pcs, L.pcs, sizeof(PlanetConsts) * n));
+    GB_CUDA(h2d(b->d_ppcs, L.ppcs, sizeof(ParticleConsts) * n));
+    GB_CUDA(h2d(b->d_np, L.np, sizeof(int32_t) * n));
+    GB_CUDA(h2d(b->d_dt, L.dt, sizeof(double) * n));
+    GB_CUDA(h2d(b->d_jac, L.jac, sizeof(double) * 6 * kMaxPlanets * n));
+    GB_CUDA(cudaMemcpyAsync(b->d_log_off, log_off.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, b->s));
+    GB_CUDA(h2d(b->d_cnt, L.cnt, sizeof(int64_t) * n));
+    if (h.n_live > 0) {
+        GB_CUDA(cudaMemcpy2DAsync(b->d_st[0], sizeof(double) * b->cap, in + L.st, sizeof(double) * (size_t)h.n_live,
+                                  sizeof(double) * (size_t)h.n_live, 6, cudaMemcpyHostToDevice, b->s));
+        GB_CUDA(h2d(b->d_id[0], L.id, sizeof(int32_t) * (size_t)h.n_live));
+        GB_CUDA(h2d(b->d_alive, L.alive, (size_t)h.n_live));
+    }
+    GB_CUDA(h2d(b->d_out_state, L.out_state, sizeof(double) * 6 * (size_t)b->n_total));
+    GB_CUDA(h2d(b->d_out_step, L.out_step, sizeof(int64_t) * (size_t)b->n_total));
+    GB_CUDA(h2d(b->d_out_reason, L.out_reason, sizeof(int32_t) * (size_t)b->n_total));
+    GB_CUDA(cudaMemcpyAsync(b->d_clock, &h.clock, sizeof(BatchClock), cudaMemcpyHostToDevice, b->s));
+    batch_tasks_kernel<<<1, 1024, 0, b->s>>>(n, b->d_cnt, b->d_task_sys, b->d_task_start, b->d_task_count,
+                                              b->d_n_tasks, b->d_nlive, nullptr, b->d_counter, b->d_clock, 0);
+    GB_CUDA(cudaGetLastError());
+    b->cur = 0;
+    b->step = h.step;
+    int rc = set_launch_shape(b, h.threads, h.tpp);
+    if (rc) return rc;
+    return refresh_host_counts(b);
+}
+
+extern "C" int glisse_batch_resume(glisse_batch** out, const void* buf, int64_t bytes, const glisse_opts* opts) {
+    glisse::NvtxRange range("glisse_batch_resume");
+    if (!out) return GLISSE_E_INVAL;
+    *out = nullptr;
+    if (!buf || bytes < (int64_t)sizeof(BCkptHeader)) return GLISSE_E_INVAL;
+    BCkptHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, kBCkptMagic, sizeof(kBCkptMagic)) != 0 || h.version != kBCkptVersion ||
+        h.header_bytes != (int32_t)sizeof(BCkptHeader))
+        return GLISSE_E_INVAL;
+    if (h.n_sys < 1 || h.chunk_steps < 1 || h.chunk_steps > (1 << 20)) return GLISSE_E_INVAL;
+    if (h.threads < 32 || h.threads > 256 || h.threads % 32 || (h.tpp != 1 && h.tpp != 2)) return GLISSE_E_INVAL;
+    if (h.enc_mode != GLISSE_ENC_HILL && h.enc_mode != GLISSE_ENC_FIXED) return GLISSE_E_INVAL;
+    if (!(h.enc_value >= 0.0) || !std::isfinite(h.enc_value) || !std::isfinite(h.r_max)) return GLISSE_E_INVAL;
+    if (h.n_total < 0 || h.n_total > INT32_MAX || h.n_live < 0 || h.n_live > h.n_total || h.step < 0 ||
+        h.clock.step != h.step || (h.clock.test_first != 0 && h.clock.test_first != 1))
+        return GLISSE_E_INVAL;
+    const BCkptLayout L = bckpt_layout(h.n_sys, h.n_total, h.n_live);
+    if (h.total_bytes != (int64_t)L.total || bytes < h.total_bytes) return GLISSE_E_INVAL;
+    const char* in = static_cast<const char*>(buf);
+    const int n = h.n_sys;
+    // the system order is a permutation, planet counts in range and matching the constants,
+    // live counts summing to the slots, every slot id a distinct particle (the kernels write
+    // per-id results through them)
+    {
+        std::vector<int32_t> order(n), np(n);
+        std::memcpy(order.data(), in + L.order, sizeof(int32_t) * n);
+        std::memcpy(np.data(), in + L.np, sizeof(int32_t) * n);
+        std::vector<bool> seen_sys(n, false);
+        int64_t sum = 0;
+        for (int k = 0; k < n; ++k) {
+            if (order[k] < 0 || order[k] >= n || seen_sys[order[k]]) return GLISSE_E_INVAL;
+            seen_sys[order[k]] = true;
+            if (np[k] < 0 || np[k] > GLISSE_MAX_PLANETS) return GLISSE_E_INVAL;
+            PlanetConsts pc;
+            std::memcpy(&pc, in + L.pcs + sizeof(PlanetConsts) * (size_t)k, sizeof(pc));
+            if (pc.np != np[k]) return GLISSE_E_INVAL;
+            int64_t c = 0;
+            std::memcpy(&c, in + L.cnt + sizeof(int64_t) * (size_t)k, sizeof(c));
+            if (c < 0) return GLISSE_E_INVAL;
+            sum += c;
+        }
+        if (sum != h.n_live) return GLISSE_E_INVAL;
+        std::vector<bool> seen((size_t)h.n_total, false);
+        for (int64_t k = 0; k < h.n_live; ++k) {
+            int32_t id = 0;
+            std::memcpy(&id, in + L.id + sizeof(int32_t) * (size_t)k, sizeof(id));
+            if (id < 0 || (int64_t)id >= h.n_total || seen[(size_t)id]) return GLISSE_E_INVAL;
+            seen[(size_t)id] = true;
+        }
+    }
+    glisse_opts o;
+    glisse_opts_default(&o);
+    o.chunk_steps = h.chunk_steps;
+    o.enc_mode = h.enc_mode;
+    o.enc_value = h.enc_value;
+    o.r_max = h.r_max;
+    if (opts) {
+        o.cuda_stream = opts->cuda_stream;
+        o.timing = opts->timing;
+    }
+    glisse_batch* b = new (std::nothrow) glisse_batch();
+    if (!b) return GLISSE_E_NOMEM;
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete b;
+        return GLISSE_E_CUDA;
+    }
+    b->o = o;
+    b->n_sys = n;
+    b->C = h.chunk_steps;
+    b->n_total = h.n_total;
+    b->timing = o.timing != 0;
+    const int rc = batch_restore(b, h, in, L);
+    if (rc != GLISSE_OK) {
+        batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return GLISSE_OK;
 }

@@ -133,6 +133,9 @@ def test_null_handles_are_rejected(G):
         lambda: L.glisse_checkpoint_size(None, None),
         lambda: L.glisse_checkpoint(None, None, 0),
         lambda: L.glisse_sizes(None, None, None),
+        lambda: L.glisse_batch_checkpoint_size(None, None),
+        lambda: L.glisse_batch_checkpoint(None, None, 0),
+        lambda: L.glisse_batch_sizes(None, None, None),
     ]
     for k, call in enumerate(calls):
         assert call() == E, k
@@ -179,3 +182,9 @@ def test_resume_rejects_what_is_not_a_checkpoint(G):
     with pytest.raises(G.GlisseError) as ei:
         G.glisse_resume(bytes(64))
     assert ei.value.code == E
+    # the batched resume, and neither accepts the other's checkpoints' magic
+    assert L.glisse_batch_resume(None, None, 0, None) == E
+    for buf in (b"", b"GLISSEBK" + bytes(4088), b"GLISSECK" + bytes(4088), np.random.default_rng(1).bytes(4096)):
+        arr = np.frombuffer(buf, dtype=np.uint8).copy() if buf else np.zeros(1, dtype=np.uint8)
+        assert L.glisse_batch_resume(C.byref(h), arr.ctypes.data, len(buf), None) == E
+        assert not h.value

@@ -10,7 +10,8 @@ create (the removal test at t_0 still to come), with removals, a compaction
 interval of several chunks, the cost-sorted particle order and the paper's
 fixed-iteration solver.  A checkpoint taken right after resume equals the
 one resumed from, byte for byte.  Buffers that are not checkpoints, or hold
-an id outside the particle range, are rejected.
+an id outside the particle range, are rejected.  Batches of independent
+systems resume the same way (graph-replayed or timed chunks, lane pairs).
 """
 import numpy as np
 import pytest
@@ -181,3 +182,63 @@ def test_empty_and_planet_free_checkpoints(G):
         got = _snapshot(b)
         b.close()
         _assert_identical(ref, got)
+
+
+# ---------------------------------------------------------------------------
+# batches of independent systems
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("first,second,chunk,shape,timing", [
+    (300, 700, 256, None, 0),       # mid-chunk, graph-replayed chunks
+    (0, 500, 128, None, 0),         # before the first step: the removal test at t_0 pending
+    (512, 512, 256, (64, 2), 1),    # lane pairs, 64-thread blocks; the resumed batch times its launches
+])
+def test_batch_resume_continues_bit_for_bit(G, first, second, chunk, shape, timing):
+    b = gi.make_batched(seed=4, n_systems=12, n_max=4096)
+    args = (b["star_mass"], b["n_planets"], b["planets"], b["n_particles"], b["particles"], b["dt"])
+    a = G.BatchSimulation(*args, chunk_steps=chunk)
+    if shape:
+        a.set_launch(*shape)
+    if first:
+        a.advance(first)
+    ck = a.checkpoint()
+    a.advance(second)
+    ref, ref_status = a.read(), a.status()
+    a.close()
+
+    r = G.BatchSimulation.resume(ck, timing=timing)
+    assert r.n == a.n == int(np.sum(b["n_particles"]))
+    assert np.array_equal(r.checkpoint(), ck)  # nothing lost or changed on the way in
+    r.advance(second)
+    got, got_status = r.read(), r.status()
+    r.close()
+    for k in ("state", "alive", "removal_step", "removal_reason"):
+        assert np.array_equal(ref[k], got[k], equal_nan=True), k
+    assert ref_status == got_status
+
+
+def test_batch_checkpoint_errors(G):
+    import ctypes as C
+
+    L = G.load()
+    b = gi.make_batched(seed=4, n_systems=6, n_max=2048)
+    sim = G.BatchSimulation(b["star_mass"], b["n_planets"], b["planets"], b["n_particles"], b["particles"],
+                            b["dt"], chunk_steps=128)
+    sim.advance(200)
+    ck = sim.checkpoint()
+    small = np.empty(ck.size - 1, dtype=np.uint8)
+    assert L.glisse_batch_checkpoint(sim.h, small.ctypes.data, small.size) == G.GLISSE_E_INVAL
+    sim.close()
+    h = C.c_void_p()
+    assert L.glisse_batch_resume(C.byref(h), ck.ctypes.data, ck.size - 1, None) == G.GLISSE_E_INVAL
+    for pos in (0, 8):  # magic, version
+        bad = ck.copy()
+        bad[pos] ^= 0xFF
+        assert L.glisse_batch_resume(C.byref(h), bad.ctypes.data, bad.size, None) == G.GLISSE_E_INVAL
+    # a single-system checkpoint is not a batch checkpoint, nor the reverse
+    w = gi.make("tiny", n=64)
+    s1 = G.Simulation(w["star_mass"], w["planets"], w["particles"], w["dt"])
+    ck1 = s1.checkpoint()
+    s1.close()
+    assert L.glisse_batch_resume(C.byref(h), ck1.ctypes.data, ck1.size, None) == G.GLISSE_E_INVAL
+    assert L.glisse_resume(C.byref(h), ck.ctypes.data, ck.size, None) == G.GLISSE_E_INVAL
+    assert not h.value
