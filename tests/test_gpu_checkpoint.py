@@ -242,3 +242,34 @@ def test_batch_checkpoint_errors(G):
     assert L.glisse_batch_resume(C.byref(h), ck1.ctypes.data, ck1.size, None) == G.GLISSE_E_INVAL
     assert L.glisse_resume(C.byref(h), ck.ctypes.data, ck.size, None) == G.GLISSE_E_INVAL
     assert not h.value
+
+
+def test_continuation_with_libration_detection(G):
+    """The paper's continuation runs: a long run, then more steps that log elements and test
+    libration (section 4.2.2).  A resumed context that starts sampling gives the same
+    elements, sample steps and libration flags as the original context sampling from the
+    same step, bit for bit (the sampled planet states come from the recomputed chunk)."""
+    w = gi.make("tiny", n=512)
+    samp = dict(max_samples=12, res_planet=3, res_p=3, res_q=2, avoid_deg=10.0)
+    a = G.Simulation(w["star_mass"], w["planets"], w["particles"], w["dt"], chunk_steps=128)
+    a.advance(1000)
+    ck = a.checkpoint()
+    a.set_sampling(20, **samp)
+    a.advance(230)
+    ref_el, ref_steps = a.elements()
+    ref_lib = a.libration()
+    ref = _snapshot(a)
+    a.close()
+
+    b = G.Simulation.resume(ck)
+    b.set_sampling(20, **samp)
+    b.advance(230)
+    el, steps = b.elements()
+    lib = b.libration()
+    got = _snapshot(b)
+    b.close()
+    assert len(steps) == 11 and np.array_equal(steps, ref_steps)
+    assert np.array_equal(el, ref_el, equal_nan=True)
+    for k in ref_lib:
+        assert np.array_equal(np.asarray(lib[k]), np.asarray(ref_lib[k])), k
+    _assert_identical(ref, got)
