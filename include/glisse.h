@@ -198,8 +198,10 @@ int glisse_timings(glisse_ctx* ctx, glisse_timing* out, int32_t reset);
  * start of the current planet chunk (the chunk is recomputed on resume, bit
  * for bit), the step counter, and the particle arrays as laid out on the device
  * (so warps keep their members), with every removed particle's frozen state,
- * step and reason.  A context resumed from it and advanced gives results
- * identical to the original context advanced by the same calls.
+ * step and reason, and, when element sampling is set, its settings, the kept
+ * samples and the libration flags and counts.  A context resumed from it and
+ * advanced gives results identical to the original context advanced by the
+ * same calls.
  *
  * glisse_checkpoint_size: *bytes receives the size of a checkpoint of ctx now.
  * glisse_checkpoint: write it to the caller's host buffer `buf` of `bytes`
@@ -211,9 +213,8 @@ int glisse_timings(glisse_ctx* ctx, glisse_timing* out, int32_t reset);
  * The buffer is plain bytes in the byte order of the machine that wrote it
  * (little-endian on every supported host).
  * Errors: INVAL (NULL pointers, a buffer too small, or not a checkpoint of this
- *   format: wrong magic, version or inconsistent sizes), STATE (element
- *   sampling set, or an external ephemeris installed: neither is saved),
- *   NOMEM, CUDA.
+ *   format: wrong magic, version or inconsistent sizes), STATE (an external
+ *   ephemeris installed: it is not saved), NOMEM, CUDA.
  */
 int glisse_checkpoint_size(glisse_ctx* ctx, int64_t* bytes);
 int glisse_checkpoint(glisse_ctx* ctx, void* buf, int64_t bytes);

@@ -619,8 +619,11 @@ class Simulation:
         self.max_samples = int(kw.get("max_samples", 0)) if every is not None else 0
         glisse_set_sampling(self.h, every, **kw)
 
-    def elements(self):
-        return glisse_read_elements(self.h, self.n, getattr(self, "max_samples", 0))
+    def elements(self, max_samples=None):
+        """(elements [k][n][6], sample steps [k]) of the kept samples; max_samples bounds k (default:
+        the max_samples given to set_sampling on this object; pass it for a resumed context)."""
+        k = getattr(self, "max_samples", 0) if max_samples is None else int(max_samples)
+        return glisse_read_elements(self.h, self.n, k)
 
     def libration(self):
         return glisse_read_libration(self.h, self.n)

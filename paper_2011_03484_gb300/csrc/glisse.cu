@@ -940,7 +940,9 @@ extern "C" int glisse_read_planets(glisse_ctx* c, double* planets, double* t) {
 // Checkpoint / resume.  Buffer: a fixed header, then the arrays, each at an
 // 8-byte offset: the chunk-start Jacobi state [np][6], the particle slots
 // [6][n_live], the per-id frozen states [n_total][6], removal steps [n_total],
-// slot ids [n_live], reasons [n_total], slot flags [n_live].
+// slot ids [n_live], reasons [n_total], slot flags [n_live]; with element
+// sampling set, the kept samples' steps [kept] and elements [kept][n_total][6]
+// and the libration flags and counts [n_total].
 // ---------------------------------------------------------------------------
 namespace {
 constexpr char kCkptMagic[8] = {'G', 'L', 'I', 'S', 'S', 'E', 'C', 'K'};
@@ -957,13 +959,17 @@ struct CkptHeader {
     int64_t n_total, n_live, step, since_compact;
     int64_t total_bytes;
     PlanetConsts pc;
+    // element sampling (glisse_set_sampling): on or off, its settings, samples taken and kept
+    int32_t samp_on, pad2;
+    int64_t samp_seen, samp_kept;
+    glisse_sampling samp;
 };
 
 struct CkptLayout {
-    size_t jac0, st, out_state, out_step, id, out_reason, alive, total;
+    size_t jac0, st, out_state, out_step, id, out_reason, alive, samp_steps, elem, near0, near180, count, total;
 };
 
-CkptLayout ckpt_layout(int np, int64_t n_total, int64_t n_live) {
+CkptLayout ckpt_layout(int np, int64_t n_total, int64_t n_live, bool samp_on = false, int64_t kept = 0) {
     CkptLayout L{};
     size_t off = (sizeof(CkptHeader) + 7) & ~size_t(7);
     auto take = [&off](size_t bytes) {
@@ -978,13 +984,23 @@ CkptLayout ckpt_layout(int np, int64_t n_total, int64_t n_live) {
     L.id = take(sizeof(int32_t) * (size_t)n_live);
     L.out_reason = take(sizeof(int32_t) * (size_t)n_total);
     L.alive = take((size_t)n_live);
+    const size_t ns = samp_on ? (size_t)n_total : 0;
+    L.samp_steps = take(sizeof(int64_t) * (samp_on ? (size_t)kept : 0));
+    L.elem = take(sizeof(double) * 6 * ns * (samp_on ? (size_t)kept : 0));
+    L.near0 = take(ns);
+    L.near180 = take(ns);
+    L.count = take(sizeof(int32_t) * ns);
     L.total = off;
     return L;
 }
 
 int ckpt_state_ok(const glisse_ctx* c) {
-    if (c->samp_on || c->external || !c->planets_valid) return GLISSE_E_STATE;
+    if (c->external || !c->planets_valid) return GLISSE_E_STATE;
     return GLISSE_OK;
+}
+
+CkptLayout ckpt_layout_of(const glisse_ctx* c) {
+    return ckpt_layout(c->np, c->n_total, c->n_live, c->samp_on, (int64_t)c->samp_steps.size());
 }
 }  // namespace
 
@@ -999,7 +1015,7 @@ extern "C" int glisse_checkpoint_size(glisse_ctx* c, int64_t* bytes) {
     if (!c || !bytes) return GLISSE_E_INVAL;
     const int st = ckpt_state_ok(c);
     if (st != GLISSE_OK) return st;
-    *bytes = (int64_t)ckpt_layout(c->np, c->n_total, c->n_live).total;
+    *bytes = (int64_t)ckpt_layout_of(c).total;
     return GLISSE_OK;
 }
 
@@ -1007,7 +1023,7 @@ extern "C" int glisse_checkpoint(glisse_ctx* c, void* buf, int64_t bytes) {
     if (!c || !buf) return GLISSE_E_INVAL;
     const int st = ckpt_state_ok(c);
     if (st != GLISSE_OK) return st;
-    const CkptLayout L = ckpt_layout(c->np, c->n_total, c->n_live);
+    const CkptLayout L = ckpt_layout_of(c);
     if (bytes < (int64_t)L.total) return GLISSE_E_INVAL;
     int prev = 0;
     cudaGetDevice(&prev);
@@ -1040,6 +1056,18 @@ extern "C" int glisse_checkpoint(glisse_ctx* c, void* buf, int64_t bytes) {
             e = cudaMemcpy(out + L.out_step, c->d_out_step, sizeof(int64_t) * (size_t)N, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess && N > 0)
             e = cudaMemcpy(out + L.out_reason, c->d_out_reason, sizeof(int32_t) * (size_t)N, cudaMemcpyDeviceToHost);
+        if (c->samp_on && N > 0) {
+            const size_t kept = c->samp_steps.size();
+            if (kept > 0) std::memcpy(out + L.samp_steps, c->samp_steps.data(), sizeof(int64_t) * kept);
+            if (e == cudaSuccess && kept > 0)
+                e = cudaMemcpy(out + L.elem, c->d_elem, sizeof(double) * 6 * (size_t)N * kept, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(out + L.near0, c->d_near0, (size_t)N, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(out + L.near180, c->d_near180, (size_t)N, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(out + L.count, c->d_count, sizeof(int32_t) * (size_t)N, cudaMemcpyDeviceToHost);
+        } else if (c->samp_on && !c->samp_steps.empty()) {
+            std::memcpy(out + L.samp_steps, c->samp_steps.data(), sizeof(int64_t) * c->samp_steps.size());
+        }
         if (rc == GLISSE_OK && e != cudaSuccess) {
             (void)cudaGetLastError();
             rc = GLISSE_E_CUDA;
@@ -1069,6 +1097,12 @@ extern "C" int glisse_checkpoint(glisse_ctx* c, void* buf, int64_t bytes) {
         h.since_compact = c->since_compact;
         h.total_bytes = (int64_t)L.total;
         h.pc = c->hpc;
+        h.samp_on = c->samp_on ? 1 : 0;
+        if (c->samp_on) {
+            h.samp = c->samp;
+            h.samp_seen = c->samp_seen;
+            h.samp_kept = (int64_t)c->samp_steps.size();
+        }
         std::memcpy(out, &h, sizeof(h));
     }
     if (prev != c->device) cudaSetDevice(prev);
@@ -1095,7 +1129,11 @@ extern "C" int glisse_resume(glisse_ctx** out, const void* buf, int64_t bytes, c
     if (h.enc_mode != GLISSE_ENC_HILL && h.enc_mode != GLISSE_ENC_FIXED) return GLISSE_E_INVAL;
     if (h.sort_mode != GLISSE_SORT_NONE && h.sort_mode != GLISSE_SORT_COST) return GLISSE_E_INVAL;
     if (!(h.enc_value >= 0.0) || !std::isfinite(h.enc_value) || !std::isfinite(h.r_max)) return GLISSE_E_INVAL;
-    const CkptLayout L = ckpt_layout(h.np, h.n_total, h.n_live);
+    if (h.samp_on != 0 && h.samp_on != 1) return GLISSE_E_INVAL;
+    if (h.samp_on && (h.samp.max_samples < 0 || (uint64_t)h.samp.max_samples > (uint64_t)1 << 40 ||
+                      h.samp_kept < 0 || h.samp_kept > h.samp.max_samples || h.samp_seen < h.samp_kept))
+        return GLISSE_E_INVAL;
+    const CkptLayout L = ckpt_layout(h.np, h.n_total, h.n_live, h.samp_on != 0, h.samp_on ? h.samp_kept : 0);
     if (h.total_bytes != (int64_t)L.total || bytes < h.total_bytes) return GLISSE_E_INVAL;
     const char* in = static_cast<const char*>(buf);
     // every slot id must name a distinct particle: the kernels write per-id outputs through them
@@ -1150,7 +1188,30 @@ extern "C" int glisse_resume(glisse_ctx** out, const void* buf, int64_t bytes, c
     r.since_compact = h.since_compact;
     r.tested_first = h.tested_first != 0;
     NvtxRange range("glisse_resume");
-    const int rc = setup(c, nullptr, nullptr, &r);
+    int rc = setup(c, nullptr, nullptr, &r);
+    if (rc == GLISSE_OK && h.samp_on) {
+        // sampling as it was: settings (validated as glisse_set_sampling does), kept
+        // samples, libration flags and counts
+        rc = glisse_set_sampling(c, &h.samp);
+        const size_t N = (size_t)c->n_total, kept = (size_t)h.samp_kept;
+        cudaError_t e = cudaSuccess;
+        if (rc == GLISSE_OK && N > 0) {
+            if (kept > 0)
+                e = cudaMemcpy(c->d_elem, in + L.elem, sizeof(double) * 6 * N * kept, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(c->d_near0, in + L.near0, N, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(c->d_near180, in + L.near180, N, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(c->d_count, in + L.count, sizeof(int32_t) * N, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                rc = GLISSE_E_CUDA;
+            }
+        }
+        if (rc == GLISSE_OK) {
+            c->samp_steps.resize(kept);
+            if (kept > 0) std::memcpy(c->samp_steps.data(), in + L.samp_steps, sizeof(int64_t) * kept);
+            c->samp_seen = h.samp_seen;
+        }
+    }
     if (rc != GLISSE_OK) {
         ctx_free(c);
         return rc;

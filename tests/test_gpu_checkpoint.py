@@ -154,12 +154,8 @@ def test_checkpoint_errors(G):
         bad[off + 4 * k: off + 4 * k + 4] = np.frombuffer(np.int32(v).tobytes(), dtype=np.uint8)
         assert L.glisse_resume(C.byref(h), bad.ctypes.data, bad.size, None) == G.GLISSE_E_INVAL, v
     assert not h.value
-    # state that a checkpoint does not hold
-    sim.set_sampling(32, max_samples=4)
-    with pytest.raises(G.GlisseError) as ei:
-        sim.checkpoint()
-    assert ei.value.code == G.GLISSE_E_STATE
     sim.close()
+    # state that a checkpoint does not hold: an external ephemeris
     sim = G.Simulation(w["star_mass"], w["planets"], w["particles"], w["dt"], chunk_steps=64)
     sim.set_ephemeris(np.tile(w["planets"][:, 1:4], (11, 1, 1)))
     with pytest.raises(G.GlisseError) as ei:
@@ -272,4 +268,32 @@ def test_continuation_with_libration_detection(G):
     assert np.array_equal(el, ref_el, equal_nan=True)
     for k in ref_lib:
         assert np.array_equal(np.asarray(lib[k]), np.asarray(ref_lib[k])), k
+    _assert_identical(ref, got)
+
+
+def test_checkpoint_while_sampling(G):
+    """A checkpoint taken between samples carries the sampling: the resumed context's
+    elements, sample steps and libration flags over the whole run equal the original's."""
+    w = gi.make("tiny", n=512)
+    samp = dict(max_samples=9, res_planet=3, res_p=3, res_q=2, avoid_deg=10.0)
+    a = G.Simulation(w["star_mass"], w["planets"], w["particles"], w["dt"], chunk_steps=128)
+    a.set_sampling(25, **samp)
+    a.advance(130)
+    ck = a.checkpoint()
+    a.advance(200)  # 13 samples in all: 9 kept, every one counted by the libration test
+    ref_el, ref_steps = a.elements()
+    ref_lib = a.libration()
+    ref = _snapshot(a)
+    a.close()
+    b = G.Simulation.resume(ck)
+    b.advance(200)
+    el, steps = b.elements(samp["max_samples"])
+    lib = b.libration()
+    got = _snapshot(b)
+    b.close()
+    assert len(steps) == 9 and np.array_equal(steps, ref_steps)
+    assert np.array_equal(el, ref_el, equal_nan=True)
+    for k in ref_lib:
+        assert np.array_equal(np.asarray(lib[k]), np.asarray(ref_lib[k])), k
+    assert int(np.asarray(ref_lib["count"]).max()) == 13
     _assert_identical(ref, got)
