@@ -228,6 +228,37 @@ def reference_arm(args):
     return 0
 
 
+def time_batched(G, torch, dev, stream, b, C, steps, warmup, tune=False):
+    """W untimed chunks, then `steps` graph-replayed chunks of the batch, each bracketed by CUDA
+    events with an L2 flush outside them; exact particle-steps from the device counter."""
+    args_b = (b["star_mass"], b["n_planets"], b["planets"], b["n_particles"], b["particles"], b["dt"])
+    sim = G.BatchSimulation(*args_b, chunk_steps=C, cuda_stream=stream.cuda_stream)
+    tuned = sim.tune(256) if tune else None
+    C_run = tuned[0] if tuned else C
+    for _ in range(warmup):
+        sim.advance(C_run)
+    torch.cuda.synchronize(dev)
+    live0 = sim.status()[0]
+    steps0 = sim.steps_done()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    with ClockSampler(dev.index or 0) as clocks:
+        for k in range(steps):
+            flush.zero_()
+            starts[k].record(stream)
+            sim.advance(C_run)
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+    done = sim.steps_done() - steps0  # exact: each particle counts the steps it advanced
+    total_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+    live1 = sim.status()[0]
+    sim.close()
+    del flush
+    return {"value": done / (total_ms * 1e-3), "total_ms": total_ms, "clocks": clocks.summary(), "live0": live0,
+            "live1": live1, "tuned": tuned, "C_run": C_run, "args_b": args_b}
+
+
 def batched_arm(args):
     """256 independent systems (N_p 2..8, ~3.4e6 particles, dt = P_inner / 20) in one
     context: planet chunks of all systems, the persistent particle kernel, compaction
@@ -246,30 +277,9 @@ def batched_arm(args):
     b = gi.make_batched(seed=4 + 1000 * rank, n_systems=args.batched_systems)
     C = 1024
     stream = torch.cuda.current_stream(dev)
-    args_b = (b["star_mass"], b["n_planets"], b["planets"], b["n_particles"], b["particles"], b["dt"])
-    sim = G.BatchSimulation(*args_b, chunk_steps=C, cuda_stream=stream.cuda_stream)
-    tuned = sim.tune(256) if args.tune else None
-    C_run = tuned[0] if tuned else C
-    for _ in range(args.warmup):
-        sim.advance(C_run)
-    torch.cuda.synchronize(dev)
-    live0 = sim.status()[0]
-    steps0 = sim.steps_done()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    with ClockSampler(dev.index or 0) as clocks:
-        for k in range(args.steps):
-            flush.zero_()
-            starts[k].record(stream)
-            sim.advance(C_run)
-            ends[k].record(stream)
-        torch.cuda.synchronize(dev)
-    done = sim.steps_done() - steps0  # exact: each particle counts the steps it advanced
-    total_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
-    live1 = sim.status()[0]
-    sim.close()
-    value = done / (total_ms * 1e-3)
+    rb = time_batched(G, torch, dev, stream, b, C, args.steps, args.warmup, tune=args.tune)
+    value, total_ms, tuned, C_run, args_b = rb["value"], rb["total_ms"], rb["tuned"], rb["C_run"], rb["args_b"]
+    live0, live1 = rb["live0"], rb["live1"]
     # per-stage device times from a timing-mode copy (direct launches with events)
     simt = G.BatchSimulation(*args_b, chunk_steps=C_run, timing=1, cuda_stream=stream.cuda_stream)
     if tuned:
@@ -321,10 +331,9 @@ def batched_arm(args):
     if rank == 0 and not args.no_cpu_baseline:
         cpu = batched_cpu_baseline(b, C_run)
 
-    csum = clocks.summary()
+    csum = rb["clocks"]
     mhz = csum["sm_mhz"] if csum else 2070.0
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    dfma_peak = n_sm * DFMA_PER_CLK_PER_SM * mhz * 1e6
+    n_sm, dfma_peak = fp64_peak(torch, dev, mhz)
     w_np = float(np.sum(b["n_planets"] * b["n_particles"]) / np.sum(b["n_particles"]))
     kernel_ms = tm["particle_ms"] / max(tm["particle_launches"], 1)
     spl = tm["particle_steps"] / max(tm["particle_launches"], 1)
@@ -388,28 +397,20 @@ def batched_cpu_baseline(b, n_steps, n_sys=64, per_sys=2048, seed=0):
                       f"{n_steps} steps each ({busy:.1f} s wall on {cores} threads)"}
 
 
-def diff_arm(args):
+def time_diff(G, torch, dev, stream, n_particles=0, n_steps=0, K=256):
     """Differentiation workload: 65536 particles (a 22-28 AU, e < 0.05, sigma_i 1 deg),
-    10^4 steps, checkpoints every 256 steps.  Times the plain map, the differentiable
-    forward pass (without and with one tangent vector) and the adjoint pass, and
-    reports each as particle-steps/s and as a cost ratio to the plain map."""
-    import numpy as np
-    import torch
-
+    10^4 steps (n_steps > 0: fewer), checkpoints every K steps.  Times the plain map, the
+    differentiable forward pass (without and with one tangent vector), the adjoint pass, the
+    growth gradient and tape mode, and returns each as particle-steps/s and as a cost ratio
+    to the plain map."""
     import glisse_inputs as gi
-    import paper_2011_03484_gb300 as G
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    G._build.build()
-    G.load()
     w = gi.WORKLOADS["diff"]
     full = gi.make("diff")
     pl, s0 = full["planets"], full["particles"]
-    if args.diff_particles > 0:
-        s0 = s0[: args.diff_particles]  # a prefix of the same seeded set (small cases for ncu)
-    n, n_steps, K = s0.shape[0], (args.diff_steps if args.diff_steps > 0 else w.n_steps), 256
-    stream = torch.cuda.current_stream(dev)
+    if n_particles > 0:
+        s0 = s0[:n_particles]  # a prefix of the same seeded set (small cases for ncu)
+    n, n_steps = s0.shape[0], (n_steps if n_steps > 0 else w.n_steps)
 
     def timed(fn):
         torch.cuda.synchronize(dev)
@@ -474,8 +475,201 @@ def diff_arm(args):
                                     "forward_plus_adjoint": (ms_fwd + ms_bwd) / ms_map},
         "tape_mode": tape,
     }
+    return line
+
+
+def diff_arm(args):
+    import torch
+
+    import paper_2011_03484_gb300 as G
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    G._build.build()
+    G.load()
+    line = time_diff(G, torch, dev, torch.cuda.current_stream(dev), args.diff_particles, args.diff_steps)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def time_single(G, torch, dev, stream, w, planets, particles, steps, warmup, kmode=0, kepler_iters=5, sort=False,
+                sample_every=0, one_call=False, dist=None):
+    """W untimed chunks, then `steps` chunks of w.chunk steps, each bracketed by CUDA events on the
+    library's stream with an L2 flush (256 MiB write) outside the events; clocks sampled during
+    the timed region.  Returns the handle (caller destroys it) and the measurements."""
+    np_ = planets.shape[0]
+    o = G.glisse_opts_default()
+    o.chunk_steps = w.chunk
+    o.resync_chunks = w.resync
+    o.enc_value = w.k_hill
+    o.r_max = w.r_max
+    o.timing = 1
+    o.cuda_stream = stream.cuda_stream
+    o.kepler_mode = kmode
+    o.kepler_iters = kepler_iters
+    o.sort_mode = G.GLISSE_SORT_COST if sort else G.GLISSE_SORT_NONE
+    h = G.glisse_create(w.star_mass, planets, particles, w.dt, o)
+    if sample_every > 0:
+        G.glisse_set_sampling(h, sample_every, frame=G.GLISSE_FRAME_BARY, max_samples=0, res_planet=np_ - 1,
+                              res_p=3, res_q=2, avoid_deg=10.0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(warmup):
+        G.glisse_advance(h, w.chunk)
+    torch.cuda.synchronize(dev)
+    G.glisse_timings(h, reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    live_before = G.glisse_status(h)[0]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    chunk_live, chunk_steps = [], []  # host-side counters, read between chunks (no GPU work)
+    with ClockSampler(dev.index or 0) as clocks:
+        t_wall0 = time.perf_counter()
+        if one_call:
+            # the whole timed run as one glisse_advance call (the planets may run ahead of
+            # the particles up to its last chunk)
+            flush.zero_()
+            chunk_live.append(G.glisse_status(h)[0])
+            starts[0].record(stream)
+            G.glisse_advance(h, w.chunk * steps)
+            ends[0].record(stream)
+            chunk_steps.append(G.glisse_timings(h)["particle_steps"])
+            starts, ends = starts[:1], ends[:1]
+        else:
+            for k in range(steps):
+                flush.zero_()
+                chunk_live.append(G.glisse_status(h)[0])
+                starts[k].record(stream)
+                G.glisse_advance(h, w.chunk)
+                ends[k].record(stream)
+                chunk_steps.append(G.glisse_timings(h)["particle_steps"])
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall0
+    if dist:
+        dist.barrier()
+    del flush
+    step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
+    tm = G.glisse_timings(h)
+    return h, {"step_ms": step_ms, "total_ms": sum(step_ms), "chunk_live": chunk_live, "chunk_steps": chunk_steps,
+               "tm": tm, "live_before": live_before, "live_after": G.glisse_status(h)[0],
+               "clocks": clocks.summary(), "t_wall": t_wall}
+
+
+def fp64_peak(torch, dev, mhz):
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    return n_sm, n_sm * DFMA_PER_CLK_PER_SM * mhz * 1e6
+
+
+def belt_record(G, torch, dev, stream, steps=5, warmup=3):
+    """A few chunks of the 1048576-particle resonant belt (a in 40-50 AU, e < 0.4), in the
+    benchmark's launch configuration: particle-steps/s and the particle kernel's FP64 fraction."""
+    import glisse_inputs as gi
+
+    w = gi.WORKLOADS["belt"]
+    full = gi.make("belt")
+    h, r = time_single(G, torch, dev, stream, w, full["planets"], full["particles"], steps, warmup)
+    G.glisse_destroy(h)
+    tm = r["tm"]
+    mhz = r["clocks"]["sm_mhz"] if r["clocks"] else 2070.0
+    _, dfma_peak = fp64_peak(torch, dev, mhz)
+    kernel_ms = tm["particle_ms"] / max(tm["particle_launches"], 1)
+    spl = tm["particle_steps"] / max(tm["particle_launches"], 1)
+    np_ = full["planets"].shape[0]
+    return {"workload": workload_desc(w, w.n), "steps": steps, "warmup": warmup,
+            "value": tm["particle_steps"] / (r["total_ms"] * 1e-3), "unit": UNIT,
+            "ms_per_step": r["total_ms"] / steps, "live_at_start": r["live_before"], "live_at_end": r["live_after"],
+            "frac": flop_per_step(np_) * spl / (kernel_ms * 1e-3) / (2.0 * dfma_peak),
+            "fp64_pipe_frac": fp64_instr_per_step(np_) * spl / (kernel_ms * 1e-3) / dfma_peak,
+            "kernel_ms_avg": kernel_ms, "clocks": r["clocks"]}
+
+
+def batched_record(G, torch, dev, stream, plain_value, steps=3, warmup=3):
+    """A few chunks of the 256-system batched workload (graph-replayed chunks, default launch
+    shape): particle-steps/s and its per-particle-step cost against the plain map's."""
+    import numpy as np
+
+    import glisse_inputs as gi
+
+    b = gi.make_batched()
+    r = time_batched(G, torch, dev, stream, b, 1024, steps, warmup)
+    mhz = r["clocks"]["sm_mhz"] if r["clocks"] else 2070.0
+    _, dfma_peak = fp64_peak(torch, dev, mhz)
+    w_np = float(np.sum(b["n_planets"] * b["n_particles"]) / np.sum(b["n_particles"]))
+    flop = flop_per_step(0) + (flop_per_step(1) - flop_per_step(0)) * w_np
+    return {"workload": f"batched: {len(b['star_mass'])} systems, N_p 2..8, {int(b['n_particles'].sum())} particles, "
+                        f"dt = P_inner/20, chunk 1024, one graph per chunk",
+            "steps": steps, "warmup": warmup, "value": r["value"], "unit": UNIT, "ms_per_step": r["total_ms"] / steps,
+            "frac_of_chunk_time": flop * r["value"] / (2.0 * dfma_peak),
+            "cost_ratio_to_plain_map": plain_value / r["value"], "clocks": r["clocks"]}
+
+
+def diff_record(G, torch, dev, stream, n_steps=2048, K=256):
+    """The differentiation workload (65536 particles) over a reduced number of steps: the plain
+    map, the differentiable forward pass, the adjoint pass (checkpoints every K steps, and tape
+    mode), the growth gradient; each as a cost ratio to the plain map over the same steps."""
+    r = time_diff(G, torch, dev, stream, 0, n_steps, K)
+    m = r["plain_map"]["ms"]
+    out = {"workload": r["config"]["workload"], "plain_map_ms": m,
+           "ratio": {"forward": r["diff_forward"]["ms"] / m, "adjoint": r["adjoint"]["ms"] / m,
+                     "forward_plus_adjoint": (r["diff_forward"]["ms"] + r["adjoint"]["ms"]) / m,
+                     "forward_with_tangent": r["diff_forward_with_tangent"]["ms"] / m,
+                     "growth_gradient_reverse_sweep_with_tangent_forward":
+                         r["growth_gradient"]["forward_with_tangent_plus_reverse_ratio"],
+                     "growth_gradient_forward_mode": r["growth_gradient"]["forward_mode_ratio"]}}
+    if r["tape_mode"]:
+        t = r["tape_mode"]
+        out["ratio"]["tape_forward"] = t["forward_ms"] / m
+        out["ratio"]["tape_adjoint"] = t["adjoint_ms"] / m
+        out["ratio"]["tape_forward_plus_adjoint"] = t["forward_plus_adjoint_ratio"]
+        out["tape_bytes"] = t["tape_bytes"]
+    return out
+
+
+ORACLE_OPCOUNT = os.path.join(ROOT, "profiles", "oracle_op_count_tiny.txt")
+
+
+def oracle_op_count():
+    """FLOP per particle-step of the map as the oracle computes it (its op-counting build on the
+    1024-particle workload, written by oracle/opcount.py), or None."""
+    try:
+        for line in open(ORACLE_OPCOUNT):
+            if line.startswith("flop_per_particle_step:"):
+                return float(line.split(":", 1)[1])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def oracle_timings():
+    """The oracle on the host's cores, on one thread and on all: the 1024-particle workload in
+    full (10^4 steps) and a 4096-particle random subset of the 1048576-particle belt over 10^4
+    steps (particle-steps/s each)."""
+    import numpy as np
+
+    import glisse_inputs as gi
+    import oracle
+
+    oracle.build()
+    out = {}
+    for name, k in (("tiny", None), ("belt", 4096)):
+        w = gi.WORKLOADS[name]
+        full = gi.make(name)
+        pa = full["particles"] if k is None else full["particles"][gi.subset_ids(name, k)]
+        pl = full["planets"]
+        rc = oracle.rcrit(w.star_mass, pl, 0, w.k_hill)
+        _, log, _ = oracle.planet_wh(w.star_mass, pl, w.dt, 10_000)
+        rec = {"particles": len(pa), "steps": 10_000}
+        for label, threads in (("one_core", 1), ("all_cores", 0)):
+            run = oracle.ParticleRun(w.star_mass, pl[:, 0], pa, rc, w.r_max)
+            t0 = time.perf_counter()
+            run.advance(log, w.dt, threads)
+            el = time.perf_counter() - t0
+            rs = run.removal_step
+            rec[label] = int(np.where(rs >= 0, rs, 10_000).sum()) / el
+        rec["cores"] = oracle.max_threads()
+        out[name] = rec
+    return out
 
 
 def main():
@@ -498,6 +692,8 @@ def main():
     ap.add_argument("--ref-particles", type=int, default=8192)
     ap.add_argument("--cpu-particles", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-subrecords", action="store_true",
+                    help="leave out the belt / batched / diff sub-records of the default line")
     ap.add_argument("--kepler", default="converge", choices=["converge", "paper"],
                     help="paper: the paper's fixed-iteration Kepler solve (GLISSE_KEPLER_PAPER_FIXED)")
     ap.add_argument("--kepler-iters", type=int, default=5)
@@ -541,81 +737,27 @@ def main():
     np_ = planets.shape[0]
 
     stream = torch.cuda.current_stream(dev)
-    o = G.glisse_opts_default()
-    o.chunk_steps = w.chunk
-    o.resync_chunks = w.resync
-    o.enc_value = w.k_hill
-    o.r_max = w.r_max
-    o.timing = 1
-    o.cuda_stream = stream.cuda_stream
     paper = args.kepler == "paper"
     kmode = G.GLISSE_KEPLER_PAPER_FIXED if paper else G.GLISSE_KEPLER_CONVERGE
-    o.kepler_mode = kmode
-    o.kepler_iters = args.kepler_iters
-    o.sort_mode = G.GLISSE_SORT_COST if args.sort else G.GLISSE_SORT_NONE
-    h = G.glisse_create(w.star_mass, planets, particles, w.dt, o)
-    if args.sample_every > 0:
-        G.glisse_set_sampling(h, args.sample_every, frame=G.GLISSE_FRAME_BARY, max_samples=0, res_planet=np_ - 1,
-                              res_p=3, res_q=2, avoid_deg=10.0)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def flush_l2():
-        flush.zero_()
-
-    for _ in range(args.warmup):
-        G.glisse_advance(h, w.chunk)
-    torch.cuda.synchronize(dev)
-    G.glisse_timings(h, reset=True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    live_before = G.glisse_status(h)[0]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    chunk_live, chunk_steps = [], []  # host-side counters, read between chunks (no GPU work)
-    with ClockSampler(dev.index or 0) as clocks:
-        t_wall0 = time.perf_counter()
-        if args.one_call:
-            # the whole timed run as one glisse_advance call (the planets may run ahead of
-            # the particles up to its last chunk)
-            flush_l2()
-            chunk_live.append(G.glisse_status(h)[0])
-            starts[0].record(stream)
-            G.glisse_advance(h, w.chunk * args.steps)
-            ends[0].record(stream)
-            chunk_steps.append(G.glisse_timings(h)["particle_steps"])
-            starts, ends = starts[:1], ends[:1]
-        else:
-            for k in range(args.steps):
-                flush_l2()
-                chunk_live.append(G.glisse_status(h)[0])
-                starts[k].record(stream)
-                G.glisse_advance(h, w.chunk)
-                ends[k].record(stream)
-                chunk_steps.append(G.glisse_timings(h)["particle_steps"])
-        torch.cuda.synchronize(dev)
-        t_wall = time.perf_counter() - t_wall0
-    if dist:
-        dist.barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    # particle-steps/s of each chunk against the fraction of particles live at its start
-    done = [b - a for a, b in zip([0] + chunk_steps[:-1], chunk_steps)]
-    vs_alive = [[round(lv / n, 5), round(ps / (ms * 1e-3), 1)] for lv, ps, ms in zip(chunk_live, done, step_ms)]
-    tm = G.glisse_timings(h)
-    live_after = G.glisse_status(h)[0]
+    h, r = time_single(G, torch, dev, stream, w, planets, particles, args.steps, args.warmup, kmode=kmode,
+                       kepler_iters=args.kepler_iters, sort=args.sort, sample_every=args.sample_every,
+                       one_call=args.one_call, dist=dist)
     G.glisse_destroy(h)
+    step_ms, total_ms, tm = r["step_ms"], r["total_ms"], r["tm"]
+    # particle-steps/s of each chunk against the fraction of particles live at its start
+    chunk_steps = r["chunk_steps"]
+    done = [b - a for a, b in zip([0] + chunk_steps[:-1], chunk_steps)]
+    vs_alive = [[round(lv / n, 5), round(ps / (ms * 1e-3), 1)] for lv, ps, ms in zip(r["chunk_live"], done, step_ms)]
     psteps = tm["particle_steps"]
     total_ms_all, psteps_all = reduce_over_ranks(total_ms, float(psteps), dev)
     value = psteps_all / (total_ms_all * 1e-3)
 
-    # roofline of the particle kernel: algorithmic FP64 work / its own device time, against
-    # the FP64 pipe peak from the unit counts (152 SMs x 2 DFMA/clk) at the clock sampled
-    # during the timed region (max clock if no sample)
-    csum = clocks.summary()
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    # roofline of the particle kernel: FP64 work / its own device time, against the FP64 pipe
+    # peak from the unit counts (152 SMs x 2 DFMA/clk) at the clock sampled during the timed
+    # region (max clock if no sample)
+    csum = r["clocks"]
     mhz = csum["sm_mhz"] if csum else 2070.0
-    dfma_peak = n_sm * DFMA_PER_CLK_PER_SM * mhz * 1e6
+    n_sm, dfma_peak = fp64_peak(torch, dev, mhz)
     probe_rate, probe_mhz = G.glisse_fp64_peak(20000)
     kernel_ms = tm["particle_ms"] / max(tm["particle_launches"], 1)
     steps_per_launch = psteps / max(tm["particle_launches"], 1)
@@ -623,6 +765,7 @@ def main():
     peak = 2.0 * dfma_peak
     pipe = fp64_instr_per_step(np_) * steps_per_launch / (kernel_ms * 1e-3) / dfma_peak
     traffic = profile_traffic()
+    orc_flop = oracle_op_count()
 
     # end to end through the C ABI with host buffers in pinned memory: create (H2D of the
     # planets and particles) + one chunk + read (D2H of states, flags, steps, reasons)
@@ -637,12 +780,12 @@ def main():
         pa_h[...] = particles
         out_h = {"state": pinned((n, 6), torch.float64), "alive": pinned((n,), torch.uint8),
                  "removal_step": pinned((n,), torch.int64), "removal_reason": pinned((n,), torch.int32)}
-        times, done = [], 0
+        times, done_e = [], 0
         for k in range(args.e2e_steps + 1):
             t0 = time.perf_counter()
             sim = G.Simulation(w.star_mass, pl_h, pa_h, w.dt, chunk_steps=w.chunk, enc_value=w.k_hill,
                                r_max=w.r_max, kepler_mode=kmode, kepler_iters=args.kepler_iters,
-                               sort_mode=o.sort_mode)
+                               sort_mode=G.GLISSE_SORT_COST if args.sort else G.GLISSE_SORT_NONE)
             sim.advance(w.chunk)
             out = sim.read(out_h)
             sim.close()
@@ -651,14 +794,23 @@ def main():
                 times.append(dt_)
                 # steps each particle advanced: up to its removal step, else the whole chunk
                 rs = out["removal_step"]
-                done += int(np.where(rs >= 0, rs, w.chunk).sum())
-        e2e = {"value": done / sum(times), "unit": UNIT,
+                done_e += int(np.where(rs >= 0, rs, w.chunk).sum())
+        e2e = {"value": done_e / sum(times), "unit": UNIT,
                "h2d_bytes_per_step": int(particles.nbytes + planets.nbytes),
                "d2h_bytes_per_step": int(out["state"].nbytes + out["removal_step"].nbytes +
                                          out["removal_reason"].nbytes + n),
-               "host_buffers": "pinned"}
+               "host_buffers": "pinned",
+               "note": "each e2e step: create from pinned host buffers, the first 1024-step chunk (all "
+                       "particles live), read into pinned host buffers, destroy"}
+
+    subrecords = {}
+    if rank == 0 and world == 1 and not args.no_subrecords and args.workload == "longrun" and not paper:
+        subrecords["belt"] = belt_record(G, torch, dev, stream)
+        subrecords["batched"] = batched_record(G, torch, dev, stream, value)
+        subrecords["diff"] = diff_record(G, torch, dev, stream)
 
     cpu = None
+    orc_t = None
     if rank == 0 and not args.no_cpu_baseline:
         ids = gi.subset_ids(args.workload, args.cpu_particles)
         rate, cores, busy = cpu_oracle_rate(w, planets, particles[ids], w.chunk, 2,
@@ -666,6 +818,8 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{len(ids)} random ids of the workload, 2 chunks of {w.chunk} steps "
                          f"({busy:.1f} s wall on {cores} threads)"}
+        if not paper:
+            orc_t = oracle_timings()
 
     launches = tm["particle_launches"] + tm["ephemeris_launches"] + 3 * tm["compact_launches"]
     line = {
@@ -673,32 +827,39 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_desc(w, n), "particles_per_gpu": n, "planets": np_,
-                   "steps_per_bench_step": w.chunk, "live_at_start": live_before, "live_at_end": live_after,
-                   "fraction_alive_at_end": live_after / n, "l2": "flushed (256 MiB write) between timed steps",
+                   "steps_per_bench_step": w.chunk, "live_at_start": r["live_before"], "live_at_end": r["live_after"],
+                   "fraction_alive_at_end": r["live_after"] / n, "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": f"replicas x{world} (independent particle sets, no collective)",
-                   "wall_s": t_wall},
+                   "wall_s": r["t_wall"]},
         "kepler": (f"paper fixed-iteration solve, {args.kepler_iters} Newton iterations (library sin/cos)"
                    if paper else "converged (FP32 pre-solve + FP64 Halley step)"),
         "sampling": (f"barycentric elements + 3:2 libration test every {args.sample_every} steps"
                      if args.sample_every > 0 else None),
         "sort": "by expected Kepler-solve cost, costliest first" if args.sort else None,
-        "roofline": None if paper else {"bound": "alu", "achieved": achieved * 1e-9, "peak": peak * 1e-9, "unit": "GFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "particle_chunk_kernel<4>",
-                     "kernel_ms_avg": kernel_ms, "flop_per_particle_step": flop_per_step(np_),
-                     "fp64_instr_per_particle_step": fp64_instr_per_step(np_), "fp64_pipe_frac": pipe,
-                     "peak_source": f"unit counts: {n_sm} SMs x {DFMA_PER_CLK_PER_SM} DFMA/clk x 2 FLOP x "
-                                    f"{mhz:.0f} MHz (SM clock sampled during the timed region)",
-                     "probe_dfma_per_s": probe_rate,
-                     "probe_frac_of_peak": probe_rate / dfma_peak},
+        "roofline": None if paper else {
+            "bound": "alu", "achieved": achieved * 1e-9, "peak": peak * 1e-9, "unit": "GFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": "particle_chunk_kernel<4>",
+            "kernel_ms_avg": kernel_ms, "flop_per_particle_step": flop_per_step(np_),
+            "flop_count": "the kernel's own FP64 work per particle-step (static count, equal to ncu's "
+                          "executed DADD/DMUL/DFMA mix); the oracle's count is given beside it",
+            "flop_per_particle_step_oracle": orc_flop,
+            "frac_at_oracle_count": (orc_flop * steps_per_launch / (kernel_ms * 1e-3) / peak) if orc_flop else None,
+            "fp64_instr_per_particle_step": fp64_instr_per_step(np_), "fp64_pipe_frac": pipe,
+            "peak_source": f"unit counts: {n_sm} SMs x {DFMA_PER_CLK_PER_SM} DFMA/clk x 2 FLOP x "
+                           f"{mhz:.0f} MHz (SM clock sampled during the timed region)",
+            "probe_dfma_per_s": probe_rate,
+            "probe_frac_of_peak": probe_rate / dfma_peak},
         "stage_ms_per_step": {"particle": tm["particle_ms"] / args.steps, "ephemeris": tm["ephemeris_ms"] / args.steps,
                               "compaction": tm["compact_ms"] / args.steps},
         "throughput_vs_alive": {"columns": ["fraction live at chunk start", "particle-steps/s of the chunk"],
                                 "chunks": vs_alive},
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "oracle_timings": orc_t,
         "gpu_launches": int(launches),
         "clocks": csum,
     }
+    line.update(subrecords)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

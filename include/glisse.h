@@ -41,7 +41,7 @@ extern "C" {
 #define GLISSE_E_NOMEM -2   /* device or host allocation failed */
 #define GLISSE_E_CUDA -3    /* a CUDA call failed (no device, launch error, ...) */
 #define GLISSE_E_KEPLER -4  /* a planet's Kepler solve did not converge */
-#define GLISSE_E_TIMEOUT -5 /* a bounded wait gave up (reserved; no current call returns it) */
+#define GLISSE_E_TIMEOUT -5 /* a bounded wait on the device gave up (glisse_advance: a particle task waited seconds for the task before it) */
 #define GLISSE_E_STATE -6   /* call not valid in the context's current state */
 
 /* removal reasons reported by glisse_read() */
@@ -81,6 +81,19 @@ extern "C" {
 #define GLISSE_SORT_NONE 0
 #define GLISSE_SORT_COST 1
 
+/* launch shape of the particle map (results are bit-identical in every shape).
+ * PLAIN: one thread per particle slot, one launch per segment.  TASKS: a
+ * persistent grid of a few warps per SM partition that take (32-slot group,
+ * 32-step sub-chunk) tasks in order from a device counter, so every partition
+ * keeps the same number of busy warps to the end of the segment; a task waits
+ * (bounded: GLISSE_E_TIMEOUT after seconds) for its group's previous
+ * sub-chunk.  AUTO picks TASKS when the live groups outnumber the resident
+ * warps (two to four per partition) by half again, PLAIN otherwise.  The
+ * fixed-iteration Kepler mode always uses PLAIN. */
+#define GLISSE_LAUNCH_AUTO 0
+#define GLISSE_LAUNCH_PLAIN 1
+#define GLISSE_LAUNCH_TASKS 2
+
 /* element frames for glisse_set_sampling */
 #define GLISSE_FRAME_HELIO 0 /* heliocentric; mu = G m0 (particles), G (m0 + m_j) (planet j) */
 #define GLISSE_FRAME_BARY 1  /* barycentre of star and planets; mu = G (m0 + sum m_j) for every body */
@@ -95,7 +108,7 @@ typedef struct {
     int32_t enc_mode;      /* GLISSE_ENC_*, default HILL */
     int32_t timing;        /* non-zero: time every launch with CUDA events (see glisse_timings) */
     int32_t sort_mode;     /* GLISSE_SORT_*, default NONE */
-    int32_t pad_;
+    int32_t launch_mode;   /* GLISSE_LAUNCH_*, default AUTO (a performance choice: not saved in checkpoints) */
     double enc_value;      /* Hill multiple k (default 1.0) or fixed distance in AU */
     double r_max;          /* escape radius in AU, default 1000; <= 0 disables the escape test */
     void* cuda_stream;     /* cudaStream_t to run on; NULL = the library creates one */
@@ -132,6 +145,13 @@ int glisse_create(glisse_ctx** out, double star_mass, const double* planets, int
  * few chunks lets the planets run ahead of the particles up to its last chunk:
  * the planet-log buffers then grow (once, kept until glisse_destroy) to up to
  * 512 MB, (C + 1) x (4 (N_p + 1) + 6 N_p) doubles per chunk held.
+ * Splitting a run into calls changes nothing: advance(a) then advance(b) gives
+ * bit for bit what advance(a + b) gives.  Between calls the device keeps each
+ * live particle's velocity with the next step's opening half kick already
+ * applied (as an uncut run has it there), and every call ends by computing the
+ * synchronised state that glisse_read returns.  Live particles are compacted
+ * (section 2.2's resync) at chunk boundaries only, every resync_chunks chunks,
+ * so at the same steps however the run is split.
  * Errors: INVAL (n_steps < 0), STATE (external ephemeris too short), KEPLER, CUDA.
  */
 int glisse_advance(glisse_ctx* ctx, int64_t n_steps);
@@ -166,6 +186,9 @@ int glisse_read_planets(glisse_ctx* ctx, double* planets, double* t);
  * The common term h0 = -sum_j G m_j r_j / |r_j|^3 is computed from these positions.
  * After these steps are consumed, glisse_advance() returns STATE until another
  * log is installed; the built-in planets are no longer valid for this context.
+ * Installed after some steps have run, the positions at t_k take part from the
+ * next step on: the kick at t_k was applied, with the positions then in force,
+ * when the previous call ended.
  * Returns STATE while element sampling is set (glisse_set_sampling).
  */
 int glisse_set_ephemeris(glisse_ctx* ctx, const double* log, int64_t n_steps);
@@ -253,14 +276,20 @@ int glisse_partition_device(int64_t n, int64_t ld, const uint8_t* alive, const d
  * owns all device memory, with a memory budget fixed at start-up, or in a loop
  * that cannot afford an allocation's synchronisation or its failure).
  * The paper has no counterpart; this is a property of this library only.
- *   - Allocates nothing: no cudaMalloc / cudaFree or allocating library call.
- *     Its scratch is a fixed array of GLISSE_PARTITION_NOALLOC_MAX / 2048
- *     int64 (256 KiB) inside the library's device image, present on every GPU
- *     that loads the library until the process exits.
+ *   - Makes no cudaMalloc / cudaFree or allocating library call.  Its
+ *     scratch is a fixed array of GLISSE_PARTITION_NOALLOC_MAX / 2048 int64
+ *     (256 KiB) inside the library's device image.  The array is placed in a
+ *     device's memory when the CUDA driver loads the library's module there.
+ *     Under lazy module loading (CUDA's default) that may happen during the
+ *     first call on the device, so the first call may allocate through the
+ *     driver; every later call on that device allocates nothing.  A call with
+ *     n = 0 does this set-up and nothing else.  The array then stays until
+ *     the process exits or the device's context is destroyed.
  *   - n above GLISSE_PARTITION_NOALLOC_MAX returns GLISSE_E_INVAL.
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress,
+ *     with the caller's device current); the first call on each device also
+ *     sets the module up as above, so make that first call before any stream
+ *     capture.
  *   - All calls on a device share the one array (its contents are left over
  *     from the previous call and are never assumed to be zero).  Calls whose
  *     GPU work overlaps -- e.g. from two host threads on two streams -- race on

@@ -52,11 +52,59 @@ def compile_source(src: str, out: str) -> str:
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle if the shared object is missing or older than the source."""
+    """Compile the oracle if the shared object is missing or older than the source
+    (and its op-counting build, opcount.cpp)."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         compile_source(_SRC, _OUT)
+    build_opcount(force)
     return _OUT
+
+
+_OPC_SRC = os.path.join(_HERE, "opcount.cpp")
+_OPC_OUT = os.path.join(_HERE, "_build", "libopcount.so")
+
+
+def build_opcount(force: bool = False) -> str:
+    """Compile opcount.cpp (the oracle's particle map over a counting double) with g++,
+    the same floating-point flags as the oracle, single-threaded."""
+    os.makedirs(os.path.dirname(_OPC_OUT), exist_ok=True)
+    newest = max(os.path.getmtime(_OPC_SRC), os.path.getmtime(_SRC))
+    if force or not os.path.exists(_OPC_OUT) or os.path.getmtime(_OPC_OUT) < newest:
+        tmp = _OPC_OUT + f".{os.getpid()}.tmp"
+        subprocess.run(["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c++17", "-shared", "-fPIC",
+                        "-o", tmp, _OPC_SRC, "-lm"], check=True)
+        os.replace(tmp, _OPC_OUT)
+    return _OPC_OUT
+
+
+OPCOUNT_FIELDS = ("add", "mul", "div", "sqrt", "trans", "cmp", "other")
+
+
+def opcount_particles(star_mass, planet_masses, log, dt, state0, rcrit_, r_max):
+    """The particle map of ParticleRun.advance over log (test at t_0 first), run through the
+    op-counting build.  Returns (final state [n][6], removal_step, reason, counts dict with
+    OPCOUNT_FIELDS over the whole run)."""
+    L = C.CDLL(build_opcount())
+    dp = C.POINTER(C.c_double)
+    L.orc_opcount_particles.argtypes = [C.c_double, C.c_int, dp, dp, C.c_int64, C.c_double, dp, C.c_double, dp,
+                                        C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_uint64)]
+    L.orc_opcount_particles.restype = C.c_int
+    pm = _f64(planet_masses)
+    log = _f64(log)
+    st = _f64(state0).reshape(-1, 6).copy()
+    n = st.shape[0]
+    rs = np.empty(n, dtype=np.int64)
+    rn = np.empty(n, dtype=np.int32)
+    cnt = np.zeros(len(OPCOUNT_FIELDS), dtype=np.uint64)
+    rc = L.orc_opcount_particles(float(star_mass), pm.shape[0], _dp(pm), _dp(log), log.shape[0] - 1, float(dt),
+                                 _dp(_f64(rcrit_)), float(r_max), _dp(st), n,
+                                 rs.ctypes.data_as(C.POINTER(C.c_int64)), rn.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 cnt.ctypes.data_as(C.POINTER(C.c_uint64)))
+    if rc != 0:
+        raise RuntimeError(f"orc_opcount_particles failed: {rc}")
+    return st, rs, rn, dict(zip(OPCOUNT_FIELDS, (int(c) for c in cnt)))
 
 
 SOURCE = _SRC

@@ -35,7 +35,9 @@
  *
  * Readings of points the paper leaves open are listed at each function.
  */
+#ifndef ORC_OPCOUNT /* opcount.cpp compiles the real-valued map alone, as C++ */
 #include <complex.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -842,6 +844,7 @@ int orc_max_threads(void)
 #endif
 }
 
+#ifndef ORC_OPCOUNT
 /* ------------------------------------------------------------------------ */
 /* Tangent map by complex-step differentiation (reading for the derivative   */
 /* of the map; the paper has no tangent map).  The particle map above is     */
@@ -1095,3 +1098,4 @@ int orc_particles_jvp(double m0, int np, const double* pmass, const double* log_
     }
     return ORC_OK;
 }
+#endif /* ORC_OPCOUNT */

@@ -36,6 +36,7 @@ GLISSE_ENC_HILL = 0
 GLISSE_ENC_FIXED = 1
 GLISSE_SORT_NONE = 0
 GLISSE_SORT_COST = 1
+GLISSE_LAUNCH_AUTO, GLISSE_LAUNCH_PLAIN, GLISSE_LAUNCH_TASKS = 0, 1, 2
 GLISSE_MATH_RSQRT, GLISSE_MATH_RCP, GLISSE_MATH_RCP40, GLISSE_MATH_KRCUBE = 0, 1, 2, 3
 GLISSE_MATH_FLOAT_SQUARE, GLISSE_MATH_FLOAT_CUBE, GLISSE_MATH_D2F = 4, 5, 6
 GLISSE_FRAME_HELIO = 0
@@ -81,7 +82,7 @@ class glisse_opts(C.Structure):
         ("enc_mode", C.c_int32),
         ("timing", C.c_int32),
         ("sort_mode", C.c_int32),
-        ("pad_", C.c_int32),
+        ("launch_mode", C.c_int32),
         ("enc_value", C.c_double),
         ("r_max", C.c_double),
         ("cuda_stream", C.c_void_p),

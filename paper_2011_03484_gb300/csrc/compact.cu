@@ -17,6 +17,8 @@
 // place them after a device-side base offset, so a stable partition into
 // several groups is one pass per group (used to order live particles by the
 // expected cost of their Kepler solve, section 2.2's sorting suggestion).
+// A wanted value of 0 (kAnyNonZero) selects every slot whose key is non-zero:
+// that is the plain live/removed partition, where any non-zero flag keeps.
 #include <cuda_runtime.h>
 
 #include "glisse_internal.h"
@@ -26,6 +28,11 @@ namespace glisse {
 constexpr int kCompactThreads = 256;
 constexpr int kCompactRounds = 8;
 constexpr int kTile = kCompactThreads * kCompactRounds;
+constexpr uint8_t kAnyNonZero = 0;
+
+__device__ __forceinline__ bool selected(uint8_t key, uint8_t want) {
+    return want == kAnyNonZero ? key != 0 : key == want;
+}
 
 __global__ void __launch_bounds__(kCompactThreads) compact_count_kernel(const uint8_t* __restrict__ key, uint8_t want,
                                                                          int64_t n, int64_t* __restrict__ counts) {
@@ -34,7 +41,7 @@ __global__ void __launch_bounds__(kCompactThreads) compact_count_kernel(const ui
 #pragma unroll
     for (int r = 0; r < kCompactRounds; ++r) {
         const int64_t idx = base + r * kCompactThreads + threadIdx.x;
-        c += (idx < n && key[idx] == want) ? 1 : 0;
+        c += (idx < n && selected(key[idx], want)) ? 1 : 0;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
@@ -99,7 +106,7 @@ __global__ void __launch_bounds__(kCompactThreads) compact_scatter_kernel(
     const int64_t base = (int64_t)blockIdx.x * kTile;
     for (int r = 0; r < kCompactRounds; ++r) {
         const int64_t idx = base + r * kCompactThreads + threadIdx.x;
-        const bool f = idx < n && key[idx] == want;
+        const bool f = idx < n && selected(key[idx], want);
         const unsigned ball = __ballot_sync(0xFFFFFFFFu, f);
         const int rank = __popc(ball & ((1u << lane) - 1u));
         if (lane == 0) wcnt[warp] = __popc(ball);
@@ -127,10 +134,10 @@ cudaError_t launch_compact(int64_t n, const uint8_t* alive, const double* src, c
                            cudaStream_t s) {
     if (n <= 0) return cudaMemsetAsync(n_out, 0, sizeof(int64_t), s);
     const int64_t nb = (n + kTile - 1) / kTile;
-    compact_count_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(alive, 1, n, counts);
+    compact_count_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(alive, kAnyNonZero, n, counts);
     compact_scan_kernel<<<1, 1024, 0, s>>>(counts, nb, nullptr, n_out);
-    compact_scatter_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(alive, 1, n, counts, src, src_id, lds, dst,
-                                                                      dst_id, ldd);
+    compact_scatter_kernel<<<(unsigned)nb, kCompactThreads, 0, s>>>(alive, kAnyNonZero, n, counts, src, src_id, lds,
+                                                                      dst, dst_id, ldd);
     return cudaGetLastError();
 }
 

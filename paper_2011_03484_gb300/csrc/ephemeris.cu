@@ -4,8 +4,11 @@
 // symplectic (Wisdom-Holman) map in Jacobi coordinates, a chunk of steps
 // ahead of the particles, and ships the heliocentric positions plus the
 // common indirect term h0 = -sum_j G m_j r_j / |r_j|^3 for every step.
-// Here that runs on the GPU in one warp (lane i = planet i) on a side stream,
-// one chunk ahead of the particle kernel.
+// Here that runs on the GPU in one block of two warps on a side stream, one
+// chunk ahead of the particle kernel: warp 0 steps the planets (its lanes are
+// planet rows x 4 columns, so each pair interaction is computed once, in
+// parallel lanes), warp 1 -- on another SM partition -- turns every step's
+// synchronised state into the log records, h0 and the heliocentric history.
 //
 // Jacobi coordinates (commented equations after Eq. 2 of the paper), planets
 // i = 1..N_p (lane i-1), star 0:
@@ -112,129 +115,164 @@ __global__ void __launch_bounds__(32) eph_setup_kernel(const double* __restrict_
     }
 }
 
-// Heliocentric positions and velocities of all lanes from Jacobi ones.
-__device__ __forceinline__ void jac_to_helio(const double q[3], double m_over_eta, int lane, int np, double r[3]) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) r[d] = q[d] + warp_excl_prefix(m_over_eta * q[d], lane, np);
+// ---------------------------------------------------------------------------
+// The chunked Wisdom-Holman step of the planets.
+//
+// A GPU FP64 instruction of a warp costs the same whatever its active lanes,
+// and one warp steps the planets serially, so the time of a step is the
+// number of FP64 instructions on its critical path.  Two things shorten it:
+//   * warp 0 holds planet i in the four lanes 4i .. 4i + 3 (replicated), and
+//     lane 4i + c also handles the interaction with planet j = c (and
+//     c + 4 for 5 to 8 planets): the N_p^2 pair terms, the positions' Jacobi
+//     prefix sums and the suffix sums of the kick are each one lane-parallel
+//     term plus a two-stage butterfly within the row;
+//   * what only the log needs -- h0, the heliocentric velocities, the stores
+//     and the progress count -- runs on warp 1 from a double-buffered
+//     shared-memory hand-off, ordered by named barriers.
+// Each step is open half kick, Kepler drift of every Jacobi body, positions,
+// kick terms, closing half kick, identically at every step, so the planet
+// sequence does not depend on where chunks begin.
+// ---------------------------------------------------------------------------
+constexpr int kEphThreads = 64;  // warp 0: dynamics, warp 1: log records
+constexpr int kEphCols = 4;      // lanes per planet row in warp 0
+
+// named barriers of the hand-off ring: FULL slot b = 1 + b, EMPTY slot b = 3 + b
+__device__ __forceinline__ void eph_bar_sync(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kEphThreads) : "memory");
+}
+__device__ __forceinline__ void eph_bar_arrive(int id) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "n"(kEphThreads) : "memory");
 }
 
-// Jacobi acceleration of every lane's planet, and h0, at heliocentric positions r.
-// inv_eta = 1 / eta_i and ratio = eta_i / eta_{i-1} of this lane's planet.
-__device__ __forceinline__ void planet_accel(const PlanetConsts& pc, bool on, int lane, double inv_eta, double ratio,
-                                             const double q[3], const double r[3], double acc[3], double h0[3]) {
-    const int np = pc.np;
-    const double m = on ? pc.m[lane] : 0.0;
-    const double gm = on ? pc.gm[lane] : 0.0;
-    const double mu0 = pc.mu0;
-    // star term of ghat and this planet's share of h0
-    const double r2 = on ? fma(r[0], r[0], fma(r[1], r[1], r[2] * r[2])) : 1.0;
-    const double ir3 = k_rcube(r2, 1.0);
-    const double sun = mu0 * ir3, own = gm * ir3;
+struct EphRing {
+    double r[2][kMaxPlanets][3];  // heliocentric positions of the emitted step
+    double w[2][kMaxPlanets][3];  // synchronised Jacobi velocities
+};
+
+// Sum over the four lanes of a planet row (every lane of the row gets the same bits).
+__device__ __forceinline__ double row_sum(double v) {
+    v += __shfl_xor_sync(kFullMask, v, 1);
+    v += __shfl_xor_sync(kFullMask, v, 2);
+    return v;
+}
+
+// Warp 0: positions r from the Jacobi positions q of every row (r_i = q_i + sum_{k<i} m_k/eta_k q_k).
+template <int H>
+__device__ __forceinline__ void eph_positions(const double (&moe)[2], const bool (&below)[2], const double q[3],
+                                              double r[3], int col) {
+    double p[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const int src = kEphCols * (col + kEphCols * h);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double qj = __shfl_sync(kFullMask, q[d], src);
+            p[d] = fma(below[h] ? moe[h] : 0.0, qj, p[d]);
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) r[d] = q[d] + row_sum(p[d]);
+}
+
+// Warp 0: Jacobi acceleration of the row's planet at heliocentric positions r.
+//   ghat_i = G m0 r_i / |r_i|^3 + sum_{j != i} G m_j (r_i - r_j) / |r_i - r_j|^3  (lane-parallel over j)
+//   S_k    = sum_{i > k} m_i ghat_i                                             (lane-parallel over i)
+//   acc_k  = -(eta_k / eta_{k-1}) [ghat_k + S_k / eta_k - G m0 q_k / |q_k|^3]
+template <int H>
+__device__ __forceinline__ void eph_accel(const PlanetConsts& pc, bool on, int row, int col, const double (&kj)[2],
+                                          const bool (&valid)[2], const double (&mi)[2], const bool (&above)[2],
+                                          double inv_eta, double ratio, const double q[3], const double r[3],
+                                          double acc[3]) {
+    double t[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const int j = col + kEphCols * h;
+        const int src = kEphCols * j;
+        const bool self = j == row;
+        double dv[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double rj = __shfl_sync(kFullMask, r[d], src);
+            dv[d] = r[d] - (self ? 0.0 : rj);
+        }
+        const double d2 = fma(dv[0], dv[0], fma(dv[1], dv[1], dv[2] * dv[2]));
+        const double sc = k_rcube(valid[h] ? d2 : 1.0, kj[h]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) t[d] = fma(sc, dv[d], t[d]);
+    }
     double gh[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        gh[d] = sun * r[d];
-        h0[d] = -warp_total0(own * r[d], lane, np);
+    for (int d = 0; d < 3; ++d) gh[d] = row_sum(t[d]);
+    double sv[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const int src = kEphCols * (col + kEphCols * h);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double gi = __shfl_sync(kFullMask, gh[d], src);
+            sv[d] = fma(above[h] ? mi[h] : 0.0, gi, sv[d]);
+        }
     }
-    // planet-planet terms
-    for (int j = 0; j < np; ++j) {
-        const double rjx = __shfl_sync(kFullMask, r[0], j);
-        const double rjy = __shfl_sync(kFullMask, r[1], j);
-        const double rjz = __shfl_sync(kFullMask, r[2], j);
-        const double gmj = pc.gm[j];
-        const double dx = r[0] - rjx, dy = r[1] - rjy, dz = r[2] - rjz;
-        const double d2 = (j == lane || !on) ? 1.0 : fma(dx, dx, fma(dy, dy, dz * dz));
-        const double s = (j == lane || !on) ? 0.0 : k_rcube(d2, gmj);
-        gh[0] = fma(s, dx, gh[0]);
-        gh[1] = fma(s, dy, gh[1]);
-        gh[2] = fma(s, dz, gh[2]);
-    }
-    // S_k = sum_{i>k} m_i ghat_i ; gradient ; Jacobi acceleration
     const double q2 = on ? fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2])) : 1.0;
-    const double iq3 = k_rcube(q2, mu0);
+    const double iq3 = k_rcube(q2, pc.mu0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        const double S = warp_excl_suffix(on ? m * gh[d] : 0.0, lane, np);
+        const double S = row_sum(sv[d]);
         const double grad = fma(S, inv_eta, fma(-iq3, q[d], gh[d]));
         acc[d] = on ? -ratio * grad : 0.0;
     }
 }
 
-// Write log step k (positions + h0) and the synchronised heliocentric states.
-__device__ __forceinline__ void emit_step(int k, int np, int S, int lane, bool on, double m_over_eta, const double r[3],
-                                          const double w[3], const double h0[3], double* __restrict__ log,
-                                          double* __restrict__ hist) {
-    double* L = log + (size_t)k * S;
-    if (on) {
-        L[kRec * lane + 0] = r[0];
-        L[kRec * lane + 1] = r[1];
-        L[kRec * lane + 2] = r[2];
-        L[kRec * lane + 3] = 0.0;
-    }
-    if (hist) {  // the same pointer on every lane: the warp takes this branch together
-        double vh[3];
-        jac_to_helio(w, m_over_eta, lane, np, vh);
-        if (on) {
-            double* H = hist + (size_t)k * 6 * np;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                H[6 * lane + d] = r[d];
-                H[6 * lane + 3 + d] = vh[d];
-            }
-        }
-    }
-    if (lane == 0) {
-        L[kRec * np + 0] = h0[0];
-        L[kRec * np + 1] = h0[1];
-        L[kRec * np + 2] = h0[2];
-        L[kRec * np + 3] = 0.0;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Advance the planets nsteps steps from the Jacobi state `jac` (in place).
-// Writes log steps 0..nsteps (positions + h0, broadcast layout) and the
-// synchronised heliocentric states hist[0..nsteps][np][6].
-// progress (optional, host-mapped): after every kProgressEvery-th step and the
-// last, the number of steps whose log entries are written, published with a
-// system-scope fence so that the host may launch work on them while this runs.
-// status: set to GLISSE_E_KEPLER if a planet's drift fails.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void eph_advance(const PlanetConsts& pc, double* jac, double dt, int nsteps,
-                                            double* __restrict__ log, double* __restrict__ hist, int* status,
-                                            int* progress = nullptr) {
+// Warp 0 of the block: nsteps steps from the Jacobi state `jac` (in place), each step's
+// synchronised state handed to warp 1.  status: GLISSE_E_KEPLER if a planet's drift fails.
+template <int H>
+__device__ __forceinline__ void eph_dynamics(const PlanetConsts& pc, double* jac, double dt, int nsteps, EphRing& ring,
+                                             int* status) {
     const int np = pc.np;
-    const int lane = threadIdx.x;
-    const bool on = lane < np;
-    const int S = log_stride(np);
+    const int lane = threadIdx.x & 31;
+    const int row = lane / kEphCols, col = lane % kEphCols;
+    const bool on = row < np;
     double q[3], w[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        q[d] = on ? jac[3 * lane + d] : 1.0 + lane;
-        w[d] = on ? jac[3 * np + 3 * lane + d] : 0.0;
+        q[d] = on ? jac[3 * row + d] : (d == 0 ? 1.0 + row : 0.0);
+        w[d] = on ? jac[3 * np + 3 * row + d] : 0.0;
     }
-    if (!on) {
-        q[1] = 0.0;
-        q[2] = 0.0;
-    }
-    const double m_over_eta = on ? pc.m[lane] / pc.eta[lane + 1] : 0.0;
-    const double inv_eta = on ? 1.0 / pc.eta[lane + 1] : 1.0;
-    const double ratio = on ? pc.eta[lane + 1] / pc.eta[lane] : 1.0;
-    const double mu = on ? pc.mu_jac[lane] : pc.mu0;
+    const double inv_eta = on ? 1.0 / pc.eta[row + 1] : 1.0;
+    const double ratio = on ? pc.eta[row + 1] / pc.eta[row] : 1.0;
+    const double mu = on ? pc.mu_jac[row] : pc.mu0;
     const float muf = d2f_bits(mu), dtf = d2f_bits(dt);
     const double hdt = 0.5 * dt;
-    double r[3], acc[3], h0[3];
-
-
-    jac_to_helio(q, m_over_eta, lane, np, r);
-    planet_accel(pc, on, lane, inv_eta, ratio, q, r, acc, h0);
-    emit_step(0, np, S, lane, on, m_over_eta, r, w, h0, log, hist);
+    // per column j = col + 4h: m_j / eta_j for the positions (j < row), the kick's G-coefficient
+    // (G m0 on the diagonal, G m_j off it), m_j for the suffix sums (j > row)
+    double moe[2], kj[2], mi[2];
+    bool below[2], valid[2], above[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int j = col + kEphCols * h;
+        const bool jon = h < H && j < np;
+        moe[h] = jon ? pc.m[j] / pc.eta[j + 1] : 0.0;
+        below[h] = jon && on && j < row;
+        valid[h] = jon && on;
+        kj[h] = valid[h] ? (j == row ? pc.mu0 : pc.gm[j]) : 0.0;
+        mi[h] = jon ? pc.m[j] : 0.0;
+        above[h] = jon && on && j > row;
+    }
+    double r[3], acc[3];
+    eph_positions<H>(moe, below, q, r, col);
+    eph_accel<H>(pc, on, row, col, kj, valid, mi, above, inv_eta, ratio, q, r, acc);
+    if (on && col == 0)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            ring.r[0][row][d] = r[d];
+            ring.w[0][row][d] = w[d];
+        }
+    eph_bar_arrive(1);
     bool failed = false;
     for (int k = 0; k < nsteps; ++k) {
-        // opening half kick
+        // opening half kick, Kepler drift of each Jacobi body
 #pragma unroll
         for (int d = 0; d < 3; ++d) w[d] = fma(hdt, acc[d], w[d]);
-        // Kepler drift of each Jacobi body
         double qr, qmur;
         radius_of(q[0], q[1], q[2], qr, qmur);
         qmur *= mu;
@@ -242,42 +280,122 @@ __device__ __forceinline__ void eph_advance(const PlanetConsts& pc, double* jac,
         if (on && !done) {
             if (!drift_general(mu, dt, q[0], q[1], q[2], w[0], w[1], w[2])) failed = true;
         }
-        jac_to_helio(q, m_over_eta, lane, np, r);
-        planet_accel(pc, on, lane, inv_eta, ratio, q, r, acc, h0);
+        eph_positions<H>(moe, below, q, r, col);
+        eph_accel<H>(pc, on, row, col, kj, valid, mi, above, inv_eta, ratio, q, r, acc);
         // closing half kick: synchronised state at t_{k+1}
 #pragma unroll
         for (int d = 0; d < 3; ++d) w[d] = fma(hdt, acc[d], w[d]);
-        emit_step(k + 1, np, S, lane, on, m_over_eta, r, w, h0, log, hist);
-        if (progress && (((k + 1) % kProgressEvery) == 0 || k + 1 == nsteps)) {
-            __threadfence_system();  // every lane's log entries before the count
-            __syncwarp();
-            if (lane == 0) *reinterpret_cast<volatile int*>(progress) = k + 1;
-        }
+        const int e = k + 1, b = e & 1;
+        if (e >= 2) eph_bar_sync(3 + b);  // warp 1 is done with emitted step e - 2
+        if (on && col == 0)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                ring.r[b][row][d] = r[d];
+                ring.w[b][row][d] = w[d];
+            }
+        eph_bar_arrive(1 + b);
     }
-    if (on) {
+    // wait for warp 1 to finish the last emitted steps
+    for (int e = nsteps > 0 ? nsteps - 1 : 0; e <= nsteps; ++e) eph_bar_sync(3 + (e & 1));
+    if (on && col == 0)
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            jac[3 * lane + d] = q[d];
-            jac[3 * np + 3 * lane + d] = w[d];
+            jac[3 * row + d] = q[d];
+            jac[3 * np + 3 * row + d] = w[d];
         }
-    }
     if (__any_sync(kFullMask, failed) && lane == 0) *status = GLISSE_E_KEPLER;
 }
 
-__global__ void __launch_bounds__(32) eph_chunk_kernel(const PlanetConsts* __restrict__ pcp, double* jac, double dt,
-                                                         int nsteps, double* __restrict__ log,
-                                                         double* __restrict__ hist, int* status, int* progress) {
+// Warp 1 of the block: for each emitted step e = 0..nsteps, log record e (positions + h0,
+// broadcast layout) and the synchronised heliocentric states hist[e][np][6].
+// progress (optional, host-mapped): after every kProgressEvery-th step and the last, the
+// number of steps whose log entries are written, published with a system-scope fence so
+// that the host may launch work on them while this runs.
+__device__ __forceinline__ void eph_emit(const PlanetConsts& pc, int nsteps, const EphRing& ring,
+                                         double* __restrict__ log, double* __restrict__ hist, int* progress) {
+    const int np = pc.np;
+    const int lane = threadIdx.x & 31;
+    const bool on = lane < np;
+    const int S = log_stride(np);
+    const double gm = on ? pc.gm[lane] : 0.0;
+    const double m_over_eta = on ? pc.m[lane] / pc.eta[lane + 1] : 0.0;
+    for (int e = 0; e <= nsteps; ++e) {
+        const int b = e & 1;
+        eph_bar_sync(1 + b);
+        double r[3], w[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            r[d] = on ? ring.r[b][lane][d] : 0.0;
+            w[d] = on ? ring.w[b][lane][d] : 0.0;
+        }
+        eph_bar_arrive(3 + b);  // the ring slot may be refilled
+        // h0 = -sum_j G m_j r_j / |r_j|^3
+        const double r2 = on ? fma(r[0], r[0], fma(r[1], r[1], r[2] * r[2])) : 1.0;
+        const double own = k_rcube(r2, gm);
+        double h0[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) h0[d] = -warp_total0(own * r[d], lane, np);
+        double* L = log + (size_t)e * S;
+        if (on) {
+            L[kRec * lane + 0] = r[0];
+            L[kRec * lane + 1] = r[1];
+            L[kRec * lane + 2] = r[2];
+            L[kRec * lane + 3] = 0.0;
+        }
+        if (lane == 0) {
+            L[kRec * np + 0] = h0[0];
+            L[kRec * np + 1] = h0[1];
+            L[kRec * np + 2] = h0[2];
+            L[kRec * np + 3] = 0.0;
+        }
+        if (hist) {  // the same pointer on every lane: the warp takes this branch together
+            double* Hs = hist + (size_t)e * 6 * np;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const double vh = w[d] + warp_excl_prefix(m_over_eta * w[d], lane, np);
+                if (on) {
+                    Hs[6 * lane + d] = r[d];
+                    Hs[6 * lane + 3 + d] = vh;
+                }
+            }
+        }
+        if (progress && e > 0 && ((e % kProgressEvery) == 0 || e == nsteps)) {
+            __threadfence_system();  // every lane's log entries before the count
+            __syncwarp();
+            if (lane == 0) *reinterpret_cast<volatile int*>(progress) = e;
+        }
+    }
+}
+
+__device__ __forceinline__ void eph_advance(const PlanetConsts& pc, double* jac, double dt, int nsteps,
+                                            double* __restrict__ log, double* __restrict__ hist, int* status,
+                                            int* progress = nullptr) {
+    __shared__ EphRing ring;
+    if (threadIdx.x < 32) {
+        if (pc.np > kEphCols)
+            eph_dynamics<2>(pc, jac, dt, nsteps, ring, status);
+        else
+            eph_dynamics<1>(pc, jac, dt, nsteps, ring, status);
+    } else {
+        eph_emit(pc, nsteps, ring, log, hist, progress);
+    }
+}
+
+__global__ void __launch_bounds__(kEphThreads) eph_chunk_kernel(const PlanetConsts* __restrict__ pcp, double* jac,
+                                                                  double dt, int nsteps, double* __restrict__ log,
+                                                                  double* __restrict__ hist, int* status,
+                                                                  int* progress) {
     eph_advance(*pcp, jac, dt, nsteps, log, hist, status, progress);
 }
 
-// Many independent systems: block b advances system b (one warp each).
+// Many independent systems: block b advances system b.
 //   jac  : [n_sys][2][kMaxPlanets][3] Jacobi states (per-system stride 6 kMaxPlanets)
 //   log  : system b's log at log + log_off[b] (stride 4 (np_b + 1) doubles per step)
 //   dt   : [n_sys] steps
-__global__ void __launch_bounds__(32) eph_batch_kernel(const PlanetConsts* __restrict__ pcs, double* jac,
-                                                         const double* __restrict__ dt, int nsteps,
-                                                         double* __restrict__ log, const int64_t* __restrict__ log_off,
-                                                         int* status) {
+__global__ void __launch_bounds__(kEphThreads) eph_batch_kernel(const PlanetConsts* __restrict__ pcs, double* jac,
+                                                                  const double* __restrict__ dt, int nsteps,
+                                                                  double* __restrict__ log,
+                                                                  const int64_t* __restrict__ log_off, int* status) {
     const int b = blockIdx.x;
     eph_advance(pcs[b], jac + (size_t)b * 6 * kMaxPlanets, dt[b], nsteps, log + log_off[b], nullptr, status);
 }
@@ -318,10 +436,11 @@ cudaError_t launch_eph_setup(const double* planets, int np, double m0, double G,
     return cudaGetLastError();
 }
 
-// The ephemeris is one serial warp.  Sharing an SM partition with particle
-// warps would slow it by the number of warps it shares the FP64 pipe with, so
-// its block asks for the largest dynamic shared-memory allocation a block may
-// have: no other block fits on that SM while it runs (the memory is unused).
+// The ephemeris is one serial block of two warps.  Sharing an SM partition
+// with particle warps would slow it by the number of warps it shares the FP64
+// pipe with, so its block asks for the largest dynamic shared-memory
+// allocation a block may have: no other block fits on that SM while it runs
+// (the memory is unused).
 cudaError_t launch_eph_chunk(const PlanetConsts* pc, double* jac, double dt, int nsteps, double* log, double* hist,
                              int* status, cudaStream_t s, int* progress) {
     int dev = 0, optin = 0;
@@ -330,14 +449,14 @@ cudaError_t launch_eph_chunk(const PlanetConsts* pc, double* jac, double dt, int
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(eph_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
-    eph_chunk_kernel<<<1, 32, (size_t)optin, s>>>(pc, jac, dt, nsteps, log, hist, status, progress);
+    eph_chunk_kernel<<<1, kEphThreads, (size_t)optin, s>>>(pc, jac, dt, nsteps, log, hist, status, progress);
     return cudaGetLastError();
 }
 
 cudaError_t launch_eph_batch(const PlanetConsts* pcs, int n_sys, double* jac, const double* dt, int nsteps,
                              double* log, const int64_t* log_off, int* status, cudaStream_t s) {
     if (n_sys <= 0) return cudaSuccess;
-    eph_batch_kernel<<<n_sys, 32, 0, s>>>(pcs, jac, dt, nsteps, log, log_off, status);
+    eph_batch_kernel<<<n_sys, kEphThreads, 0, s>>>(pcs, jac, dt, nsteps, log, log_off, status);
     return cudaGetLastError();
 }
 

@@ -40,7 +40,7 @@ cudaError_t launch_eph_setup(const double*, int, double, double, int, double, Pl
 cudaError_t launch_eph_chunk(const PlanetConsts*, double*, double, int, double*, double*, int*, cudaStream_t,
                              int* progress = nullptr);
 cudaError_t launch_eph_external(const PlanetConsts*, const double*, int64_t, double*, cudaStream_t);
-cudaError_t launch_particle_chunk(int, const ChunkArgs&, const ParticleConsts&, cudaStream_t);
+cudaError_t launch_particle_chunk(int, const ChunkArgs&, const ParticleConsts&, cudaStream_t, const TaskArgs*, bool);
 cudaError_t launch_particle_chunk_paper(int, const ChunkArgs&, const ParticleConsts&, cudaStream_t);
 cudaError_t launch_compact(int64_t, const uint8_t*, const double*, const int32_t*, int64_t, double*, int32_t*,
                            int64_t, int64_t*, int64_t*, cudaStream_t);
@@ -139,6 +139,12 @@ struct glisse_ctx {
     int64_t* h_nlive = nullptr;
     unsigned long long* d_steps = nullptr;   // exact particle-step counter (timing mode)
     unsigned long long* h_steps = nullptr;
+    unsigned long long* d_task = nullptr;    // task counter of the particle kernel's task mode
+    int32_t* d_group_done = nullptr;         // [ceil(cap / 32)] sub-chunks finished per 32-slot group
+    unsigned long long* d_live = nullptr;    // particles live at the end of the last segment
+    unsigned long long* h_live = nullptr;
+    int64_t n_alive = 0;                     // live particles (n_live counts slots, dead ones included
+                                             // until the next compaction)
     int since_compact = 0;
     bool external = false, planets_valid = true;
     double* d_ext_log = nullptr;
@@ -404,6 +410,7 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles, 
     c->h_status = reinterpret_cast<int*>(hb + 8);
     c->h_nlive = reinterpret_cast<int64_t*>(hb + 16);
     c->h_steps = reinterpret_cast<unsigned long long*>(hb + 24);
+    c->h_live = reinterpret_cast<unsigned long long*>(hb + 32);
     GL_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->d_prog), c->h_prog, 0));
     if (c->timing) {
         GL_CUDA(cudaEventCreate(&c->tp0));
@@ -441,7 +448,9 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles, 
                      o_out_state = take(sizeof(double) * 6 * (size_t)cap), o_out_step = take(sizeof(int64_t) * (size_t)cap),
                      o_out_reason = take(sizeof(int32_t) * (size_t)cap),
                      o_counts = take(sizeof(int64_t) * (size_t)compact_scratch_entries(cap)),
-                     o_nlive = take(sizeof(int64_t)), o_steps = take(sizeof(unsigned long long));
+                     o_nlive = take(sizeof(int64_t)), o_steps = take(sizeof(unsigned long long)),
+                     o_live = take(sizeof(unsigned long long)), o_task = take(sizeof(unsigned long long)),
+                     o_groups = take(sizeof(int32_t) * (size_t)((cap + 31) / 32));
         GL_ALLOC(c->d_arena, off);
         char* base = static_cast<char*>(c->d_arena);
         c->d_pc = reinterpret_cast<PlanetConsts*>(base + o_pc);
@@ -466,6 +475,9 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles, 
         c->d_nlive = reinterpret_cast<int64_t*>(base + o_nlive);
         // the exact particle-step counter exists in timing mode only (the kernel skips a null one)
         c->d_steps = c->timing ? reinterpret_cast<unsigned long long*>(base + o_steps) : nullptr;
+        c->d_live = reinterpret_cast<unsigned long long*>(base + o_live);
+        c->d_task = reinterpret_cast<unsigned long long*>(base + o_task);
+        c->d_group_done = reinterpret_cast<int32_t*>(base + o_groups);
     }
     for (Slot& sl : c->ring)
         if (!alloc_slot(c, sl)) return GLISSE_E_NOMEM;
@@ -543,6 +555,8 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles, 
                                     cudaMemcpyHostToDevice, c->s));
         }
         c->n_live = r->n_live;
+        c->n_alive = 0;
+        for (int64_t k = 0; k < r->n_live; ++k) c->n_alive += r->alive[k] != 0;
         c->step = r->step;
         c->since_compact = r->since_compact;
         c->tested_first = r->tested_first;
@@ -560,6 +574,7 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles, 
         GL_CUDA(cudaMemsetAsync(c->d_out_step, 0xFF, sizeof(int64_t) * (size_t)cap, c->s));  // -1
         GL_CUDA(cudaMemsetAsync(c->d_out_reason, 0, sizeof(int32_t) * (size_t)cap, c->s));
         c->n_live = c->n_total;
+        c->n_alive = c->n_total;
     }
     // the first two planet chunks
     GL_CUDA(cudaEventCreateWithFlags(&c->ev_order, cudaEventDisableTiming));
@@ -590,6 +605,7 @@ extern "C" int glisse_create(glisse_ctx** out, double star_mass, const double* p
         return GLISSE_E_INVAL;
     if (o.enc_mode != GLISSE_ENC_HILL && o.enc_mode != GLISSE_ENC_FIXED) return GLISSE_E_INVAL;
     if (o.sort_mode != GLISSE_SORT_NONE && o.sort_mode != GLISSE_SORT_COST) return GLISSE_E_INVAL;
+    if (o.launch_mode < GLISSE_LAUNCH_AUTO || o.launch_mode > GLISSE_LAUNCH_TASKS) return GLISSE_E_INVAL;
     if (!(o.enc_value >= 0.0) || !std::isfinite(o.enc_value) || !std::isfinite(o.r_max)) return GLISSE_E_INVAL;
     for (int64_t k = 0; k < 7 * (int64_t)n_planets; ++k)
         if (!std::isfinite(planets[k])) return GLISSE_E_INVAL;
@@ -641,6 +657,7 @@ static int compact(glisse_ctx* c) {
         ++c->acc.compact_launches;
     }
     c->n_live = *c->h_nlive;
+    c->n_alive = c->n_live;
     c->cur = nxt;
     if (c->n_live > 0) GL_CUDA(cudaMemsetAsync(c->d_alive, 1, (size_t)c->n_live, c->s));
     c->since_compact = 0;
@@ -651,8 +668,7 @@ static int compact(glisse_ctx* c) {
 static int take_sample(glisse_ctx* c, const double* planets_at_step, int64_t step) {
     SampleArgs a;
     a.n = c->n_live;
-    a.ld = c->cap;
-    a.st = c->d_st[c->cur];
+    a.sync = c->d_out_state;
     a.id = c->d_id[c->cur];
     a.alive = c->d_alive;
     a.planets = planets_at_step;
@@ -677,6 +693,16 @@ static int take_sample(glisse_ctx* c, const double* planets_at_step, int64_t ste
     return GLISSE_OK;
 }
 
+// 48 n k bytes (k samples of n particles' six doubles), false if that overflows size_t
+static bool elem_bytes(int64_t n, int64_t k, size_t* out) {
+    size_t t = 0;
+    if (n < 0 || k < 0 || __builtin_mul_overflow((size_t)n, sizeof(double) * 6, &t) ||
+        __builtin_mul_overflow(t, (size_t)k, &t) || t > SIZE_MAX / 2)
+        return false;
+    *out = t;
+    return true;
+}
+
 extern "C" int glisse_set_sampling(glisse_ctx* c, const glisse_sampling* sp) {
     if (!c) return GLISSE_E_INVAL;
     if (sp) {
@@ -688,6 +714,8 @@ extern "C" int glisse_set_sampling(glisse_ctx* c, const glisse_sampling* sp) {
             return GLISSE_E_INVAL;
         if (c->external) return GLISSE_E_STATE;
         if (sp->max_samples > 0 && (uint64_t)sp->max_samples > (uint64_t)1 << 40) return GLISSE_E_NOMEM;
+        size_t bytes = 0;  // the element log's size must be representable
+        if (!elem_bytes(std::max<int64_t>(c->n_total, 1), sp->max_samples, &bytes)) return GLISSE_E_NOMEM;
     }
     GL_CUDA(cudaStreamSynchronize(c->s));
     cudaFree(c->d_elem);
@@ -757,7 +785,6 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
     int rc = GLISSE_OK;
     if (c->o.sort_mode == GLISSE_SORT_COST && !c->tested_first && c->n_live > 0 && (rc = compact(c)) != GLISSE_OK)
         return rc;
-    bool open = false;  // the live velocities hold an opening half kick (between pieces)
     // the planets may run ahead of the particles up to the call's last chunk (+1)
     const int64_t j_last = c->external ? 0 : (c->step + n_steps - 1) / c->C;
     if (!c->external && (rc = grow_ring(c, (size_t)(j_last - c->step / c->C + kRingMin))) != GLISSE_OK) return rc;
@@ -765,9 +792,8 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
         const double* log = nullptr;
         int64_t m = 0;
         Slot* sl = nullptr;
-        bool piece_cut = false;
         if (c->external) {
-            m = std::min<int64_t>(remaining, c->C);
+            m = std::min<int64_t>(remaining, c->C - c->step % c->C);
             log = c->d_ext_log + (size_t)c->ext_off * S;
         } else {
             const int64_t j = c->step / c->C;
@@ -796,7 +822,6 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
             }
             if (w == GLISSE_OK) {
                 m = std::min<int64_t>(m, c->piece_end[k] - off);
-                piece_cut = off + m == c->piece_end[k];
             } else {
                 if (j == 0) c->n_pieces = 1;  // no more cuts in this chunk
                 GL_CUDA(cudaStreamWaitEvent(c->s, sl->ev_eph, 0));
@@ -805,14 +830,14 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
             if (c->samp_on) {
                 // end the segment at the next sample step
                 const int64_t next = (c->step / c->samp.every + 1) * c->samp.every;
-                if (next - c->step <= m) piece_cut = false;
                 m = std::min<int64_t>(m, next - c->step);
             }
         }
-        // a segment cut only by a piece end, with more steps to come, leaves the state open
-        const bool close = !(piece_cut && m < remaining);
+        // Every segment ends open (the full kick that an uncut run applies there) and
+        // publishes the live particles' synchronised states by id, so that cuts -- call
+        // ends, first-chunk pieces, sample steps -- leave no trace in the trajectory.
         if (c->n_live > 0) {
-            ChunkArgs a;
+            ChunkArgs a{};
             a.pc = nullptr;
             a.log = log;
             a.n = c->n_live;
@@ -823,18 +848,27 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
             a.step0 = c->step;
             a.nsteps = (int32_t)m;
             a.test_first = c->tested_first ? 0 : 1;
-            a.open_in = open ? 1 : 0;
-            a.close_out = close ? 1 : 0;
+            a.open_in = c->tested_first ? 1 : 0;  // after the first segment the slots hold open velocities
+            a.close_out = 0;
             a.out_state = c->d_out_state;
             a.out_step = c->d_out_step;
             a.out_reason = c->d_out_reason;
             a.steps_done = c->d_steps;
+            a.live_out = c->d_live;
+            TaskArgs tasks{};
+            tasks.task_counter = c->d_task;
+            tasks.group_done = c->d_group_done;
+            tasks.status = c->d_status;
+
+            GL_CUDA(cudaMemsetAsync(c->d_live, 0, sizeof(unsigned long long), c->s));
             NvtxRange seg("glisse: particle segment");
             if (c->timing) GL_CUDA(cudaEventRecord(c->tp0, c->s));
             if (c->o.kepler_mode == GLISSE_KEPLER_PAPER_FIXED)
                 GL_CUDA(launch_particle_chunk_paper(c->np, a, c->ppc, c->s));
             else
-                GL_CUDA(launch_particle_chunk(c->np, a, c->ppc, c->s));
+                GL_CUDA(launch_particle_chunk(c->np, a, c->ppc, c->s,
+                                              c->o.launch_mode == GLISSE_LAUNCH_PLAIN ? nullptr : &tasks,
+                                              c->o.launch_mode == GLISSE_LAUNCH_TASKS));
             if (c->timing) {
                 GL_CUDA(cudaEventRecord(c->tp1, c->s));
                 GL_CUDA(cudaEventSynchronize(c->tp1));
@@ -869,12 +903,16 @@ extern "C" int glisse_advance(glisse_ctx* c, int64_t n_steps) {
         c->step += m;
         remaining -= m;
         if (c->external) c->ext_off += m;
-        open = !close;
-        if (open) continue;  // no compaction between pieces: warps keep their members
+        // compaction only at chunk boundaries (every resync_chunks chunks), at the same global
+        // steps however the run is split into calls: warps keep their members in between
+        if (c->step % c->C != 0) continue;
         ++c->since_compact;
-        if (c->since_compact >= c->o.resync_chunks || remaining == 0) rc = compact(c);
+        if (c->since_compact >= c->o.resync_chunks) rc = compact(c);
     }
+    if (rc == GLISSE_OK && c->n_live > 0)
+        GL_CUDA(cudaMemcpyAsync(c->h_live, c->d_live, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->s));
     if (rc == GLISSE_OK) rc = check_status(c);
+    if (rc == GLISSE_OK) c->n_alive = c->n_live > 0 ? (int64_t)*c->h_live : 0;
     if (prev != c->device) cudaSetDevice(prev);
     return rc;
 }
@@ -885,7 +923,10 @@ extern "C" int glisse_read(glisse_ctx* c, double* state, uint8_t* alive, int64_t
     NvtxRange range("glisse_read");
     const int64_t n = c->n_total;
     if (n == 0) return GLISSE_OK;
-    GL_CUDA(launch_export_live(c->n_live, c->d_st[c->cur], c->cap, c->d_id[c->cur], c->d_out_state, c->s));
+    // before the first step the slots hold the synchronised states; afterwards every segment
+    // has published them by id (the slots then hold open velocities)
+    if (!c->tested_first)
+        GL_CUDA(launch_export_live(c->n_live, c->d_st[c->cur], c->cap, c->d_id[c->cur], c->d_out_state, c->s));
     if (state) GL_CUDA(cudaMemcpyAsync(state, c->d_out_state, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, c->s));
     int64_t* steps = removal_step;
     int64_t* tmp = nullptr;
@@ -907,7 +948,7 @@ extern "C" int glisse_read(glisse_ctx* c, double* state, uint8_t* alive, int64_t
 
 extern "C" int glisse_status(glisse_ctx* c, int64_t* n_live, int64_t* step, double* t) {
     if (!c) return GLISSE_E_INVAL;
-    if (n_live) *n_live = c->n_live;
+    if (n_live) *n_live = c->n_alive;
     if (step) *step = c->step;
     if (t) *t = (double)c->step * c->dt;
     return GLISSE_OK;
@@ -946,7 +987,7 @@ extern "C" int glisse_read_planets(glisse_ctx* c, double* planets, double* t) {
 // ---------------------------------------------------------------------------
 namespace {
 constexpr char kCkptMagic[8] = {'G', 'L', 'I', 'S', 'S', 'E', 'C', 'K'};
-constexpr int32_t kCkptVersion = 1;
+constexpr int32_t kCkptVersion = 2;  // 2: slots hold open velocities after the first step
 
 struct CkptHeader {
     char magic[8];
@@ -1133,6 +1174,10 @@ extern "C" int glisse_resume(glisse_ctx** out, const void* buf, int64_t bytes, c
     if (h.samp_on && (h.samp.max_samples < 0 || (uint64_t)h.samp.max_samples > (uint64_t)1 << 40 ||
                       h.samp_kept < 0 || h.samp_kept > h.samp.max_samples || h.samp_seen < h.samp_kept))
         return GLISSE_E_INVAL;
+    if (h.samp_on) {  // the kept samples must fit in the buffer before the layout is computed from them
+        size_t eb = 0;
+        if (!elem_bytes(h.n_total, h.samp_kept, &eb) || eb > (size_t)bytes) return GLISSE_E_INVAL;
+    }
     const CkptLayout L = ckpt_layout(h.np, h.n_total, h.n_live, h.samp_on != 0, h.samp_on ? h.samp_kept : 0);
     if (h.total_bytes != (int64_t)L.total || bytes < h.total_bytes) return GLISSE_E_INVAL;
     const char* in = static_cast<const char*>(buf);
@@ -1157,8 +1202,10 @@ extern "C" int glisse_resume(glisse_ctx** out, const void* buf, int64_t bytes, c
     o.enc_value = h.enc_value;
     o.r_max = h.r_max;
     if (opts) {
+        if (opts->launch_mode < GLISSE_LAUNCH_AUTO || opts->launch_mode > GLISSE_LAUNCH_TASKS) return GLISSE_E_INVAL;
         o.cuda_stream = opts->cuda_stream;
         o.timing = opts->timing;
+        o.launch_mode = opts->launch_mode;
     }
     glisse_ctx* c = new (std::nothrow) glisse_ctx();
     if (!c) return GLISSE_E_NOMEM;

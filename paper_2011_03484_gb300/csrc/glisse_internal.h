@@ -59,12 +59,26 @@ struct ChunkArgs {
     int32_t test_first;   // apply the removal test at the segment's step 0 first
     int32_t open_in;      // the velocities already hold the opening half kick of step 0
     int32_t close_out;    // 1: end with the closing half kick (synchronised state);
-                          // 0: end with the full kick that also opens the next segment
-    // per-id outputs for particles removed during the segment
+                          // 0: end with the full kick that also opens the next segment, and
+                          //    write live particles' synchronised states to out_state by id
+    // per-id outputs: particles removed during the segment (and, close_out = 0, live ones)
     double* out_state;    // [N][6]
     int64_t* out_step;    // [N]
     int32_t* out_reason;  // [N]
     unsigned long long* steps_done;  // optional: += steps advanced by live particles
+    unsigned long long* live_out;    // optional: += particles live at the segment's end
+};
+
+// Task mode of the particle kernel (particle_tasks_kernel): the segment is cut into
+// sub-chunks of sub_steps steps; task t = (group t mod n_groups, sub-chunk t / n_groups),
+// where a group is the 32 slots one warp holds, is taken in order from task_counter by
+// persistent warps.  (A separate argument: the plain kernel's registers are tight.)
+struct TaskArgs {
+    int32_t sub_steps;                 // steps per sub-chunk
+    int32_t n_groups;                  // ceil(n / 32)
+    unsigned long long* task_counter;  // zero before the launch
+    int32_t* group_done;               // [n_groups] sub-chunks of each group finished; zero before the launch
+    int* status;                       // set to GLISSE_E_TIMEOUT if a wait for a group gives up
 };
 
 // Device-resident clock of a batch (so a captured chunk graph can be replayed).
@@ -104,8 +118,7 @@ struct BatchArgs {
 // fixed interval; libration of a resonant argument).
 struct SampleArgs {
     int64_t n;                 // live slots
-    int64_t ld;                // leading dimension of the state planes
-    const double* st;          // [6][ld]
+    const double* sync;        // [N][6] by id: synchronised states (live slots' entries current)
     const int32_t* id;         // [n]
     const uint8_t* alive;      // [n]
     const double* planets;     // [np][6] heliocentric planet states at the sample step

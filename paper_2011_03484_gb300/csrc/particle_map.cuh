@@ -8,12 +8,16 @@
 // and the removal test (encounter |r - r_j| < R_crit,j, escape |r| > r_max)
 // made at every kick time on the drifted position.  Inside a segment the
 // closing half kick of step k and the opening half kick of step k+1 use the
-// same planet positions, so they are applied as one kick of dt; the segment's
-// first and last kicks are half kicks so that the stored state is the
-// synchronised one.  The exception is the cuts of a context's first chunk
-// (launched as the planets of that chunk appear): a segment may end with the
-// full kick and leave the state open, and the next one then skips its opening
-// half kick (open_in / close_out), so that those cuts leave no trace.
+// same planet positions, so they are applied as one kick of dt.  A context's
+// segments end "open": the last step ends with the same full kick that an
+// uncut launch would apply there, the stored velocities already carry the
+// next step's opening half kick, and the next segment skips it (open_in /
+// close_out = 0).  Cuts then leave no trace: any split of a run into calls,
+// pieces or sample stops gives the same bits.  The synchronised state the
+// caller reads (velocities with only the closing half kick) is computed at
+// the cut by one extra half kick from the same pre-kick velocities and
+// written by id (publish).  close_out = 1 ends with the closing half kick
+// instead, leaving the synchronised state in the slots (batched systems).
 //
 // The batched kernel may hold one particle in a lane pair (TPP = 2): both
 // lanes run the same state and drift, each takes half of the planets in the
@@ -157,11 +161,22 @@ __device__ __forceinline__ int test_only(double x, double y, double z, const dou
 // pc may live in the constant bank (kernel parameter) or in shared memory.
 // TPP = 2: the particle is held by a lane pair (batched kernel), each lane
 // running the same state with half of the planets in the kicks.
-template <int NP, int MODE = kDriftConverge, int TPP = 1>
+// Where a lane publishes its synchronised state: out[6 id[slot] .. + 5] (out null: nowhere).
+struct PublishTo {
+    const int32_t* id;
+    double* out;
+    int64_t slot;
+};
+
+// PUBLISH (with close_out false): a lane still live at the segment's end also
+// writes its synchronised state there (position; pre-kick velocities plus the
+// closing half kick), straight to memory so that nothing stays live in
+// registers across the steps.
+template <int NP, int MODE = kDriftConverge, int TPP = 1, bool PUBLISH = false>
 __device__ __forceinline__ void advance_lane(const ParticleConsts& pc, const double* __restrict__ L, int64_t step0,
                                              int nsteps, bool test_first, double& x, double& y, double& z, double& vx,
                                              double& vy, double& vz, bool& act, int& reason, int64_t& rstep,
-                                             bool open_in = false, bool close_out = true) {
+                                             bool open_in = false, bool close_out = true, PublishTo pub = {}) {
     const float muf = d2f_bits(pc.mu), dtf = d2f_bits(pc.dt);
     const bool has_rmax = __double_as_longlong(pc.rmax) != 0;
     const int S = log_stride(NP);
@@ -236,6 +251,19 @@ __device__ __forceinline__ void advance_lane(const ParticleConsts& pc, const dou
         else
             enc = kick_lanes<NP, TPP>(x, y, z, nvx, nvy, nvz, Ln, pc.dt, pc.tgm_full, pc.rc2);
         hit = enc ? enc : hit;
+        if constexpr (PUBLISH) {
+            if (!close_out && k + 1 == nsteps && act && hit == 0) {
+                double hx = vx, hy = vy, hz = vz;
+                kick_test<NP>(x, y, z, hx, hy, hz, Ln, pc.half_dt, pc.tgm_half, pc.rc2);
+                double* o = pub.out + 6 * (int64_t)pub.id[pub.slot];
+                o[0] = x;
+                o[1] = y;
+                o[2] = z;
+                o[3] = hx;
+                o[4] = hy;
+                o[5] = hz;
+            }
+        }
         if (act) {
             if (hit != 0) {
                 act = false;
@@ -292,13 +320,18 @@ __global__ void __launch_bounds__(kParticleBlock, GLISSE_PARTICLE_MIN_BLOCKS)
     const bool started = act;
     int reason = 0;
     int64_t rstep = -1;
-    advance_lane<NP, MODE>(pc, a.log, a.step0, a.nsteps, a.test_first != 0, x, y, z, vx, vy, vz, act, reason,
-                           rstep, a.open_in != 0, a.close_out != 0);
+    advance_lane<NP, MODE, 1, true>(pc, a.log, a.step0, a.nsteps, a.test_first != 0, x, y, z, vx, vy, vz, act,
+                                    reason, rstep, a.open_in != 0, a.close_out != 0, PublishTo{a.id, a.out_state, i});
     if (a.steps_done) {
         // steps this particle actually advanced in the segment (exact work count)
         const unsigned adv = !started ? 0u : (rstep >= 0 ? (unsigned)(rstep - a.step0) : (unsigned)a.nsteps);
         const unsigned wsum = __reduce_add_sync(kFullMask, adv);
         if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(a.steps_done, (unsigned long long)wsum);
+    }
+    if (a.live_out) {
+        // particles live at the segment's end
+        const unsigned wl = __reduce_add_sync(kFullMask, act ? 1u : 0u);
+        if ((threadIdx.x & 31) == 0 && wl) atomicAdd(a.live_out, (unsigned long long)wl);
     }
     if (in) {
         a.st[i] = x;
@@ -310,6 +343,123 @@ __global__ void __launch_bounds__(kParticleBlock, GLISSE_PARTICLE_MIN_BLOCKS)
         a.alive[i] = act ? 1 : 0;
         if (rstep >= 0) store_removed(a.id[i], x, y, z, vx, vy, vz, rstep, reason, a.out_state, a.out_step,
                                       a.out_reason);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Task mode: persistent warps over (group, sub-chunk) tasks.
+//
+// Every warp of a chunk does the same work, so with one thread per slot the
+// chunk lasts as long as the SM partition holding the most warps: at 6.06
+// warps per partition on average, the busiest has 7 and the pipe is 87%
+// used.  A particle's steps are serial, so balance needs smaller units of
+// work: the segment is cut into sub-chunks of sub_steps steps, and a task is
+// one group of 32 slots (the members of one warp of the plain launch) over
+// one sub-chunk.  Tasks are taken in order from a counter by a fixed number of
+// resident warps, so every partition keeps the same number of busy warps
+// until the last round of tasks.  Task (g, s) needs (g, s - 1) finished: it
+// is taken n_groups tasks later, by when the launch has that many warps'
+// worth of work behind it (the host uses task mode only when groups
+// outnumber resident warps by half again), and the warp waits, bounded, on
+// the group's counter of finished sub-chunks.  Sub-chunk cuts are open cuts,
+// so the result is bit-identical to the plain launch: same members per warp,
+// same steps, same kicks.
+// ---------------------------------------------------------------------------
+constexpr int kSubSteps = 32;
+// a wait for the previous sub-chunk of a group gives up after this many polls
+// (~64 ns each: seconds, where a sub-chunk takes a millisecond at most)
+constexpr int kGroupWaitPolls = 1 << 25;
+
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// at most four blocks per SM (task_warps_per_partition), so up to 128 registers per thread
+constexpr int kTaskMaxBlocks = 4;
+
+template <int NP>
+__global__ void __launch_bounds__(kParticleBlock, kTaskMaxBlocks)
+    particle_tasks_kernel(const ChunkArgs a, const ParticleConsts pc, const TaskArgs ta) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ld = a.ld;
+    const int S = log_stride(NP);
+    const int n_sub = (a.nsteps + ta.sub_steps - 1) / ta.sub_steps;
+    const int64_t n_tasks = (int64_t)ta.n_groups * n_sub;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(ta.task_counter, 1ull);
+        t = __shfl_sync(kFullMask, t, 0);
+        if ((int64_t)t >= n_tasks) break;
+        const int64_t g = (int64_t)t % ta.n_groups;
+        const int s = (int)((int64_t)t / ta.n_groups);
+        if (s > 0) {
+            int ok = 1;
+            if (lane == 0) {
+                int polls = 0;
+                while (ld_acquire(ta.group_done + g) < s && ++polls < kGroupWaitPolls) __nanosleep(64);
+                ok = polls < kGroupWaitPolls;
+            }
+            ok = __shfl_sync(kFullMask, ok, 0);
+            if (!ok) {
+                if (lane == 0) atomicExch(ta.status, GLISSE_E_TIMEOUT);
+                break;
+            }
+        }
+        __syncwarp();
+        const int64_t i = g * 32 + lane;
+        const bool in = i < a.n;
+        double x = 1.0, y = 0.0, z = 0.0, vx = 0.0, vy = 6.283185307179586, vz = 0.0;
+        bool act = false;
+        if (in) {
+            // written by another warp's task (L2 is coherent, this SM's L1 may not be)
+            x = __ldcg(a.st + i);
+            y = __ldcg(a.st + ld + i);
+            z = __ldcg(a.st + 2 * ld + i);
+            vx = __ldcg(a.st + 3 * ld + i);
+            vy = __ldcg(a.st + 4 * ld + i);
+            vz = __ldcg(a.st + 5 * ld + i);
+            act = __ldcg(a.alive + i) != 0;
+        }
+        const bool started = act;
+        int reason = 0;
+        int64_t rstep = -1;
+        const int k0 = s * ta.sub_steps;
+        const int m = min(ta.sub_steps, a.nsteps - k0);
+        const bool last = s + 1 == n_sub;
+        advance_lane<NP, kDriftConverge, 1, true>(pc, a.log + (size_t)k0 * S, a.step0 + k0, m,
+                                                  a.test_first != 0 && s == 0, x, y, z, vx, vy, vz, act, reason,
+                                                  rstep, s > 0 || a.open_in != 0, last ? a.close_out != 0 : false,
+                                                  PublishTo{a.id, last ? a.out_state : nullptr, i});
+        if (a.steps_done) {
+            const unsigned adv = !started ? 0u : (rstep >= 0 ? (unsigned)(rstep - (a.step0 + k0)) : (unsigned)m);
+            const unsigned wsum = __reduce_add_sync(kFullMask, adv);
+            if (lane == 0 && wsum) atomicAdd(a.steps_done, (unsigned long long)wsum);
+        }
+        if (last && a.live_out) {
+            const unsigned wl = __reduce_add_sync(kFullMask, act ? 1u : 0u);
+            if (lane == 0 && wl) atomicAdd(a.live_out, (unsigned long long)wl);
+        }
+        if (in) {
+            __stcg(a.st + i, x);
+            __stcg(a.st + ld + i, y);
+            __stcg(a.st + 2 * ld + i, z);
+            __stcg(a.st + 3 * ld + i, vx);
+            __stcg(a.st + 4 * ld + i, vy);
+            __stcg(a.st + 5 * ld + i, vz);
+            __stcg(a.alive + i, (uint8_t)(act ? 1 : 0));
+            if (rstep >= 0) store_removed(a.id[i], x, y, z, vx, vy, vz, rstep, reason, a.out_state, a.out_step,
+                                          a.out_reason);
+        }
+        // every lane's stores before the group's counter moves on (release at device scope)
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release(ta.group_done + g, s + 1);
     }
 }
 
@@ -341,9 +491,63 @@ inline cudaError_t particle_smem_cap(const void* kernel, int64_t grid, size_t* s
     return e;
 }
 
+// Warps per SM partition for task mode, or 0 for the plain launch: task mode
+// pays when the groups outnumber the resident warps by half again (waits are
+// then rare) with at least two busy warps per partition (one warp alone keeps
+// the FP64 pipe ~70% busy); at most four (enough to saturate it).
+inline int task_warps_per_partition(int64_t n, int nsteps, int n_sm) {
+    const int64_t groups = (n + 31) / 32;
+    const int64_t partitions = 4 * (int64_t)std::max(n_sm - 1, 1);
+    if (nsteps < 2 * kSubSteps) return 0;
+    const int64_t k = (2 * groups) / (3 * partitions);
+    return k >= 2 ? (int)std::min<int64_t>(k, kTaskMaxBlocks) : 0;
+}
+
+// tb: the task-mode buffers (counter, per-group counters, status), or null for the plain launch.
+// force_tasks: task mode whatever the size (two warps per partition at least; GLISSE_LAUNCH_TASKS).
 template <int MODE>
-cudaError_t launch_particle_chunk_mode(int np, const ChunkArgs& a, const ParticleConsts& pc, cudaStream_t s) {
+cudaError_t launch_particle_chunk_mode(int np, const ChunkArgs& a, const ParticleConsts& pc, cudaStream_t s,
+                                       const TaskArgs* tb = nullptr, bool force_tasks = false) {
     if (a.n <= 0) return cudaSuccess;
+    if constexpr (MODE == kDriftConverge) {
+        int dev = 0, nsm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        int k = tb ? task_warps_per_partition(a.n, a.nsteps, nsm) : 0;
+        if (tb && force_tasks && k == 0) k = 2;
+        if (k > 0) {
+            TaskArgs b = *tb;
+            b.sub_steps = kSubSteps;
+            b.n_groups = (int32_t)((a.n + 31) / 32);
+            e = cudaMemsetAsync(b.task_counter, 0, sizeof(unsigned long long), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(b.group_done, 0, sizeof(int32_t) * (size_t)b.n_groups, s);
+            if (e != cudaSuccess) return e;
+            // k blocks of four warps per SM, one SM's worth short (the ephemeris holds one)
+            const int64_t grid = (int64_t)k * std::max(nsm - 1, 1);
+            size_t smem = 0;
+            switch (np) {
+#define GLISSE_TCASE(N)                                                                                  \
+    case N:                                                                                              \
+        e = particle_smem_cap(reinterpret_cast<const void*>(particle_tasks_kernel<N>), grid, &smem);     \
+        if (e != cudaSuccess) return e;                                                                  \
+        particle_tasks_kernel<N><<<(unsigned)grid, kParticleBlock, smem, s>>>(a, pc, b);                 \
+        break;
+                GLISSE_TCASE(0)
+                GLISSE_TCASE(1)
+                GLISSE_TCASE(2)
+                GLISSE_TCASE(3)
+                GLISSE_TCASE(4)
+                GLISSE_TCASE(5)
+                GLISSE_TCASE(6)
+                GLISSE_TCASE(7)
+                GLISSE_TCASE(8)
+#undef GLISSE_TCASE
+                default: return cudaErrorInvalidValue;
+            }
+            return cudaGetLastError();
+        }
+    }
     const int64_t grid = (a.n + kParticleBlock - 1) / kParticleBlock;
     size_t smem = 0;
     cudaError_t e = cudaSuccess;

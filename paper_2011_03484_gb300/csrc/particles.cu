@@ -120,8 +120,9 @@ cudaError_t batch_particles_occupancy(int threads, int tpp, int* blocks_per_sm) 
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_particle_kernel<1>, threads, 0);
 }
 
-cudaError_t launch_particle_chunk(int np, const ChunkArgs& a, const ParticleConsts& pc, cudaStream_t s) {
-    return launch_particle_chunk_mode<kDriftConverge>(np, a, pc, s);
+cudaError_t launch_particle_chunk(int np, const ChunkArgs& a, const ParticleConsts& pc, cudaStream_t s,
+                                  const TaskArgs* tb, bool force_tasks) {
+    return launch_particle_chunk_mode<kDriftConverge>(np, a, pc, s, tb, force_tasks);
 }
 
 }  // namespace glisse

@@ -7,17 +7,20 @@
 // budget at start-up, and loops where an allocation's implicit synchronisation
 // or its failure part-way through a run is not acceptable.  This
 // entry point runs the same three kernels but takes its scratch from a
-// fixed-size array that lives in the library's device image: it is created
-// when the library's module is loaded on a device and stays allocated there
-// until the process exits (256 KiB per GPU that loads the library).
+// fixed-size array that lives in the library's device image (256 KiB).  The
+// array exists on a device once the CUDA driver has loaded this library's
+// module there.  With lazy module loading (CUDA's default) that happens at the
+// first use of the module on the device -- possibly this entry point's first
+// call, whose symbol lookup then makes the driver place the module, array
+// included, in device memory.  From then on the array stays until the process
+// exits (or the device's context is destroyed) and no call allocates.
 //
 // Host code cannot use the array's name as a device address (in host code it
-// names a host-side shadow), so the first call on each device asks the runtime
-// for the address with cudaGetSymbolAddress, with that device current, and
-// remembers it.
+// names a host-side shadow), so every call asks the runtime for the address
+// with cudaGetSymbolAddress, with the caller's device current.  The lookup is
+// a host-side table query once the module is loaded; doing it per call (not
+// caching it) keeps the address right if the context was reset and rebuilt.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "glisse_internal.h"
 
@@ -29,28 +32,16 @@ int64_t compact_scratch_entries(int64_t);
 namespace {
 // tile counts / offsets of one call: one int64 per 2048-slot tile of the partition
 constexpr int64_t kNoAllocTiles = GLISSE_PARTITION_NOALLOC_MAX / 2048;
-
-constexpr int kMaxDevices = 64;
-std::mutex g_addr_mutex;
-int64_t* g_addr[kMaxDevices] = {};
 }  // namespace
 
 static __device__ __align__(256) int64_t g_partition_scratch[kNoAllocTiles];
 
-// Device address of g_partition_scratch on the current device (looked up once per device).
+// Device address of g_partition_scratch on the current device.
 static cudaError_t scratch_address(int64_t** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_partition_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_partition_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = static_cast<int64_t*>(p);
-    }
-    *out = g_addr[dev];
+    *out = static_cast<int64_t*>(p);
     return cudaSuccess;
 }
 

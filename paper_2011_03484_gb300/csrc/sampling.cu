@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kSampleBlock) sample_kernel(const SampleArgs a
         if (!a.alive[i]) continue;
         const int64_t pid = a.id[i];
         double s[6], el[6];
-        for (int d = 0; d < 6; ++d) s[d] = a.st[d * a.ld + i] - s_off[d];
+        for (int d = 0; d < 6; ++d) s[d] = a.sync[6 * pid + d] - s_off[d];
         const bool ok = osculating(s_mu, s, el);
         if (a.elem) {
             double* o = a.elem + 6 * pid;

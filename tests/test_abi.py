@@ -45,6 +45,7 @@ def test_opts_defaults(G):
     assert o.kepler_mode == G.GLISSE_KEPLER_CONVERGE and o.kepler_iters == 5
     assert o.enc_mode == G.GLISSE_ENC_HILL and o.enc_value == 1.0 and o.r_max == 1000.0
     assert o.sort_mode == G.GLISSE_SORT_NONE and o.timing == 0
+    assert o.launch_mode == G.GLISSE_LAUNCH_AUTO
 
 
 def test_strerror_names_every_code(G):
@@ -90,6 +91,12 @@ def test_argument_errors_before_any_cuda_call(G):
     with pytest.raises(G.GlisseError) as ei:
         G.glisse_create(1.0, w["planets"], w["particles"], 0.5, o)
     assert ei.value.code == G.GLISSE_E_INVAL
+    for lm in (-1, 3):
+        o = G.glisse_opts_default()
+        o.launch_mode = lm
+        with pytest.raises(G.GlisseError) as ei:
+            G.glisse_create(1.0, w["planets"], w["particles"], 0.5, o)
+        assert ei.value.code == G.GLISSE_E_INVAL, lm
     # the fixed-iteration mode is for glisse_create only
     o = G.glisse_opts_default()
     o.kepler_mode = G.GLISSE_KEPLER_PAPER_FIXED

@@ -104,12 +104,14 @@ def test_batch_matches_oracle_system_by_system(G, orc):
 @pytest.mark.parametrize("chunk", [128, 1024])
 def test_batch_equals_single_system_runs(G, chunk):
     """Each system of a batch evolves as the single-system path evolves it: same removal
-    steps, and bit-identical states except on lanes that needed the general Kepler
-    solver, whose plain expressions the compiler may contract into FMAs differently
-    in the two kernels (rounding-level differences).  The single-system path runs its
-    first chunk in segments (cut at steps 64, 128, 256, 512) that pass the open kick
-    between them; the batch path does not cut, so this also checks that the cuts leave
-    no trace."""
+    steps, and, within one chunk (chunk >= n), bit-identical states except on lanes that
+    needed the general Kepler solver, whose plain expressions the compiler may contract
+    into FMAs differently in the two kernels (rounding-level differences).  The
+    single-system path runs its first chunk in segments (cut at steps 64, 128, 256, 512)
+    that pass the open kick between them; the batch path does not cut, so this also checks
+    that the cuts leave no trace.  With several chunks (chunk 128) the batch closes every
+    chunk with a half kick while the single-system path keeps its chunk ends open: the
+    states then differ by rounding at each chunk end, within the parity tolerance."""
     b = small_batch(n_systems=6, seed=8)
     n = 700
     g = run_batch(G, b, n, chunk_steps=chunk)
@@ -124,7 +126,8 @@ def test_batch_equals_single_system_runs(G, chunk):
         np.testing.assert_array_equal(g["removal_step"][rows], r["removal_step"])
         np.testing.assert_array_equal(g["removal_reason"][rows], r["removal_reason"])
         e = parity.rel_err(g["state"][rows], r["state"])
-        assert np.mean(e == 0.0) > 0.5, (s, np.mean(e == 0.0))
+        if chunk >= n:
+            assert np.mean(e == 0.0) > 0.5, (s, np.mean(e == 0.0))
         assert e.max() <= parity.state_tol(n), (s, e.max())
 
 
@@ -183,6 +186,20 @@ def test_full_batched_workload_sampled(G, orc):
     parity.assert_parity(rep)
     assert g["n_live"] == int(g["alive"].sum())
     assert np.all((g["removal_step"] >= 0) == ~g["alive"])
+
+
+def test_batch_long_horizon_against_the_oracle(G, orc):
+    """Six systems of the batched workload's shape (2-8 planets, dt = P_inner / 20) over
+    10^4 steps, in 1024-step chunks with graph replay, against the oracle system by system
+    under the phase-scaled bounds."""
+    b = small_batch(n_systems=6, seed=21, n_min=20, n_max=64)
+    n = 10_000
+    g = run_batch(G, b, n, chunk_steps=1024)
+    o, sens, unst, ids, ph = oracle_batch(orc, b, n)
+    rep = parity.compare(sub(g, ids), o, n, sens, unst, ph)
+    print(rep)
+    parity.assert_parity(rep)
+    assert rep["n"] >= 200 and rep["regular"] >= 20
 
 
 def test_steps_done_counts_each_particles_steps(G):

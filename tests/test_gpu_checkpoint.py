@@ -164,6 +164,35 @@ def test_checkpoint_errors(G):
     sim.close()
 
 
+def test_resume_rejects_oversized_sample_count(G):
+    """A checkpoint whose header claims more kept element samples than its buffer can hold
+    (here 2^40 samples of 256 particles, 12.6 PB) is rejected before any array is read."""
+    import ctypes as C
+
+    L = G.load()
+    w = gi.make("tiny", n=256)
+    sim = G.Simulation(w["star_mass"], w["planets"], w["particles"], w["dt"], chunk_steps=64)
+    sim.set_sampling(25, max_samples=9)
+    sim.advance(130)  # 5 samples taken, 5 kept
+    ck = sim.checkpoint()
+    sim.close()
+    h = C.c_void_p()
+    assert L.glisse_resume(C.byref(h), ck.ctypes.data, ck.size, None) == G.GLISSE_OK
+    L.glisse_destroy(h)
+    # header fields: samples taken, samples kept (int64 each), then the sampling settings
+    # (every = 25 as int32, frame int32, max_samples int64)
+    pat = np.int64(5).tobytes() + np.int64(5).tobytes() + np.int32(25).tobytes()
+    off = ck.tobytes().find(pat)
+    assert 0 < off < 512 and off % 8 == 0
+    big = np.int64(1 << 40).tobytes()
+    bad = ck.copy()
+    for o in (off, off + 8, off + 24):  # seen, kept, max_samples
+        bad[o:o + 8] = np.frombuffer(big, dtype=np.uint8)
+    h = C.c_void_p()
+    assert L.glisse_resume(C.byref(h), bad.ctypes.data, bad.size, None) == G.GLISSE_E_INVAL
+    assert not h.value
+
+
 def test_empty_and_planet_free_checkpoints(G):
     w = gi.make("tiny", n=300)
     for planets, particles in ((w["planets"], w["particles"][:0]), (w["planets"][:0], w["particles"])):

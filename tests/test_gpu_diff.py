@@ -84,20 +84,24 @@ def test_jacobian_is_symplectic(G):
 
 
 def test_tangent_matches_central_differences(G):
-    import torch
-
+    """Every column of the Jacobian (positions and velocities) against central differences of the
+    map: h = 1e-7 AU for positions and 1e-8 AU/yr for velocities (about 4e-9 and 8e-9 of the
+    coordinates).  Such a quotient is good to about eps |x| / h (rounding, ~3e-8 here) plus
+    h^2 times the third derivative, relative to the Jacobian's scale."""
     w, pl, s0 = _workload(32)
     n = 2000
     _, J, rstep, _ = gpu_jacobian(G, pl, s0, w["dt"], n)
     dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n)
-    h = 1e-7  # AU
-    for c in range(3):
+    scale = np.abs(J).max(axis=(1, 2))
+    for c in range(6):
+        h = 1e-7 if c < 3 else 1e-8
         e = np.zeros_like(s0)
         e[:, c] = h
         sp = dm.forward(_cuda(s0 + e))[0].cpu().numpy()
         sm = dm.forward(_cuda(s0 - e))[0].cpu().numpy()
         fd = (sp - sm) / (2 * h)
-        err = np.abs(fd - J[:, :, c]).max(axis=1) / np.abs(J).max(axis=(1, 2))
+        err = np.abs(fd - J[:, :, c]).max(axis=1) / scale
+        print("column", c, "max", err[rstep < 0].max(), "median", np.median(err[rstep < 0]))
         assert err[rstep < 0].max() < 1e-5, (c, err.max())
     dm.close()
 
@@ -231,6 +235,36 @@ def test_growth_gradient_matches_oracle(G, orc):
           int(regular.sum()))
     assert regular.sum() >= 16
     assert rel[regular].max() < 1e-6
+
+
+def test_growth_gradient_long_horizon(G, orc):
+    """The gradient of the growth indicator on 128 particles over the differentiation workload's
+    full 10^4 steps, by both GPU routes (forward mode, and the reverse sweep after a
+    checkpointed forward pass), against the oracle's difference quotients, on orbits that never
+    came within 5 R_crit.  Over 10^4 steps the growth is strongly nonlinear in the state and
+    the quotients are the limit: with steps of 1e-5 and 1e-6 AU (Richardson-extrapolated) they
+    differ from each other by a median 4e-7 and at most 4e-6 of the gradient, so the GPU is held
+    to 1e-5 of each particle's gradient scale (median 1e-6) against the 1e-6 AU quotients."""
+    w, pl, s0 = _workload(128)
+    n = 10_000
+    t0 = _seed(s0)
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n, 256)
+    fwd, _ = dm.growth_gradient(_cuda(s0), _cuda(t0))
+    _, tan1, _, _, _ = dm.forward(_cuda(s0), _cuda(t0[None]))
+    rev, _ = dm.backward_growth(None, _cuda(np.ones(len(s0))), tan1[0])
+    dm.close()
+    _, log, _ = orc.planet_wh(1.0, pl, w["dt"], n)
+    rc = orc.rcrit(1.0, pl)
+    ref, _, ok = orc.growth_gradient(1.0, pl[:, 0], log, w["dt"], s0, t0, rc, 1000.0, h_pos=1e-6, h_vel=1e-7)
+    o = orc.run(1.0, pl, s0, w["dt"], n)
+    scale = np.abs(ref).max(axis=1)
+    good = ok & (o["closest"] >= 25.0) & (o["removal_step"] < 0)
+    for name, got in (("forward", fwd.cpu().numpy()), ("reverse", rev.cpu().numpy())):
+        rel = np.abs(got - ref).max(axis=1) / scale
+        print(name, "growth gradient over 1e4 steps: max", rel[good].max(), "median", np.median(rel[good]),
+              "compared", int(good.sum()))
+        assert rel[good].max() < 1e-5 and np.median(rel[good]) < 1e-6
+    assert good.sum() >= 48
 
 
 def test_growth_gradient_gives_the_directional_derivative(G):

@@ -108,7 +108,8 @@ def test_long_call_equals_chunk_sized_calls(G):
     one = run_gpu(G, w, n, chunk_steps=C)
     many = run_gpu(G, w, n, splits=[C] * (n // C) + [n % C], chunk_steps=C)
     grown = run_gpu(G, w, n, splits=[192, 2808], chunk_steps=C)
-    for g in (many, grown):
+    odd = run_gpu(G, w, n, splits=[37] * 81 + [3], chunk_steps=C)
+    for g in (many, grown, odd):
         for k in ("state", "removal_step", "removal_reason", "planets"):
             np.testing.assert_array_equal(g[k], one[k], err_msg=k)
     assert (one["removal_step"] >= 0).sum() > 0
@@ -126,9 +127,10 @@ def test_tiny_workload_parity(G, orc):
     print(rep)
     assert_parity(rep)
     assert rep["removed"] > 0  # the workload exercises removal
-    # regular = insensitive to one ulp and never within 5 R_crit (~15% of this workload over 1e4 steps);
-    # the far-only criterion below covers the ~500 particles that never came within 5 R_crit
-    assert rep["regular"] > 0.1 * rep["n"]
+    # regular = insensitive to one ulp under all eight reruns and never within 5 R_crit (~7% of this
+    # workload over 1e4 steps); the far-only criterion below covers the ~500 particles that never
+    # came within 5 R_crit
+    assert rep["regular"] > 0.05 * rep["n"]
     # without the sensitivity reruns: never within 5 R_crit -> 1e-10
     rep5 = compare(g, o, n)
     assert rep5["regular_over_tol"] == 0, rep5
@@ -199,7 +201,7 @@ def test_kepler_drift_all_orbit_types(G, orc):
         err = parity.rel_err(g["state"], o["state"])
         # orbits that cover many radians per step are ill-conditioned in any FP64
         # implementation: compare with the oracle's own one-ulp sensitivity
-        bound = np.maximum(1e-13 * n**1.5, parity.SENS_FACTOR * sens)
+        bound = np.maximum(1e-13 * n**1.5, parity.sens_factor(n) * sens)
         bad = err > bound
         assert not bad.any(), (n, err[bad][:5], bound[bad][:5], np.where(bad)[0][:5])
 
@@ -235,22 +237,61 @@ def test_fixed_distance_criterion(G, orc):
 # ---------------------------------------------------------------------------
 # segment / chunk / compaction boundaries
 # ---------------------------------------------------------------------------
-def test_split_invariance(G):
-    """advance(a) + advance(b) equals advance(a + b): removal steps exactly; live states to
-    the parity tolerance (a split replaces one merged kick by two half kicks, a
-    rounding-level change that the later steps carry like any other)."""
+def test_split_invariance(G, orc):
+    """advance(a) + advance(b) equals advance(a + b) bit for bit at a fixed chunk length and
+    compaction interval: between calls the slots keep the velocities an uncut run has there
+    (the next opening half kick applied), and compaction happens at chunk boundaries only.
+    A different chunk length or compaction interval moves the compaction points, which can
+    change the warp a particle shares and with it the degree of its drift's Stumpff
+    polynomials (a rounding-level change); there removal steps are still exact, and states
+    agree within the sensitivity bound.  (A rounding-level change cannot meet 1e-13 on this
+    workload: after 2500 steps the oracle's one-ulp reruns move every particle by at least
+    1e-13, the median by 8e-13.)"""
     w = gi.make("tiny", n=1024)
     n = 2500
-    ref = run_gpu(G, w, n)
+    refs = {}
     for splits, opt in [([1000, 1500], {}), ([1, 1, 2498], {}), ([700, 700, 1100], {"chunk_steps": 300}),
-                        ([n], {"chunk_steps": 128, "resync_chunks": 3})]:
-        g = run_gpu(G, w, n, splits=splits, **opt)
-        np.testing.assert_array_equal(g["removal_step"], ref["removal_step"])
-        np.testing.assert_array_equal(g["removal_reason"], ref["removal_reason"])
-        alive = g["alive"]
-        e = parity.rel_err(g["state"][alive], ref["state"][alive])
-        assert np.median(e) < 1e-12, (splits, opt, np.median(e))
-        assert e.max() < 1e3 * parity.state_tol(n), (splits, opt, e.max())
+                        ([1024, 1476], {}), ([64] * 39 + [4], {"chunk_steps": 128, "resync_chunks": 3}),
+                        ([99] * 25 + [25], {"chunk_steps": 128, "resync_chunks": 3})]:
+        key = tuple(sorted(opt.items()))
+        if key not in refs:
+            refs[key] = run_gpu(G, w, n, **opt)
+        ref = refs[key]
+        g = run_gpu(G, w, sum(splits), splits=splits, **opt)
+        if sum(splits) == n:
+            for k in ("state", "alive", "removal_step", "removal_reason", "planets"):
+                np.testing.assert_array_equal(g[k], ref[k], err_msg=f"{splits} {opt} {k}")
+    # across chunk lengths / compaction intervals: rounding-level differences only
+    o, sens, unstable = run_orc_sens(orc, w, n)
+    base = refs[()]
+    for key, g in refs.items():
+        if key == ():
+            continue
+        ok = ~unstable & (o["margin"] >= parity.BAND)
+        np.testing.assert_array_equal(g["removal_step"][ok], base["removal_step"][ok])
+        alive = g["alive"] & base["alive"]
+        e = parity.rel_err(g["state"][alive], base["state"][alive])
+        assert (e <= np.maximum(1e-15, parity.sens_factor(n) * sens[alive])).all(), (key, e.max())
+
+
+@pytest.mark.parametrize("name,n,steps,opt", [
+    ("longrun", 131072, 2100, {}),                                   # AUTO picks tasks; first-chunk pieces
+    ("longrun", 33, 300, {}),
+    ("longrun", 1025, 700, {"chunk_steps": 128, "resync_chunks": 3}),
+    ("eccentric", 4096, 900, {"chunk_steps": 256}),                  # removals, general-solver lanes
+    ("tiny", 1024, 500, {"chunk_steps": 100}),
+])
+def test_launch_shapes_are_bit_identical(G, name, n, steps, opt):
+    """The persistent task launch (32-slot groups over 32-step sub-chunks, open cuts between
+    them) gives what one thread per slot gives, bit for bit, at any size (TASKS forces it on
+    sizes AUTO would launch plainly)."""
+    w = gi.make(name, n=n)
+    outs = [run_gpu(G, w, steps, launch_mode=m, **opt)
+            for m in (G.GLISSE_LAUNCH_PLAIN, G.GLISSE_LAUNCH_TASKS, G.GLISSE_LAUNCH_AUTO)]
+    for g in outs[1:]:
+        for k in ("state", "alive", "removal_step", "removal_reason", "planets"):
+            np.testing.assert_array_equal(g[k], outs[0][k], err_msg=k)
+        assert g["n_live"] == outs[0]["n_live"] == int(outs[0]["alive"].sum())
 
 
 # ---------------------------------------------------------------------------
@@ -285,11 +326,42 @@ def test_external_ephemeris_cr3bp(G, orc):
     base = orc_run(st0)
     sens, _ = parity.sensitivity(base, [orc_run(p) for p in parity.perturbed_inputs(st0)])
     e = parity.rel_err(g["state"], base["state"])
-    bound = np.maximum(parity.state_tol(n), parity.SENS_FACTOR * sens)
+    bound = np.maximum(parity.state_tol(n), parity.sens_factor(n) * sens)
     assert (e <= bound).all(), (e.max(), np.where(e > bound)[0])
     cj0 = pins.jacobi_constant(1.0, m1, a1, 0.0, r1[0], v1[0], st0)
     cj1 = pins.jacobi_constant(1.0, m1, a1, t[-1], r1[-1], v1[-1], g["state"])
     assert np.abs((cj1 - cj0) / cj0).max() < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# close passes: the kick at small separation, short horizon, absolute bound
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,n_ids", [("tiny", 1024), ("longrun", 2048)])
+def test_close_pass_absolute_parity(G, orc, name, n_ids):
+    """Particles passing within 1-5 R_crit of a planet (and those a pass removes), started 20
+    steps before their deepest approach from the oracle's state there, with the same planet
+    positions on both sides (glisse_set_ephemeris), and compared after 50 steps.  Over so few
+    steps rounding has not been amplified (the oracle's eight one-ulp reruns move nearly all of
+    them by at most 1e-13), so the kick at small separation is held to an absolute bound:
+    1e-12 relative in position and velocity; removal step and reason exact."""
+    w = gi.make(name)
+    ids = np.arange(n_ids) if name == "tiny" else gi.subset_ids(name, n_ids)
+    log, groups = parity.close_pass_groups(orc, w, ids)
+    reps = []
+    for k0, _, st0 in groups:
+        sl = log[k0:k0 + parity.CLOSE_SPAN + 1]
+        sim = G.Simulation(w["star_mass"], w["planets"], st0, w["dt"], chunk_steps=64)
+        sim.set_ephemeris(sl)
+        sim.advance(parity.CLOSE_SPAN)
+        g = sim.read()
+        sim.close()
+        reps.append(parity.close_pass_compare(orc, w, st0, sl, g))
+    t = parity.close_pass_totals(reps)
+    print(name, t)
+    assert t["mismatch"] == 0, t
+    assert t["quiet_over"] == 0 and t["loud_over"] == 0, t
+    assert t["cases"] >= 100 and t["deep"] >= 20 and t["removed"] >= 5, t
+    assert t["loud"] <= 0.05 * t["cases"], t
 
 
 # ---------------------------------------------------------------------------
@@ -335,7 +407,7 @@ def test_eccentric_workload_parity(G, orc):
     assert rep["removed"] > 100
 
 
-@pytest.mark.parametrize("name,n_steps,k", [("longrun", 10_000, 2048), ("belt", 4096, 1024)])
+@pytest.mark.parametrize("name,n_steps,k", [("longrun", 10_000, 2048), ("belt", 10_000, 1024)])
 def test_full_size_sampled_parity(G, orc, name, n_steps, k):
     w = gi.make(name)
     g = run_gpu(G, w, n_steps)  # chunk 1024, compaction every chunk (defaults)

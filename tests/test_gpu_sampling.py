@@ -91,8 +91,9 @@ def test_resonant_particles_librate_on_the_gpu(G, orc):
 
 
 def test_sampling_leaves_the_map_unchanged(G):
-    """Sampling ends segments at the sample steps (half kicks there instead of one merged kick):
-    the states differ from an unsampled run only by rounding, as in the split-invariance tests."""
+    """Sampling ends segments at the sample steps; those cuts are open (the merged kick is
+    applied as in an uncut run, the sampled state is computed beside it), so the run is the
+    unsampled run bit for bit."""
     w = gi.make("tiny")
     n = 2000
     a = run_gpu(G, w["planets"], w["particles"], w["dt"], n, 300, 2, frame=G.GLISSE_FRAME_HELIO)
@@ -100,10 +101,8 @@ def test_sampling_leaves_the_map_unchanged(G):
     sim.advance(n)
     b = sim.read()
     sim.close()
-    assert np.mean(a["removal_step"] == b["removal_step"]) > 0.99
-    both = a["alive"] & b["alive"]
-    e = parity.rel_err(a["state"][both], b["state"][both])
-    assert np.median(e) < 1e-12 and e.max() < 1e3 * parity.state_tol(n)
+    for k in ("state", "alive", "removal_step", "removal_reason"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
 
 
 def test_element_log_capacity_and_flags_count(G):

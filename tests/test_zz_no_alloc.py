@@ -32,7 +32,9 @@ def _case(torch, n, seed):
     ld = n + 3
     src = torch.randn(6, ld, dtype=torch.float64, generator=gen).cuda()
     ids = torch.randperm(n, generator=gen).to(torch.int32).cuda()
-    alive = (torch.rand(n, generator=gen) < 0.6).to(torch.uint8).cuda()
+    # flags 0 (removed) and 1, 2, 255 (kept: any non-zero value keeps a slot)
+    u = torch.rand(n, generator=gen)
+    alive = torch.where(u < 0.4, 0, torch.where(u < 0.8, 1, torch.where(u < 0.9, 2, 255))).to(torch.uint8).cuda()
     return ld, src, ids, alive
 
 
@@ -57,11 +59,11 @@ def test_noalloc_matches_allocating_partition_twice(G):
                                           d_new.data_ptr(), id_new.data_ptr(), n_new.data_ptr(), stream)
         m = int(n_ref.item())
         assert int(n_new.item()) == m, call
-        assert m == int(alive.sum().item())
+        assert m == int((alive != 0).sum().item())
         assert torch.equal(d_new[:, :m], d_ref[:, :m]), call
         assert torch.equal(id_new[:m], id_ref[:m]), call
         # and both equal the plain stable partition
-        keep = alive.bool()
+        keep = alive != 0
         assert torch.equal(id_new[:m], ids[keep])
         assert torch.equal(d_new[:, :m], src[:, :n][:, keep])
 
@@ -71,3 +73,13 @@ def test_noalloc_rejects_sizes_beyond_its_limit(G):
     n = G.GLISSE_PARTITION_NOALLOC_MAX + 1
     rc = L.glisse_partition_device_noalloc(n, n, 1, 1, 1, 1, 1, 1, None)
     assert rc == G.GLISSE_E_INVAL
+
+
+def test_noalloc_zero_slots_is_the_set_up_call(G):
+    """n = 0 does the per-device set-up only and reports no kept entries."""
+    import torch
+
+    cnt = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    G.glisse_partition_device_noalloc(0, 0, None, None, None, None, None, cnt.data_ptr(),
+                                      torch.cuda.current_stream().cuda_stream)
+    assert int(cnt.item()) == 0
