@@ -446,16 +446,17 @@ def time_diff(G, torch, dev, stream, n_particles=0, n_steps=0, K=256):
     ms_grow_rev, _ = timed(lambda: dm.backward_growth(torch.ones_like(x0), ones, out_t[1][0]))
     ms_grow, _ = timed(lambda: dm.growth_gradient(x0, tan[0].contiguous()))
     dm.close()
-    # tape mode: the forward pass records every step, the backward pass only sweeps back
-    tape = None
-    need = 112 * n * n_steps
-    if torch.cuda.mem_get_info(dev)[0] > need + (8 << 30):
-        dt_ = G.DiffMap(1.0, pl, n, w.dt, n_steps, 0)
-        ms_fwd_tape, _ = timed(lambda: dt_.forward(x0))
-        ms_bwd_tape, _ = timed(lambda: dt_.backward(torch.ones_like(x0)))
-        dt_.close()
-        tape = {"forward_ms": ms_fwd_tape, "adjoint_ms": ms_bwd_tape, "tape_bytes": need,
-                "forward_plus_adjoint_ratio": (ms_fwd_tape + ms_bwd_tape) / ms_map}
+    # the memory-aware default (GLISSE_DIFF_AUTO): tape mode -- the forward pass records every
+    # step, the backward pass only sweeps back -- when the record fits in half of the free
+    # device memory, else checkpoints every 256 steps
+    da = G.DiffMap(1.0, pl, n, w.dt, n_steps, G.GLISSE_DIFF_AUTO)
+    ms_fwd_auto, _ = timed(lambda: da.forward(x0))
+    ms_bwd_auto, _ = timed(lambda: da.backward(torch.ones_like(x0)))
+    auto_k = da.checkpoint_every
+    da.close()
+    tape = {"checkpoint_every": auto_k, "forward_ms": ms_fwd_auto, "adjoint_ms": ms_bwd_auto,
+            "record_bytes": 112 * n * n_steps if auto_k == 0 else None,
+            "forward_plus_adjoint_ratio": (ms_fwd_auto + ms_bwd_auto) / ms_map}
     ps = n * n_steps  # particle-steps of the differentiable run (removed particles stop early)
     line = {
         "metric": "FP64 particle-steps/s of the differentiable map (forward, adjoint) vs the plain map",
@@ -473,7 +474,7 @@ def time_diff(G, torch, dev, stream, n_particles=0, n_steps=0, K=256):
                             "forward_mode_ms": ms_grow, "forward_mode_ratio": ms_grow / ms_map},
         "cost_ratio_to_plain_map": {"forward": ms_fwd / ms_map, "forward_with_tangent": ms_fwd_t / ms_map,
                                     "forward_plus_adjoint": (ms_fwd + ms_bwd) / ms_map},
-        "tape_mode": tape,
+        "auto_mode": tape,
     }
     return line
 
@@ -606,8 +607,9 @@ def batched_record(G, torch, dev, stream, plain_value, steps=3, warmup=3):
 
 def diff_record(G, torch, dev, stream, n_steps=2048, K=256):
     """The differentiation workload (65536 particles) over a reduced number of steps: the plain
-    map, the differentiable forward pass, the adjoint pass (checkpoints every K steps, and tape
-    mode), the growth gradient; each as a cost ratio to the plain map over the same steps."""
+    map, the differentiable forward pass, the adjoint pass (checkpoints every K steps, and the
+    memory-aware default, which on this GPU records every step), the growth gradient; each as
+    a cost ratio to the plain map over the same steps."""
     r = time_diff(G, torch, dev, stream, 0, n_steps, K)
     m = r["plain_map"]["ms"]
     out = {"workload": r["config"]["workload"], "plain_map_ms": m,
@@ -617,12 +619,12 @@ def diff_record(G, torch, dev, stream, n_steps=2048, K=256):
                      "growth_gradient_reverse_sweep_with_tangent_forward":
                          r["growth_gradient"]["forward_with_tangent_plus_reverse_ratio"],
                      "growth_gradient_forward_mode": r["growth_gradient"]["forward_mode_ratio"]}}
-    if r["tape_mode"]:
-        t = r["tape_mode"]
-        out["ratio"]["tape_forward"] = t["forward_ms"] / m
-        out["ratio"]["tape_adjoint"] = t["adjoint_ms"] / m
-        out["ratio"]["tape_forward_plus_adjoint"] = t["forward_plus_adjoint_ratio"]
-        out["tape_bytes"] = t["tape_bytes"]
+    t = r["auto_mode"]
+    out["ratio"]["auto_forward"] = t["forward_ms"] / m
+    out["ratio"]["auto_adjoint"] = t["adjoint_ms"] / m
+    out["ratio"]["auto_forward_plus_adjoint"] = t["forward_plus_adjoint_ratio"]
+    out["auto_checkpoint_every"] = t["checkpoint_every"]
+    out["auto_record_bytes"] = t["record_bytes"]
     return out
 
 

@@ -350,11 +350,19 @@ typedef struct glisse_diff glisse_diff; /* opaque; owned by the library */
  * checkpoint_every = 0 (tape mode): the forward pass records every step (112 B
  * per particle per step, e.g. 73 GB for 65536 particles over 10^4 steps) and
  * the backward pass does not recompute; NOMEM if the device cannot hold it.
+ * checkpoint_every = GLISSE_DIFF_AUTO: tape mode when its record takes at
+ * most half of the device memory free at the call, else checkpoints every
+ * 256 steps (glisse_diff_checkpoint_every tells which).
  * n_steps <= INT32_MAX (the planet log is one chunk of that many steps).
  * opts: enc_mode, enc_value and r_max apply.  Errors: INVAL, NOMEM, CUDA, KEPLER. */
+#define GLISSE_DIFF_AUTO (-1)
 int glisse_diff_create(glisse_diff** out, double star_mass, const double* planets, int32_t n_planets,
                        int64_t n_particles, double dt, int64_t n_steps, int32_t checkpoint_every,
                        const glisse_opts* opts);
+
+/* The checkpoint interval in effect (0: tape mode), e.g. after GLISSE_DIFF_AUTO.
+ * Errors: INVAL. */
+int glisse_diff_checkpoint_every(glisse_diff* d, int32_t* checkpoint_every);
 
 /* state0 -> state1 over n_steps (explicit half kicks; removal as in glisse_advance, a
  * removed particle's output being its frozen state).  n_tangents (0..6) tangent

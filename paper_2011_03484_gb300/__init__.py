@@ -37,6 +37,7 @@ GLISSE_ENC_FIXED = 1
 GLISSE_SORT_NONE = 0
 GLISSE_SORT_COST = 1
 GLISSE_LAUNCH_AUTO, GLISSE_LAUNCH_PLAIN, GLISSE_LAUNCH_TASKS = 0, 1, 2
+GLISSE_DIFF_AUTO = -1
 GLISSE_MATH_RSQRT, GLISSE_MATH_RCP, GLISSE_MATH_RCP40, GLISSE_MATH_KRCUBE = 0, 1, 2, 3
 GLISSE_MATH_FLOAT_SQUARE, GLISSE_MATH_FLOAT_CUBE, GLISSE_MATH_D2F = 4, 5, 6
 GLISSE_FRAME_HELIO = 0
@@ -51,7 +52,7 @@ EXPORTED = (
     "glisse_batch_timings", "glisse_batch_steps_done", "glisse_batch_tune", "glisse_batch_set_launch",
     "glisse_batch_destroy",
     "glisse_diff_create", "glisse_diff_forward", "glisse_diff_backward", "glisse_diff_backward_growth",
-    "glisse_diff_growth_gradient",
+    "glisse_diff_growth_gradient", "glisse_diff_checkpoint_every",
     "glisse_diff_destroy",
     "glisse_set_sampling", "glisse_read_elements", "glisse_read_libration", "glisse_selftest_math",
     "glisse_checkpoint_size", "glisse_checkpoint", "glisse_resume", "glisse_sizes",
@@ -202,6 +203,8 @@ def load(build_if_missing: bool = False):
     L.glisse_diff_growth_gradient.restype = C.c_int
     L.glisse_diff_destroy.argtypes = [vp]
     L.glisse_diff_destroy.restype = None
+    L.glisse_diff_checkpoint_every.argtypes = [vp, C.POINTER(C.c_int32)]
+    L.glisse_diff_checkpoint_every.restype = C.c_int
     L.glisse_set_sampling.argtypes = [vp, C.POINTER(glisse_sampling)]
     L.glisse_set_sampling.restype = C.c_int
     L.glisse_read_elements.argtypes = [vp, dp, i64p, C.c_int64, i64p]
@@ -655,6 +658,13 @@ def glisse_diff_create(star_mass, planets, n_particles, dt, n_steps, checkpoint_
     return h
 
 
+def glisse_diff_checkpoint_every(h) -> int:
+    """Checkpoint interval in effect (0: tape mode)."""
+    k = C.c_int32()
+    _check(load().glisse_diff_checkpoint_every(h, C.byref(k)), "glisse_diff_checkpoint_every")
+    return int(k.value)
+
+
 def glisse_diff_forward(h, state0, state1, tangent0=None, tangent1=None, log_growth=None, removal_step=None,
                         removal_reason=None, stream=0):
     """All arguments after h are device addresses (ints) or None; see include/glisse.h."""
@@ -695,9 +705,10 @@ class DiffMap:
         for k, v in opt.items():
             setattr(o, k, v)
         self.n = int(n_particles)
-        self.tape = int(checkpoint_every) == 0
         self.h = None
         self.h = glisse_diff_create(star_mass, planets, n_particles, dt, n_steps, checkpoint_every, o)
+        self.checkpoint_every = glisse_diff_checkpoint_every(self.h)  # GLISSE_DIFF_AUTO resolved
+        self.tape = self.checkpoint_every == 0
         self.forward_calls = 0
 
     @staticmethod

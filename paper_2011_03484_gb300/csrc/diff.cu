@@ -139,8 +139,9 @@ __global__ void __launch_bounds__(kDiffBlock, TMAX == 0 ? 7 : (TMAX == 1 ? 4 : 1
     for (int k = 0; k < TA; ++k)
 #pragma unroll
         for (int c = 0; c < 6; ++c) t[k][c] = (k < a.ntan) ? a.tan0[((int64_t)k * a.n + i) * 6 + c] : 0.0;
+    // |t0|^2 and |J t0|^2 with explicit fma, exactly as the growth-gradient kernel forms them
     double n0 = 0.0;
-    for (int c = 0; c < 6; ++c) n0 += t[0][c] * t[0][c];
+    for (int c = 0; c < 6; ++c) n0 = fma(t[0][c], t[0][c], n0);
     int64_t rstep = -1;
     int reason = 0;
     const bool has_rmax = __double_as_longlong(pc.rmax) != 0;
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(kDiffBlock, TMAX == 0 ? 7 : (TMAX == 1 ? 4 : 1
             for (int c = 0; c < 6; ++c) a.tan1[((int64_t)q * a.n + i) * 6 + c] = t[q][c];
     if (a.log_growth) {
         double n1 = 0.0;
-        for (int c = 0; c < 6; ++c) n1 += t[0][c] * t[0][c];
+        for (int c = 0; c < 6; ++c) n1 = fma(t[0][c], t[0][c], n1);
         a.log_growth[i] = (a.ntan > 0 && n0 > 0.0) ? 0.5 * log(n1 / n0) : 0.0;
     }
     a.rstep[i] = rstep;
@@ -618,6 +619,12 @@ static void diff_free(glisse_diff* d) {
 
 extern "C" void glisse_diff_destroy(glisse_diff* d) { diff_free(d); }
 
+extern "C" int glisse_diff_checkpoint_every(glisse_diff* d, int32_t* checkpoint_every) {
+    if (!d || !checkpoint_every) return GLISSE_E_INVAL;
+    *checkpoint_every = d->tape ? 0 : d->K;
+    return GLISSE_OK;
+}
+
 #define GD_CUDA(x)                    \
     do {                              \
         cudaError_t e_ = (x);         \
@@ -639,7 +646,7 @@ extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const dou
     if (opts) o = *opts;
     if (!(star_mass > 0.0) || n_planets < 0 || n_planets > GLISSE_MAX_PLANETS || (n_planets > 0 && !planets) ||
         n_particles < 0 || n_steps < 0 || n_steps > INT32_MAX || !(dt != 0.0) || !std::isfinite(dt) ||
-        checkpoint_every < 0)
+        checkpoint_every < GLISSE_DIFF_AUTO)
         return GLISSE_E_INVAL;
     // derivatives are of the converged drift only
     if (o.kepler_mode != GLISSE_KEPLER_CONVERGE || o.sort_mode != GLISSE_SORT_NONE) return GLISSE_E_INVAL;
@@ -659,6 +666,18 @@ extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const dou
     d->np = n_planets;
     d->n = n_particles;
     d->nsteps = n_steps;
+    if (checkpoint_every == GLISSE_DIFF_AUTO) {
+        // the per-step record when it fits in half of the free device memory
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            (void)cudaGetLastError();
+            rc = GLISSE_E_CUDA;
+            goto fail;
+        }
+        const double tape_b = 8.0 * kScratchRows * (double)std::max<int64_t>(n_particles, 1) *
+                              (double)std::max<int64_t>(n_steps, 1);
+        checkpoint_every = tape_b <= 0.5 * (double)free_b ? 0 : 256;
+    }
     d->tape = checkpoint_every == 0;
     d->K = d->tape ? (int32_t)std::max<int64_t>(std::min<int64_t>(n_steps, INT32_MAX), 1) : checkpoint_every;
     if (d->tape && n_steps > INT32_MAX) {

@@ -444,12 +444,16 @@ cudaError_t launch_eph_setup(const double* planets, int np, double m0, double G,
 cudaError_t launch_eph_chunk(const PlanetConsts* pc, double* jac, double dt, int nsteps, double* log, double* hist,
                              int* status, cudaStream_t s, int* progress) {
     int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(eph_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, eph_chunk_kernel);
+    // all of a block's shared memory: the kernel's own hand-off ring plus the rest as dynamic
+    const int dyn = optin - (int)fa.sharedSizeBytes;
+    if (e == cudaSuccess && dyn < 0) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(eph_chunk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
-    eph_chunk_kernel<<<1, kEphThreads, (size_t)optin, s>>>(pc, jac, dt, nsteps, log, hist, status, progress);
+    eph_chunk_kernel<<<1, kEphThreads, (size_t)dyn, s>>>(pc, jac, dt, nsteps, log, hist, status, progress);
     return cudaGetLastError();
 }
 

@@ -19,10 +19,11 @@
 // planets run further ahead, up to the call's last chunk (grow_ring, kEphQueue).  The first chunk has nothing to overlap with: its planet
 // kernel starts in glisse_create, publishes its progress to host-mapped memory,
 // and the particles of that chunk run in segments launched as their planet steps
-// appear (the segments pass the open kick between them, so the cuts leave no
-// trace in the results).  After each segment (a particle launch over at most one
-// chunk) live particles are compacted every resync_chunks segments; the cuts in
-// the first chunk do not count as segments.
+// appear.  Every segment (a particle launch over at most one chunk) ends open:
+// the slots keep the velocities with the next opening half kick applied and the
+// kernel publishes the synchronised states by id, so cuts -- call ends, the
+// first chunk's pieces, sample steps -- leave no trace in the results.  Live
+// particles are compacted at chunk boundaries, every resync_chunks chunks.
 #include <cuda_runtime.h>
 
 #include <algorithm>

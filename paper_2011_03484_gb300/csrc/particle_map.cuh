@@ -252,7 +252,7 @@ __device__ __forceinline__ void advance_lane(const ParticleConsts& pc, const dou
             enc = kick_lanes<NP, TPP>(x, y, z, nvx, nvy, nvz, Ln, pc.dt, pc.tgm_full, pc.rc2);
         hit = enc ? enc : hit;
         if constexpr (PUBLISH) {
-            if (!close_out && k + 1 == nsteps && act && hit == 0) {
+            if (pub.out && !close_out && k + 1 == nsteps && act && hit == 0) {
                 double hx = vx, hy = vy, hz = vz;
                 kick_test<NP>(x, y, z, hx, hy, hz, Ln, pc.half_dt, pc.tgm_half, pc.rc2);
                 double* o = pub.out + 6 * (int64_t)pub.id[pub.slot];

@@ -241,9 +241,11 @@ def test_two_lanes_per_particle_match_the_oracle(G, orc):
     assert done == int(np.where(rs >= 0, rs, n).sum())  # each particle counted once
 
 
-def test_two_lanes_equal_one_lane_up_to_rounding(G):
+def test_two_lanes_equal_one_lane_up_to_rounding(G, orc):
     """The pair sums its two partial kicks, so states differ from the one-lane kernel by
-    rounding only; removal steps agree."""
+    rounding only; removal steps agree, and states agree within the parity bound (the
+    regular-orbit tolerance, or sens_factor(n) times the oracle's one-ulp sensitivity for
+    orbits a planet passage makes chaotic)."""
     b = small_batch(n_systems=5, seed=13)
     n = 800
     out = []
@@ -255,9 +257,13 @@ def test_two_lanes_equal_one_lane_up_to_rounding(G):
         out.append(sim.read())
         sim.close()
     assert np.mean(out[0]["removal_step"] == out[1]["removal_step"]) > 0.999
+    _, sens, _, ids, _ = oracle_batch(orc, b, n)
+    s_by_id = np.zeros(len(out[0]["alive"]))
+    s_by_id[ids] = sens
     both = out[0]["alive"] & out[1]["alive"]
     e = parity.rel_err(out[0]["state"][both], out[1]["state"][both])
-    assert np.median(e) < 1e-12 and e.max() < parity.state_tol(n), (np.median(e), e.max())
+    bound = np.maximum(parity.state_tol(n), parity.sens_factor(n) * s_by_id[both])
+    assert np.median(e) < 1e-12 and (e <= bound).all(), (np.median(e), e.max(), (e / bound).max())
 
 
 def test_set_launch_rejects_bad_shapes(G):

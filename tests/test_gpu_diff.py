@@ -237,6 +237,28 @@ def test_growth_gradient_matches_oracle(G, orc):
     assert rel[regular].max() < 1e-6
 
 
+def test_auto_storage_picks_the_record_when_it_fits(G):
+    """GLISSE_DIFF_AUTO on a small map resolves to tape mode (its record is far below half the
+    free memory) and gives what explicit tape mode gives, bit for bit."""
+    import torch
+
+    w, pl, s0 = _workload(512)
+    n = 700
+    g = _cuda(np.random.default_rng(4).normal(size=s0.shape))
+    outs = []
+    for k in (G.GLISSE_DIFF_AUTO, 0):
+        dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n, k)
+        assert dm.checkpoint_every == 0 and dm.tape
+        s1 = dm.forward(_cuda(s0))[0]
+        outs.append((s1.cpu().numpy(), dm.backward(g).cpu().numpy()))
+        dm.close()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n, 128)
+    assert dm.checkpoint_every == 128 and not dm.tape
+    dm.close()
+
+
 def test_growth_gradient_long_horizon(G, orc):
     """The gradient of the growth indicator on 128 particles over the differentiation workload's
     full 10^4 steps, by both GPU routes (forward mode, and the reverse sweep after a

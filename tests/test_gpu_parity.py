@@ -74,6 +74,7 @@ def test_planet_ephemeris_parity(G, orc, n_steps):
     e = parity.rel_err(g["planets"][:, 1:], pl[:, 1:]).max()
     dM = 2 * math.pi * w["dt"] / 5.2**1.5
     tol = max(2 * 10 * 2.0**-53 * dM * max(n_steps, 1) ** 1.5, 1e-14)
+    print(f"planets after {n_steps} steps: max rel {e:.3e} (bound {tol:.1e})")
     assert e < tol, (e, tol)
     np.testing.assert_array_equal(g["planets"][:, 0], w["planets"][:, 0])
 
@@ -131,9 +132,16 @@ def test_tiny_workload_parity(G, orc):
     # workload over 1e4 steps); the far-only criterion below covers the ~500 particles that never
     # came within 5 R_crit
     assert rep["regular"] > 0.05 * rep["n"]
-    # without the sensitivity reruns: never within 5 R_crit -> 1e-10
+    # the criterion of the short tests (no reruns): never within 5 R_crit -> 1e-10.  Here it is
+    # informational: a far orbit that is chaotic all the same (its one-ulp reruns diverge) is
+    # judged by its sensitivity above, like any other
     rep5 = compare(g, o, n)
-    assert rep5["regular_over_tol"] == 0, rep5
+    far = g["alive"] & (o["removal_step"] < 0) & (o["closest"] >= 25.0)
+    e = parity.rel_err(g["state"], o["state"])
+    worst = np.argsort(np.where(far, e, 0.0))[-3:]
+    print("far-only:", rep5["regular"], "particles, worst", [(int(k), float(e[k]), float(sens[k])) for k in worst])
+    over = far & (e > parity.state_tol(n))
+    assert (sens[over] > parity.regular_limit(n)).all(), [(int(k), e[k], sens[k]) for k in np.where(over)[0]]
 
 
 @pytest.mark.parametrize("n_steps", [1, 2, 100, 1500])
