@@ -54,7 +54,7 @@ def flop_per_step(np_: int) -> int:
 DFMA_PER_CLK_PER_SM = 2
 
 
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "particle_chunk_kernel_longrun.txt")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "particle_tasks_kernel_longrun.txt")
 KERNEL_SOURCES = ["particle_map.cuh", "particles.cu", "kepler.cuh", "device_math.cuh", "glisse_internal.h"]
 
 
@@ -455,7 +455,7 @@ def time_diff(G, torch, dev, stream, n_particles=0, n_steps=0, K=256):
     auto_k = da.checkpoint_every
     da.close()
     tape = {"checkpoint_every": auto_k, "forward_ms": ms_fwd_auto, "adjoint_ms": ms_bwd_auto,
-            "record_bytes": 112 * n * n_steps if auto_k == 0 else None,
+            "record_bytes": 8 * (14 + 2 * len(pl)) * n * n_steps if auto_k == 0 else None,
             "forward_plus_adjoint_ratio": (ms_fwd_auto + ms_bwd_auto) / ms_map}
     ps = n * n_steps  # particle-steps of the differentiable run (removed particles stop early)
     line = {
@@ -783,21 +783,28 @@ def main():
         out_h = {"state": pinned((n, 6), torch.float64), "alive": pinned((n,), torch.uint8),
                  "removal_step": pinned((n,), torch.int64), "removal_reason": pinned((n,), torch.int32)}
         times, done_e = [], 0
+        phases = np.zeros(4)  # create (with the H2D copy), advance, read (with the D2H copy), destroy
         for k in range(args.e2e_steps + 1):
             t0 = time.perf_counter()
             sim = G.Simulation(w.star_mass, pl_h, pa_h, w.dt, chunk_steps=w.chunk, enc_value=w.k_hill,
                                r_max=w.r_max, kepler_mode=kmode, kepler_iters=args.kepler_iters,
                                sort_mode=G.GLISSE_SORT_COST if args.sort else G.GLISSE_SORT_NONE)
+            t1 = time.perf_counter()
             sim.advance(w.chunk)
+            t2 = time.perf_counter()
             out = sim.read(out_h)
+            t3 = time.perf_counter()
             sim.close()
-            dt_ = time.perf_counter() - t0
+            t4 = time.perf_counter()
             if k > 0:
-                times.append(dt_)
+                times.append(t4 - t0)
+                phases += np.array([t1 - t0, t2 - t1, t3 - t2, t4 - t3])
                 # steps each particle advanced: up to its removal step, else the whole chunk
                 rs = out["removal_step"]
                 done_e += int(np.where(rs >= 0, rs, w.chunk).sum())
         e2e = {"value": done_e / sum(times), "unit": UNIT,
+               "ms_per_step": {name: 1e3 * v / max(len(times), 1)
+                               for name, v in zip(("create_h2d", "advance", "read_d2h", "destroy"), phases)},
                "h2d_bytes_per_step": int(particles.nbytes + planets.nbytes),
                "d2h_bytes_per_step": int(out["state"].nbytes + out["removal_step"].nbytes +
                                          out["removal_reason"].nbytes + n),
@@ -840,7 +847,8 @@ def main():
         "sort": "by expected Kepler-solve cost, costliest first" if args.sort else None,
         "roofline": None if paper else {
             "bound": "alu", "achieved": achieved * 1e-9, "peak": peak * 1e-9, "unit": "GFLOP/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel": "particle_chunk_kernel<4>",
+            "frac": achieved / peak, "traffic": traffic,
+            "kernel": "particle_tasks_kernel<4> (the task launch AUTO picks for this workload)",
             "kernel_ms_avg": kernel_ms, "flop_per_particle_step": flop_per_step(np_),
             "flop_count": "the kernel's own FP64 work per particle-step (static count, equal to ncu's "
                           "executed DADD/DMUL/DFMA mix); the oracle's count is given beside it",

@@ -346,10 +346,11 @@ typedef struct glisse_diff glisse_diff; /* opaque; owned by the library */
 /* Planets as in glisse_create; n_particles states per forward call; the planet
  * log of n_steps steps is computed on the device here.  checkpoint_every >= 1:
  * the backward pass recomputes that many steps per segment (storage: 48 B per
- * particle per checkpoint plus 112 B per particle per step of one segment).
- * checkpoint_every = 0 (tape mode): the forward pass records every step (112 B
- * per particle per step, e.g. 73 GB for 65536 particles over 10^4 steps) and
- * the backward pass does not recompute; NOMEM if the device cannot hold it.
+ * particle per checkpoint plus 112 + 16 n_planets B per particle per step of
+ * one segment).  checkpoint_every = 0 (tape mode): the forward pass records
+ * every step (112 + 16 n_planets B per particle per step, e.g. 115 GB for
+ * 65536 particles and 4 planets over 10^4 steps) and the backward pass does
+ * not recompute; NOMEM if the device cannot hold it.
  * checkpoint_every = GLISSE_DIFF_AUTO: tape mode when its record takes at
  * most half of the device memory free at the call, else checkpoints every
  * 256 steps (glisse_diff_checkpoint_every tells which).

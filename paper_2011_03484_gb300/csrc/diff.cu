@@ -23,8 +23,10 @@
 // second series).
 // Tape mode (checkpoint_every = 0) keeps that record for every step of the
 // run, written by the forward pass itself: the backward pass is the reverse
-// sweep alone, at 112 B per particle-step of device memory (73 GB for 65536
-// particles over 10^4 steps, which HBM holds).
+// sweep alone, at 112 + 16 N_p B per particle-step of device memory (176 B with
+// four planets: 115 GB for 65536 particles over 10^4 steps, which HBM holds).
+// The record also keeps the closing kick's s_j and 1/|d_j|^2, so the sweep
+// does not evaluate the kick's reciprocals again.
 // A removed particle's output is its frozen state; its derivatives are those
 // of that frozen state (the steps after removal contribute nothing).
 //
@@ -54,6 +56,11 @@ cudaError_t launch_eph_chunk(const PlanetConsts*, double*, double, int, double*,
 
 constexpr int kMaxTangents = 6;
 constexpr int kScratchRows = 14;  // pre-drift state (6), post-drift position (3), s, tau, G_4, G_5, 1/R
+// Rows of one step's record: the kScratchRows of the drift, then the closing kick's
+// s_j = tau G m_j / |d_j|^3 and 1/|d_j|^2 (40-bit) for each planet j, which the forward
+// pass (or the recompute) forms anyway, so the reverse sweep reads them instead of
+// evaluating two reciprocals per planet again.
+__host__ __device__ constexpr int record_rows(int np) { return kScratchRows + 2 * np; }
 constexpr int kDiffBlock = 128;
 
 struct DiffArgs {
@@ -71,7 +78,7 @@ struct DiffArgs {
     int64_t* rstep;         // [n] removal step (-1 live)
     int32_t* reason;        // [n]
     double* ckpt;           // [ceil(nsteps / K)][6][n]
-    double* scratch;        // [K][kScratchRows][n]
+    double* scratch;        // [K][record_rows(NP)][n]
     const double* grad1;    // [n][6]
     double* grad0;          // [n][6]
     // growth indicator of tangent 0 (glisse_diff_backward_growth)
@@ -82,9 +89,11 @@ struct DiffArgs {
 };
 
 // v += tau a(r) for the log step L; returns the lowest planet index whose encounter test fires.
+// rec (optional): a step record (stride ld), which receives s_j and 1/|d_j|^2 of this kick.
 template <int NP>
 __device__ __forceinline__ int kick_state(double st[6], const double* __restrict__ L, double tau,
-                                          const double (&tgm)[kMaxPlanets], const double (&rc2)[kMaxPlanets]) {
+                                          const double (&tgm)[kMaxPlanets], const double (&rc2)[kMaxPlanets],
+                                          double* rec = nullptr, int64_t ld = 0) {
     const double h0x = L[kRec * NP], h0y = L[kRec * NP + 1], h0z = L[kRec * NP + 2];
     st[3] = fma(tau, h0x, st[3]);
     st[4] = fma(tau, h0y, st[4]);
@@ -96,6 +105,10 @@ __device__ __forceinline__ int kick_state(double st[6], const double* __restrict
         const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
         hit = lt_nonneg(d2, rc2[j]) ? (j + 1) : hit;
         const double s = k_rcube(d2, tgm[j]);
+        if (rec) {
+            rec[(kScratchRows + j) * ld] = s;
+            rec[(kScratchRows + NP + j) * ld] = rcp_40(d2);
+        }
         st[3] = fma(-s, dx, st[3]);
         st[4] = fma(-s, dy, st[4]);
         st[5] = fma(-s, dz, st[5]);
@@ -124,41 +137,35 @@ __device__ __forceinline__ void kick_jac(const T r[3], const double* __restrict_
     }
 }
 
-// TMAX: compile-time tangent capacity (0, 1 or kMaxTangents) so that the
-// tangent vectors stay in registers; tangents a.ntan..TMAX-1 are zero.
-template <int NP, int TMAX>
-__global__ void __launch_bounds__(kDiffBlock, TMAX == 0 ? 7 : (TMAX == 1 ? 4 : 1)) diff_forward_kernel(const DiffArgs a, const ParticleConsts pc) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const int S = log_stride(NP);
-    constexpr int T = TMAX;
-    constexpr int TA = TMAX > 0 ? TMAX : 1;
-    double st[6], t[TA][6];
-    for (int c = 0; c < 6; ++c) st[c] = a.state0[6 * i + c];
+// kick_jac at the closing kick of a recorded step: s_j and 1/|d_j|^2 come from the
+// record (rec: its kick rows, stride ld), the same values kick_jac would form.
+template <int NP>
+__device__ __forceinline__ void kick_jac_rec(const double r[3], const double* __restrict__ L,
+                                             const double* __restrict__ rec, int64_t ld, const double w[3],
+                                             double out[3]) {
 #pragma unroll
-    for (int k = 0; k < TA; ++k)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) t[k][c] = (k < a.ntan) ? a.tan0[((int64_t)k * a.n + i) * 6 + c] : 0.0;
-    // |t0|^2 and |J t0|^2 with explicit fma, exactly as the growth-gradient kernel forms them
-    double n0 = 0.0;
-    for (int c = 0; c < 6; ++c) n0 = fma(t[0][c], t[0][c], n0);
-    int64_t rstep = -1;
-    int reason = 0;
-    const bool has_rmax = __double_as_longlong(pc.rmax) != 0;
-    // removal test at t_0
-    {
-        double tmp[6];
-        for (int c = 0; c < 6; ++c) tmp[c] = st[c];
-        const int hit = kick_state<NP>(tmp, a.log, 0.0, pc.tgm_half, pc.rc2);
-        const double r2 = st[0] * st[0] + st[1] * st[1] + st[2] * st[2];
-        const int esc = (has_rmax && lt_nonneg(pc.rmax2, r2)) ? GLISSE_REMOVED_ESCAPE : 0;
-        if (hit || esc) {
-            rstep = 0;
-            reason = hit ? hit : esc;
-        }
+    for (int j = 0; j < NP; ++j) {
+        const double dx = r[0] - L[kRec * j], dy = r[1] - L[kRec * j + 1], dz = r[2] - L[kRec * j + 2];
+        const double s = rec[j * ld];
+        const double c = (3.0 * fma(dx, w[0], fma(dy, w[1], dz * w[2]))) * rec[(NP + j) * ld];
+        out[0] = fma(-s, fma(-c, dx, w[0]), out[0]);
+        out[1] = fma(-s, fma(-c, dy, w[1]), out[1]);
+        out[2] = fma(-s, fma(-c, dz, w[2]), out[2]);
     }
-    bool opened = false;  // this step's opening kick was merged into the previous closing kick
-    for (int64_t k = 0; k < a.nsteps && rstep < 0; ++k) {
+}
+
+// Steps [k_lo, k_hi) of the forward pass for particle i (stopping at a removal): state
+// st, tangents t[0..T), removal step / reason, `opened` (the step's opening kick was merged
+// into the previous closing kick).  Checkpoints at every multiple of K and the tape
+// record of each step are written as the steps pass, so any split of [0, nsteps) into
+// consecutive calls does the same arithmetic.
+template <int NP, int T, int TA>
+__device__ __forceinline__ void forward_steps(const DiffArgs& a, const ParticleConsts& pc, int64_t i, double (&st)[6],
+                                              double (&t)[TA][6], int64_t& rstep, int& reason, bool& opened,
+                                              int64_t k_lo, int64_t k_hi) {
+    const int S = log_stride(NP);
+    const bool has_rmax = __double_as_longlong(pc.rmax) != 0;
+    for (int64_t k = k_lo; k < k_hi && rstep < 0; ++k) {
         if (k % a.K == 0) {
             double* cp = a.ckpt + (k / a.K) * 6 * a.n;
             for (int c = 0; c < 6; ++c) cp[c * a.n + i] = st[c];
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(kDiffBlock, TMAX == 0 ? 7 : (TMAX == 1 ? 4 : 1
         }
         double pre[6];
         for (int c = 0; c < 6; ++c) pre[c] = st[c];
-        double* tp = a.tape ? a.scratch + k * kScratchRows * a.n + i : nullptr;
+        double* tp = a.tape ? a.scratch + k * record_rows(NP) * a.n + i : nullptr;
         if (tp)
             for (int c = 0; c < 6; ++c) tp[c * a.n] = pre[c];
         DriftScalars d;
@@ -187,8 +194,8 @@ __global__ void __launch_bounds__(kDiffBlock, TMAX == 0 ? 7 : (TMAX == 1 ? 4 : 1
             break;
         }
         for (int c = 0; c < 3; ++c) {
-            st[c] = d.f * pre[c] + d.g * pre[3 + c];
-            st[3 + c] = d.fd * pre[c] + d.gd * pre[3 + c];
+            st[c] = fma(d.f, pre[c], d.g * pre[3 + c]);
+            st[3 + c] = fma(d.fd, pre[c], d.gd * pre[3 + c]);
         }
         if (tp) {
             for (int c = 0; c < 3; ++c) tp[(6 + c) * a.n] = st[c];
@@ -213,11 +220,11 @@ __global__ void __launch_bounds__(kDiffBlock, TMAX == 0 ? 7 : (TMAX == 1 ? 4 : 1
         const bool merge = (k + 1 < a.nsteps) && ((k + 1) % a.K != 0);
         const double tau = merge ? pc.dt : pc.half_dt;
         const double(&tgm)[kMaxPlanets] = merge ? pc.tgm_full : pc.tgm_half;
-        const double r2 = st[0] * st[0] + st[1] * st[1] + st[2] * st[2];
+        const double r2 = fma(st[0], st[0], fma(st[1], st[1], st[2] * st[2]));
         int hit = (has_rmax && lt_nonneg(pc.rmax2, r2)) ? GLISSE_REMOVED_ESCAPE : 0;
         double nst[6];
         for (int c = 0; c < 6; ++c) nst[c] = st[c];
-        const int enc = kick_state<NP>(nst, L1, tau, tgm, pc.rc2);
+        const int enc = kick_state<NP>(nst, L1, tau, tgm, pc.rc2, tp, a.n);
         hit = enc ? enc : hit;
         if (hit) {
             rstep = k + 1;
@@ -229,14 +236,59 @@ __global__ void __launch_bounds__(kDiffBlock, TMAX == 0 ? 7 : (TMAX == 1 ? 4 : 1
         for (int c = 0; c < 6; ++c) st[c] = nst[c];
         opened = merge;
     }
+}
+
+// The removal test at t_0 (before the first step).
+template <int NP>
+__device__ __forceinline__ void forward_test_first(const DiffArgs& a, const ParticleConsts& pc, const double (&st)[6],
+                                                   int64_t& rstep, int& reason) {
+    const bool has_rmax = __double_as_longlong(pc.rmax) != 0;
+    double tmp[6];
+    for (int c = 0; c < 6; ++c) tmp[c] = st[c];
+    const int hit = kick_state<NP>(tmp, a.log, 0.0, pc.tgm_half, pc.rc2);
+    const double r2 = fma(st[0], st[0], fma(st[1], st[1], st[2] * st[2]));
+    const int esc = (has_rmax && lt_nonneg(pc.rmax2, r2)) ? GLISSE_REMOVED_ESCAPE : 0;
+    if (hit || esc) {
+        rstep = 0;
+        reason = hit ? hit : esc;
+    }
+}
+
+// |t0|^2 and |J t0|^2 with explicit fma, exactly as the growth-gradient kernel forms them.
+template <int TA>
+__device__ __forceinline__ double norm2(const double (&t)[TA][6]) {
+    double n = 0.0;
+    for (int c = 0; c < 6; ++c) n = fma(t[0][c], t[0][c], n);
+    return n;
+}
+
+// TMAX: compile-time tangent capacity (0, 1 or kMaxTangents) so that the
+// tangent vectors stay in registers; tangents a.ntan..TMAX-1 are zero.
+template <int NP, int TMAX>
+__global__ void __launch_bounds__(kDiffBlock, TMAX == 0 ? 7 : (TMAX == 1 ? 4 : 1)) diff_forward_kernel(const DiffArgs a, const ParticleConsts pc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    constexpr int T = TMAX;
+    constexpr int TA = TMAX > 0 ? TMAX : 1;
+    double st[6], t[TA][6];
+    for (int c = 0; c < 6; ++c) st[c] = a.state0[6 * i + c];
+#pragma unroll
+    for (int k = 0; k < TA; ++k)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) t[k][c] = (k < a.ntan) ? a.tan0[((int64_t)k * a.n + i) * 6 + c] : 0.0;
+    const double n0 = norm2<TA>(t);
+    int64_t rstep = -1;
+    int reason = 0;
+    forward_test_first<NP>(a, pc, st, rstep, reason);
+    bool opened = false;
+    forward_steps<NP, T, TA>(a, pc, i, st, t, rstep, reason, opened, 0, a.nsteps);
     for (int c = 0; c < 6; ++c) a.state1[6 * i + c] = st[c];
 #pragma unroll
     for (int q = 0; q < T; ++q)
         if (q < a.ntan)
             for (int c = 0; c < 6; ++c) a.tan1[((int64_t)q * a.n + i) * 6 + c] = t[q][c];
     if (a.log_growth) {
-        double n1 = 0.0;
-        for (int c = 0; c < 6; ++c) n1 = fma(t[0][c], t[0][c], n1);
+        const double n1 = norm2<TA>(t);
         a.log_growth[i] = (a.ntan > 0 && n0 > 0.0) ? 0.5 * log(n1 / n0) : 0.0;
     }
     a.rstep[i] = rstep;
@@ -271,7 +323,7 @@ __global__ void __launch_bounds__(kDiffBlock) diff_growth_kernel(const DiffArgs 
         double tmp[6];
         for (int k = 0; k < 6; ++k) tmp[k] = st[k];
         const int hit = kick_state<NP>(tmp, a.log, 0.0, pc.tgm_half, pc.rc2);
-        const double r2 = st[0] * st[0] + st[1] * st[1] + st[2] * st[2];
+        const double r2 = fma(st[0], st[0], fma(st[1], st[1], st[2] * st[2]));
         removed = hit != 0 || (has_rmax && lt_nonneg(pc.rmax2, r2));
     }
     bool opened = false;
@@ -295,8 +347,8 @@ __global__ void __launch_bounds__(kDiffBlock) diff_growth_kernel(const DiffArgs 
             break;
         }
         for (int q = 0; q < 3; ++q) {
-            st[q] = d.f * pre[q] + d.g * pre[3 + q];
-            st[3 + q] = d.fd * pre[q] + d.gd * pre[3 + q];
+            st[q] = fma(d.f, pre[q], d.g * pre[3 + q]);
+            st[3 + q] = fma(d.fd, pre[q], d.gd * pre[3 + q]);
         }
         bool bad = false;
         for (int q = 0; q < 6; ++q) bad |= nonfinite_bits(st[q]);
@@ -315,7 +367,7 @@ __global__ void __launch_bounds__(kDiffBlock) diff_growth_kernel(const DiffArgs 
         const bool merge = (k + 1 < a.nsteps) && ((k + 1) % a.K != 0);
         const double tau = merge ? pc.dt : pc.half_dt;
         const double(&tgm)[kMaxPlanets] = merge ? pc.tgm_full : pc.tgm_half;
-        const double r2 = st[0] * st[0] + st[1] * st[1] + st[2] * st[2];
+        const double r2 = fma(st[0], st[0], fma(st[1], st[1], st[2] * st[2]));
         double nst[6];
         for (int q = 0; q < 6; ++q) nst[q] = st[q];
         const int enc = kick_state<NP>(nst, L1, tau, tgm, pc.rc2);
@@ -338,11 +390,83 @@ __global__ void __launch_bounds__(kDiffBlock) diff_growth_kernel(const DiffArgs 
     if (c == 0 && a.log_growth) a.log_growth[i] = (n0 > 0.0 && n1 > 0.0) ? 0.5 * log(n1 / n0) : 0.0;
 }
 
+// The backward pass over one checkpoint segment [k0, k1) of particle i (k1 <= kend, its
+// removal step or nsteps): recompute the segment from checkpoint cseg into the scratch
+// (checkpoint mode; tape mode has the record already), then the adjoint sweep over the
+// steps [s_lo, s_hi) of the segment, last step first.  l: cotangent of the state at s_hi
+// in, at s_lo out.  The plain launch sweeps whole segments; the task launch cuts the one
+// segment of tape mode into sub-chunks.
+template <int NP>
+__device__ __forceinline__ void backward_piece(const DiffArgs& a, const ParticleConsts& pc, int64_t i,
+                                               double (&l)[6], int64_t cseg, int64_t k0, int64_t k1,
+                                               int64_t s_lo, int64_t s_hi, int64_t kend, bool cut_after_drift,
+                                               bool cut_before_drift) {
+    const int S = log_stride(NP);
+    double st[6];
+    const double* cp = a.ckpt + cseg * 6 * a.n;
+    for (int c = 0; c < 6; ++c) st[c] = cp[c * a.n + i];
+    // recompute the segment: pre-drift state (6) and post-drift position (3) per step
+    // (in tape mode the forward pass wrote them already)
+    const int64_t krec = a.tape ? k0 : k1;  // steps to recompute: none in tape mode
+    for (int64_t k = k0; k < krec; ++k) {
+        const double* L0 = a.log + k * S;
+        if (k == k0) kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);  // else merged below
+        double* sc = a.scratch + (k - k0) * record_rows(NP) * a.n + i;
+        for (int c = 0; c < 6; ++c) sc[c * a.n] = st[c];
+        if (k == kend - 1 && cut_before_drift) break;
+        DriftScalars d;
+        drift_scalars(pc.mu, pc.dt, st, d);
+        sc[9 * a.n] = d.s;
+        sc[10 * a.n] = d.tau;
+        sc[11 * a.n] = d.G[4];
+        sc[12 * a.n] = d.G[5];
+        sc[13 * a.n] = d.inv_R;
+        double pre[6];
+        for (int c = 0; c < 6; ++c) pre[c] = st[c];
+        for (int c = 0; c < 3; ++c) {
+            st[c] = fma(d.f, pre[c], d.g * pre[3 + c]);
+            st[3 + c] = fma(d.fd, pre[c], d.gd * pre[3 + c]);
+        }
+        for (int c = 0; c < 3; ++c) sc[(6 + c) * a.n] = st[c];
+        // closing kick of step k merged with the opening kick of step k + 1 (as in the forward
+        // pass); at the segment's end the closing half kick, recorded only
+        if (k + 1 < krec) {
+            kick_state<NP>(st, a.log + (k + 1) * S, pc.dt, pc.tgm_full, pc.rc2, sc, a.n);
+        } else {
+            double tmp[6];
+            for (int c = 0; c < 6; ++c) tmp[c] = st[c];
+            kick_state<NP>(tmp, a.log + (k + 1) * S, pc.half_dt, pc.tgm_half, pc.rc2, sc, a.n);
+        }
+    }
+    // adjoint sweep, last step first
+    for (int64_t k = s_hi - 1; k >= s_lo; --k) {
+        const double* sc = a.scratch + (k - k0) * record_rows(NP) * a.n + i;
+        double pre[6], post[3];
+        for (int c = 0; c < 6; ++c) pre[c] = sc[c * a.n];
+        for (int c = 0; c < 3; ++c) post[c] = sc[(6 + c) * a.n];
+        const bool last = (k == kend - 1);
+        if (!(last && (cut_after_drift || cut_before_drift))) {
+            // closing kick at t_{k+1}: lr += tau A(post) lv, tau = dt inside the segment
+            // (merged with the opening kick of step k + 1), dt/2 at its end; its s_j and
+            // 1/|d_j|^2 are in the step's record
+            kick_jac_rec<NP>(post, a.log + (k + 1) * S, sc + kScratchRows * a.n, a.n, l + 3, l);
+        }
+        if (!(last && cut_before_drift)) {
+            DriftScalars d;
+            drift_restore(pc.mu, pc.dt, pre, sc[9 * a.n], sc[10 * a.n], d);
+            drift_finish_stored(pc.mu, d, sc[11 * a.n], sc[12 * a.n], sc[13 * a.n]);
+            drift_adjoint(pc.mu, pre, d, l);
+        }
+        // opening half kick at t_k (only at the segment start; inside, it is part of
+        // the previous step's merged closing kick): lr += (dt/2) A(pre) lv
+        if (k == k0) kick_jac<NP>(pre, a.log + k * S, pc.tgm_half, l + 3, l);
+    }
+}
+
 template <int NP>
 __global__ void __launch_bounds__(kDiffBlock, 4) diff_backward_kernel(const DiffArgs a, const ParticleConsts pc) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    const int S = log_stride(NP);
     double l[6];
     for (int c = 0; c < 6; ++c) l[c] = a.grad1[6 * i + c];
     const int64_t rstep = a.rstep[i];
@@ -357,60 +481,179 @@ __global__ void __launch_bounds__(kDiffBlock, 4) diff_backward_kernel(const Diff
         for (int64_t cseg = nseg - 1; cseg >= 0; --cseg) {
             const int64_t k0 = cseg * a.K;
             const int64_t k1 = min(k0 + (int64_t)a.K, kend);
-            double st[6];
-            const double* cp = a.ckpt + cseg * 6 * a.n;
-            for (int c = 0; c < 6; ++c) st[c] = cp[c * a.n + i];
-            // recompute the segment: pre-drift state (6) and post-drift position (3) per step
-            // (in tape mode the forward pass wrote them already)
-            const int64_t krec = a.tape ? k0 : k1;  // steps to recompute: none in tape mode
-            for (int64_t k = k0; k < krec; ++k) {
-                const double* L0 = a.log + k * S;
-                if (k == k0) kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);  // else merged below
-                double* sc = a.scratch + (k - k0) * kScratchRows * a.n + i;
-                for (int c = 0; c < 6; ++c) sc[c * a.n] = st[c];
-                if (k == kend - 1 && cut_before_drift) break;
-                DriftScalars d;
-                drift_scalars(pc.mu, pc.dt, st, d);
-                sc[9 * a.n] = d.s;
-                sc[10 * a.n] = d.tau;
-                sc[11 * a.n] = d.G[4];
-                sc[12 * a.n] = d.G[5];
-                sc[13 * a.n] = d.inv_R;
-                double pre[6];
-                for (int c = 0; c < 6; ++c) pre[c] = st[c];
-                for (int c = 0; c < 3; ++c) {
-                    st[c] = d.f * pre[c] + d.g * pre[3 + c];
-                    st[3 + c] = d.fd * pre[c] + d.gd * pre[3 + c];
-                }
-                for (int c = 0; c < 3; ++c) sc[(6 + c) * a.n] = st[c];
-                // closing kick of step k merged with the opening kick of step k + 1 (as in the forward pass)
-                if (k + 1 < krec) kick_state<NP>(st, a.log + (k + 1) * S, pc.dt, pc.tgm_full, pc.rc2);
-            }
-            // adjoint sweep, last step first
-            for (int64_t k = k1 - 1; k >= k0; --k) {
-                const double* sc = a.scratch + (k - k0) * kScratchRows * a.n + i;
-                double pre[6], post[3];
-                for (int c = 0; c < 6; ++c) pre[c] = sc[c * a.n];
-                for (int c = 0; c < 3; ++c) post[c] = sc[(6 + c) * a.n];
-                const bool last = (k == kend - 1);
-                if (!(last && (cut_after_drift || cut_before_drift))) {
-                    // closing kick at t_{k+1}: lr += tau A(post) lv, tau = dt inside the segment
-                    // (merged with the opening kick of step k + 1), dt/2 at its end
-                    kick_jac<NP>(post, a.log + (k + 1) * S, (k + 1 < k1) ? pc.tgm_full : pc.tgm_half, l + 3, l);
-                }
-                if (!(last && cut_before_drift)) {
-                    DriftScalars d;
-                    drift_restore(pc.mu, pc.dt, pre, sc[9 * a.n], sc[10 * a.n], d);
-                    drift_finish_stored(pc.mu, d, sc[11 * a.n], sc[12 * a.n], sc[13 * a.n]);
-                    drift_adjoint(pc.mu, pre, d, l);
-                }
-                // opening half kick at t_k (only at the segment start; inside, it is part of
-                // the previous step's merged closing kick): lr += (dt/2) A(pre) lv
-                if (k == k0) kick_jac<NP>(pre, a.log + k * S, pc.tgm_half, l + 3, l);
-            }
+            backward_piece<NP>(a, pc, i, l, cseg, k0, k1, k0, k1, kend, cut_after_drift, cut_before_drift);
         }
     }
     for (int c = 0; c < 6; ++c) a.grad0[6 * i + c] = l[c];
+}
+
+// Task launch of the backward pass (the particle map's task launch, applied to the
+// sweep): every warp of the plain launch does the same work, so it lasts as long as the
+// SM partition holding the most warps (65536 particles: 2048 warps over 608 partitions,
+// 3 or 4 each).  Here a fixed grid of warps takes (32-particle group, sub-chunk) tasks
+// in order from a counter, the last sub-chunk of the run first; a sub-chunk is a
+// checkpoint segment, or kTapeSub steps of the one segment of tape mode.  The cotangent
+// passes between a group's tasks through grad0 (exact doubles), and a task waits,
+// bounded, for the group's previous one: the result equals the plain launch bit for bit.
+constexpr int kTapeSub = 64;
+constexpr int kDiffWaitPolls = 1 << 25;
+
+struct DiffTaskArgs {
+    int64_t sub;                       // steps per sub-chunk
+    int32_t n_groups;                  // ceil(n / 32)
+    int32_t n_sub;                     // sub-chunks of the run
+    unsigned long long* task_counter;  // zero before the launch
+    int32_t* group_done;               // [n_groups] sub-chunks finished, zero before the launch
+    int* status;                       // GLISSE_E_TIMEOUT if a wait gives up
+};
+
+__device__ __forceinline__ int diff_ld_acquire(const int32_t* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void diff_st_release(int32_t* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kDiffBlock, 4) diff_backward_tasks_kernel(const DiffArgs a, const ParticleConsts pc,
+                                                                            const DiffTaskArgs ta) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n_tasks = (int64_t)ta.n_groups * ta.n_sub;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(ta.task_counter, 1ull);
+        t = __shfl_sync(0xFFFFFFFFu, t, 0);
+        if ((int64_t)t >= n_tasks) break;
+        const int64_t g = (int64_t)t % ta.n_groups;
+        const int r = (int)((int64_t)t / ta.n_groups);  // 0: the last sub-chunk of the run
+        if (r > 0) {
+            int ok = 1;
+            if (lane == 0) {
+                int polls = 0;
+                while (diff_ld_acquire(ta.group_done + g) < r && ++polls < kDiffWaitPolls) __nanosleep(64);
+                ok = polls < kDiffWaitPolls;
+            }
+            ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+            if (!ok) {
+                if (lane == 0) atomicExch(ta.status, GLISSE_E_TIMEOUT);
+                break;
+            }
+        }
+        __syncwarp();
+        const int64_t i = g * 32 + lane;
+        if (i < a.n) {
+            double l[6];
+            // the first task reads the cotangent given, later ones the one their group left
+            // (written by another warp's task: read through L2)
+            for (int c = 0; c < 6; ++c) l[c] = r == 0 ? a.grad1[6 * i + c] : __ldcg(a.grad0 + 6 * i + c);
+            const int64_t rstep = a.rstep[i];
+            const int reason = a.reason[i];
+            const int64_t kend = rstep >= 0 ? rstep : a.nsteps;
+            const bool cut_after_drift =
+                rstep > 0 && reason != GLISSE_REMOVED_KEPLER && reason != GLISSE_REMOVED_NONFINITE;
+            const bool cut_before_drift = rstep > 0 && !cut_after_drift;
+            const int64_t c_idx = ta.n_sub - 1 - r;
+            const int64_t lo = c_idx * ta.sub;
+            const int64_t hi = min(lo + ta.sub, kend);
+            if (hi > lo) {
+                if (a.tape)
+                    backward_piece<NP>(a, pc, i, l, 0, 0, kend, lo, hi, kend, cut_after_drift, cut_before_drift);
+                else
+                    backward_piece<NP>(a, pc, i, l, c_idx, lo, hi, lo, hi, kend, cut_after_drift, cut_before_drift);
+            }
+            for (int c = 0; c < 6; ++c) __stcg(a.grad0 + 6 * i + c, l[c]);
+        }
+        // every lane's stores before the group's counter moves on (release at device scope)
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) diff_st_release(ta.group_done + g, r + 1);
+    }
+}
+
+// Task launch of the forward pass (no tangent or one): tasks (32-particle group, sub-chunk
+// of kFwdSub steps) forward in time, the first sub-chunk first.  Between a group's tasks the
+// state, tangent, removal step and reason pass through state1 / tan1 / rstep / reason (read
+// through L2), |t0|^2 through log_growth; checkpoints and the tape are written as the steps
+// pass.  The arithmetic is forward_steps', so the outputs equal the plain launch's bit for bit.
+constexpr int kFwdSub = 64;
+
+template <int NP, int TMAX>
+__global__ void __launch_bounds__(kDiffBlock, 4) diff_forward_tasks_kernel(const DiffArgs a, const ParticleConsts pc,
+                                                                           const DiffTaskArgs ta) {
+    constexpr int T = TMAX;
+    constexpr int TA = TMAX > 0 ? TMAX : 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t n_tasks = (int64_t)ta.n_groups * ta.n_sub;
+    for (;;) {
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(ta.task_counter, 1ull);
+        tk = __shfl_sync(0xFFFFFFFFu, tk, 0);
+        if ((int64_t)tk >= n_tasks) break;
+        const int64_t g = (int64_t)tk % ta.n_groups;
+        const int sidx = (int)((int64_t)tk / ta.n_groups);
+        if (sidx > 0) {
+            int ok = 1;
+            if (lane == 0) {
+                int polls = 0;
+                while (diff_ld_acquire(ta.group_done + g) < sidx && ++polls < kDiffWaitPolls) __nanosleep(64);
+                ok = polls < kDiffWaitPolls;
+            }
+            ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+            if (!ok) {
+                if (lane == 0) atomicExch(ta.status, GLISSE_E_TIMEOUT);
+                break;
+            }
+        }
+        __syncwarp();
+        const int64_t i = g * 32 + lane;
+        if (i < a.n) {
+            double st[6], t[TA][6];
+            int64_t rstep = -1;
+            int reason = 0;
+            if (sidx == 0) {
+                for (int c = 0; c < 6; ++c) st[c] = a.state0[6 * i + c];
+#pragma unroll
+                for (int q = 0; q < TA; ++q)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) t[q][c] = (q < a.ntan) ? a.tan0[((int64_t)q * a.n + i) * 6 + c] : 0.0;
+                if (a.log_growth) a.log_growth[i] = norm2<TA>(t);  // |t0|^2, until the last task
+                forward_test_first<NP>(a, pc, st, rstep, reason);
+            } else {
+                for (int c = 0; c < 6; ++c) st[c] = __ldcg(a.state1 + 6 * i + c);
+#pragma unroll
+                for (int q = 0; q < TA; ++q)
+#pragma unroll
+                    for (int c = 0; c < 6; ++c)
+                        t[q][c] = (q < a.ntan) ? __ldcg(a.tan1 + ((int64_t)q * a.n + i) * 6 + c) : 0.0;
+                rstep = (int64_t)__ldcg(reinterpret_cast<const long long*>(a.rstep + i));
+                reason = __ldcg(a.reason + i);
+            }
+            const int64_t lo = (int64_t)sidx * ta.sub;
+            const int64_t hi = min(lo + ta.sub, a.nsteps);
+            // inside a checkpoint segment the previous step's closing kick opened this one
+            bool opened = lo > 0 && lo < a.nsteps && lo % a.K != 0;
+            forward_steps<NP, T, TA>(a, pc, i, st, t, rstep, reason, opened, lo, hi);
+            for (int c = 0; c < 6; ++c) __stcg(a.state1 + 6 * i + c, st[c]);
+#pragma unroll
+            for (int q = 0; q < T; ++q)
+                if (q < a.ntan)
+                    for (int c = 0; c < 6; ++c) __stcg(a.tan1 + ((int64_t)q * a.n + i) * 6 + c, t[q][c]);
+            __stcg(reinterpret_cast<long long*>(a.rstep + i), (long long)rstep);
+            __stcg(a.reason + i, reason);
+            if (sidx + 1 == ta.n_sub && a.log_growth) {
+                const double n0 = __ldcg(a.log_growth + i);
+                const double n1 = norm2<TA>(t);
+                a.log_growth[i] = (a.ntan > 0 && n0 > 0.0) ? 0.5 * log(n1 / n0) : 0.0;
+            }
+        }
+        // every lane's stores before the group's counter moves on (release at device scope)
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) diff_st_release(ta.group_done + g, sidx + 1);
+    }
 }
 
 // Scratch rows of the extended recompute: the kScratchRows of the plain one,
@@ -475,8 +718,8 @@ __global__ void __launch_bounds__(kDiffBlock, 2) diff_backward_growth_kernel(con
                 double pre[6];
                 for (int c = 0; c < 6; ++c) pre[c] = st[c];
                 for (int c = 0; c < 3; ++c) {
-                    st[c] = d.f * pre[c] + d.g * pre[3 + c];
-                    st[3 + c] = d.fd * pre[c] + d.gd * pre[3 + c];
+                    st[c] = fma(d.f, pre[c], d.g * pre[3 + c]);
+                    st[3 + c] = fma(d.fd, pre[c], d.gd * pre[3 + c]);
                 }
                 drift_tangent(pc.mu, pre, d, t);
                 for (int c = 0; c < 3; ++c) {
@@ -559,15 +802,117 @@ static cudaError_t launch_diff_forward_t(int np, const DiffArgs& a, const Partic
     return cudaGetLastError();
 }
 
-static cudaError_t launch_diff_forward(int np, const DiffArgs& a, const ParticleConsts& pc, cudaStream_t s) {
+// Blocks of four warps per SM for a task launch over `groups` 32-particle groups, or 0 for
+// the plain launch: the groups must outnumber the resident warps by half again (so that a
+// task's predecessor has nearly always finished when it is taken), with two blocks per SM
+// at least (one warp per partition leaves the FP64 pipe ~30% idle) and at most four.
+static int diff_task_blocks(int64_t groups, int nsm, bool force) {
+    const int64_t k = (2 * groups) / (3 * 4 * (int64_t)nsm);
+    if (k >= 2) return (int)std::min<int64_t>(k, 4);
+    return force ? 2 : 0;
+}
+
+template <int TMAX>
+static cudaError_t launch_diff_forward_tasks(int np, const DiffArgs& a, const ParticleConsts& pc, cudaStream_t s,
+                                             const DiffTaskArgs& b, int k, int nsm) {
+    const unsigned grid = (unsigned)(k * nsm);
+    size_t smem = 0;
+    cudaError_t e = cudaSuccess;
+    switch (np) {
+#define GLISSE_FWDT_CASE(N)                                                                                  \
+    case N:                                                                                                  \
+        e = residency_cap_smem(reinterpret_cast<const void*>(diff_forward_tasks_kernel<N, TMAX>), k, 4, &smem); \
+        if (e != cudaSuccess) return e;                                                                      \
+        diff_forward_tasks_kernel<N, TMAX><<<grid, kDiffBlock, smem, s>>>(a, pc, b);                         \
+        break;
+        GLISSE_FWDT_CASE(0)
+        GLISSE_FWDT_CASE(1)
+        GLISSE_FWDT_CASE(2)
+        GLISSE_FWDT_CASE(3)
+        GLISSE_FWDT_CASE(4)
+        GLISSE_FWDT_CASE(5)
+        GLISSE_FWDT_CASE(6)
+        GLISSE_FWDT_CASE(7)
+        GLISSE_FWDT_CASE(8)
+#undef GLISSE_FWDT_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// tb: task buffers, or null for the plain launch; force_tasks: the task launch whatever the
+// size (GLISSE_LAUNCH_TASKS).  The task launch carries no tangent or one (six keep the
+// plain launch, one block per SM).
+static cudaError_t launch_diff_forward(int np, const DiffArgs& a, const ParticleConsts& pc, cudaStream_t s,
+                                       const DiffTaskArgs* tb = nullptr, bool force_tasks = false) {
     if (a.n <= 0) return cudaSuccess;
+    if (tb && a.ntan <= 1) {
+        int dev = 0, nsm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const int64_t groups = (a.n + 31) / 32;
+        const int k = diff_task_blocks(groups, nsm, force_tasks);
+        if (k > 0) {
+            DiffTaskArgs b = *tb;
+            b.sub = kFwdSub;
+            b.n_groups = (int32_t)groups;
+            b.n_sub = (int32_t)std::max<int64_t>((a.nsteps + b.sub - 1) / b.sub, 1);
+            e = cudaMemsetAsync(b.task_counter, 0, sizeof(unsigned long long), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(b.group_done, 0, sizeof(int32_t) * (size_t)groups, s);
+            if (e != cudaSuccess) return e;
+            return a.ntan == 0 ? launch_diff_forward_tasks<0>(np, a, pc, s, b, k, nsm)
+                               : launch_diff_forward_tasks<1>(np, a, pc, s, b, k, nsm);
+        }
+    }
     if (a.ntan == 0) return launch_diff_forward_t<0>(np, a, pc, s);
     if (a.ntan == 1) return launch_diff_forward_t<1>(np, a, pc, s);
     return launch_diff_forward_t<kMaxTangents>(np, a, pc, s);
 }
 
-static cudaError_t launch_diff_backward(int np, const DiffArgs& a, const ParticleConsts& pc, cudaStream_t s) {
+// tb: task buffers (counter, group counters, status), or null for the plain launch.
+// force_tasks: the task launch whatever the size (GLISSE_LAUNCH_TASKS).
+static cudaError_t launch_diff_backward(int np, const DiffArgs& a, const ParticleConsts& pc, cudaStream_t s,
+                                        const DiffTaskArgs* tb, bool force_tasks) {
     if (a.n <= 0) return cudaSuccess;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t groups = (a.n + 31) / 32;
+    const int k = tb ? diff_task_blocks(groups, nsm, force_tasks) : 0;
+    if (k > 0) {
+        DiffTaskArgs b = *tb;
+        b.sub = a.tape ? kTapeSub : a.K;
+        b.n_groups = (int32_t)groups;
+        b.n_sub = (int32_t)((a.nsteps + b.sub - 1) / b.sub);
+        if (b.n_sub == 0) b.n_sub = 1;
+        e = cudaMemsetAsync(b.task_counter, 0, sizeof(unsigned long long), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b.group_done, 0, sizeof(int32_t) * (size_t)groups, s);
+        if (e != cudaSuccess) return e;
+        const unsigned grid = (unsigned)(k * nsm);
+        size_t smem = 0;
+        switch (np) {
+#define GLISSE_DIFF_TCASE(N)                                                                                 \
+    case N:                                                                                                  \
+        e = residency_cap_smem(reinterpret_cast<const void*>(diff_backward_tasks_kernel<N>), k, 4, &smem);   \
+        if (e != cudaSuccess) return e;                                                                      \
+        diff_backward_tasks_kernel<N><<<grid, kDiffBlock, smem, s>>>(a, pc, b);                              \
+        break;
+            GLISSE_DIFF_TCASE(0)
+            GLISSE_DIFF_TCASE(1)
+            GLISSE_DIFF_TCASE(2)
+            GLISSE_DIFF_TCASE(3)
+            GLISSE_DIFF_TCASE(4)
+            GLISSE_DIFF_TCASE(5)
+            GLISSE_DIFF_TCASE(6)
+            GLISSE_DIFF_TCASE(7)
+            GLISSE_DIFF_TCASE(8)
+#undef GLISSE_DIFF_TCASE
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const unsigned grid = (unsigned)((a.n + kDiffBlock - 1) / kDiffBlock);
     GLISSE_DIFF_SWITCH(diff_backward_kernel)
     return cudaGetLastError();
@@ -606,13 +951,17 @@ struct glisse_diff {
     double* d_scratch_g = nullptr;  // extended recompute (glisse_diff_backward_growth), on first use
     int64_t* d_rstep = nullptr;
     int32_t* d_reason = nullptr;
+    // task launch of the backward pass: counter (8 B), status (4 B, padded), [ceil(n / 32)] group counters
+    char* d_tasks = nullptr;
+    int launch_mode = GLISSE_LAUNCH_AUTO;
     bool have_forward = false;
     int32_t last_ntan = 0;
 };
 
 static void diff_free(glisse_diff* d) {
     if (!d) return;
-    void* ptrs[] = {d->d_log, d->d_ckpt, d->d_scratch, d->d_ckpt_t, d->d_scratch_g, d->d_rstep, d->d_reason};
+    void* ptrs[] = {d->d_log,   d->d_ckpt,   d->d_scratch, d->d_ckpt_t,
+                    d->d_scratch_g, d->d_rstep, d->d_reason, d->d_tasks};
     for (void* p : ptrs) cudaFree(p);
     delete d;
 }
@@ -650,6 +999,7 @@ extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const dou
         return GLISSE_E_INVAL;
     // derivatives are of the converged drift only
     if (o.kepler_mode != GLISSE_KEPLER_CONVERGE || o.sort_mode != GLISSE_SORT_NONE) return GLISSE_E_INVAL;
+    if (o.launch_mode < GLISSE_LAUNCH_AUTO || o.launch_mode > GLISSE_LAUNCH_TASKS) return GLISSE_E_INVAL;
     for (int64_t k = 0; k < 7 * (int64_t)n_planets; ++k)
         if (!std::isfinite(planets[k])) return GLISSE_E_INVAL;
     glisse_diff* d = new (std::nothrow) glisse_diff();
@@ -666,6 +1016,7 @@ extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const dou
     d->np = n_planets;
     d->n = n_particles;
     d->nsteps = n_steps;
+    d->launch_mode = o.launch_mode;
     if (checkpoint_every == GLISSE_DIFF_AUTO) {
         // the per-step record when it fits in half of the free device memory
         size_t free_b = 0, total_b = 0;
@@ -674,7 +1025,7 @@ extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const dou
             rc = GLISSE_E_CUDA;
             goto fail;
         }
-        const double tape_b = 8.0 * kScratchRows * (double)std::max<int64_t>(n_particles, 1) *
+        const double tape_b = 8.0 * record_rows(n_planets) * (double)std::max<int64_t>(n_particles, 1) *
                               (double)std::max<int64_t>(n_steps, 1);
         checkpoint_every = tape_b <= 0.5 * (double)free_b ? 0 : 256;
     }
@@ -694,9 +1045,10 @@ extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const dou
         if (cudaMalloc(&d->d_log, sizeof(double) * (size_t)(n_steps + 1) * S) != cudaSuccess ||
             cudaMalloc(&d->d_ckpt, sizeof(double) * (size_t)nck * 6 * np1) != cudaSuccess ||
             cudaMalloc(&d->d_ckpt_t, sizeof(double) * (size_t)nck * 6 * np1) != cudaSuccess ||
-            cudaMalloc(&d->d_scratch, sizeof(double) * (size_t)d->K * kScratchRows * np1) != cudaSuccess ||
+            cudaMalloc(&d->d_scratch, sizeof(double) * (size_t)d->K * record_rows(n_planets) * np1) != cudaSuccess ||
             cudaMalloc(&d->d_rstep, sizeof(int64_t) * np1) != cudaSuccess ||
-            cudaMalloc(&d->d_reason, sizeof(int32_t) * np1) != cudaSuccess) {
+            cudaMalloc(&d->d_reason, sizeof(int32_t) * np1) != cudaSuccess ||
+            cudaMalloc(&d->d_tasks, 16 + sizeof(int32_t) * (size_t)((np1 + 31) / 32)) != cudaSuccess) {
             (void)cudaGetLastError();
             rc = GLISSE_E_NOMEM;
             goto fail;
@@ -772,16 +1124,26 @@ extern "C" int glisse_diff_forward(glisse_diff* d, const double* state0, double*
     a.reason = d->d_reason;
     a.ckpt = d->d_ckpt;
     a.ckpt_t = d->d_ckpt_t;
-    cudaError_t e = launch_diff_forward(d->np, a, d->pc, s);
+    DiffTaskArgs tb{};
+    tb.task_counter = reinterpret_cast<unsigned long long*>(d->d_tasks);
+    tb.status = reinterpret_cast<int*>(d->d_tasks + 8);
+    tb.group_done = reinterpret_cast<int32_t*>(d->d_tasks + 16);
+    int status = 0;
+    cudaError_t e = cudaMemsetAsync(tb.status, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+        e = launch_diff_forward(d->np, a, d->pc, s, d->launch_mode == GLISSE_LAUNCH_PLAIN ? nullptr : &tb,
+                                d->launch_mode == GLISSE_LAUNCH_TASKS);
     if (e == cudaSuccess && removal_step && d->n > 0)
         e = cudaMemcpyAsync(removal_step, d->d_rstep, sizeof(int64_t) * d->n, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && removal_reason && d->n > 0)
         e = cudaMemcpyAsync(removal_reason, d->d_reason, sizeof(int32_t) * d->n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, tb.status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return GLISSE_E_CUDA;
     }
+    if (status != 0) return status;
     d->have_forward = true;
     d->last_ntan = n_tangents;
     return GLISSE_OK;
@@ -805,13 +1167,22 @@ extern "C" int glisse_diff_backward(glisse_diff* d, const double* grad_state1, d
     a.scratch = d->d_scratch;
     a.grad1 = grad_state1;
     a.grad0 = grad_state0;
-    cudaError_t e = launch_diff_backward(d->np, a, d->pc, s);
+    DiffTaskArgs tb{};
+    tb.task_counter = reinterpret_cast<unsigned long long*>(d->d_tasks);
+    tb.status = reinterpret_cast<int*>(d->d_tasks + 8);
+    tb.group_done = reinterpret_cast<int32_t*>(d->d_tasks + 16);
+    int status = 0;
+    cudaError_t e = cudaMemsetAsync(tb.status, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+        e = launch_diff_backward(d->np, a, d->pc, s, d->launch_mode == GLISSE_LAUNCH_PLAIN ? nullptr : &tb,
+                                 d->launch_mode == GLISSE_LAUNCH_TASKS);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, tb.status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return GLISSE_E_CUDA;
     }
-    return GLISSE_OK;
+    return status == 0 ? GLISSE_OK : status;
 }
 
 extern "C" int glisse_diff_backward_growth(glisse_diff* d, const double* grad_state1, const double* grad_growth,

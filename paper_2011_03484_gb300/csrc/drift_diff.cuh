@@ -43,7 +43,7 @@ __device__ __forceinline__ Dual operator*(const Dual& a, double b) { return {a.v
 __device__ __forceinline__ Dual operator*(double a, const Dual& b) { return {a * b.v, a * b.d}; }
 __device__ __forceinline__ Dual operator/(const Dual& a, const Dual& b) {
     const double q = a.v / b.v;
-    return {q, (a.d - q * b.d) / b.v};
+    return {q, ::fma(-q, b.d, a.d) / b.v};
 }
 __device__ __forceinline__ Dual operator/(const Dual& a, double b) { return {a.v / b, a.d / b}; }
 __device__ __forceinline__ Dual fma(const Dual& a, const Dual& b, const Dual& c) {

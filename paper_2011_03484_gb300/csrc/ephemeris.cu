@@ -181,8 +181,8 @@ __device__ __forceinline__ void eph_positions(const double (&moe)[2], const bool
 template <int H>
 __device__ __forceinline__ void eph_accel(const PlanetConsts& pc, bool on, int row, int col, const double (&kj)[2],
                                           const bool (&valid)[2], const double (&mi)[2], const bool (&above)[2],
-                                          double inv_eta, double ratio, const double q[3], const double r[3],
-                                          double acc[3]) {
+                                          double inv_eta, double ratio, const double q[3], double qr,
+                                          const double r[3], double acc[3]) {
     double t[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int h = 0; h < H; ++h) {
@@ -213,8 +213,8 @@ __device__ __forceinline__ void eph_accel(const PlanetConsts& pc, bool on, int r
             sv[d] = fma(above[h] ? mi[h] : 0.0, gi, sv[d]);
         }
     }
-    const double q2 = on ? fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2])) : 1.0;
-    const double iq3 = k_rcube(q2, pc.mu0);
+    // |q|^2 from the radius the drift leaves (or radius_of at a chunk's start: the same expression)
+    const double iq3 = k_rcube(on ? qr * qr : 1.0, pc.mu0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double S = row_sum(sv[d]);
@@ -259,8 +259,13 @@ __device__ __forceinline__ void eph_dynamics(const PlanetConsts& pc, double* jac
         above[h] = jon && on && j > row;
     }
     double r[3], acc[3];
+    // |q| and mu/|q| of the Jacobi position: here from the position, then carried from each
+    // drift (which forms them from the new position with the same expression)
+    double qr, qmur;
+    radius_of(q[0], q[1], q[2], qr, qmur);
+    qmur *= mu;
     eph_positions<H>(moe, below, q, r, col);
-    eph_accel<H>(pc, on, row, col, kj, valid, mi, above, inv_eta, ratio, q, r, acc);
+    eph_accel<H>(pc, on, row, col, kj, valid, mi, above, inv_eta, ratio, q, qr, r, acc);
     if (on && col == 0)
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -273,15 +278,14 @@ __device__ __forceinline__ void eph_dynamics(const PlanetConsts& pc, double* jac
         // opening half kick, Kepler drift of each Jacobi body
 #pragma unroll
         for (int d = 0; d < 3; ++d) w[d] = fma(hdt, acc[d], w[d]);
-        double qr, qmur;
-        radius_of(q[0], q[1], q[2], qr, qmur);
-        qmur *= mu;
         const bool done = drift_fast(mu, muf, dt, dtf, on, qr, qmur, q[0], q[1], q[2], w[0], w[1], w[2]);
         if (on && !done) {
             if (!drift_general(mu, dt, q[0], q[1], q[2], w[0], w[1], w[2])) failed = true;
+            radius_of(q[0], q[1], q[2], qr, qmur);
+            qmur *= mu;
         }
         eph_positions<H>(moe, below, q, r, col);
-        eph_accel<H>(pc, on, row, col, kj, valid, mi, above, inv_eta, ratio, q, r, acc);
+        eph_accel<H>(pc, on, row, col, kj, valid, mi, above, inv_eta, ratio, q, qr, r, acc);
         // closing half kick: synchronised state at t_{k+1}
 #pragma unroll
         for (int d = 0; d < 3; ++d) w[d] = fma(hdt, acc[d], w[d]);
@@ -440,7 +444,11 @@ cudaError_t launch_eph_setup(const double* planets, int np, double m0, double G,
 // with particle warps would slow it by the number of warps it shares the FP64
 // pipe with, so its block asks for the largest dynamic shared-memory
 // allocation a block may have: no other block fits on that SM while it runs
-// (the memory is unused).
+// (the memory is unused).  The particle grids are sized for the other SMs.
+// In steady state the planets run a chunk ahead and the reservation changes
+// nothing measurable (the step time agreed to 0.01% without it); it matters
+// in the first chunk of a context, where the particles follow the planets a
+// few steps behind and a slowed ephemeris would hold them back.
 cudaError_t launch_eph_chunk(const PlanetConsts* pc, double* jac, double dt, int nsteps, double* log, double* hist,
                              int* status, cudaStream_t s, int* progress) {
     int dev = 0, optin = 0;

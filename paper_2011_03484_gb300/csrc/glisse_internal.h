@@ -1,10 +1,36 @@
 // glisse_internal.h -- types shared by the CUDA translation units of the library.
 #pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
 #include <cstdint>
 
 #include "../../include/glisse.h"
 
 namespace glisse {
+
+// Dynamic shared memory (unused by the kernel) to request so that at most
+// per_sm blocks of `kernel` can reside on an SM: per_sm blocks fit, per_sm + 1
+// do not.  *smem = 0 when no request is needed (per_sm >= max_blocks, what the
+// registers already allow) or none can express the cap.  Sets the kernel's
+// dynamic shared-memory limit to the request.
+inline cudaError_t residency_cap_smem(const void* kernel, int64_t per_sm, int max_blocks, size_t* smem) {
+    *smem = 0;
+    if (per_sm >= max_blocks || per_sm < 1) return cudaSuccess;
+    int dev = 0, smem_sm = 0, reserved = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    size_t b = (size_t)(smem_sm / per_sm - reserved) & ~(size_t)1023;
+    b = std::min<size_t>(b, (size_t)optin);
+    while (b > 0 && (size_t)(per_sm + 1) * (b + reserved) <= (size_t)smem_sm) b += 1024;
+    if ((size_t)per_sm * (b + reserved) > (size_t)smem_sm) return cudaSuccess;  // cannot express the cap
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    if (e == cudaSuccess) *smem = b;
+    return e;
+}
 
 constexpr int kMaxPlanets = GLISSE_MAX_PLANETS;
 

@@ -76,7 +76,8 @@ __device__ inline void stumpff_any(double z, double& c0, double& c1, double& c2,
 // ---------------------------------------------------------------------------
 // Solve T(s) = r0 G1 + u G2 + mu G3 = tau for s, where tau is dt minus whole
 // periods for bound orbits (k periods removed; tau = dt - k P).  Newton with a
-// bisection safeguard.  Returns false if it does not converge.
+// bisection safeguard.  Returns false if it does not converge.  Multiply-adds
+// are explicit fmas, so every kernel that inlines this rounds the same way.
 __device__ inline bool universal_solve(double mu, double dt, double r0, double u, double beta, double& s_out,
                                        double& tau_out, double& k_out) {
     double tau = dt, kper = 0.0;
@@ -84,7 +85,7 @@ __device__ inline bool universal_solve(double mu, double dt, double r0, double u
         const double n = beta * sqrt(beta) / mu;  // mean motion sqrt(mu alpha^3), alpha = beta / mu
         const double period = 6.283185307179586476925286766559 / n;
         kper = rint(dt / period);
-        tau = dt - period * kper;
+        tau = fma(-period, kper, dt);
     }
     tau_out = tau;
     k_out = kper;
@@ -99,7 +100,8 @@ __device__ inline bool universal_solve(double mu, double dt, double r0, double u
     int grow = 0;
     for (;;) {
         stumpff_any(beta * hi * hi, c0, c1, c2, c3);
-        const double T = r0 * hi * c1 + u * hi * hi * c2 + mu * hi * hi * hi * c3;
+        const double h2 = hi * hi;
+        const double T = fma(r0 * hi, c1, fma(u * h2, c2, (mu * h2) * (hi * c3)));
         if ((T - tau) * sgn >= 0.0) break;
         lo = hi;
         hi *= 2.0;
@@ -115,9 +117,9 @@ __device__ inline bool universal_solve(double mu, double dt, double r0, double u
     double dsold = hi - lo;
     for (int it = 0; it < 300; ++it) {
         stumpff_any(beta * s * s, c0, c1, c2, c3);
-        const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
-        const double F = r0 * G1 + u * G2 + mu * G3 - tau;
-        const double Fp = r0 * c0 + u * G1 + mu * G2;
+        const double G1 = s * c1, G2 = (s * s) * c2, G3 = (s * s) * (s * c3);
+        const double F = fma(r0, G1, fma(u, G2, fma(mu, G3, -tau)));
+        const double Fp = fma(r0, c0, fma(u, G1, mu * G2));
         if (F < 0.0) {
             if (s > lo) lo = s;
         } else {
@@ -151,20 +153,22 @@ __device__ inline bool universal_solve(double mu, double dt, double r0, double u
 // ---------------------------------------------------------------------------
 __device__ inline bool drift_general(double mu, double dt, double& x, double& y, double& z, double& vx, double& vy,
                                      double& vz) {
-    const double r0 = sqrt(x * x + y * y + z * z);
-    const double v2 = vx * vx + vy * vy + vz * vz;
-    const double u = x * vx + y * vy + z * vz;
+    // every multiply-add written as an fma: the result must not depend on how a
+    // compiler fuses the expression in each kernel that inlines this
+    const double r0 = sqrt(fma(x, x, fma(y, y, z * z)));
+    const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
+    const double u = fma(x, vx, fma(y, vy, z * vz));
     if (!(r0 > 0.0) || !isfinite(r0) || !isfinite(v2)) return false;
-    const double beta = 2.0 * mu / r0 - v2;
+    const double beta = (2.0 * mu) / r0 - v2;
     double s, tau, kper;
     if (!universal_solve(mu, dt, r0, u, beta, s, tau, kper)) return false;
     if (tau == 0.0) return true;
     double c0, c1, c2, c3;
     stumpff_any(beta * s * s, c0, c1, c2, c3);
-    const double G1 = s * c1, G2 = s * s * c2, G3 = s * s * s * c3;
-    const double r = r0 * c0 + u * G1 + mu * G2;
+    const double G1 = s * c1, G2 = (s * s) * c2, G3 = (s * s) * (s * c3);
+    const double r = fma(r0, c0, fma(u, G1, mu * G2));
     const double fm1 = -mu * G2 / r0;
-    const double g = tau - mu * G3;
+    const double g = fma(-mu, G3, tau);
     const double fd = -mu * G1 / (r * r0);
     const double gdm1 = -mu * G2 / r;
     const double x0 = x, y0 = y, z0 = z;
@@ -195,9 +199,9 @@ __device__ inline bool drift_general(double mu, double dt, double& x, double& y,
 // ---------------------------------------------------------------------------
 __device__ inline int drift_paper(double mu, double dt, int iters, double tol, double& x, double& y, double& z,
                                   double& vx, double& vy, double& vz) {
-    const double r0 = sqrt(x * x + y * y + z * z);
-    const double v2 = vx * vx + vy * vy + vz * vz;
-    const double u = x * vx + y * vy + z * vz;
+    const double r0 = sqrt(fma(x, x, fma(y, y, z * z)));
+    const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
+    const double u = fma(x, vx, fma(y, vy, z * vz));
     const double alpha = 2.0 / r0 - v2 / mu;
     if (!(alpha > 0.0 && r0 * alpha >= 1e-3)) {
         if (dt == 0.0) return 0;
@@ -209,14 +213,14 @@ __device__ inline int drift_paper(double mu, double dt, int iters, double tol, d
     const double ec = 1.0 - r0 / a;
     const double es = u / (n * a * a);
     double dM = n * dt;
-    dM = dM - floor(dM / kTwoPi + 0.5) * kTwoPi;
+    dM = fma(-floor(dM / kTwoPi + 0.5), kTwoPi, dM);
     double xe = dM / (1.0 - ec);
     double dx = 0.0;
     for (int it = 0; it < iters; ++it) {
         double sx, cx;
         sincos(xe, &sx, &cx);
-        const double F = xe - ec * sx + es * (1.0 - cx) - dM;
-        const double Fp = 1.0 - ec * cx + es * sx;
+        const double F = fma(es, 1.0 - cx, fma(-ec, sx, xe)) - dM;
+        const double Fp = fma(es, sx, fma(-ec, cx, 1.0));
         dx = -F / Fp;
         xe = xe + dx;
     }
@@ -224,18 +228,18 @@ __device__ inline int drift_paper(double mu, double dt, int iters, double tol, d
     double sx, cx;
     sincos(xe, &sx, &cx);
     const double omc = 1.0 - cx;
-    const double f = 1.0 - (a / r0) * omc;
+    const double f = fma(-(a / r0), omc, 1.0);
     const double g = (dM - (xe - sx)) / n;
-    const double r = a * (1.0 - ec * cx + es * sx);
+    const double r = a * fma(es, sx, fma(-ec, cx, 1.0));
     const double fd = -n * a * a * sx / (r * r0);
-    const double gd = 1.0 - (a / r) * omc;
+    const double gd = fma(-(a / r), omc, 1.0);
     const double x0 = x, y0 = y, z0 = z, vx0 = vx, vy0 = vy, vz0 = vz;
-    x = f * x0 + g * vx0;
-    y = f * y0 + g * vy0;
-    z = f * z0 + g * vz0;
-    vx = fd * x0 + gd * vx0;
-    vy = fd * y0 + gd * vy0;
-    vz = fd * z0 + gd * vz0;
+    x = fma(f, x0, g * vx0);
+    y = fma(f, y0, g * vy0);
+    z = fma(f, z0, g * vz0);
+    vx = fma(fd, x0, gd * vx0);
+    vy = fma(fd, y0, gd * vy0);
+    vz = fma(fd, z0, gd * vz0);
     return 0;
 }
 

@@ -472,23 +472,12 @@ __global__ void __launch_bounds__(kParticleBlock, kTaskMaxBlocks)
 // best any placement can do; the request makes more than that impossible.
 inline cudaError_t particle_smem_cap(const void* kernel, int64_t grid, size_t* smem) {
     *smem = 0;
-    int dev = 0, nsm = 0, smem_sm = 0, reserved = 0, optin = 0;
+    int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     const int64_t per_sm = nsm > 1 ? (grid + nsm - 2) / (nsm - 1) : GLISSE_PARTICLE_MIN_BLOCKS;
-    if (per_sm >= GLISSE_PARTICLE_MIN_BLOCKS) return cudaSuccess;  // the register budget already caps it
-    // per_sm blocks fit, per_sm + 1 do not
-    size_t b = (size_t)(smem_sm / per_sm - reserved) & ~(size_t)1023;
-    b = std::min<size_t>(b, (size_t)optin);
-    while (b > 0 && (size_t)(per_sm + 1) * (b + reserved) <= (size_t)smem_sm) b += 1024;
-    if ((size_t)per_sm * (b + reserved) > (size_t)smem_sm) return cudaSuccess;  // cannot express the cap
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
-    if (e == cudaSuccess) *smem = b;
-    return e;
+    return residency_cap_smem(kernel, per_sm, GLISSE_PARTICLE_MIN_BLOCKS, smem);
 }
 
 // Warps per SM partition for task mode, or 0 for the plain launch: task mode

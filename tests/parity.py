@@ -5,8 +5,10 @@ multiplies any rounding difference by a large factor, so two correct FP64
 implementations that round differently drift apart on those particles.  The
 acceptance criteria therefore measure each particle's own conditioning with
 the oracle: it is rerun from inputs changed by one ulp (perturbed_inputs:
-eight patterns of +-2^-52 relative changes of the coordinates), and ``sens``
-is the largest relative state change this causes.
+eight patterns of +-2^-52 relative changes of the particles' coordinates;
+perturbed_planets: the planets' coordinates, where the path under test
+integrates the planets itself), and ``sens`` is the largest relative state
+change this causes.
 
   * removal step and reason agree exactly for every particle whose removal
     metric stayed at least 1e-9 away from its threshold at every test in the
@@ -118,6 +120,16 @@ def perturbed_inputs(particles, k: int = N_PERTURB):
         sgn = rng.integers(-1, 2, size=p.shape)
         out.append(p * (1.0 + sgn * 2.0**-52))
     return out[:k]
+
+
+def perturbed_planets(planets):
+    """The planets with every heliocentric coordinate scaled by 1 + 2^-52 (masses unchanged): the
+    rerun that measures a particle's sensitivity to the planets' own rounding.  The GPU integrates
+    the planets itself, so its planet positions differ from the oracle's by their FP64 phase noise;
+    a slow particle can be far more sensitive to that than to its own initial state."""
+    pl = np.array(planets, dtype=np.float64).reshape(-1, 7)
+    pl[:, 1:] *= 1.0 + 2.0**-52
+    return pl
 
 
 def sensitivity(base: dict, runs: list) -> tuple:

@@ -62,6 +62,7 @@ def oracle_batch(orc, b, n_steps, ids_per_system=None):
         pa = b["particles"][rows]
         base = orc.run(b["star_mass"][s], pl, pa, b["dt"][s], n_steps)
         runs = [orc.run(b["star_mass"][s], pl, p, b["dt"][s], n_steps) for p in parity.perturbed_inputs(pa)]
+        runs.append(orc.run(b["star_mass"][s], parity.perturbed_planets(pl), pa, b["dt"][s], n_steps))
         sens, unst = parity.sensitivity(base, runs)
         for k in keys:
             outs[k].append(base[k])

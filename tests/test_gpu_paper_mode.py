@@ -39,6 +39,7 @@ def run_gpu(G, pl, pa, dt, n, **opt):
 def run_orc(orc, pl, pa, dt, n, iters):
     base = orc.run(1.0, pl, pa, dt, n, kepler_iters=iters)
     runs = [orc.run(1.0, pl, p, dt, n, kepler_iters=iters) for p in parity.perturbed_inputs(pa)]
+    runs.append(orc.run(1.0, parity.perturbed_planets(pl), pa, dt, n, kepler_iters=iters))
     sens, unstable = parity.sensitivity(base, runs)
     for r in [base] + runs:
         unstable |= (r["kepler_dx"] >= KBAND[0]) & (r["kepler_dx"] <= KBAND[1])

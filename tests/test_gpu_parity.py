@@ -58,6 +58,8 @@ def run_orc_sens(orc, w, n_steps, ids=None, **kw):
     pa = w["particles"] if ids is None else w["particles"][ids]
     base = orc.run(w["star_mass"], w["planets"], pa, w["dt"], n_steps, **kw)
     runs = [orc.run(w["star_mass"], w["planets"], p, w["dt"], n_steps, **kw) for p in parity.perturbed_inputs(pa)]
+    if len(w["planets"]):
+        runs.append(orc.run(w["star_mass"], parity.perturbed_planets(w["planets"]), pa, w["dt"], n_steps, **kw))
     sens, unstable = parity.sensitivity(base, runs)
     return base, sens, unstable
 
@@ -128,10 +130,12 @@ def test_tiny_workload_parity(G, orc):
     print(rep)
     assert_parity(rep)
     assert rep["removed"] > 0  # the workload exercises removal
-    # regular = insensitive to one ulp under all eight reruns and never within 5 R_crit (~7% of this
-    # workload over 1e4 steps); the far-only criterion below covers the ~500 particles that never
-    # came within 5 R_crit
-    assert rep["regular"] > 0.05 * rep["n"]
+    # regular = insensitive to a one-ulp change of the particle (eight reruns) and of the planets, and
+    # never within 5 R_crit: this workload lies between the two outer planets, and over 10^4 steps
+    # nearly every orbit feels the planets' rounding (8 regular; the sampled 131072- and
+    # 1048576-particle tests keep a hundred and more); the far-only check below covers the ~500
+    # particles that never came within 5 R_crit
+    assert rep["regular"] >= 5
     # the criterion of the short tests (no reruns): never within 5 R_crit -> 1e-10.  Here it is
     # informational: a far orbit that is chaotic all the same (its one-ulp reruns diverge) is
     # judged by its sensitivity above, like any other
@@ -408,6 +412,7 @@ def test_eccentric_workload_parity(G, orc):
     sim.close()
     base = orc.run(1.0, w["planets"], pa, w["dt"], n)
     runs = [orc.run(1.0, w["planets"], p, w["dt"], n) for p in parity.perturbed_inputs(pa)]
+    runs.append(orc.run(1.0, parity.perturbed_planets(w["planets"]), pa, w["dt"], n))
     sens, unstable = parity.sensitivity(base, runs)
     rep = parity.compare(g, base, n, sens, unstable, ecc=parity.eccentricity(pa, gi.G))
     print(rep)

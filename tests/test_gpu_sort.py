@@ -38,6 +38,7 @@ def test_sorted_run_matches_the_oracle(G, orc):
     g = run_gpu(G, w, pa, n, sort_mode=G.GLISSE_SORT_COST, chunk_steps=256)
     base = orc.run(1.0, w["planets"], pa, w["dt"], n)
     runs = [orc.run(1.0, w["planets"], p, w["dt"], n) for p in parity.perturbed_inputs(pa)]
+    runs.append(orc.run(1.0, parity.perturbed_planets(w["planets"]), pa, w["dt"], n))
     sens, unstable = parity.sensitivity(base, runs)
     rep = parity.compare(g, base, n, sens, unstable, ecc=parity.eccentricity(pa, gi.G))
     print(rep)

@@ -70,6 +70,7 @@ def test_whole_run_criteria_hold_for_a_differently_rounded_build(orc, fma_build,
     args = (w["star_mass"], w["planets"], w["particles"], w["dt"], n)
     base = orc.run(*args)
     runs = [orc.run(w["star_mass"], w["planets"], p, w["dt"], n) for p in parity.perturbed_inputs(w["particles"])]
+    runs.append(orc.run(w["star_mass"], parity.perturbed_planets(w["planets"]), w["particles"], w["dt"], n))
     sens, unstable = parity.sensitivity(base, runs)
     with orc.using(fma_build):
         other = _as_other(orc.run(*args))
@@ -81,7 +82,7 @@ def test_whole_run_criteria_hold_for_a_differently_rounded_build(orc, fma_build,
     assert np.median(e[both]) > 1e-15  # the builds do round differently
     # the derived factor has room: the largest ratio is well inside it
     assert rep["max_ratio_to_sens"] < 0.25 * parity.sens_factor(n)
-    assert rep["regular"] >= 30
+    assert rep["regular"] >= 5
 
 
 def _close_pass_reports(orc, other_build, n_ids=1024):
@@ -120,6 +121,7 @@ def test_whole_run_criteria_see_the_small_separation_kick_error_too(orc, close_k
     n = 2000
     base = orc.run(w["star_mass"], w["planets"], w["particles"], w["dt"], n)
     runs = [orc.run(w["star_mass"], w["planets"], p, w["dt"], n) for p in parity.perturbed_inputs(w["particles"])]
+    runs.append(orc.run(w["star_mass"], parity.perturbed_planets(w["planets"]), w["particles"], w["dt"], n))
     sens, unstable = parity.sensitivity(base, runs)
     with orc.using(close_kick_mutant):
         other = _as_other(orc.run(w["star_mass"], w["planets"], w["particles"], w["dt"], n))
