@@ -122,11 +122,12 @@ __device__ __forceinline__ int kick_state(double st[6], const double* __restrict
 // ~tau G m_j / |d|^3 (1e-4 or less) of the step's Jacobian.
 // Generic over the scalar type: with ad::Dual components (r, dr) and (w, dw) it
 // also gives d(tau A(r) w) = tau A(r) dw + tau (dA(r)[dr]) w.
+// Planets in kick_state's order (last first), as kick_tangents sums them.
 template <int NP, class T>
 __device__ __forceinline__ void kick_jac(const T r[3], const double* __restrict__ L,
                                          const double (&tgm)[kMaxPlanets], const T w[3], T out[3]) {
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
+    for (int j = NP - 1; j >= 0; --j) {
         const T dx = r[0] - L[kRec * j], dy = r[1] - L[kRec * j + 1], dz = r[2] - L[kRec * j + 2];
         const T d2 = fma(dx, dx, fma(dy, dy, dz * dz));
         const T s = k_rcube(d2, tgm[j]);
@@ -135,6 +136,42 @@ __device__ __forceinline__ void kick_jac(const T r[3], const double* __restrict_
         out[1] = fma(-s, fma(-c, dy, w[1]), out[1]);
         out[2] = fma(-s, fma(-c, dz, w[2]), out[2]);
     }
+}
+
+// kick_state and the tangent's kick_jac in one pass over the planets, sharing the
+// separation, |d|^2 and s_j: the velocity v and the tangent's velocity part tv get
+// exactly what kick_state and kick_jac give them (same expressions, same order);
+// w is the tangent's position part.  Returns what kick_state returns.
+template <int NP>
+__device__ __forceinline__ int kick_tangent(const double r[3], double v[3], const double w[3], double tv[3],
+                                            const double* __restrict__ L, double tau,
+                                            const double (&tgm)[kMaxPlanets], const double (&rc2)[kMaxPlanets],
+                                            double* rec = nullptr, int64_t ld = 0) {
+    const double h0x = L[kRec * NP], h0y = L[kRec * NP + 1], h0z = L[kRec * NP + 2];
+    v[0] = fma(tau, h0x, v[0]);
+    v[1] = fma(tau, h0y, v[1]);
+    v[2] = fma(tau, h0z, v[2]);
+    int hit = 0;
+#pragma unroll
+    for (int j = NP - 1; j >= 0; --j) {
+        const double dx = r[0] - L[kRec * j], dy = r[1] - L[kRec * j + 1], dz = r[2] - L[kRec * j + 2];
+        const double d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        hit = lt_nonneg(d2, rc2[j]) ? (j + 1) : hit;
+        const double s = k_rcube(d2, tgm[j]);
+        const double inv = rcp_40(d2);
+        if (rec) {
+            rec[(kScratchRows + j) * ld] = s;
+            rec[(kScratchRows + NP + j) * ld] = inv;
+        }
+        v[0] = fma(-s, dx, v[0]);
+        v[1] = fma(-s, dy, v[1]);
+        v[2] = fma(-s, dz, v[2]);
+        const double c = (3.0 * fma(dx, w[0], fma(dy, w[1], dz * w[2]))) * inv;
+        tv[0] = fma(-s, fma(-c, dx, w[0]), tv[0]);
+        tv[1] = fma(-s, fma(-c, dy, w[1]), tv[1]);
+        tv[2] = fma(-s, fma(-c, dz, w[2]), tv[2]);
+    }
+    return hit;
 }
 
 // kick_jac at the closing kick of a recorded step: s_j and 1/|d_j|^2 come from the
@@ -176,11 +213,15 @@ __device__ __forceinline__ void forward_steps(const DiffArgs& a, const ParticleC
         }
         const double* L0 = a.log + k * S;
         const double* L1 = L0 + S;
-        // opening half kick (tangents first: A is evaluated at r, which the kick leaves unchanged)
+        // opening half kick (A is evaluated at r, which the kick leaves unchanged)
         if (!opened) {
+            if constexpr (T == 1) {
+                kick_tangent<NP>(st, st + 3, t[0], t[0] + 3, L0, pc.half_dt, pc.tgm_half, pc.rc2);
+            } else {
 #pragma unroll
-            for (int q = 0; q < T; ++q) kick_jac<NP>(st, L0, pc.tgm_half, t[q], t[q] + 3);
-            kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);
+                for (int q = 0; q < T; ++q) kick_jac<NP>(st, L0, pc.tgm_half, t[q], t[q] + 3);
+                kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);
+            }
         }
         double pre[6];
         for (int c = 0; c < 6; ++c) pre[c] = st[c];
@@ -222,17 +263,27 @@ __device__ __forceinline__ void forward_steps(const DiffArgs& a, const ParticleC
         const double(&tgm)[kMaxPlanets] = merge ? pc.tgm_full : pc.tgm_half;
         const double r2 = fma(st[0], st[0], fma(st[1], st[1], st[2] * st[2]));
         int hit = (has_rmax && lt_nonneg(pc.rmax2, r2)) ? GLISSE_REMOVED_ESCAPE : 0;
-        double nst[6];
+        double nst[6], ntv[3];
         for (int c = 0; c < 6; ++c) nst[c] = st[c];
-        const int enc = kick_state<NP>(nst, L1, tau, tgm, pc.rc2, tp, a.n);
+        int enc;
+        if constexpr (T == 1) {
+            for (int c = 0; c < 3; ++c) ntv[c] = t[0][3 + c];
+            enc = kick_tangent<NP>(st, nst + 3, t[0], ntv, L1, tau, tgm, pc.rc2, tp, a.n);
+        } else {
+            enc = kick_state<NP>(nst, L1, tau, tgm, pc.rc2, tp, a.n);
+        }
         hit = enc ? enc : hit;
         if (hit) {
             rstep = k + 1;
             reason = hit;
             break;
         }
+        if constexpr (T == 1) {
+            for (int c = 0; c < 3; ++c) t[0][3 + c] = ntv[c];
+        } else {
 #pragma unroll
-        for (int q = 0; q < T; ++q) kick_jac<NP>(st, L1, tgm, t[q], t[q] + 3);
+            for (int q = 0; q < T; ++q) kick_jac<NP>(st, L1, tgm, t[q], t[q] + 3);
+        }
         for (int c = 0; c < 6; ++c) st[c] = nst[c];
         opened = merge;
     }
