@@ -182,6 +182,31 @@ def test_fewer_planets(G, orc, np_):
     assert_parity(rep)
 
 
+@pytest.mark.parametrize("np_", [3, 5, 6, 7, 8])
+def test_more_planets(G, orc, np_):
+    """Systems of 3 and of 5 to 8 planets (drawn by the batched workload's generator: planets
+    10+ mutual Hill radii apart, particles between and beyond the outer two, dt = P_inner/20)
+    through the single-system path: the plain launch and the task launch (forced; its
+    instantiations for 5+ planets keep some values in local memory) give the same bits, and
+    both match the oracle under the batched workload's phase-scaled bounds."""
+    b = gi.make_batched(seed=12, n_systems=64, n_min=256, n_max=256)
+    s = int(np.nonzero(b["n_planets"] == np_)[0][0])
+    po = np.concatenate([[0], np.cumsum(b["n_planets"])])
+    ao = np.concatenate([[0], np.cumsum(b["n_particles"])])
+    w = {"star_mass": float(b["star_mass"][s]), "planets": b["planets"][po[s]:po[s + 1]],
+         "particles": b["particles"][ao[s]:ao[s + 1]], "dt": float(b["dt"][s])}
+    n = 1500
+    outs = [run_gpu(G, w, n, launch_mode=m) for m in (G.GLISSE_LAUNCH_PLAIN, G.GLISSE_LAUNCH_TASKS)]
+    for k in ("state", "removal_step", "removal_reason"):
+        np.testing.assert_array_equal(outs[0][k], outs[1][k])
+    o, sens, unstable = run_orc_sens(orc, w, n)
+    phase = parity.phase_advance(w["particles"], gi.G * w["star_mass"], w["dt"], n)
+    rep = compare(outs[0], o, n, sens, unstable, phase)
+    print(np_, rep)
+    assert_parity(rep)
+    assert rep["regular"] >= 5
+
+
 def _orbit_states(mu, specs):
     out = []
     for a, e, inc, node, peri, M in specs:

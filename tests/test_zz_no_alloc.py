@@ -68,6 +68,32 @@ def test_noalloc_matches_allocating_partition_twice(G):
         assert torch.equal(d_new[:, :m], src[:, :n][:, keep])
 
 
+def test_noalloc_at_its_maximum_size(G):
+    """n = GLISSE_PARTITION_NOALLOC_MAX (67,108,864 slots, every scratch tile in use, ld = n):
+    the result is the plain stable partition.  About 8 GB of device memory."""
+    import torch
+
+    n = G.GLISSE_PARTITION_NOALLOC_MAX
+    gen = torch.Generator(device="cuda").manual_seed(21)
+    src = torch.randn(6, n, dtype=torch.float64, device="cuda", generator=gen)
+    ids = torch.arange(n, dtype=torch.int32, device="cuda")
+    u = torch.rand(n, device="cuda", generator=gen)
+    alive = torch.where(u < 0.5, 0, torch.where(u < 0.9, 1, 2)).to(torch.uint8)
+    dst, did, cnt = _outputs(torch, n, n)
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = G.glisse_partition_device_noalloc(n, n, alive.data_ptr(), src.data_ptr(), ids.data_ptr(), dst.data_ptr(),
+                                           did.data_ptr(), cnt.data_ptr(), stream)
+    assert rc in (None, 0)
+    keep = alive != 0
+    m = int(keep.sum().item())
+    assert int(cnt.item()) == m
+    assert torch.equal(did[:m], ids[keep])
+    for c in range(6):
+        assert torch.equal(dst[c, :m], src[c][keep]), c
+    del src, ids, alive, dst, did, cnt, keep, u
+    torch.cuda.empty_cache()
+
+
 def test_noalloc_rejects_sizes_beyond_its_limit(G):
     L = G.load()
     n = G.GLISSE_PARTITION_NOALLOC_MAX + 1
