@@ -321,6 +321,22 @@ int glisse_partition_device_noalloc(int64_t n, int64_t ld, const uint8_t* alive,
 #define GLISSE_MATH_D2F 6
 int glisse_selftest_math(int32_t fn, const double* a, const double* b, double* out, int64_t n, void* stream);
 
+/* Test hook: make one task launch's bounded wait run out.  The task launches
+ * of glisse_advance (which = PARTICLE_TASKS), of the differentiable forward
+ * pass (DIFF_FORWARD) and of the reverse sweep (DIFF_BACKWARD) order a
+ * particle group's sub-chunks with a device-side wait on the group's counter,
+ * limited to seconds of polling.  Here the same kernel runs on two groups of
+ * 32 slots whose first sub-chunks no task runs, with the limit set to `polls`
+ * polls (>= 1, each ~64 ns or more): every wait gives up, the kernel writes
+ * GLISSE_E_TIMEOUT to its status word and returns without touching particle
+ * data.  *status receives that word (GLISSE_E_TIMEOUT expected, 0 if no wait
+ * gave up).  Allocates and frees a few bytes of device memory; synchronises
+ * the stream.  Not part of the method.  Errors: INVAL, CUDA. */
+#define GLISSE_WAIT_PARTICLE_TASKS 0
+#define GLISSE_WAIT_DIFF_FORWARD 1
+#define GLISSE_WAIT_DIFF_BACKWARD 2
+int glisse_selftest_wait(int32_t which, int32_t polls, int32_t* status, void* stream);
+
 /*
  * FP64 throughput probe: runs independent chains of fused multiply-adds on
  * every SM for about `iterations` x 8 operations per thread and reports the

@@ -40,6 +40,7 @@ GLISSE_LAUNCH_AUTO, GLISSE_LAUNCH_PLAIN, GLISSE_LAUNCH_TASKS = 0, 1, 2
 GLISSE_DIFF_AUTO = -1
 GLISSE_MATH_RSQRT, GLISSE_MATH_RCP, GLISSE_MATH_RCP40, GLISSE_MATH_KRCUBE = 0, 1, 2, 3
 GLISSE_MATH_FLOAT_SQUARE, GLISSE_MATH_FLOAT_CUBE, GLISSE_MATH_D2F = 4, 5, 6
+GLISSE_WAIT_PARTICLE_TASKS, GLISSE_WAIT_DIFF_FORWARD, GLISSE_WAIT_DIFF_BACKWARD = 0, 1, 2
 GLISSE_FRAME_HELIO = 0
 GLISSE_FRAME_BARY = 1
 
@@ -55,6 +56,7 @@ EXPORTED = (
     "glisse_diff_growth_gradient", "glisse_diff_checkpoint_every",
     "glisse_diff_destroy",
     "glisse_set_sampling", "glisse_read_elements", "glisse_read_libration", "glisse_selftest_math",
+    "glisse_selftest_wait",
     "glisse_checkpoint_size", "glisse_checkpoint", "glisse_resume", "glisse_sizes",
     "glisse_batch_checkpoint_size", "glisse_batch_checkpoint", "glisse_batch_resume", "glisse_batch_sizes",
 )
@@ -213,6 +215,8 @@ def load(build_if_missing: bool = False):
     L.glisse_read_libration.restype = C.c_int
     L.glisse_selftest_math.argtypes = [C.c_int32, vp, vp, vp, C.c_int64, vp]
     L.glisse_selftest_math.restype = C.c_int
+    L.glisse_selftest_wait.argtypes = [C.c_int32, C.c_int32, i32p, vp]
+    L.glisse_selftest_wait.restype = C.c_int
     _lib = L
     return L
 
@@ -320,6 +324,14 @@ def glisse_selftest_math(fn, a, b=None):
     _check(load().glisse_selftest_math(int(fn), a.data_ptr(), bp, out.data_ptr(), a.numel(), stream),
            "glisse_selftest_math")
     return out
+
+
+def glisse_selftest_wait(which, polls=1000, stream=None) -> int:
+    """Run one task launch whose bounded wait is made to run out (see include/glisse.h);
+    returns the kernel's status word (GLISSE_E_TIMEOUT expected)."""
+    st = C.c_int32(0)
+    _check(load().glisse_selftest_wait(int(which), int(polls), C.byref(st), stream), "glisse_selftest_wait")
+    return st.value
 
 
 def glisse_status(h):

@@ -556,6 +556,7 @@ struct DiffTaskArgs {
     unsigned long long* task_counter;  // zero before the launch
     int32_t* group_done;               // [n_groups] sub-chunks finished, zero before the launch
     int* status;                       // GLISSE_E_TIMEOUT if a wait gives up
+    int32_t wait_polls;                // polls before a wait gives up; 0: the default (seconds)
 };
 
 __device__ __forceinline__ int diff_ld_acquire(const int32_t* p) {
@@ -583,9 +584,10 @@ __global__ void __launch_bounds__(kDiffBlock, 4) diff_backward_tasks_kernel(cons
         if (r > 0) {
             int ok = 1;
             if (lane == 0) {
+                const int limit = ta.wait_polls > 0 ? ta.wait_polls : kDiffWaitPolls;
                 int polls = 0;
-                while (diff_ld_acquire(ta.group_done + g) < r && ++polls < kDiffWaitPolls) __nanosleep(64);
-                ok = polls < kDiffWaitPolls;
+                while (diff_ld_acquire(ta.group_done + g) < r && ++polls < limit) __nanosleep(64);
+                ok = polls < limit;
             }
             ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
             if (!ok) {
@@ -648,9 +650,10 @@ __global__ void __launch_bounds__(kDiffBlock, 4) diff_forward_tasks_kernel(const
         if (sidx > 0) {
             int ok = 1;
             if (lane == 0) {
+                const int limit = ta.wait_polls > 0 ? ta.wait_polls : kDiffWaitPolls;
                 int polls = 0;
-                while (diff_ld_acquire(ta.group_done + g) < sidx && ++polls < kDiffWaitPolls) __nanosleep(64);
-                ok = polls < kDiffWaitPolls;
+                while (diff_ld_acquire(ta.group_done + g) < sidx && ++polls < limit) __nanosleep(64);
+                ok = polls < limit;
             }
             ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
             if (!ok) {
@@ -982,6 +985,53 @@ static cudaError_t launch_diff_growth(int np, const DiffArgs& a, const ParticleC
     const dim3 grid((unsigned)((a.n + kDiffBlock - 1) / kDiffBlock), 6);
     GLISSE_DIFF_SWITCH(diff_growth_kernel)
     return cudaGetLastError();
+}
+
+// Self-test of the bounded waits of the task launches (which = 1: forward pass, 2: reverse
+// sweep).  Two groups, two sub-chunks; the task counter starts past the first sub-chunk of
+// both groups, so each task handed out waits for a sub-chunk that no task runs: its warp
+// gives up after `polls` polls, sets *status to GLISSE_E_TIMEOUT and leaves before touching
+// a particle (the other warps find no task left).  scratch: zeroed device memory holding
+// the task counter (8 bytes) and the groups' counters (8 bytes); the particle arrays point
+// at it too, never read.
+cudaError_t diff_wait_selftest(int which, int polls, char* scratch, int* status, cudaStream_t s) {
+    constexpr int kGroups = 2;
+    double* d = reinterpret_cast<double*>(scratch);
+    DiffArgs a{};
+    a.log = d;
+    a.n = 32 * kGroups;
+    a.K = 1 << 20;
+    a.state0 = d;
+    a.state1 = d;
+    a.rstep = reinterpret_cast<int64_t*>(scratch);
+    a.reason = reinterpret_cast<int32_t*>(scratch);
+    a.ckpt = d;
+    a.scratch = d;
+    a.grad1 = d;
+    a.grad0 = d;
+    DiffTaskArgs ta{};
+    ta.n_groups = kGroups;
+    ta.n_sub = 2;
+    ta.task_counter = reinterpret_cast<unsigned long long*>(scratch);
+    ta.group_done = reinterpret_cast<int32_t*>(scratch + 8);
+    ta.status = status;
+    ta.wait_polls = polls;
+    const unsigned long long first = kGroups;
+    cudaError_t e = cudaMemcpyAsync(ta.task_counter, &first, sizeof(first), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    if (which == 1) {
+        ta.sub = kFwdSub;
+        a.nsteps = 2 * kFwdSub;
+        diff_forward_tasks_kernel<0, 0><<<4, kDiffBlock, 0, s>>>(a, ParticleConsts{}, ta);
+    } else {
+        ta.sub = kTapeSub;
+        a.nsteps = 2 * kTapeSub;
+        a.tape = 1;
+        diff_backward_tasks_kernel<0><<<4, kDiffBlock, 0, s>>>(a, ParticleConsts{}, ta);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
 }
 
 }  // namespace glisse

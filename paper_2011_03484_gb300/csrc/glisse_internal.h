@@ -105,6 +105,7 @@ struct TaskArgs {
     unsigned long long* task_counter;  // zero before the launch
     int32_t* group_done;               // [n_groups] sub-chunks of each group finished; zero before the launch
     int* status;                       // set to GLISSE_E_TIMEOUT if a wait for a group gives up
+    int32_t wait_polls;                // polls before a wait gives up; 0: the default (seconds)
 };
 
 // Device-resident clock of a batch (so a captured chunk graph can be replayed).

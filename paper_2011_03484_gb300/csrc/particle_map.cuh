@@ -401,9 +401,10 @@ __global__ void __launch_bounds__(kParticleBlock, kTaskMaxBlocks)
         if (s > 0) {
             int ok = 1;
             if (lane == 0) {
+                const int limit = ta.wait_polls > 0 ? ta.wait_polls : kGroupWaitPolls;
                 int polls = 0;
-                while (ld_acquire(ta.group_done + g) < s && ++polls < kGroupWaitPolls) __nanosleep(64);
-                ok = polls < kGroupWaitPolls;
+                while (ld_acquire(ta.group_done + g) < s && ++polls < limit) __nanosleep(64);
+                ok = polls < limit;
             }
             ok = __shfl_sync(kFullMask, ok, 0);
             if (!ok) {

@@ -125,4 +125,36 @@ cudaError_t launch_particle_chunk(int np, const ChunkArgs& a, const ParticleCons
     return launch_particle_chunk_mode<kDriftConverge>(np, a, pc, s, tb, force_tasks);
 }
 
+// Self-test of the task launch's bounded wait.  Two groups of 32 slots, two sub-chunks;
+// the task counter starts past the first sub-chunk of both groups, so each task handed out
+// waits for a sub-chunk that no task runs: its warp gives up after `polls` polls, sets
+// *status to GLISSE_E_TIMEOUT and leaves before touching a particle (the other warps find
+// no task left).  scratch: zeroed device memory holding the task counter (8 bytes) and
+// the groups' counters (8 bytes); the particle arrays point at it too, never read.
+cudaError_t particle_wait_selftest(int polls, char* scratch, int* status, cudaStream_t s) {
+    constexpr int kGroups = 2;
+    ChunkArgs a{};
+    a.n = 32 * kGroups;
+    a.ld = a.n;
+    a.nsteps = 2 * kSubSteps;
+    a.log = reinterpret_cast<const double*>(scratch);
+    a.st = reinterpret_cast<double*>(scratch);
+    a.id = reinterpret_cast<const int32_t*>(scratch);
+    a.alive = reinterpret_cast<uint8_t*>(scratch);
+    TaskArgs ta{};
+    ta.sub_steps = kSubSteps;
+    ta.n_groups = kGroups;
+    ta.task_counter = reinterpret_cast<unsigned long long*>(scratch);
+    ta.group_done = reinterpret_cast<int32_t*>(scratch + 8);
+    ta.status = status;
+    ta.wait_polls = polls;
+    const unsigned long long first = kGroups;
+    cudaError_t e = cudaMemcpyAsync(ta.task_counter, &first, sizeof(first), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    particle_tasks_kernel<0><<<4, kParticleBlock, 0, s>>>(a, ParticleConsts{}, ta);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+}
+
 }  // namespace glisse

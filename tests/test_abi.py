@@ -115,6 +115,11 @@ def test_argument_errors_before_any_cuda_call(G):
     assert L.glisse_read(None, None, None, None, None) == G.GLISSE_E_INVAL
     assert L.glisse_partition_device(-1, 0, None, None, None, None, None, None, None) == G.GLISSE_E_INVAL
     assert L.glisse_fp64_peak(0, None, None) == G.GLISSE_E_INVAL
+    st = C.c_int32(7)
+    for which, polls in ((-1, 10), (3, 10), (G.GLISSE_WAIT_PARTICLE_TASKS, 0)):
+        assert L.glisse_selftest_wait(which, polls, C.byref(st), None) == G.GLISSE_E_INVAL, (which, polls)
+    assert L.glisse_selftest_wait(G.GLISSE_WAIT_DIFF_FORWARD, 10, None, None) == G.GLISSE_E_INVAL
+    assert st.value == 7
     L.glisse_destroy(None)
 
 
