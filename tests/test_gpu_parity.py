@@ -101,6 +101,21 @@ def test_first_chunk_pieces_are_exact(G):
         np.testing.assert_array_equal(g["removal_step"], ref["removal_step"])
 
 
+def test_first_chunk_piece_schedules_agree(G):
+    """The 131072-particle context fills more than five warps per SM partition, so its first
+    chunk runs in pieces growing four-fold (16, 64, 256, 1024 steps), mostly as task launches;
+    a context holding only its first 32768 particles runs pieces growing two-fold, as plain
+    launches.  Particles are independent and every cut is open, so the shared particles end
+    the first chunk bit-identical (before any compaction changes who shares a warp)."""
+    w = gi.make("longrun")
+    n_small = 32768
+    big = run_gpu(G, w, 1024)
+    small = run_gpu(G, dict(w, particles=w["particles"][:n_small]), 1024)
+    for k in ("state", "removal_step", "removal_reason"):
+        np.testing.assert_array_equal(big[k][:n_small], small[k], err_msg=k)
+    np.testing.assert_array_equal(big["planets"], small["planets"])
+
+
 def test_long_call_equals_chunk_sized_calls(G):
     """A long glisse_advance call grows the planet ring and lets the planets run ahead of
     the particles; its segments are the same as those of chunk-sized calls, so the
