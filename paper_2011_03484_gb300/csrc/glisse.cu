@@ -545,6 +545,8 @@ static int setup(glisse_ctx* c, const double* planets, const double* particles, 
     const int64_t j0 = r ? r->step / c->C : 0;
     c->next_chunk = j0;
     c->eph_done = j0;
+    // the live count sizes the first chunk's particle segments (ensure_chunk)
+    c->n_live = r ? r->n_live : c->n_total;
     if (c->n_total > 0) {
         const int er = ensure_chunk(c, j0);
         if (er != GLISSE_OK) return er;
