@@ -710,7 +710,14 @@ class DiffMap:
 
     forward(state0 [n, 6]) -> state1 [n, 6] (plus tangents J t and a growth
     indicator); backward(g [n, 6]) -> J^T g for the last forward call.  Both run
-    in the library's kernels; tensors must be CUDA float64 and contiguous."""
+    in the library's kernels; tensors must be CUDA float64 and contiguous.
+
+    checkpoint_every: K >= 1 stores the state every K steps and recomputes each
+    segment in the backward pass; 0 (tape) records every step in the forward
+    pass ((112 + 16 N_p) B per particle-step) so the backward pass is the reverse
+    sweep alone (about half the cost); GLISSE_DIFF_AUTO takes the tape when it
+    fits in half of the free device memory.  The reverse sweep for the growth
+    indicator's gradient needs checkpoints, so the default stays K = 256."""
 
     def __init__(self, star_mass, planets, n_particles, dt, n_steps, checkpoint_every=256, **opt):
         o = glisse_opts_default()
