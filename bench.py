@@ -457,6 +457,18 @@ def time_diff(G, torch, dev, stream, n_particles=0, n_steps=0, K=256):
     tape = {"checkpoint_every": auto_k, "forward_ms": ms_fwd_auto, "adjoint_ms": ms_bwd_auto,
             "record_bytes": 8 * (14 + 2 * len(pl)) * n * n_steps if auto_k == 0 else None,
             "forward_plus_adjoint_ratio": (ms_fwd_auto + ms_bwd_auto) / ms_map}
+    # the growth gradient with a tape that keeps tangent 0 (GLISSE_DIFF_TAPE_TANGENT): the forward
+    # pass with the tangent records every step, the reverse sweep recomputes nothing; run when
+    # the record fits in half of the free device memory
+    tt_bytes = 8 * (23 + 2 * len(pl)) * n * n_steps
+    growth_tape = None
+    if tt_bytes <= 0.5 * torch.cuda.mem_get_info(dev)[0]:
+        dt_ = G.DiffMap(1.0, pl, n, w.dt, n_steps, G.GLISSE_DIFF_TAPE_TANGENT)
+        ms_fwd_tt, out_tt = timed(lambda: dt_.forward(x0, tan))
+        ms_grow_tt, _ = timed(lambda: dt_.backward_growth(torch.ones_like(x0), ones, out_tt[1][0]))
+        dt_.close()
+        growth_tape = {"forward_with_tangent_ms": ms_fwd_tt, "reverse_sweep_ms": ms_grow_tt,
+                       "record_bytes": tt_bytes, "ratio": (ms_fwd_tt + ms_grow_tt) / ms_map}
     ps = n * n_steps  # particle-steps of the differentiable run (removed particles stop early)
     line = {
         "metric": "FP64 particle-steps/s of the differentiable map (forward, adjoint) vs the plain map",
@@ -475,6 +487,7 @@ def time_diff(G, torch, dev, stream, n_particles=0, n_steps=0, K=256):
         "cost_ratio_to_plain_map": {"forward": ms_fwd / ms_map, "forward_with_tangent": ms_fwd_t / ms_map,
                                     "forward_plus_adjoint": (ms_fwd + ms_bwd) / ms_map},
         "auto_mode": tape,
+        "growth_gradient_tangent_tape": growth_tape,
     }
     return line
 
@@ -625,6 +638,8 @@ def diff_record(G, torch, dev, stream, n_steps=2048, K=256):
     out["ratio"]["auto_forward_plus_adjoint"] = t["forward_plus_adjoint_ratio"]
     out["auto_checkpoint_every"] = t["checkpoint_every"]
     out["auto_record_bytes"] = t["record_bytes"]
+    gt = r.get("growth_gradient_tangent_tape")
+    out["ratio"]["growth_gradient_tangent_tape"] = gt["ratio"] if gt else None
     return out
 
 

@@ -370,14 +370,20 @@ typedef struct glisse_diff glisse_diff; /* opaque; owned by the library */
  * checkpoint_every = GLISSE_DIFF_AUTO: tape mode when its record takes at
  * most half of the device memory free at the call, else checkpoints every
  * 256 steps (glisse_diff_checkpoint_every tells which).
+ * checkpoint_every = GLISSE_DIFF_TAPE_TANGENT: tape mode whose record also
+ * keeps tangent 0 (184 + 16 n_planets B per particle per step), written by a
+ * forward call with at least one tangent, so that glisse_diff_backward_growth
+ * needs no recompute either.
  * n_steps <= INT32_MAX (the planet log is one chunk of that many steps).
  * opts: enc_mode, enc_value and r_max apply.  Errors: INVAL, NOMEM, CUDA, KEPLER. */
 #define GLISSE_DIFF_AUTO (-1)
+#define GLISSE_DIFF_TAPE_TANGENT (-2)
 int glisse_diff_create(glisse_diff** out, double star_mass, const double* planets, int32_t n_planets,
                        int64_t n_particles, double dt, int64_t n_steps, int32_t checkpoint_every,
                        const glisse_opts* opts);
 
-/* The checkpoint interval in effect (0: tape mode), e.g. after GLISSE_DIFF_AUTO.
+/* The checkpoint interval in effect (0: tape mode; GLISSE_DIFF_TAPE_TANGENT),
+ * e.g. after GLISSE_DIFF_AUTO.
  * Errors: INVAL. */
 int glisse_diff_checkpoint_every(glisse_diff* d, int32_t* checkpoint_every);
 
@@ -407,10 +413,12 @@ int glisse_diff_backward(glisse_diff* d, const double* grad_state1, double* grad
  *   grad_growth   : device [n] or NULL (zero)
  *   tangent1      : device [n][6], J t_0 as returned by that forward call
  *   grad_state0, grad_tangent0 : device [n][6] out
- * Needs checkpoints (checkpoint_every >= 1) and a forward call with at least one
- * tangent; the extended recompute takes 184 B per particle per step of one
- * segment on first use.  Errors: STATE (no such forward call, or tape mode),
- * INVAL, NOMEM, CUDA. */
+ * Needs checkpoints (checkpoint_every >= 1) or GLISSE_DIFF_TAPE_TANGENT, and a
+ * forward call with at least one tangent.  With checkpoints, the extended
+ * recompute takes 184 B per particle per step of one segment on first use;
+ * with GLISSE_DIFF_TAPE_TANGENT the sweep reads the forward call's record and
+ * recomputes nothing.  Errors: STATE (no such forward call, or plain tape
+ * mode), INVAL, NOMEM, CUDA. */
 int glisse_diff_backward_growth(glisse_diff* d, const double* grad_state1, const double* grad_growth,
                                 const double* tangent1, double* grad_state0, double* grad_tangent0, void* stream);
 

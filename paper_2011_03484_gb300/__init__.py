@@ -38,6 +38,7 @@ GLISSE_SORT_NONE = 0
 GLISSE_SORT_COST = 1
 GLISSE_LAUNCH_AUTO, GLISSE_LAUNCH_PLAIN, GLISSE_LAUNCH_TASKS = 0, 1, 2
 GLISSE_DIFF_AUTO = -1
+GLISSE_DIFF_TAPE_TANGENT = -2
 GLISSE_MATH_RSQRT, GLISSE_MATH_RCP, GLISSE_MATH_RCP40, GLISSE_MATH_KRCUBE = 0, 1, 2, 3
 GLISSE_MATH_FLOAT_SQUARE, GLISSE_MATH_FLOAT_CUBE, GLISSE_MATH_D2F = 4, 5, 6
 GLISSE_WAIT_PARTICLE_TASKS, GLISSE_WAIT_DIFF_FORWARD, GLISSE_WAIT_DIFF_BACKWARD = 0, 1, 2
@@ -717,7 +718,9 @@ class DiffMap:
     pass ((112 + 16 N_p) B per particle-step) so the backward pass is the reverse
     sweep alone (about half the cost); GLISSE_DIFF_AUTO takes the tape when it
     fits in half of the free device memory.  The reverse sweep for the growth
-    indicator's gradient needs checkpoints, so the default stays K = 256."""
+    indicator's gradient needs checkpoints, or GLISSE_DIFF_TAPE_TANGENT: a tape
+    that also keeps tangent 0 ((184 + 16 N_p) B per particle-step), after which
+    that sweep recomputes nothing either.  The default stays K = 256."""
 
     def __init__(self, star_mass, planets, n_particles, dt, n_steps, checkpoint_every=256, **opt):
         o = glisse_opts_default()
@@ -727,7 +730,9 @@ class DiffMap:
         self.h = None
         self.h = glisse_diff_create(star_mass, planets, n_particles, dt, n_steps, checkpoint_every, o)
         self.checkpoint_every = glisse_diff_checkpoint_every(self.h)  # GLISSE_DIFF_AUTO resolved
-        self.tape = self.checkpoint_every == 0
+        self.tape = self.checkpoint_every in (0, GLISSE_DIFF_TAPE_TANGENT)
+        # the growth gradient's reverse sweep needs checkpoints or a record that keeps tangent 0
+        self.reverse_growth = self.checkpoint_every != 0
         self.forward_calls = 0
 
     @staticmethod
@@ -770,7 +775,8 @@ class DiffMap:
         """One reverse sweep for the last forward call (which carried tangent 0 = t0):
         (J^T grad_state1 + grad_growth dg/dstate0, grad_growth dg/dt0) for
         g = log(|J t0| / |t0|); tangent1 = J t0 from that call [n, 6].  Needs
-        checkpoints (not tape mode).  grad_state1 / grad_growth may be None."""
+        checkpoints or GLISSE_DIFF_TAPE_TANGENT (not the plain tape).
+        grad_state1 / grad_growth may be None."""
         import torch
 
         t1 = tangent1.contiguous()
@@ -856,7 +862,7 @@ def _make_autograd():
             g1 = torch.zeros_like(state0) if grad_state1 is None else grad_state1
             grad_seed = None
             has_growth = grad_growth is not None and bool((grad_growth != 0).any())
-            if has_growth and not ctx.dmap.tape:
+            if has_growth and ctx.dmap.reverse_growth:
                 # one reverse sweep of the map extended by its tangent
                 grad_state0, grad_seed = ctx.dmap.backward_growth(g1, grad_growth, tn)
                 if ctx.default_seed:

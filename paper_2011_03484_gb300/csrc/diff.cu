@@ -70,6 +70,9 @@ struct DiffArgs {
     int32_t K;              // checkpoint interval
     int32_t ntan;           // tangent vectors (0..kMaxTangents)
     int32_t tape;           // 1: scratch holds every step, written by the forward pass
+    int32_t rec_rows;       // rows of one step's record in scratch: record_rows(NP), or
+                            // record_rows(NP) + 9 when the tape also keeps tangent 0
+    int32_t tan_row;        // first of tangent 0's 9 rows in a record (0: not kept)
     const double* state0;   // [n][6]
     double* state1;         // [n][6]
     const double* tan0;     // [ntan][n][6]
@@ -78,7 +81,7 @@ struct DiffArgs {
     int64_t* rstep;         // [n] removal step (-1 live)
     int32_t* reason;        // [n]
     double* ckpt;           // [ceil(nsteps / K)][6][n]
-    double* scratch;        // [K][record_rows(NP)][n]
+    double* scratch;        // [K][rec_rows][n]
     const double* grad1;    // [n][6]
     double* grad0;          // [n][6]
     // growth indicator of tangent 0 (glisse_diff_backward_growth)
@@ -225,9 +228,13 @@ __device__ __forceinline__ void forward_steps(const DiffArgs& a, const ParticleC
         }
         double pre[6];
         for (int c = 0; c < 6; ++c) pre[c] = st[c];
-        double* tp = a.tape ? a.scratch + k * record_rows(NP) * a.n + i : nullptr;
+        double* tp = a.tape ? a.scratch + k * a.rec_rows * a.n + i : nullptr;
         if (tp)
             for (int c = 0; c < 6; ++c) tp[c * a.n] = pre[c];
+        // the tape of the growth gradient's sweep also keeps tangent 0 (before the drift)
+        if constexpr (T >= 1)
+            if (tp && a.tan_row > 0)
+                for (int c = 0; c < 6; ++c) tp[(a.tan_row + c) * a.n] = t[0][c];
         DriftScalars d;
         if (!drift_scalars(pc.mu, pc.dt, pre, d)) {
             rstep = k + 1;
@@ -256,6 +263,9 @@ __device__ __forceinline__ void forward_steps(const DiffArgs& a, const ParticleC
         }
 #pragma unroll
         for (int q = 0; q < T; ++q) drift_tangent(pc.mu, pre, d, t[q]);
+        if constexpr (T >= 1)
+            if (tp && a.tan_row > 0)
+                for (int c = 0; c < 3; ++c) tp[(a.tan_row + 6 + c) * a.n] = t[0][c];
         // tests at t_{k+1}, then the closing kick (merged with the next opening one
         // inside a segment)
         const bool merge = (k + 1 < a.nsteps) && ((k + 1) % a.K != 0);
@@ -462,7 +472,7 @@ __device__ __forceinline__ void backward_piece(const DiffArgs& a, const Particle
     for (int64_t k = k0; k < krec; ++k) {
         const double* L0 = a.log + k * S;
         if (k == k0) kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);  // else merged below
-        double* sc = a.scratch + (k - k0) * record_rows(NP) * a.n + i;
+        double* sc = a.scratch + (k - k0) * a.rec_rows * a.n + i;
         for (int c = 0; c < 6; ++c) sc[c * a.n] = st[c];
         if (k == kend - 1 && cut_before_drift) break;
         DriftScalars d;
@@ -491,7 +501,7 @@ __device__ __forceinline__ void backward_piece(const DiffArgs& a, const Particle
     }
     // adjoint sweep, last step first
     for (int64_t k = s_hi - 1; k >= s_lo; --k) {
-        const double* sc = a.scratch + (k - k0) * record_rows(NP) * a.n + i;
+        const double* sc = a.scratch + (k - k0) * a.rec_rows * a.n + i;
         double pre[6], post[3];
         for (int c = 0; c < 6; ++c) pre[c] = sc[c * a.n];
         for (int c = 0; c < 3; ++c) post[c] = sc[(6 + c) * a.n];
@@ -719,7 +729,8 @@ constexpr int kScratchRowsG = kScratchRows + 9;
 // grad_growth (J t0) / |J t0|^2) at the end.  Each piece (kick, drift) runs its
 // adjoint in dual numbers: state (x, t), cotangent (lt, lx) -> (M^T lt,
 // (dM[t])^T lt + M^T lx); see drift_adjoint.  Segments are recomputed from the
-// state and tangent checkpoints, as the plain backward pass does.
+// state and tangent checkpoints, as the plain backward pass does, or, with
+// GLISSE_DIFF_TAPE_TANGENT, read from the forward call's record of every step.
 // a.grad0 <- lx at t_0 (= J^T grad_state1 + grad_growth dg/dstate0 at fixed t0);
 // a.gradt0 <- lt at t_0 minus grad_growth t0 / |t0|^2 (= dg/dt0 times grad_growth).
 template <int NP>
@@ -738,11 +749,15 @@ __global__ void __launch_bounds__(kDiffBlock, 2) diff_backward_growth_kernel(con
     const int64_t kend = rstep >= 0 ? rstep : a.nsteps;
     const bool cut_after_drift = rstep > 0 && reason != GLISSE_REMOVED_KEPLER && reason != GLISSE_REMOVED_NONFINITE;
     const bool cut_before_drift = rstep > 0 && !cut_after_drift;
+    // records: the tape (tangent 0 kept beside the state's rows) or the segment's recompute
+    const int64_t rows = a.tape ? a.rec_rows : kScratchRowsG;
+    const int trow = a.tape ? a.tan_row : kScratchRows;
     if (kend > 0) {
         const int64_t nseg = (kend + a.K - 1) / a.K;
         for (int64_t cseg = nseg - 1; cseg >= 0; --cseg) {
             const int64_t k0 = cseg * a.K;
             const int64_t k1 = min(k0 + (int64_t)a.K, kend);
+            const int64_t krec = a.tape ? k0 : k1;  // steps to recompute: none with a tape
             double st[6], t[6];
             const double* cp = a.ckpt + cseg * 6 * a.n;
             const double* ct = a.ckpt_t + cseg * 6 * a.n;
@@ -750,16 +765,16 @@ __global__ void __launch_bounds__(kDiffBlock, 2) diff_backward_growth_kernel(con
                 st[c] = cp[c * a.n + i];
                 t[c] = ct[c * a.n + i];
             }
-            for (int64_t k = k0; k < k1; ++k) {
+            for (int64_t k = k0; k < krec; ++k) {
                 const double* L0 = a.log + k * S;
                 if (k == k0) {
                     kick_jac<NP>(st, L0, pc.tgm_half, t, t + 3);
                     kick_state<NP>(st, L0, pc.half_dt, pc.tgm_half, pc.rc2);
                 }
-                double* sc = a.scratch + (k - k0) * kScratchRowsG * a.n + i;
+                double* sc = a.scratch + (k - k0) * rows * a.n + i;
                 for (int c = 0; c < 6; ++c) {
                     sc[c * a.n] = st[c];
-                    sc[(kScratchRows + c) * a.n] = t[c];
+                    sc[(trow + c) * a.n] = t[c];
                 }
                 if (k == kend - 1 && cut_before_drift) break;
                 DriftScalars d;
@@ -778,7 +793,7 @@ __global__ void __launch_bounds__(kDiffBlock, 2) diff_backward_growth_kernel(con
                 drift_tangent(pc.mu, pre, d, t);
                 for (int c = 0; c < 3; ++c) {
                     sc[(6 + c) * a.n] = st[c];
-                    sc[(kScratchRows + 6 + c) * a.n] = t[c];
+                    sc[(trow + 6 + c) * a.n] = t[c];
                 }
                 if (k + 1 < k1) {
                     kick_jac<NP>(st, a.log + (k + 1) * S, pc.tgm_full, t, t + 3);
@@ -786,14 +801,14 @@ __global__ void __launch_bounds__(kDiffBlock, 2) diff_backward_growth_kernel(con
                 }
             }
             for (int64_t k = k1 - 1; k >= k0; --k) {
-                const double* sc = a.scratch + (k - k0) * kScratchRowsG * a.n + i;
+                const double* sc = a.scratch + (k - k0) * rows * a.n + i;
                 double pre[6];
                 Dual pd[6], qd[3];
                 for (int c = 0; c < 6; ++c) {
                     pre[c] = sc[c * a.n];
-                    pd[c] = {pre[c], sc[(kScratchRows + c) * a.n]};
+                    pd[c] = {pre[c], sc[(trow + c) * a.n]};
                 }
-                for (int c = 0; c < 3; ++c) qd[c] = {sc[(6 + c) * a.n], sc[(kScratchRows + 6 + c) * a.n]};
+                for (int c = 0; c < 3; ++c) qd[c] = {sc[(6 + c) * a.n], sc[(trow + 6 + c) * a.n]};
                 const bool last = (k == kend - 1);
                 if (!(last && (cut_after_drift || cut_before_drift)))
                     kick_jac<NP>(qd, a.log + (k + 1) * S, (k + 1 < k1) ? pc.tgm_full : pc.tgm_half, l + 3, l);
@@ -1043,7 +1058,8 @@ struct glisse_diff {
     int np = 0;
     int64_t n = 0, nsteps = 0;
     int K = 256;
-    bool tape = false;  // checkpoint_every = 0: the forward pass records every step
+    bool tape = false;      // checkpoint_every = 0: the forward pass records every step
+    bool tan_tape = false;  // GLISSE_DIFF_TAPE_TANGENT: the record also keeps tangent 0
     ParticleConsts pc{};
     double* d_log = nullptr;
     double* d_ckpt = nullptr;
@@ -1069,9 +1085,18 @@ static void diff_free(glisse_diff* d) {
 
 extern "C" void glisse_diff_destroy(glisse_diff* d) { diff_free(d); }
 
+// Rows of one step's record: the drift's, the closing kick's, and with
+// GLISSE_DIFF_TAPE_TANGENT tangent 0's 9 (before the drift, and its position after).
+static int32_t rec_rows(const glisse_diff* d) { return record_rows(d->np) + (d->tan_tape ? 9 : 0); }
+
+static void set_record_layout(const glisse_diff* d, DiffArgs& a) {
+    a.rec_rows = rec_rows(d);
+    a.tan_row = d->tan_tape ? record_rows(d->np) : 0;
+}
+
 extern "C" int glisse_diff_checkpoint_every(glisse_diff* d, int32_t* checkpoint_every) {
     if (!d || !checkpoint_every) return GLISSE_E_INVAL;
-    *checkpoint_every = d->tape ? 0 : d->K;
+    *checkpoint_every = d->tan_tape ? GLISSE_DIFF_TAPE_TANGENT : d->tape ? 0 : d->K;
     return GLISSE_OK;
 }
 
@@ -1096,7 +1121,7 @@ extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const dou
     if (opts) o = *opts;
     if (!(star_mass > 0.0) || n_planets < 0 || n_planets > GLISSE_MAX_PLANETS || (n_planets > 0 && !planets) ||
         n_particles < 0 || n_steps < 0 || n_steps > INT32_MAX || !(dt != 0.0) || !std::isfinite(dt) ||
-        checkpoint_every < GLISSE_DIFF_AUTO)
+        checkpoint_every < GLISSE_DIFF_TAPE_TANGENT)
         return GLISSE_E_INVAL;
     // derivatives are of the converged drift only
     if (o.kepler_mode != GLISSE_KEPLER_CONVERGE || o.sort_mode != GLISSE_SORT_NONE) return GLISSE_E_INVAL;
@@ -1130,7 +1155,8 @@ extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const dou
                               (double)std::max<int64_t>(n_steps, 1);
         checkpoint_every = tape_b <= 0.5 * (double)free_b ? 0 : 256;
     }
-    d->tape = checkpoint_every == 0;
+    d->tan_tape = checkpoint_every == GLISSE_DIFF_TAPE_TANGENT;
+    d->tape = checkpoint_every == 0 || d->tan_tape;
     d->K = d->tape ? (int32_t)std::max<int64_t>(std::min<int64_t>(n_steps, INT32_MAX), 1) : checkpoint_every;
     if (d->tape && n_steps > INT32_MAX) {
         rc = GLISSE_E_INVAL;
@@ -1146,7 +1172,7 @@ extern "C" int glisse_diff_create(glisse_diff** out, double star_mass, const dou
         if (cudaMalloc(&d->d_log, sizeof(double) * (size_t)(n_steps + 1) * S) != cudaSuccess ||
             cudaMalloc(&d->d_ckpt, sizeof(double) * (size_t)nck * 6 * np1) != cudaSuccess ||
             cudaMalloc(&d->d_ckpt_t, sizeof(double) * (size_t)nck * 6 * np1) != cudaSuccess ||
-            cudaMalloc(&d->d_scratch, sizeof(double) * (size_t)d->K * record_rows(n_planets) * np1) != cudaSuccess ||
+            cudaMalloc(&d->d_scratch, sizeof(double) * (size_t)d->K * rec_rows(d) * np1) != cudaSuccess ||
             cudaMalloc(&d->d_rstep, sizeof(int64_t) * np1) != cudaSuccess ||
             cudaMalloc(&d->d_reason, sizeof(int32_t) * np1) != cudaSuccess ||
             cudaMalloc(&d->d_tasks, 16 + sizeof(int32_t) * (size_t)((np1 + 31) / 32)) != cudaSuccess) {
@@ -1214,6 +1240,7 @@ extern "C" int glisse_diff_forward(glisse_diff* d, const double* state0, double*
     a.nsteps = d->nsteps;
     a.K = d->K;
     a.tape = d->tape ? 1 : 0;
+    set_record_layout(d, a);
     a.scratch = d->d_scratch;
     a.ntan = n_tangents;
     a.state0 = state0;
@@ -1262,6 +1289,7 @@ extern "C" int glisse_diff_backward(glisse_diff* d, const double* grad_state1, d
     a.nsteps = d->nsteps;
     a.K = d->K;
     a.tape = d->tape ? 1 : 0;
+    set_record_layout(d, a);
     a.rstep = d->d_rstep;
     a.reason = d->d_reason;
     a.ckpt = d->d_ckpt;
@@ -1291,9 +1319,9 @@ extern "C" int glisse_diff_backward_growth(glisse_diff* d, const double* grad_st
                                            void* stream) {
     glisse::NvtxRange range("glisse_diff_backward_growth");
     if (!d) return GLISSE_E_INVAL;
-    if (!d->have_forward || d->last_ntan < 1 || d->tape) return GLISSE_E_STATE;
+    if (!d->have_forward || d->last_ntan < 1 || (d->tape && !d->tan_tape)) return GLISSE_E_STATE;
     if (d->n > 0 && (!tangent1 || !grad_state0 || !grad_tangent0)) return GLISSE_E_INVAL;
-    if (!d->d_scratch_g && d->n > 0) {
+    if (!d->tape && !d->d_scratch_g && d->n > 0) {
         const size_t bytes = sizeof(double) * (size_t)d->K * kScratchRowsG * (size_t)d->n;
         if (cudaMalloc(&d->d_scratch_g, bytes) != cudaSuccess) {
             (void)cudaGetLastError();
@@ -1311,7 +1339,9 @@ extern "C" int glisse_diff_backward_growth(glisse_diff* d, const double* grad_st
     a.reason = d->d_reason;
     a.ckpt = d->d_ckpt;
     a.ckpt_t = d->d_ckpt_t;
-    a.scratch = d->d_scratch_g;
+    a.tape = d->tape ? 1 : 0;
+    set_record_layout(d, a);
+    a.scratch = d->tape ? d->d_scratch : d->d_scratch_g;  // the forward call's record, or the recompute's
     a.grad1 = grad_state1;
     a.gradg = grad_growth;
     a.tanN = tangent1;

@@ -97,9 +97,9 @@ def test_argument_errors_before_any_cuda_call(G):
         with pytest.raises(G.GlisseError) as ei:
             G.glisse_create(1.0, w["planets"], w["particles"], 0.5, o)
         assert ei.value.code == G.GLISSE_E_INVAL, lm
-    # checkpoint intervals below GLISSE_DIFF_AUTO
+    # checkpoint intervals below GLISSE_DIFF_TAPE_TANGENT
     with pytest.raises(G.GlisseError) as ei:
-        G.glisse_diff_create(1.0, w["planets"], 4, 0.5, 10, -2)
+        G.glisse_diff_create(1.0, w["planets"], 4, 0.5, 10, -3)
     assert ei.value.code == G.GLISSE_E_INVAL
     # the fixed-iteration mode is for glisse_create only
     o = G.glisse_opts_default()

@@ -462,8 +462,41 @@ def test_reverse_growth_sweep_needs_a_tangent_and_checkpoints(G):
     dm = G.DiffMap(1.0, pl, len(s0), w["dt"], 100, 0)
     dm.forward(_cuda(s0), t[None])
     with pytest.raises(RuntimeError):
-        dm.backward_growth(None, None, t)  # tape mode
+        dm.backward_growth(None, None, t)  # tape mode without tangent 0 in the record
     dm.close()
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], 100, G.GLISSE_DIFF_TAPE_TANGENT)
+    assert dm.checkpoint_every == G.GLISSE_DIFF_TAPE_TANGENT and dm.tape and dm.reverse_growth
+    dm.forward(_cuda(s0))
+    with pytest.raises(RuntimeError):
+        dm.backward_growth(None, None, t)  # the forward call wrote no tangent rows
+    dm.forward(_cuda(s0), t[None])
+    dm.backward_growth(None, None, t)
+    dm.close()
+
+
+def test_tangent_tape_gives_the_recomputed_growth_gradient(G):
+    """GLISSE_DIFF_TAPE_TANGENT keeps tangent 0 in the forward call's record of every step, so
+    the growth gradient's reverse sweep recomputes nothing.  With one checkpoint segment
+    (K = n) the recompute writes the same rows, so the two routes give the same bits: the
+    growth sweep's state and seed gradients, and the plain adjoint, removals included."""
+    w, pl, s0 = _workload(512)
+    n = 900
+    t0 = _seed(s0)
+    rng = np.random.default_rng(11)
+    g = rng.normal(size=s0.shape)
+    gg = rng.normal(size=len(s0))
+    outs = []
+    for K in (G.GLISSE_DIFF_TAPE_TANGENT, n):
+        dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n, K)
+        s1, tan1, _, rstep, _ = dm.forward(_cuda(s0), _cuda(t0[None]))
+        gs, gt = dm.backward_growth(_cuda(g), _cuda(gg), tan1[0])
+        jtg = dm.backward(_cuda(g))
+        outs.append([x.cpu().numpy() for x in (s1, tan1[0], gs, gt, jtg, rstep)])
+        dm.close()
+    for a, b, name in zip(outs[0], outs[1], ("state1", "J t0", "growth sweep lx", "growth sweep lt", "J^T g",
+                                             "removal step")):
+        np.testing.assert_array_equal(a, b, err_msg=name)
+    assert (outs[0][5] >= 0).sum() > 0  # removals on the way
 
 
 @pytest.mark.parametrize("K", [256, 0])
