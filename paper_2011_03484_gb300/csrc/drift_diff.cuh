@@ -187,7 +187,7 @@ struct DriftScalarsT {
     T G[6], Gb[4];  // G_0..G_5 and dG_n/dbeta, n = 0..3
     T R, f, g, fd, gd;
     T inv_r0, inv_R;    // 1/r0 and 1/R (MUFU seed + one correction: no divisions downstream)
-    T mg2r, mg2R, irR;  // mu G2 / r0 (= 1 - f), mu G2 / R (= 1 - gd), 1 / (R r0), unrounded by the 1 -
+    T mg2r, mg2R, irR;  // mu G2 / r0 (1 - f), mu G2 / R (1 - gd), 1 / (R r0), not rounded through 1 -
 };
 using DriftScalars = DriftScalarsT<double>;
 
@@ -321,10 +321,10 @@ __device__ __forceinline__ void drift_fg(double mu, DriftScalarsT<T>& d) {
     d.mg2r = mg2 * d.inv_r0;
     d.mg2R = mg2 * d.inv_R;
     d.irR = d.inv_R * d.inv_r0;
-    d.f = 1.0 - d.mg2r;
+    d.f = fma(-mg2, d.inv_r0, 1.0);  // explicit: kernels that also use mg2r must round f alike
     d.g = fma(-mu, d.G[3], d.tau);
     d.fd = (-mu * d.G[1]) * d.irR;
-    d.gd = 1.0 - d.mg2R;
+    d.gd = fma(-mg2, d.inv_R, 1.0);
 }
 
 __device__ inline void drift_finish(double mu, DriftScalars& d) {
@@ -457,7 +457,7 @@ __device__ inline void drift_adjoint(double mu, const T st[6], const DriftScalar
     // s(tau, r0, u, beta): ds = (dtau - G1 dr0 - G2 du - Tb dbeta) / R
     const T Tb = fma(d.r0, d.Gb[1], fma(d.u, d.Gb[2], mu * d.Gb[3]));
     const T lsR = ls * d.inv_R;
-    const T ltau = lg + lsR;
+    const T ltau = fma(ls, d.inv_R, lg);
     lr0 = fma(-d.G[1], lsR, lr0);
     lu = fma(-d.G[2], lsR, lu);
     lbeta = fma(-Tb, lsR, lbeta);

@@ -168,6 +168,13 @@ def test_tape_mode_equals_one_recomputed_segment(G):
     np.testing.assert_array_equal(outs[0][0], outs[1][0])
     np.testing.assert_array_equal(outs[0][1], outs[1][1])
     assert (outs[0][2] >= 0).sum() > 0  # removals on the way (frozen-state derivatives on the tape)
+    # a tape written by a forward pass that carries a tangent (another kernel, the same arithmetic
+    # for the state and the record) gives the same bits too
+    dm = G.DiffMap(1.0, pl, len(s0), w["dt"], n, 0)
+    s1, _, _, _, _ = dm.forward(_cuda(s0), _cuda(_seed(s0)[None]))
+    np.testing.assert_array_equal(s1.cpu().numpy(), outs[0][0])
+    np.testing.assert_array_equal(dm.backward(_cuda(g)).cpu().numpy(), outs[0][1])
+    dm.close()
 
 
 def test_autograd_function(G):
